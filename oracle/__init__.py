@@ -1,0 +1,220 @@
+"""Test infrastructure: ctypes wrapper around the plain C oracle (oracle.c).
+
+The oracle restates the definitions of the bi-directed de Bruijn graph
+(Section 2 of Kundeti et al., arXiv 1003.1940), the adjacency of STEP-4
+(Section 3) and chain compaction (Section 6) on the CPU.  Only the tests,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use it;
+the GPU library never imports it and shares no code with it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_EINTERNAL = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compiles oracle.c with gcc into oracle/_build/liboracle.so."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall",
+                           "-o", tmp, _SRC])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_uint32),
+        ("n_nodes", ctypes.c_uint64),
+        ("n_edges", ctypes.c_uint64),
+        ("node_keys", ctypes.POINTER(ctypes.c_uint64)),
+        ("edge_keys", ctypes.POINTER(ctypes.c_uint64)),
+        ("src", ctypes.POINTER(ctypes.c_uint32)),
+        ("dst", ctypes.POINTER(ctypes.c_uint32)),
+        ("orient", ctypes.POINTER(ctypes.c_uint8)),
+        ("mult", ctypes.POINTER(ctypes.c_uint32)),
+        ("row_ptr", ctypes.POINTER(ctypes.c_uint64)),
+        ("adj_nbr", ctypes.POINTER(ctypes.c_uint32)),
+        ("adj_edge", ctypes.POINTER(ctypes.c_uint32)),
+        ("adj_role", ctypes.POINTER(ctypes.c_uint8)),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class _Unitigs(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_uint64),
+        ("node_off", ctypes.POINTER(ctypes.c_uint64)),
+        ("nodes", ctypes.POINTER(ctypes.c_uint64)),
+        ("seq_off", ctypes.POINTER(ctypes.c_uint64)),
+        ("seq", ctypes.POINTER(ctypes.c_char)),
+        ("circular", ctypes.POINTER(ctypes.c_uint8)),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.orc_build.restype = ctypes.c_int
+            lib.orc_build.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                      ctypes.c_uint32, ctypes.POINTER(ctypes.POINTER(_Graph))]
+            lib.orc_graph_free.restype = None
+            lib.orc_graph_free.argtypes = [ctypes.POINTER(_Graph)]
+            lib.orc_compact.restype = ctypes.c_int
+            lib.orc_compact.argtypes = [ctypes.POINTER(_Graph),
+                                        ctypes.POINTER(ctypes.POINTER(_Unitigs))]
+            lib.orc_unitigs_free.restype = None
+            lib.orc_unitigs_free.argtypes = [ctypes.POINTER(_Unitigs)]
+            lib.orc_count_kplus1.restype = ctypes.c_int
+            lib.orc_count_kplus1.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                             ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
+                                             ctypes.c_void_p]
+            _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what} failed with oracle status {code}")
+        self.code = code
+
+
+def _as_reads(reads, lengths):
+    if isinstance(reads, (bytes, bytearray)):
+        reads = np.frombuffer(bytes(reads), dtype=np.uint8)
+    reads = np.ascontiguousarray(reads, dtype=np.uint8)
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint32)
+    return reads, lengths
+
+
+def _copy(ptr, n, dtype):
+    if n == 0:
+        return np.zeros(0, dtype=dtype)
+    return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
+
+
+def _key_words(words: np.ndarray) -> list[int]:
+    """(high, low) word pairs -> Python ints."""
+    w = words.reshape(-1, 2)
+    return [(int(h) << 64) | int(l) for h, l in w]
+
+
+class OracleGraph:
+    """Bi-directed de Bruijn graph computed by the oracle.
+
+    Arrays: ``node_keys`` (n_nodes, 2) u64 high/low words of the canonical
+    k-mer; ``edge_keys`` (n_edges, 2) canonical (k+1)-mer; ``src``/``dst``
+    node IDs; ``orient`` = (o1 << 1) | o2; ``mult``; CSR ``row_ptr``,
+    ``adj_nbr``, ``adj_edge``, ``adj_role``.
+    """
+
+    def __init__(self, ptr):
+        self._ptr = ptr
+        g = ptr.contents
+        self.k = int(g.k)
+        self.n_nodes = int(g.n_nodes)
+        self.n_edges = int(g.n_edges)
+        nv, ne = self.n_nodes, self.n_edges
+        self.node_keys = _copy(g.node_keys, 2 * nv, np.uint64).reshape(nv, 2)
+        self.edge_keys = _copy(g.edge_keys, 2 * ne, np.uint64).reshape(ne, 2)
+        self.src = _copy(g.src, ne, np.uint32)
+        self.dst = _copy(g.dst, ne, np.uint32)
+        self.orient = _copy(g.orient, ne, np.uint8)
+        self.mult = _copy(g.mult, ne, np.uint32)
+        self.row_ptr = _copy(g.row_ptr, nv + 1, np.uint64)
+        self.adj_nbr = _copy(g.adj_nbr, 2 * ne, np.uint32)
+        self.adj_edge = _copy(g.adj_edge, 2 * ne, np.uint32)
+        self.adj_role = _copy(g.adj_role, 2 * ne, np.uint8)
+        self.flags = int(g.flags)
+
+    def node_ints(self) -> list[int]:
+        return _key_words(self.node_keys)
+
+    def edge_ints(self) -> list[int]:
+        return _key_words(self.edge_keys)
+
+    def __del__(self):
+        ptr, self._ptr = getattr(self, "_ptr", None), None
+        if ptr is not None and _lib is not None:
+            _lib.orc_graph_free(ptr)
+
+
+class OracleUnitigs:
+    def __init__(self, ptr, k):
+        u = ptr.contents
+        self.count = int(u.count)
+        self.node_off = _copy(u.node_off, self.count + 1, np.uint64)
+        n_nodes = int(self.node_off[-1]) if self.count else 0
+        self.nodes = _copy(u.nodes, n_nodes, np.uint64)
+        self.seq_off = _copy(u.seq_off, self.count + 1, np.uint64)
+        n_seq = int(self.seq_off[-1]) if self.count else 0
+        self.seq = ctypes.string_at(u.seq, n_seq) if n_seq else b""
+        self.circular = _copy(u.circular, self.count, np.uint8)
+        self.k = k
+        _lib.orc_unitigs_free(ptr)
+
+    def strings(self) -> list[str]:
+        return [self.seq[self.seq_off[i]:self.seq_off[i + 1]].decode()
+                for i in range(self.count)]
+
+    def node_lists(self) -> list[list[tuple[int, int]]]:
+        out = []
+        for i in range(self.count):
+            seg = self.nodes[self.node_off[i]:self.node_off[i + 1]]
+            out.append([(int(x) >> 1, int(x) & 1) for x in seg])
+        return out
+
+
+def build_graph(reads, lengths, k: int) -> OracleGraph:
+    """Graph of the reads by the definitions of Section 2 (forward reads only)."""
+    lib = _load()
+    reads, lengths = _as_reads(reads, lengths)
+    out = ctypes.POINTER(_Graph)()
+    rc = lib.orc_build(reads.ctypes.data, lengths.ctypes.data, len(lengths), k, ctypes.byref(out))
+    if rc != ORC_OK:
+        raise OracleError(rc, "orc_build")
+    return OracleGraph(out)
+
+
+def compact(graph: OracleGraph) -> OracleUnitigs:
+    """Unitigs of the graph by walking its mergeable chains (Section 6)."""
+    lib = _load()
+    out = ctypes.POINTER(_Unitigs)()
+    rc = lib.orc_compact(graph._ptr, ctypes.byref(out))
+    if rc != ORC_OK:
+        raise OracleError(rc, "orc_compact")
+    return OracleUnitigs(out, graph.k)
+
+
+def count_kplus1(reads, lengths, k: int, queries: list[str]) -> np.ndarray:
+    """Multiplicity of the edge spelled by each query (k+1)-mer."""
+    lib = _load()
+    reads, lengths = _as_reads(reads, lengths)
+    q = "".join(queries).encode()
+    if any(len(s) != k + 1 for s in queries):
+        raise ValueError("queries must be (k+1)-mers")
+    qbuf = np.frombuffer(q, dtype=np.uint8) if q else np.zeros(1, np.uint8)
+    counts = np.zeros(max(1, len(queries)), dtype=np.uint64)
+    rc = lib.orc_count_kplus1(reads.ctypes.data, lengths.ctypes.data, len(lengths), k,
+                              qbuf.ctypes.data, len(queries), counts.ctypes.data)
+    if rc != ORC_OK:
+        raise OracleError(rc, "orc_count_kplus1")
+    return counts[:len(queries)]

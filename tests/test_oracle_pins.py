@@ -1,0 +1,307 @@
+"""Pins for the CPU oracle: worked examples printed in the paper, an
+independent string-only model on exhaustive and random tiny inputs, closed
+forms and invariants.  No GPU involved."""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import strings_model as sm
+from golden_io import all_fixtures, load
+from paper_1003_1940_gb300 import readgen
+
+
+def kmer_str(v: int, m: int) -> str:
+    return "".join("ACGT"[(v >> (2 * (m - 1 - i))) & 3] for i in range(m))
+
+
+def build(reads: list[str], k: int):
+    lengths = np.array([len(r) for r in reads], dtype=np.uint32)
+    return oracle.build_graph("".join(reads).encode(), lengths, k)
+
+
+def graph_strings(g):
+    k = g.k
+    nodes = [kmer_str(v, k) for v in g.node_ints()]
+    edges = []
+    for i in range(g.n_edges):
+        o = int(g.orient[i])
+        edges.append((nodes[g.src[i]], nodes[g.dst[i]], o >> 1, o & 1, int(g.mult[i])))
+    return nodes, edges
+
+
+# --------------------------------------------------------------------------
+# worked examples (tests/golden, each citing its section)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", all_fixtures())
+def test_golden_example(name):
+    fx = load(name)
+    k = fx["k"]
+    g = build(fx["reads"], k)
+    nodes, edges = graph_strings(g)
+    if fx["nodes"]:
+        assert nodes == sorted(fx["nodes"])
+    if fx["edges"]:
+        assert sorted(edges) == sorted(fx["edges"])
+    u = oracle.compact(g)
+    assert sorted(u.strings()) == sorted(fx["unitigs"])
+    kp1 = {kmer_str(z, k + 1) for z in g.edge_ints()}
+    for what, args in fx["paper"]:
+        if what == "kmers":
+            # every printed k-mer is on one strand of a node
+            for s in args:
+                assert sm.canonical(s) in nodes
+        elif what == "absent_pair":
+            a, b = (sm.canonical(s) for s in args)
+            assert not any({e[0], e[1]} == {a, b} for e in edges)
+        elif what == "molecule":
+            pos, neg = args
+            assert pos in nodes and sm.rc(pos) == neg
+        elif what == "edge":
+            a, b, o1, o2 = args[0], args[1], int(args[2]), int(args[3])
+            # the named edge may be stored from its other end
+            alt = (b, a, 1 - o2, 1 - o1)
+            assert any(e[:4] in ((a, b, o1, o2), alt) for e in edges)
+        elif what == "walk":
+            w = args[0]
+            for j in range(len(w) - k):
+                assert sm.canonical(w[j:j + k + 1]) in kp1
+        elif what == "label":
+            assert len(args[0]) == 4 + k - 1
+        elif what == "label_reverse":
+            assert sm.rc(args[0]) in [a for t, (a, *_) in fx["paper"] if t == "label"]
+
+
+# --------------------------------------------------------------------------
+# the oracle against the string-only model
+# --------------------------------------------------------------------------
+
+def check_against_strings(reads: list[str], k: int):
+    g = build(reads, k)
+    nodes, edges = graph_strings(g)
+    assert nodes == sm.nodes_of(reads, k)
+    want = sm.edge_multiset(reads, k)
+    got = {}
+    for (a, b, o1, o2, m) in edges:
+        x, y = sm.oriented_kmer(a, o1), sm.oriented_kmer(b, o2)
+        assert x[1:] == y[:-1]
+        assert a <= b
+        cls = sm.edge_class(x, y)
+        assert cls not in got
+        got[cls] = m
+    assert got == dict(want)
+    # edges are listed by the canonical (k+1)-mer they spell
+    keys = [kmer_str(z, k + 1) for z in g.edge_ints()]
+    for (a, b, o1, o2, _), key in zip(edges, keys):
+        x, y = sm.oriented_kmer(a, o1), sm.oriented_kmer(b, o2)
+        assert key == sm.canonical(x + y[-1])
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
+    # adjacency rows list each node's edge ends in edge order
+    for v in range(g.n_nodes):
+        row = range(int(g.row_ptr[v]), int(g.row_ptr[v + 1]))
+        ends = [(int(g.adj_edge[p]), int(g.adj_role[p])) for p in row]
+        assert ends == sorted(ends)
+        for p in row:
+            e, role = int(g.adj_edge[p]), int(g.adj_role[p])
+            assert (g.src[e], g.dst[e])[role] == v
+            assert (g.dst[e], g.src[e])[role] == g.adj_nbr[p]
+    assert int(g.row_ptr[-1]) == 2 * g.n_edges
+    return g
+
+
+@pytest.mark.parametrize("k,L", [(1, 1), (1, 4), (3, 3), (3, 4), (3, 5), (3, 6), (5, 6), (5, 7)])
+def test_exhaustive_single_reads(k, L):
+    """Every read over {A,C,G,T}^L (sampled at L = 7) as a one-read input."""
+    rng = np.random.default_rng(L * 10 + k)
+    reads = ["".join(t) for t in itertools.product("ACGT", repeat=L)]
+    if len(reads) > 1500:
+        reads = [reads[i] for i in rng.choice(len(reads), 1500, replace=False)]
+    for r in reads:
+        check_against_strings([r], k)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 7, 9])
+def test_random_read_sets(k):
+    rng = np.random.default_rng(100 + k)
+    for trial in range(60):
+        alphabet = "ACGT" if trial % 3 else "AC"  # small alphabets force repeats
+        n = int(rng.integers(1, 8))
+        reads = ["".join(rng.choice(list(alphabet), size=int(rng.integers(1, 3 * k + 6))))
+                 for _ in range(n)]
+        check_against_strings(reads, k)
+
+
+def test_reads_shorter_than_k_and_exactly_k():
+    # a read of length k adds its node but no edge; a shorter read adds nothing
+    g = check_against_strings(["ACGTA", "GGA", "TTTTTT", "AC"], 5)
+    nodes, _ = graph_strings(g)
+    assert "ACGTA" in nodes or sm.rc("ACGTA") in nodes
+
+
+def test_empty_input():
+    g = build([], 21)
+    assert g.n_nodes == 0 and g.n_edges == 0
+    assert oracle.compact(g).count == 0
+
+
+@pytest.mark.parametrize("k", [0, 2, 64, 65])
+def test_bad_k_rejected(k):
+    with pytest.raises(oracle.OracleError):
+        build(["ACGTACGT"], k)
+
+
+@pytest.mark.parametrize("bad", ["ACGN", "acgt", "ACG-"])
+def test_bad_bases_rejected(bad):
+    with pytest.raises(oracle.OracleError):
+        build([bad + "ACGT"], 3)
+
+
+def test_long_k_63():
+    rng = np.random.default_rng(5)
+    reads = ["".join(rng.choice(list("ACGT"), size=80)) for _ in range(4)]
+    reads.append(reads[0][10:75])  # overlapping read: multiplicities above 1
+    check_against_strings(reads, 63)
+
+
+# --------------------------------------------------------------------------
+# invariants on a workload-shaped input
+# --------------------------------------------------------------------------
+
+def test_invariants_tiny_workload():
+    spec = readgen.tiny_spec()
+    spec = readgen.ReadSetSpec(20_000, 2_000, 36, 0.01, 21, 0)
+    reads, lengths = readgen.generate(spec)
+    g = oracle.build_graph(reads, lengths, 21)
+    # summed multiplicity = sum over reads of (L - k)
+    assert int(g.mult.sum()) == int(np.maximum(lengths.astype(np.int64) - 21, 0).sum())
+    # node count = number of distinct canonical k-mers
+    strs = sm.split_reads(reads.tobytes(), lengths)
+    assert g.n_nodes == len(sm.nodes_of(strs, 21))
+    assert np.all(g.src <= g.dst)
+    # every read spells a valid walk: at each inner k-mer the read enters the
+    # node through one side and leaves through the other (Section 2)
+    nodes = [kmer_str(v, 21) for v in g.node_ints()]
+    by_key = {kmer_str(z, 22): i for i, z in enumerate(g.edge_ints())}
+
+    def side_at(e, v):
+        o = int(g.orient[e])
+        if g.src[e] == v:
+            return "R" if (o >> 1) == 0 else "L"
+        return "L" if (o & 1) == 0 else "R"
+
+    index = {s: i for i, s in enumerate(nodes)}
+    checked = 0
+    for r in strs[:400]:
+        for j in range(len(r) - 22):
+            e1 = by_key[sm.canonical(r[j:j + 22])]
+            e2 = by_key[sm.canonical(r[j + 1:j + 23])]
+            v = index[sm.canonical(r[j + 1:j + 22])]
+            if g.src[e1] == g.dst[e1] or g.src[e2] == g.dst[e2]:
+                continue
+            assert side_at(e1, v) != side_at(e2, v)
+            checked += 1
+    assert checked > 1000
+
+
+# --------------------------------------------------------------------------
+# compaction: closed forms, the string model, invariants
+# --------------------------------------------------------------------------
+
+def distinct_kmer_read(rng, length, k):
+    """A random read whose k-mers and their reverse complements are all distinct."""
+    while True:
+        r = "".join(rng.choice(list("ACGT"), size=length))
+        kms = [r[j:j + k] for j in range(length - k + 1)]
+        can = [sm.canonical(x) for x in kms]
+        if len(set(can)) == len(can):
+            return r
+
+
+def test_single_read_is_one_unitig():
+    rng = np.random.default_rng(7)
+    for k in (3, 5, 21, 31):
+        r = distinct_kmer_read(rng, 4 * k + 10, k)
+        u = oracle.compact(build([r], k))
+        assert u.count == 1
+        assert u.strings() == [min(r, sm.rc(r))]
+        assert int(u.circular[0]) == 0
+        assert len(u.strings()[0]) == (len(r) - k + 1) + k - 1
+
+
+def test_circular_genome_is_one_cycle():
+    rng = np.random.default_rng(8)
+    k = 11
+    while True:
+        gnm = "".join(rng.choice(list("ACGT"), size=200))
+        ext = gnm + gnm[:k]
+        can = [sm.canonical(ext[j:j + k]) for j in range(len(gnm))]
+        if len(set(can)) == len(can):
+            break
+    # reads tile the circle, each shifted by 7 bases
+    reads = [(gnm + gnm)[s:s + 40] for s in range(0, len(gnm), 7)]
+    u = oracle.compact(build(reads, k))
+    assert u.count == 1 and int(u.circular[0]) == 1
+    s = u.strings()[0]
+    assert len(s) == len(gnm) + k - 1
+    # it starts at the smallest k-mer molecule, on its positive strand
+    assert s[:k] == min(can)
+    assert s in (gnm + gnm) or sm.rc(s) in (gnm + gnm)
+
+
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_compaction_against_string_model(k):
+    rng = np.random.default_rng(200 + k)
+    for trial in range(40):
+        glen = int(rng.integers(k + 2, 40))
+        gnm = "".join(rng.choice(list("ACGT" if trial % 4 else "ACG"), size=glen))
+        reads = []
+        for _ in range(int(rng.integers(1, 10))):
+            s = int(rng.integers(0, glen - k))
+            e = int(rng.integers(s + k, glen + 1))
+            rd = gnm[s:e]
+            reads.append(rd if rng.random() < 0.5 else sm.rc(rd))
+        g = build(reads, k)
+        u = oracle.compact(g)
+        got = sorted(("C" if c else "P", s) for c, s in zip(u.circular, u.strings()))
+        assert got == sm.unitigs_of(reads, k)
+        check_unitig_invariants(g, u)
+
+
+def check_unitig_invariants(g, u):
+    k = g.k
+    nodes = [kmer_str(v, k) for v in g.node_ints()]
+    lists = u.node_lists()
+    allnodes = [v for lst in lists for v, _ in lst]
+    # every node in exactly one unitig
+    assert sorted(allnodes) == list(range(g.n_nodes))
+    # total sequence is preserved: sum of m = |V|, each string m + k - 1 long
+    for lst, s in zip(lists, u.strings()):
+        assert len(s) == len(lst) + k - 1
+        for i, (v, strand) in enumerate(lst):
+            assert s[i:i + k] == sm.oriented_kmer(nodes[v], strand)
+    heads = [lst[0][0] for lst in lists]
+    assert heads == sorted(heads)
+
+
+def test_compaction_invariants_tiny_workload():
+    spec = readgen.ReadSetSpec(5_000, 1_500, 36, 0.01, 21, 0)
+    reads, lengths = readgen.generate(spec)
+    g = oracle.build_graph(reads, lengths, 21)
+    check_unitig_invariants(g, oracle.compact(g))
+
+
+def test_sampled_counts_match_full_build():
+    spec = readgen.ReadSetSpec(3_000, 800, 50, 0.01, 15, 4)
+    reads, lengths = readgen.generate(spec)
+    g = oracle.build_graph(reads, lengths, 15)
+    keys = [kmer_str(z, 16) for z in g.edge_ints()]
+    pick = list(range(0, len(keys), 37))
+    got = oracle.count_kplus1(reads, lengths, 15, [keys[i] for i in pick])
+    assert list(got) == [int(g.mult[i]) for i in pick]
+    # a (k+1)-mer given as its reverse complement counts the same edge
+    got_rc = oracle.count_kplus1(reads, lengths, 15, [sm.rc(keys[i]) for i in pick])
+    assert list(got_rc) == list(got)
