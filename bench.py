@@ -1,0 +1,362 @@
+"""Benchmark: bi-directed de Bruijn graph construction + chain compaction.
+
+One step = dbg_build (2-bit pack, canonical (k+1)-mer emission, onesweep
+radix sort, run-length reduce, node sort, node IDs, CSR adjacency) followed
+by dbg_compact (list-ranking chain compaction), on the 50 Mbp repeat-genome
+workload: 15 M reads x 100 bp (30x), 0.5 % errors, k = 31, 1.035 G edge
+instances.  Inputs are synthetic (seeded) and resident in HBM for `value`;
+`e2e` repeats the step through the same C ABI from pinned host buffers.
+
+Metric: edge instances (sum over reads of L - k) built per second, whole job.
+With --gpus N > 1 (torchrun) every rank builds its own replica on its GPU
+(weak scaling, no data-path collective); time = max over ranks.
+
+--impl reference times the CPU oracle (plain C, one core) on a bounded
+sample of the same workload, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1003_1940_gb300 import readgen  # noqa: E402
+
+METRIC = "bi-directed edges built/s"
+UNIT = "edges/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["large", "long_k", "tiny"], default="large")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle sample time")
+    return ap.parse_args()
+
+
+def workload(name):
+    if name == "large":
+        return readgen.large_spec(), "50Mbp-repeats 15Mx100bp 30x 0.5%err k=31 (build+compact)"
+    if name == "long_k":
+        return readgen.long_k_spec(), "20Mbp-repeats+tandem 4Mx150bp 30x 0.3%err k=55 (build+compact)"
+    return readgen.tiny_spec(), "100kbp 10000x36bp 1%err k=21 (build+compact)"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._drain, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _drain(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded prefix of the same reads
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(reads, lengths, k, target_s):
+    import oracle
+    oracle.build()
+    lengths64 = lengths.astype(np.int64)
+    edges_per_read = np.maximum(lengths64 - k, 0)
+    # calibrate on a small prefix, then size the sample for ~target_s
+    m0 = min(len(lengths), 2000)
+    t = time.perf_counter()
+    g = oracle.build_graph(reads[:int(lengths64[:m0].sum())], lengths[:m0], k)
+    oracle.compact(g)
+    t0 = max(time.perf_counter() - t, 1e-3)
+    m = int(min(len(lengths), max(m0, m0 * target_s / t0)))
+    nb = int(lengths64[:m].sum())
+    t = time.perf_counter()
+    g = oracle.build_graph(reads[:nb], lengths[:m], k)
+    oracle.compact(g)
+    dt = time.perf_counter() - t
+    edges = int(edges_per_read[:m].sum())
+    return edges / dt, dt, m, edges
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    spec, wl = workload(args.workload)
+    reads, lengths = readgen.generate(spec)
+    import oracle
+    oracle.build()
+    # size one step so that warmup + steps finish within a few minutes
+    rate0, dt0, m0, _ = oracle_sample_rate(reads, lengths, spec.k, 2.0)
+    m = max(1, int(m0 * min(15.0, 150.0 / max(1, args.steps + args.warmup)) / 2.0))
+    m = min(m, len(lengths))
+    nb = int(lengths[:m].astype(np.int64).sum())
+    edges = int(np.maximum(lengths[:m].astype(np.int64) - spec.k, 0).sum())
+
+    def step():
+        g = oracle.build_graph(reads[:nb], lengths[:m], spec.k)
+        oracle.compact(g)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t
+    value = edges * args.steps / el
+    sample = f"first {m} of {len(lengths)} reads ({edges} edge instances) per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": wl, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_1003_1940_gb300 import build_lib, dbg
+    build_lib.build()
+    dbg.load()
+    spec, wl = workload(args.workload)
+    reads, lengths = readgen.generate(spec)
+    k = spec.k
+    N = int(np.maximum(lengths.astype(np.int64) - k, 0).sum())
+
+    stream = torch.cuda.Stream()
+    ctx = dbg.Context(device=local, stream=stream)
+    with torch.cuda.stream(stream):
+        d_reads = torch.from_numpy(reads).to("cuda", non_blocking=False)
+        d_len = torch.from_numpy(lengths.view(np.int32)).to("cuda")
+    torch.cuda.synchronize()
+
+    info = {}
+
+    def step():
+        g = dbg.dbg_build(ctx, d_reads, d_len, k)
+        u = dbg.dbg_compact(ctx, g)
+        info["nodes"], info["edges"] = dbg.dbg_graph_num_nodes(g), dbg.dbg_graph_num_edges(g)
+        info["unitigs"] = dbg.dbg_unitigs_count(u)
+        u.free()
+        g.free()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dbg.dbg_profile_enable(ctx, True)
+    launches0 = dbg.dbg_launch_count(ctx)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = dbg.dbg_launch_count(ctx) - launches0
+    prof = dbg.dbg_profile_read(ctx)
+    dbg.dbg_profile_enable(ctx, False)
+    ms_max = max_over_ranks(ms, ws)
+    value = N * args.steps * ws / (ms_max / 1000.0)
+
+    peak, peak_kind = load_peaks()
+    srt = prof.get("sort_edges", {"launches": 0, "ms": 0.0, "bytes": 0.0})
+    # the dominant kernel: one onesweep pass over the edge keys (the first
+    # launch of each sort is the digit-prefix kernel, which moves ~no bytes)
+    n_pass = srt["launches"] - args.steps
+    pass_ms = srt["ms"] / max(1, srt["launches"] - args.steps) if n_pass > 0 else 0.0
+    pass_bytes = srt["bytes"] / max(1, n_pass)
+    achieved = pass_bytes / (pass_ms / 1000.0) / 1e9 if pass_ms > 0 else 0.0
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "onesweep_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            tr = json.load(open(tr_path))
+            if tr.get("workload") == args.workload:
+                traffic = tr.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    stages = {name: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                     "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
+              for name, v in prof.items()}
+
+    # end to end through the same C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        h_reads = torch.from_numpy(reads).pin_memory()
+        h_len = torch.from_numpy(lengths.view(np.int32)).pin_memory()
+        out_bytes = {}
+
+        def step_host():
+            g = dbg.dbg_build(ctx, h_reads, h_len, k)
+            u = dbg.dbg_compact(ctx, g)
+            e = dbg.dbg_graph_num_edges(g)
+            # the step's result read back: the edge multiplicities
+            mult = np.empty(e, dtype=np.uint32)
+            dbg._check(dbg._lib.dbg_graph_edges(g.handle, None, None, None, None,
+                                                mult.ctypes.data if e else None), "dbg_graph_edges")
+            out_bytes["d2h"] = mult.nbytes
+            u.free()
+            g.free()
+
+        step_host()
+        barrier(ws)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t, ws)
+        e2e = {"value": N * args.steps * ws / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(reads.nbytes + lengths.nbytes),
+               "d2h_bytes_per_step": int(out_bytes.get("d2h", 0))}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, dt, m, edges = oracle_sample_rate(reads, lengths, k, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {m} reads ({edges} edge instances) of the same workload, build+compact, "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64" if k <= 31 else "u128",
+            "data": "synthetic",
+            "config": {"workload": wl, "edge_instances": N, "reads": int(len(lengths)), "k": k,
+                       "nodes": info.get("nodes"), "edges": info.get("edges"), "unitigs": info.get("unitigs"),
+                       "l2": "inputs and sort buffers far larger than L2 (1.5 GB reads, 8.3 GB keys)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "kernel": "k_onesweep (edge keys, one 8-bit digit pass)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if peak else None, "peak_kind": peak_kind,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": pass_bytes,
+                         "launch_ms": pass_ms},
+            "stages": stages,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

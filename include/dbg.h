@@ -1,0 +1,205 @@
+/*
+ * dbg.h -- C ABI of the GB300 bi-directed de Bruijn graph builder.
+ *
+ * The library builds the bi-directed de Bruijn graph of a set of DNA reads
+ * by the sort-based method of Kundeti, Rajasekaran, Dinh, Vaughn and Thapar,
+ * "Efficient Parallel and Out of Core Algorithms for Constructing Large
+ * Bi-directed de Bruijn Graphs" (arXiv 1003.1940), on one GPU, and compacts
+ * its chains into unitigs.
+ *
+ * Problem statement (Section 3): given reads R_f = {r_1..r_n} over
+ * {A,C,G,T} and an odd k, produce the node list V (canonical k-mers), the
+ * edge list E (canonical bi-directed edges with multiplicities) and the
+ * adjacency lists.  Compaction (Section 6) merges chains of nodes joined by
+ * a valid bi-directed walk into unitigs.
+ *
+ * Conventions for every call
+ *   - The status code is the only error channel.  On error, *out is NULL and
+ *     no partial result is returned.
+ *   - Inputs are borrowed for the duration of the call only.  Pointers to
+ *     caller data may be host pointers or device pointers of the context's
+ *     device; the library tells them apart with cudaPointerGetAttributes.
+ *   - Results (dbg_graph, dbg_unitigs) are owned by the library until the
+ *     matching *_free call; accessors copy into caller buffers (host or
+ *     device) and return when the copy is complete.
+ *   - Calls on one dbg_ctx are not thread-safe; use one context per host
+ *     thread, or the dbg_submit/dbg_poll serving calls.
+ *
+ * Encoding (all integer, bit-exact)
+ *   - Bases A=0 C=1 G=2 T=3.  An m-mer is stored most-significant-base
+ *     first, so integer order equals lexicographic order with A<C<G<T.
+ *   - Keys of k <= 31 are one uint64_t; keys of 33 <= k <= 63 are two
+ *     uint64_t words (high word first).  "key words" W below is 1 or 2.
+ *     A node key holds k bases, an edge key k+1 bases.
+ *   - orient = (o1 << 1) | o2, o = 1 when the k-mer read at that end of the
+ *     edge is the negative strand (the reverse complement of the node key).
+ *
+ * Output orders (defined so that results are reproducible bit for bit)
+ *   - nodes: ascending canonical k-mer; node ID = rank.
+ *   - edges: ascending canonical (k+1)-mer; edge ID = rank; src <= dst.
+ *   - adjacency row of a node: its edge ends by ascending (edge ID, role).
+ *   - unitigs: ascending ID of their first node.
+ */
+#ifndef DBG_H
+#define DBG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dbg_status {
+  DBG_OK = 0,
+  DBG_EINVAL = 1,      /* bad argument: k even or outside [1, 63], NULL, a byte outside {A,C,G,T} */
+  DBG_ENOMEM = 2,      /* device or host allocation failed, or over the memory budget */
+  DBG_ECUDA = 3,       /* a CUDA runtime call failed */
+  DBG_ETIMEOUT = 4,    /* a bounded device-side wait reached its limit */
+  DBG_ECANCELLED = 5,  /* request cancelled (serving) */
+  DBG_EOVERFLOW = 6    /* more than 2^32 - 1 edge instances, edges or nodes in one build */
+} dbg_status;
+
+typedef struct dbg_ctx dbg_ctx;
+typedef struct dbg_graph dbg_graph;
+typedef struct dbg_unitigs dbg_unitigs;
+
+/* Optional device-memory hooks.  alloc returns device memory usable on
+ * `stream` (NULL on failure); free releases it in stream order. */
+typedef void *(*dbg_alloc_fn)(void *user, size_t bytes, void *stream);
+typedef void (*dbg_free_fn)(void *user, void *ptr, size_t bytes, void *stream);
+
+typedef struct dbg_options {
+  uint32_t struct_size;    /* sizeof(dbg_options) */
+  int32_t device;          /* CUDA device ordinal; -1 = the current device */
+  void *stream;            /* cudaStream_t for all work; NULL = a stream the context creates */
+  dbg_alloc_fn alloc;      /* NULL = stream-ordered cudaMallocAsync from the device pool */
+  dbg_free_fn free;
+  void *alloc_user;
+  uint64_t mem_budget;     /* bytes a request may hold on the device; 0 = no limit */
+  uint32_t spin_limit;     /* iterations a device wait may spin before DBG_ETIMEOUT; 0 = default */
+  uint32_t sort_block;     /* radix sort tile shape, 0 = tuned default */
+  uint32_t sort_items;
+  uint32_t reserved[8];
+} dbg_options;
+
+/* Fills *opt with defaults. */
+void dbg_options_init(dbg_options *opt);
+
+/* Creates a context on the device named by opt (NULL = defaults). */
+dbg_status dbg_create(dbg_ctx **ctx, const dbg_options *opt);
+void dbg_destroy(dbg_ctx *ctx);
+
+/* Message for the last error of this host thread ("" if none). */
+const char *dbg_last_error(void);
+
+/* ----------------------------------------------------------------------
+ * dbg_build -- the sort-based construction of Section 3 (BiConstruct):
+ *   STEP-1: one canonical (k+1)-mer key per consecutive k-mer pair of every
+ *           read (its canonical edge), STEP-2: radix sort + run-length
+ *           reduce (edges with multiplicities), STEP-3: sort of the edge
+ *           ends (nodes), STEP-4: adjacency lists.
+ *   reads    all reads back to back, ASCII 'A','C','G','T' (no separators)
+ *   lengths  n read lengths (bases)
+ *   n        number of reads; n = 0 gives an empty graph
+ *   k        odd, 1 <= k <= 63 (Section 2: k odd, so no k-mer is its own
+ *            reverse complement)
+ *   out      receives the graph (library-owned; release with dbg_graph_free)
+ * Multiplicities count the forward reads (sum of multiplicities =
+ * sum over reads of max(0, L - k)).  A read of length exactly k adds its
+ * k-mer as a node without edges (Section 2 takes every k-mer of the reads as
+ * a node; STEP-3 alone would collect only edge ends); a shorter read adds
+ * nothing.
+ * Errors: DBG_EINVAL (k, NULL, non-ACGT byte), DBG_EOVERFLOW (>= 2^32
+ * edge instances), DBG_ENOMEM, DBG_ECUDA, DBG_ETIMEOUT.
+ * -------------------------------------------------------------------- */
+dbg_status dbg_build(dbg_ctx *ctx, const char *reads, const uint32_t *lengths, uint64_t n,
+                     uint32_t k, dbg_graph **out);
+
+uint32_t dbg_graph_k(const dbg_graph *g);
+uint32_t dbg_graph_key_words(const dbg_graph *g);  /* W: 1 for k <= 31, 2 above */
+uint64_t dbg_graph_num_nodes(const dbg_graph *g);
+uint64_t dbg_graph_num_edges(const dbg_graph *g);
+uint64_t dbg_graph_num_instances(const dbg_graph *g);  /* sum over reads of max(0, L - k) */
+
+/* Node keys: W words per node, ascending.  Buffer: num_nodes * W uint64_t. */
+dbg_status dbg_graph_nodes(const dbg_graph *g, uint64_t *keys);
+
+/* Edges by ascending canonical (k+1)-mer.  Any pointer may be NULL to skip
+ * that array.  keys: num_edges * W words; src, dst: node IDs; orient as
+ * above; mult: multiplicity. */
+dbg_status dbg_graph_edges(const dbg_graph *g, uint64_t *keys, uint32_t *src, uint32_t *dst,
+                           uint8_t *orient, uint32_t *mult);
+
+/* Adjacency (STEP-4) in CSR form: row_ptr has num_nodes + 1 entries; entry
+ * p of a row holds the neighbour node ID, the edge ID and the role (0: the
+ * row's node is the edge's src end, 1: its dst end).  A self-loop appears
+ * twice in its node's row.  Any pointer may be NULL. */
+dbg_status dbg_graph_csr(const dbg_graph *g, uint64_t *row_ptr, uint32_t *nbr, uint32_t *edge,
+                         uint8_t *role);
+
+/* Device pointers to the graph's arrays, valid until dbg_graph_free. */
+typedef struct dbg_graph_view {
+  uint32_t k, key_words;
+  uint64_t num_nodes, num_edges, num_instances;
+  const uint64_t *node_keys, *edge_keys, *row_ptr;
+  const uint32_t *src, *dst, *mult, *adj_nbr, *adj_edge;
+  const uint8_t *orient, *adj_role;
+} dbg_graph_view;
+dbg_status dbg_graph_device_view(const dbg_graph *g, dbg_graph_view *view);
+
+void dbg_graph_free(dbg_graph *g);
+
+/* ----------------------------------------------------------------------
+ * dbg_compact -- bi-directed chain compaction (Section 6).
+ * Each node has a left and a right side; the src end of (u, v, o1, o2) sits
+ * on u's right side if o1 = 0, else its left; the dst end on v's left side
+ * if o2 = 0, else its right.  An edge is merged when u != v and both of its
+ * sides carry exactly one edge end.  The nodes split into unitigs: maximal
+ * chains of merged edges (open or circular), singletons included.  The
+ * chains are found by list ranking over the 2|V| strands of the
+ * ListRankingTransform (each node v becomes v+ and v-).
+ * Each open unitig is reported as the copy whose spelled string is
+ * lexicographically smaller; a circular one starts at its smallest node,
+ * positive strand.  Spelled length = nodes + k - 1.
+ * -------------------------------------------------------------------- */
+dbg_status dbg_compact(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs **out);
+
+uint64_t dbg_unitigs_count(const dbg_unitigs *u);
+uint64_t dbg_unitigs_total_bases(const dbg_unitigs *u);
+/* node_off, seq_off: count + 1 entries; nodes: num_nodes entries, each
+ * (node ID << 1) | strand with strand 1 = read as reverse complement;
+ * seq: ASCII, unitigs back to back; circular: count entries of 0/1.
+ * Any pointer may be NULL. */
+dbg_status dbg_unitigs_get(const dbg_unitigs *u, uint64_t *node_off, uint64_t *nodes,
+                           uint64_t *seq_off, char *seq, uint8_t *circular);
+void dbg_unitigs_free(dbg_unitigs *u);
+
+/* ----------------------------------------------------------------------
+ * Profiling (tracing).  When enabled, the context brackets every kernel it
+ * launches with CUDA events on its stream and accumulates, per stage, the
+ * launches, device time and algorithmic bytes (the bytes the stage must
+ * read and write by its definition, not measured traffic).  Stage names:
+ * offsets, pack, emit, sort_edges, rle, endpoints, sort_nodes, node_ids,
+ * adjacency, copies, compact_links, compact_rank, compact_cycles,
+ * compact_output.
+ * -------------------------------------------------------------------- */
+typedef struct dbg_stage_stat {
+  char name[24];
+  uint64_t launches;   /* kernel launches of the stage */
+  double ms;           /* summed device time of those launches */
+  double bytes;        /* summed algorithmic bytes */
+} dbg_stage_stat;
+
+/* on != 0 enables timing; any call resets the statistics. */
+dbg_status dbg_profile_enable(dbg_ctx *ctx, int on);
+/* Copies up to cap stage records; returns the number of stages. */
+uint32_t dbg_profile_read(dbg_ctx *ctx, dbg_stage_stat *out, uint32_t cap);
+/* Kernels launched by this context since it was created. */
+uint64_t dbg_launch_count(const dbg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBG_H */

@@ -373,11 +373,20 @@ int orc_count_kplus1(const char *reads, const uint32_t *lengths, uint64_t n, uin
     u128 z = mer_canonical(mer_value(queries + q * M, M), M);
     if (!table_find(&t, z, 0, 0, 1)) { free(t.slots); return ORC_ENOMEM; }
   }
+  /* slide a (k+1)-base window along each read, keeping the window and its
+   * reverse complement up to date one base at a time */
+  u128 mask = (M == 64) ? ~(u128)0 : ((((u128)1) << (2 * M)) - 1);
   const char *read = reads;
   for (uint64_t r = 0; r < n; r++) {
     int64_t L = lengths[r];
-    for (int64_t j = 0; j + M <= L; j++) {
-      u128 z = mer_canonical(mer_value(read + j, M), M);
+    u128 fwd = 0, rev = 0;
+    for (int64_t j = 0; j < L; j++) {
+      int c = base_code(read[j]);
+      if (c < 0) { free(t.slots); return ORC_EINVAL; }
+      fwd = ((fwd << 2) | (u128)c) & mask;
+      rev = (rev >> 2) | ((u128)(3 - c) << (2 * (M - 1)));
+      if (j + 1 < M) continue;
+      u128 z = rev < fwd ? rev : fwd;
       slot_t *s = table_find(&t, z, 0, 0, 0);
       if (s) s->count++;
     }

@@ -1,0 +1,270 @@
+// build_pipeline.cuh -- host side of dbg_build for one key width: plans the
+// buffers, launches STEP-1..4 on the context's stream, and fills the graph.
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+
+#include "k_build.cuh"
+
+namespace dbg {
+
+inline int passes_for_bits(int bits) { return (bits + RADIX_BITS - 1) / RADIX_BITS; }
+
+// Tile shape of the onesweep kernel for each key width; the shared-memory
+// staging area holds one tile of keys (and payloads).
+template <class K, bool HAS_VAL> struct SortCfg;
+template <> struct SortCfg<uint64_t, false> { static constexpr int BLOCK = 256, ITEMS = 16; };
+template <> struct SortCfg<uint64_t, true> { static constexpr int BLOCK = 256, ITEMS = 12; };
+template <> struct SortCfg<Key128, false> { static constexpr int BLOCK = 256, ITEMS = 8; };
+template <> struct SortCfg<Key128, true> { static constexpr int BLOCK = 256, ITEMS = 8; };
+
+template <class K, bool HAS_VAL>
+constexpr size_t sort_smem_bytes() {
+  constexpr int TILE = SortCfg<K, HAS_VAL>::BLOCK * SortCfg<K, HAS_VAL>::ITEMS;
+  return (size_t)TILE * sizeof(K) + (HAS_VAL ? (size_t)TILE * sizeof(uint32_t) : 0);
+}
+
+// Ascending LSD radix sort of n keys (with optional u32 payloads) whose
+// significant bits are the low `bits`.  `hist` holds the per-pass digit
+// histograms (passes x 256), already accumulated by the producer kernel.
+// On return the sorted data is in *keys / *vals (the buffers may have been
+// swapped with *alt_keys / *alt_vals).
+template <class K, bool HAS_VAL>
+dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uint32_t **alt_vals, uint64_t n,
+                      int bits, const unsigned long long *d_hist, uint64_t *d_digit_base) {
+  if (n <= 1) return DBG_OK;
+  using C = SortCfg<K, HAS_VAL>;
+  constexpr int TILE = C::BLOCK * C::ITEMS;
+  const int passes = passes_for_bits(bits);
+  const uint64_t tiles = (n + TILE - 1) / TILE;
+  if (tiles > 0x7fffffffull) return DBG_EOVERFLOW;
+  DBG_TRY(ensure_status(ctx, (size_t)tiles * RADIX));
+  cudaStream_t s = ctx->stream;
+  {
+    DBG_LAUNCH(ctx, HAS_VAL ? ST_SORT_NODES : ST_SORT_EDGES, 0.0,
+               k_digit_base<<<passes, RADIX, 0, s>>>(d_hist, d_digit_base));
+  }
+  auto kern = k_onesweep<K, HAS_VAL, C::BLOCK, C::ITEMS>;
+  constexpr size_t smem = sort_smem_bytes<K, HAS_VAL>();
+  DBG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int p = 0; p < passes; p++) {
+    uint32_t epoch;
+    DBG_TRY(next_epoch(ctx, &epoch));
+    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), s));
+    Span sp(ctx, HAS_VAL ? ST_SORT_NODES : ST_SORT_EDGES,
+            2.0 * (double)n * (double)(sizeof(K) + (HAS_VAL ? sizeof(uint32_t) : 0)));
+    kern<<<(unsigned)tiles, C::BLOCK, smem, s>>>(*keys, *alt_keys, HAS_VAL ? *vals : nullptr,
+                                                 HAS_VAL ? *alt_vals : nullptr, n, p * RADIX_BITS,
+                                                 d_digit_base + p * RADIX, ctx->d_status, ctx->d_counters,
+                                                 epoch, ctx->spin_limit, ctx->d_err);
+    std::swap(*keys, *alt_keys);
+    if (HAS_VAL) std::swap(*vals, *alt_vals);
+  }
+  DBG_CUDA_TRY(cudaGetLastError());
+  return DBG_OK;
+}
+
+inline unsigned grid_for(uint64_t n, int per_block) {
+  uint64_t g = (n + per_block - 1) / per_block;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 0x7fffffffull));
+}
+
+template <class K>
+dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
+  cudaStream_t s = ctx->stream;
+  const uint32_t k = in.k;
+  const uint64_t n = in.n;
+  g->k = k;
+  g->key_words = sizeof(K) / 8;
+
+  // ---- per-read offsets (exclusive scans of L and max(0, L - k)) ----
+  DevBuf base_off, edge_off, tile_sums, small;
+  const uint64_t off_tiles = (n + OFF_TILE - 1) / OFF_TILE;
+  DBG_TRY(alloc_buf(ctx, base_off, (n + 1) * sizeof(uint64_t)));
+  DBG_TRY(alloc_buf(ctx, edge_off, (n + 1) * sizeof(uint64_t)));
+  DBG_TRY(alloc_buf(ctx, tile_sums, std::max<uint64_t>(1, off_tiles) * sizeof(Sum3)));
+  DBG_TRY(alloc_buf(ctx, small, 64 * sizeof(uint64_t) + (MAX_PASSES * RADIX) * 16));
+  uint64_t *d_totals = small.as<uint64_t>();
+  unsigned long long *d_hist = reinterpret_cast<unsigned long long *>(d_totals + 64);
+  uint64_t *d_digit_base = reinterpret_cast<uint64_t *>(d_hist + MAX_PASSES * RADIX);
+  if (n > 0) {
+    DBG_LAUNCH(ctx, ST_OFFSETS, 4.0 * n,
+               k_read_tile_sums<<<(unsigned)off_tiles, OFF_BLOCK, 0, s>>>(in.d_lengths, n, k, tile_sums.as<Sum3>()));
+  }
+  {
+    DBG_LAUNCH(ctx, ST_OFFSETS, 0.0,
+               k_scan_tile_sums<<<1, 1024, 0, s>>>(tile_sums.as<Sum3>(), (uint32_t)off_tiles, d_totals,
+                                      base_off.as<uint64_t>(), edge_off.as<uint64_t>(), n));
+  }
+  if (n > 0) {
+    DBG_LAUNCH(ctx, ST_OFFSETS, 20.0 * n,
+               k_read_offsets<<<(unsigned)off_tiles, OFF_BLOCK, 0, s>>>(in.d_lengths, n, k, tile_sums.as<Sum3>(),
+                                                             base_off.as<uint64_t>(), edge_off.as<uint64_t>()));
+  }
+  DBG_CUDA_TRY(cudaGetLastError());
+  uint64_t totals[3];
+  DBG_TRY(read_small(ctx, d_totals, sizeof(totals), totals));
+  const uint64_t total_bases = totals[0], N = totals[1], I = totals[2];
+  tile_sums.release();
+  g->num_instances = N;
+  if (N > 0xffffffffull) {
+    set_error("%llu edge instances exceed one in-memory build (2^32 - 1)", (unsigned long long)N);
+    return DBG_EOVERFLOW;
+  }
+
+  // ---- K1 pack ----
+  DevBuf packed;
+  const uint64_t nwords = (total_bases + 31) / 32;
+  DBG_TRY(alloc_buf(ctx, packed, (nwords + 3) * sizeof(uint64_t)));
+  DBG_CUDA_TRY(cudaMemsetAsync(packed.as<uint64_t>() + nwords, 0, 3 * sizeof(uint64_t), s));
+  if (nwords > 0) {
+    DBG_LAUNCH(ctx, ST_PACK, (double)total_bases + 8.0 * nwords,
+               k_pack<<<grid_for(nwords, 256), 256, 0, s>>>(in.d_reads, total_bases, packed.as<uint64_t>(), nwords,
+                                                 ctx->d_err));
+  }
+
+  // ---- K2 emit + digit histograms, K3 sort, K4 run-length reduce ----
+  const int kbits = 2 * ((int)k + 1);
+  const int kpasses = passes_for_bits(kbits);
+  DevBuf keys_a, keys_b, headpos, uniq;
+  uint64_t E = 0;
+  K *sorted = nullptr;
+  if (N > 0) {
+    DBG_TRY(alloc_buf(ctx, keys_a, N * sizeof(K)));
+    DBG_TRY(alloc_buf(ctx, keys_b, N * sizeof(K)));
+    DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
+    {
+      DBG_LAUNCH(ctx, ST_EMIT, 8.0 * nwords + 16.0 * n + (double)N * sizeof(K),
+                 k_emit<K><<<grid_for(N, EMIT_TILE), EMIT_BLOCK, 0, s>>>(packed.as<uint64_t>(), base_off.as<uint64_t>(),
+                                                              edge_off.as<uint64_t>(), n, N, k, keys_a.as<K>(),
+                                                              kpasses, d_hist));
+    }
+    DBG_CUDA_TRY(cudaGetLastError());
+    K *kp = keys_a.as<K>(), *alt = keys_b.as<K>();
+    uint32_t *vn = nullptr, *van = nullptr;
+    DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, N, kbits, d_hist, d_digit_base)));
+    sorted = kp;
+    // run-length reduce into the other buffer
+    DBG_TRY(alloc_buf(ctx, headpos, (N + 1) * sizeof(uint32_t)));
+    const uint64_t tiles = (N + SCAN_TILE - 1) / SCAN_TILE;
+    DBG_TRY(ensure_status(ctx, tiles));
+    uint32_t epoch;
+    DBG_TRY(next_epoch(ctx, &epoch));
+    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(uint32_t), s));
+    {
+      DBG_LAUNCH(ctx, ST_RLE, (double)N * sizeof(K),
+                 k_rle<K><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(sorted, N, alt, headpos.as<uint32_t>(), ctx->d_status,
+                                                     ctx->d_counters, epoch, ctx->spin_limit, ctx->d_err,
+                                                     ctx->d_counters + 1));
+    }
+    DBG_CUDA_TRY(cudaGetLastError());
+    uint32_t e32;
+    DBG_TRY(read_small(ctx, ctx->d_counters + 1, sizeof(uint32_t), &e32));
+    DBG_TRY(check_device_error(ctx));
+    E = e32;
+    // keep the buffer holding the unique keys; the sorted keys are done
+    if (sorted == keys_a.as<K>()) { uniq = std::move(keys_b); keys_a.release(); }
+    else { uniq = std::move(keys_a); keys_b.release(); }
+  }
+  if (E >= 0x80000000ull) {
+    set_error("%llu unique edges exceed one in-memory build (2^31 - 1)", (unsigned long long)E);
+    return DBG_EOVERFLOW;
+  }
+  g->num_edges = E;
+
+  // ---- K5 edge ends + records of reads of length k ----
+  const uint64_t R = 2 * E + I;
+  const int nbits = 2 * (int)k;
+  const int npasses = passes_for_bits(nbits);
+  DBG_TRY(alloc_buf(ctx, g->edge_keys, std::max<uint64_t>(1, E) * sizeof(K)));
+  DBG_TRY(alloc_buf(ctx, g->mult, std::max<uint64_t>(1, E) * sizeof(uint32_t)));
+  DBG_TRY(alloc_buf(ctx, g->orient, std::max<uint64_t>(1, E)));
+  DevBuf rk_a, rk_b, rv_a, rv_b;
+  DBG_TRY(alloc_buf(ctx, rk_a, std::max<uint64_t>(1, R) * sizeof(K)));
+  DBG_TRY(alloc_buf(ctx, rk_b, std::max<uint64_t>(1, R) * sizeof(K)));
+  DBG_TRY(alloc_buf(ctx, rv_a, std::max<uint64_t>(1, R) * sizeof(uint32_t)));
+  DBG_TRY(alloc_buf(ctx, rv_b, std::max<uint64_t>(1, R) * sizeof(uint32_t)));
+  DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
+  if (E > 0) {
+    DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)E * (3 * sizeof(K) + 4 + 4 + 1 + 8),
+               k_endpoints<K><<<grid_for(E, EMIT_TILE), EMIT_BLOCK, 0, s>>>(
+        uniq.as<K>(), headpos.as<uint32_t>(), E, k, g->edge_keys.as<K>(), g->mult.as<uint32_t>(),
+        g->orient.as<uint8_t>(), rk_a.as<K>(), rv_a.as<uint32_t>(), npasses, d_hist));
+  }
+  if (I > 0) {
+    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 2, 0, sizeof(uint32_t), s));
+    DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)n * 4 + (double)I * (sizeof(K) + 4),
+               k_isolated<K><<<grid_for(n, 256), 256, 0, s>>>(packed.as<uint64_t>(), base_off.as<uint64_t>(),
+                                                   in.d_lengths, n, k, rk_a.as<K>() + 2 * E,
+                                                   rv_a.as<uint32_t>() + 2 * E, ctx->d_counters + 2, npasses,
+                                                   d_hist));
+  }
+  DBG_CUDA_TRY(cudaGetLastError());
+  uniq.release();
+  headpos.release();
+  packed.release();
+  base_off.release();
+  edge_off.release();
+
+  // ---- STEP-3 sort of the node records (stable: payload order kept) ----
+  K *rk = rk_a.as<K>(), *rk_alt = rk_b.as<K>();
+  uint32_t *rv = rv_a.as<uint32_t>(), *rv_alt = rv_b.as<uint32_t>();
+  DBG_TRY((radix_sort<K, true>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, d_hist, d_digit_base)));
+
+  // ---- K6 node IDs + adjacency rows, K7 neighbours ----
+  DevBuf row_tmp;
+  DBG_TRY(alloc_buf(ctx, row_tmp, (R + 1) * sizeof(uint64_t)));
+  DBG_TRY(alloc_buf(ctx, g->src, std::max<uint64_t>(1, E) * sizeof(uint32_t)));
+  DBG_TRY(alloc_buf(ctx, g->dst, std::max<uint64_t>(1, E) * sizeof(uint32_t)));
+  DBG_TRY(alloc_buf(ctx, g->adj_edge, std::max<uint64_t>(1, 2 * E) * sizeof(uint32_t)));
+  DBG_TRY(alloc_buf(ctx, g->adj_role, std::max<uint64_t>(1, 2 * E)));
+  DBG_TRY(alloc_buf(ctx, g->adj_nbr, std::max<uint64_t>(1, 2 * E) * sizeof(uint32_t)));
+  uint64_t V = 0;
+  if (R > 0) {
+    const uint64_t tiles = (R + SCAN_TILE - 1) / SCAN_TILE;
+    DBG_TRY(ensure_status(ctx, 2 * tiles));
+    uint32_t eh, ee;
+    DBG_TRY(next_epoch(ctx, &eh));
+    DBG_TRY(next_epoch(ctx, &ee));
+    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(uint32_t), s));
+    // node keys go to the free record buffer first (|V| is known only after)
+    {
+      DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (sizeof(K) + 4) + (double)E * (2 * 5 + 8),
+                 k_node_ids<K><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
+          rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g->src.as<uint32_t>(), g->dst.as<uint32_t>(),
+          g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), ctx->d_status, ctx->d_status + tiles,
+          ctx->d_counters, eh, ee, ctx->spin_limit, ctx->d_err, ctx->d_counters + 1));
+    }
+    DBG_CUDA_TRY(cudaGetLastError());
+    uint32_t tot[2];
+    DBG_TRY(read_small(ctx, ctx->d_counters + 1, sizeof(tot), tot));
+    DBG_TRY(check_device_error(ctx));
+    V = tot[0];
+    if (tot[1] != 2 * E) {
+      set_error("adjacency holds %u edge ends, expected %llu", tot[1], (unsigned long long)(2 * E));
+      return DBG_ECUDA;
+    }
+  }
+  g->num_nodes = V;
+  DBG_TRY(alloc_buf(ctx, g->node_keys, std::max<uint64_t>(1, V) * sizeof(K)));
+  DBG_TRY(alloc_buf(ctx, g->row_ptr, (V + 1) * sizeof(uint64_t)));
+  if (V > 0) {
+    Span sp(ctx, ST_COPIES, 2.0 * V * (sizeof(K) + 8), 0);
+    DBG_CUDA_TRY(cudaMemcpyAsync(g->node_keys.p, rk_alt, V * sizeof(K), cudaMemcpyDeviceToDevice, s));
+    DBG_CUDA_TRY(cudaMemcpyAsync(g->row_ptr.p, row_tmp.p, (V + 1) * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  } else {
+    DBG_CUDA_TRY(cudaMemsetAsync(g->row_ptr.p, 0, sizeof(uint64_t), s));
+  }
+  if (E > 0) {
+    DBG_LAUNCH(ctx, ST_ADJACENCY, 2.0 * E * (4 + 1 + 4 + 4),
+               k_adj_nbr<<<grid_for(2 * E, 256 * 8), 256, 0, s>>>(g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
+                                                     g->src.as<uint32_t>(), g->dst.as<uint32_t>(), 2 * E,
+                                                     g->adj_nbr.as<uint32_t>()));
+    DBG_CUDA_TRY(cudaGetLastError());
+  }
+  DBG_CUDA_TRY(cudaStreamSynchronize(s));
+  return check_device_error(ctx);
+}
+
+}  // namespace dbg

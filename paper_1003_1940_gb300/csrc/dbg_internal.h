@@ -1,0 +1,181 @@
+// dbg_internal.h -- host-side state shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/dbg.h"
+
+namespace dbg {
+
+void set_error(const char *fmt, ...);
+
+// Stream-ordered device memory through the context's hooks.
+struct Allocator {
+  dbg_alloc_fn alloc = nullptr;
+  dbg_free_fn free = nullptr;
+  void *user = nullptr;
+  cudaStream_t stream = nullptr;
+  void *get(size_t bytes);
+  void put(void *p, size_t bytes);
+};
+
+// One device buffer; released in stream order when it goes out of scope.
+struct DevBuf {
+  Allocator *al = nullptr;
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept { *this = std::move(o); }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    if (this != &o) {
+      release();
+      al = o.al; p = o.p; bytes = o.bytes;
+      o.p = nullptr; o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p && al) al->put(p, bytes);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+enum Stage {
+  ST_OFFSETS, ST_PACK, ST_EMIT, ST_SORT_EDGES, ST_RLE, ST_ENDPOINTS, ST_SORT_NODES, ST_NODE_IDS,
+  ST_ADJACENCY, ST_COPIES, ST_COMPACT_LINKS, ST_COMPACT_RANK, ST_COMPACT_CYCLES, ST_COMPACT_OUTPUT,
+  ST_COUNT
+};
+extern const char *const kStageNames[ST_COUNT];
+
+struct ProfRecord {
+  int stage;
+  cudaEvent_t a, b;
+  double bytes;
+  uint32_t launches;
+};
+
+// Radix sort tile shape.
+struct SortShape {
+  int block = 256;
+  int items = 16;
+};
+
+}  // namespace dbg
+
+struct dbg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  dbg::Allocator al;
+  uint64_t mem_budget = 0;
+  uint32_t spin_limit = 1u << 22;
+  dbg::SortShape shape;
+  int num_sms = 0;
+  // persistent scratch: the look-back status words of every scan and sort
+  // pass, tagged by epoch so they never need clearing between uses
+  uint64_t *d_status = nullptr;
+  size_t status_words = 0;
+  uint32_t epoch = 1;
+  uint32_t *d_err = nullptr;       // device error word
+  uint32_t *d_counters = nullptr;  // small per-call counters (tile tickets, totals)
+  uint32_t *h_pinned = nullptr;    // pinned host mirror for small read-backs
+  cudaEvent_t ev = nullptr;
+  // profiling
+  bool prof = false;
+  uint64_t launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<dbg::ProfRecord> pending;
+  dbg_stage_stat stats[dbg::ST_COUNT] = {};
+};
+
+struct dbg_graph {
+  uint32_t k = 0, key_words = 1;
+  uint64_t num_nodes = 0, num_edges = 0, num_instances = 0;
+  dbg::Allocator al;  // copy of the creating context's allocator
+  int device = 0;
+  dbg::DevBuf node_keys, edge_keys, src, dst, orient, mult, row_ptr, adj_nbr, adj_edge, adj_role;
+};
+
+struct dbg_unitigs {
+  uint64_t count = 0, num_nodes = 0, total_bases = 0;
+  dbg::Allocator al;
+  int device = 0;
+  dbg::DevBuf node_off, nodes, seq_off, seq, circular;
+};
+
+namespace dbg {
+
+#define DBG_CUDA_TRY(expr)                                                              \
+  do {                                                                                  \
+    cudaError_t e__ = (expr);                                                           \
+    if (e__ != cudaSuccess) {                                                           \
+      ::dbg::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e__), __FILE__, \
+                       __LINE__);                                                       \
+      return DBG_ECUDA;                                                                 \
+    }                                                                                   \
+  } while (0)
+
+#define DBG_TRY(expr)                  \
+  do {                                 \
+    dbg_status s__ = (expr);           \
+    if (s__ != DBG_OK) return s__;     \
+  } while (0)
+
+dbg_status alloc_buf(dbg_ctx *ctx, DevBuf &b, size_t bytes);
+// grows the persistent look-back status array to at least `words` words
+dbg_status ensure_status(dbg_ctx *ctx, size_t words);
+// next epoch for a look-back scan; clears the status array when it wraps
+dbg_status next_epoch(dbg_ctx *ctx, uint32_t *epoch);
+// reads the device error word and maps it to a status (and clears it)
+dbg_status check_device_error(dbg_ctx *ctx);
+
+// Reads a few bytes of device memory through the pinned mirror (synchronizes).
+dbg_status read_small(dbg_ctx *ctx, const void *d_src, size_t bytes, void *h_dst);
+
+// Host copy of n words from device or host memory (synchronous on ctx stream).
+dbg_status copy_out(dbg_ctx *ctx, void *dst, const void *src, size_t bytes);
+
+// Brackets the kernels launched in its scope: counts them and, when the
+// context profiles, records CUDA events around them.
+struct Span {
+  dbg_ctx *ctx;
+  int stage;
+  double bytes;
+  uint32_t launches;
+  cudaEvent_t a = nullptr;
+  Span(dbg_ctx *c, int st, double algo_bytes, uint32_t n_launches = 1);
+  ~Span();
+};
+// Launches one kernel (or a few statements) inside its own Span.
+#define DBG_LAUNCH(ctx, stage, bytes, ...)        \
+  do {                                            \
+    ::dbg::Span dbg_span__((ctx), (stage), (bytes)); \
+    __VA_ARGS__;                                  \
+  } while (0)
+
+// folds finished event pairs into the per-stage statistics (after a sync)
+void prof_resolve(dbg_ctx *ctx);
+
+// The build pipeline for one key width (k <= 31: uint64_t, else 128-bit).
+struct BuildInput {
+  const uint8_t *d_reads;     // device ASCII
+  const uint32_t *d_lengths;  // device
+  uint64_t n;
+  uint64_t total_bases;
+  uint32_t k;
+};
+
+dbg_status build_graph_u64(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g);
+dbg_status build_graph_u128(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g);
+
+}  // namespace dbg

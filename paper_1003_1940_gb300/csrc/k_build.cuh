@@ -1,0 +1,695 @@
+// k_build.cuh -- kernels of the sort-based construction (Section 3,
+// BiConstruct STEP-1..4) and the pipeline that runs them, templated on the
+// key width: uint64_t for k <= 31 ((k+1)-mers of <= 64 bits), Key128 above.
+//
+// Data layout in HBM for one build (N edge instances, E unique edges):
+//   reads    ASCII, back to back                          total_bases bytes
+//   packed   2-bit codes, base i at bits 63-2(i%32) of word i/32 (MSB first)
+//   base_off / edge_off  per-read exclusive prefix of L and max(0, L-k)
+//   keys     N canonical (k+1)-mer keys, double-buffered for the radix sort
+//   uniq, headpos        E unique keys and the index of each run's head
+//   records  2E (+ reads of length k) node keys + u32 payload (e<<1|role),
+//            double-buffered for the radix sort
+// and the graph's own arrays (node keys, edge keys, src, dst, orient, mult,
+// row_ptr, adjacency).
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+
+#include "dbg_device.cuh"
+#include "dbg_internal.h"
+
+namespace dbg {
+
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int MAX_PASSES = 16;             // 128-bit keys / 8-bit digits
+constexpr uint32_t REC_NONE = 0xffffffffu;  // payload of a node record that is not an edge end
+
+// ---------------------------------------------------------------------------
+// small block-wide helpers
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread over the first 256 threads of the
+// block (all threads must call it).  `tmp` holds 8 entries.
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *tmp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t incl = warp_incl_scan(v);
+  if (tid < 256 && lane == 31) tmp[warp] = incl;
+  __syncthreads();
+  uint32_t add = 0;
+  if (tid < 256)
+    for (int w = 0; w < warp; w++) add += tmp[w];
+  __syncthreads();
+  return add + incl - v;
+}
+
+// ---------------------------------------------------------------------------
+// read offsets: base_off[r] = sum of L before r, edge_off[r] = sum of
+// max(0, L - k) before r, plus the number of reads of length exactly k.
+// Three phases: per-tile sums, one-block scan of the tile sums, per-tile
+// exclusive scan.  All values are 64-bit.
+// ---------------------------------------------------------------------------
+constexpr int OFF_BLOCK = 256, OFF_ITEMS = 16, OFF_TILE = OFF_BLOCK * OFF_ITEMS;
+
+struct Sum3 {
+  uint64_t bases, edges, iso;
+};
+
+__device__ __forceinline__ Sum3 warp_reduce3(Sum3 s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s.bases += __shfl_xor_sync(0xffffffffu, s.bases, o);
+    s.edges += __shfl_xor_sync(0xffffffffu, s.edges, o);
+    s.iso += __shfl_xor_sync(0xffffffffu, s.iso, o);
+  }
+  return s;
+}
+
+static __global__ void k_read_tile_sums(const uint32_t *__restrict__ len, uint64_t n, uint32_t k,
+                                 Sum3 *__restrict__ tile_sums) {
+  __shared__ Sum3 part[OFF_BLOCK / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * OFF_TILE;
+  Sum3 s{0, 0, 0};
+  for (int i = 0; i < OFF_ITEMS; i++) {
+    uint64_t r = base + (uint64_t)i * OFF_BLOCK + threadIdx.x;
+    if (r < n) {
+      uint32_t L = len[r];
+      s.bases += L;
+      s.edges += L > k ? L - k : 0;
+      s.iso += L == k;
+    }
+  }
+  s = warp_reduce3(s);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Sum3 t{0, 0, 0};
+    for (int w = 0; w < OFF_BLOCK / 32; w++) {
+      t.bases += part[w].bases; t.edges += part[w].edges; t.iso += part[w].iso;
+    }
+    tile_sums[blockIdx.x] = t;
+  }
+}
+
+// one block: exclusive scan of the tile sums in place; totals -> totals[0..2]
+static __global__ void k_scan_tile_sums(Sum3 *tile_sums, uint32_t num_tiles, uint64_t *totals,
+                                 uint64_t *base_off, uint64_t *edge_off, uint64_t n) {
+  __shared__ Sum3 carry;
+  if (threadIdx.x == 0) carry = Sum3{0, 0, 0};
+  __syncthreads();
+  for (uint32_t start = 0; start < num_tiles; start += blockDim.x) {
+    uint32_t i = start + threadIdx.x;
+    Sum3 v = i < num_tiles ? tile_sums[i] : Sum3{0, 0, 0};
+    // simple serial-per-warp scan through shared memory (num_tiles is small)
+    __shared__ Sum3 buf[1024];
+    buf[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Sum3 run = carry;
+      for (uint32_t j = 0; j < blockDim.x && start + j < num_tiles; j++) {
+        Sum3 x = buf[j];
+        buf[j] = run;
+        run.bases += x.bases; run.edges += x.edges; run.iso += x.iso;
+      }
+      carry = run;
+    }
+    __syncthreads();
+    if (i < num_tiles) tile_sums[i] = buf[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    totals[0] = carry.bases;
+    totals[1] = carry.edges;
+    totals[2] = carry.iso;
+    base_off[n] = carry.bases;
+    edge_off[n] = carry.edges;
+  }
+}
+
+static __global__ void k_read_offsets(const uint32_t *__restrict__ len, uint64_t n, uint32_t k,
+                               const Sum3 *__restrict__ tile_sums, uint64_t *__restrict__ base_off,
+                               uint64_t *__restrict__ edge_off) {
+  // blocked: thread t owns reads [base + t*ITEMS, base + (t+1)*ITEMS)
+  const uint64_t base = (uint64_t)blockIdx.x * OFF_TILE + (uint64_t)threadIdx.x * OFF_ITEMS;
+  uint32_t L[OFF_ITEMS];
+  uint64_t sb = 0, se = 0;
+  for (int i = 0; i < OFF_ITEMS; i++) {
+    uint64_t r = base + i;
+    L[i] = r < n ? len[r] : 0;
+    sb += L[i];
+    se += L[i] > k ? L[i] - k : 0;
+  }
+  // block exclusive scans of the per-thread sums, in 64 bits
+  __shared__ uint64_t wsum_b[OFF_BLOCK / 32], wsum_e[OFF_BLOCK / 32];
+  uint64_t ib = warp_incl_scan(sb), ie = warp_incl_scan(se);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 31) { wsum_b[warp] = ib; wsum_e[warp] = ie; }
+  __syncthreads();
+  uint64_t ab = 0, ae = 0;
+  for (int w = 0; w < warp; w++) { ab += wsum_b[w]; ae += wsum_e[w]; }
+  uint64_t ob = tile_sums[blockIdx.x].bases + ab + ib - sb;
+  uint64_t oe = tile_sums[blockIdx.x].edges + ae + ie - se;
+  for (int i = 0; i < OFF_ITEMS; i++) {
+    uint64_t r = base + i;
+    if (r < n) {
+      base_off[r] = ob;
+      edge_off[r] = oe;
+    }
+    ob += L[i];
+    oe += L[i] > k ? L[i] - k : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1 pack: ASCII -> 2-bit codes, 32 bases per 64-bit word.  code(c) =
+// ((c >> 1) ^ (c >> 2)) & 3 maps 'A','C','G','T' (0x41,0x43,0x47,0x54) to
+// 0,1,2,3; any other byte sets ERR_BAD_BASE.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack4(uint32_t x, bool &ok) {
+  uint32_t okm = __vcmpeq4(x, 0x41414141u) | __vcmpeq4(x, 0x43434343u) |
+                 __vcmpeq4(x, 0x47474747u) | __vcmpeq4(x, 0x54545454u);
+  ok = ok && (okm == 0xffffffffu);
+  uint32_t c = ((x >> 1) ^ (x >> 2)) & 0x03030303u;
+  // byte 0 holds the first base; it goes to the most significant position
+  return ((c & 3u) << 6) | (((c >> 8) & 3u) << 4) | (((c >> 16) & 3u) << 2) | ((c >> 24) & 3u);
+}
+
+static __global__ void k_pack(const uint8_t *__restrict__ ascii, uint64_t total, uint64_t *__restrict__ packed,
+                       uint64_t nwords, uint32_t *err) {
+  const bool aligned = (reinterpret_cast<uintptr_t>(ascii) & 15u) == 0;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b0 = w * 32;
+    uint64_t word = 0;
+    bool ok = true;
+    if (aligned && b0 + 32 <= total) {
+      const uint4 *p = reinterpret_cast<const uint4 *>(ascii + b0);
+      uint4 a = __ldg(p), b = __ldg(p + 1);
+      uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 8; i++) word = (word << 8) | pack4(v[i], ok);
+    } else {
+      for (int i = 0; i < 32; i++) {
+        uint64_t b = b0 + i;
+        uint32_t code = 0;
+        if (b < total) {
+          uint8_t c = ascii[b];
+          bool good = c == 'A' || c == 'C' || c == 'G' || c == 'T';
+          ok = ok && good;
+          code = ((c >> 1) ^ (c >> 2)) & 3u;
+        }
+        word = (word << 2) | code;
+      }
+    }
+    packed[w] = word;
+    if (!ok) atomicOr(err, ERR_BAD_BASE);
+  }
+}
+
+// The m bases starting at base position p, in the low 2m bits.
+template <class K> __device__ __forceinline__ K load_window(const uint64_t *packed, uint64_t p, int m);
+
+template <>
+__device__ __forceinline__ uint64_t load_window<uint64_t>(const uint64_t *packed, uint64_t p, int m) {
+  const uint64_t w = p >> 5;
+  const int o = (int)(p & 31) * 2;
+  uint64_t a = __ldg(packed + w), b = __ldg(packed + w + 1);
+  uint64_t v = o ? (a << o) | (b >> (64 - o)) : a;
+  return v >> (64 - 2 * m);
+}
+
+template <>
+__device__ __forceinline__ Key128 load_window<Key128>(const uint64_t *packed, uint64_t p, int m) {
+  const uint64_t w = p >> 5;
+  const int o = (int)(p & 31) * 2;
+  uint64_t a = __ldg(packed + w), b = __ldg(packed + w + 1), c = __ldg(packed + w + 2);
+  uint64_t hi = o ? (a << o) | (b >> (64 - o)) : a;
+  uint64_t lo = o ? (b << o) | (c >> (64 - o)) : b;
+  return KeyOps<Key128>::shr(Key128{hi, lo}, 128 - 2 * m);
+}
+
+// ---------------------------------------------------------------------------
+// K2 emit (STEP-1): key e of read r at position j = e - edge_off[r] is the
+// canonical (k+1)-mer min(z, revcomp z) of z = r[j .. j+k].  The block also
+// accumulates the digit histograms of every radix pass of the sort that
+// follows (one upfront histogram for all passes, as in onesweep).
+// ---------------------------------------------------------------------------
+constexpr int EMIT_BLOCK = 256, EMIT_ITEMS = 8, EMIT_TILE = EMIT_BLOCK * EMIT_ITEMS;
+
+__device__ __forceinline__ uint64_t last_le(const uint64_t *__restrict__ a, uint64_t lo, uint64_t hi,
+                                            uint64_t x) {
+  // largest i in [lo, hi) with a[i] <= x (a nondecreasing, a[lo] <= x)
+  while (hi - lo > 1) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (__ldg(a + mid) <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <class K>
+__global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict__ packed,
+                                                     const uint64_t *__restrict__ base_off,
+                                                     const uint64_t *__restrict__ edge_off, uint64_t n_reads,
+                                                     uint64_t n_keys, uint32_t k, K *__restrict__ keys,
+                                                     int passes, unsigned long long *__restrict__ hist) {
+  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  __shared__ uint64_t s_r0, s_r1;
+  for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK) s_hist[i] = 0;
+  const uint64_t t0 = (uint64_t)blockIdx.x * EMIT_TILE;
+  const uint64_t t1 = min(n_keys, t0 + EMIT_TILE);
+  if (threadIdx.x == 0) {
+    s_r0 = last_le(edge_off, 0, n_reads, t0);
+    s_r1 = last_le(edge_off, s_r0, n_reads, t1 - 1) + 1;
+  }
+  __syncthreads();
+  const uint64_t r0 = s_r0, r1 = s_r1;
+  const int m = (int)k + 1;
+  uint64_t r = r0;
+  for (uint64_t e = t0 + threadIdx.x; e < t1; e += EMIT_BLOCK) {
+    r = last_le(edge_off, r, r1, e);
+    const uint64_t p = __ldg(base_off + r) + (e - __ldg(edge_off + r));
+    const K z = load_window<K>(packed, p, m);
+    const K key = kmin(z, revcomp(z, m));
+    keys[e] = key;
+    for (int ps = 0; ps < passes; ps++)
+      atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(key, ps * RADIX_BITS, RADIX_BITS)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK)
+    if (s_hist[i]) atomicAdd(hist + i, (unsigned long long)s_hist[i]);
+}
+
+// digit_base[p][d] = number of keys whose digit p is below d
+static __global__ void k_digit_base(const unsigned long long *__restrict__ hist, uint64_t *__restrict__ digit_base) {
+  __shared__ uint64_t s[RADIX];
+  const int p = blockIdx.x, d = threadIdx.x;
+  s[d] = hist[p * RADIX + d];
+  __syncthreads();
+  if (d == 0) {
+    uint64_t run = 0;
+    for (int i = 0; i < RADIX; i++) {
+      uint64_t c = s[i];
+      s[i] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  digit_base[p * RADIX + d] = s[d];
+}
+
+// ---------------------------------------------------------------------------
+// K3 onesweep radix pass (Adinets & Merrill): one launch per 8-bit digit.
+// Tiles are taken in launch order from an atomic ticket, so every tile that
+// a tile waits for is already running.  Per tile:
+//   1. load keys warp-striped (coalesced), rank each key among equal digits
+//      of its warp (stable: item order, then lane order) with a ballot-based
+//      match and warp-private shared-memory digit counters;
+//   2. publish the tile's per-digit counts, look back over predecessor tiles
+//      for the exclusive prefix of each digit, publish the inclusive prefix;
+//   3. stage the keys in shared memory in digit order and write each digit's
+//      run to digit_base[d] + prefix (contiguous, coalesced writes).
+// ---------------------------------------------------------------------------
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS>
+__global__ __launch_bounds__(BLOCK) void k_onesweep(const K *__restrict__ kin, K *__restrict__ kout,
+                                                    const uint32_t *__restrict__ vin,
+                                                    uint32_t *__restrict__ vout, uint64_t n, int shift,
+                                                    const uint64_t *__restrict__ digit_base,
+                                                    uint64_t *__restrict__ status, uint32_t *ticket,
+                                                    uint32_t epoch, uint32_t spin_limit, uint32_t *err) {
+  constexpr int WARPS = BLOCK / 32;
+  constexpr int TILE = BLOCK * ITEMS;
+  static_assert(BLOCK >= RADIX, "one thread per digit");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  K *s_keys = reinterpret_cast<K *>(smem_raw);
+  uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + TILE);
+  __shared__ uint32_t s_whist[WARPS][RADIX];
+  __shared__ uint32_t s_tile_start[RADIX];
+  __shared__ uint64_t s_gbase[RADIX];
+  __shared__ uint32_t s_tmp[8];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < WARPS * RADIX; i += BLOCK) (&s_whist[0][0])[i] = 0;
+  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * TILE;
+  const uint64_t wbase = base + (uint64_t)warp * 32 * ITEMS;
+
+  K key[ITEMS];
+  uint32_t val[ITEMS];
+  uint32_t rank[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; i++) {
+    const uint64_t idx = wbase + (uint64_t)i * 32 + lane;
+    if (idx < n) {
+      key[i] = kin[idx];
+      if (HAS_VAL) val[i] = vin[idx];
+    } else {
+      key[i] = KeyOps<K>::zero();
+      val[i] = 0;
+    }
+  }
+  const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < ITEMS; i++) {
+    const uint64_t idx = wbase + (uint64_t)i * 32 + lane;
+    // digit, with bit 8 set for slots past the end of the input
+    const uint32_t d = idx < n ? KeyOps<K>::digit(key[i], shift, RADIX_BITS) : (uint32_t)RADIX;
+    unsigned peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b <= RADIX_BITS; b++) {
+      const bool bit = (d >> b) & 1u;
+      const unsigned bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
+    const int leader = __ffs(peers) - 1;
+    uint32_t before = 0;
+    if (lane == leader && d < RADIX) {
+      before = s_whist[warp][d];
+      s_whist[warp][d] = before + __popc(peers);
+    }
+    before = __shfl_sync(0xffffffffu, before, leader);
+    rank[i] = before + __popc(peers & lt_mask);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  uint32_t cnt = 0;
+  if (tid < RADIX) {
+    for (int w = 0; w < WARPS; w++) {
+      const uint32_t c = s_whist[w][tid];
+      s_whist[w][tid] = cnt;
+      cnt += c;
+    }
+    st_relaxed(status + (size_t)tile * RADIX + tid,
+               lb_word(epoch, tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE, cnt));
+  }
+  const uint32_t tstart = block_excl_scan_256(cnt, s_tmp);
+  if (tid < RADIX) {
+    s_tile_start[tid] = tstart;
+    uint32_t excl = 0;
+    if (tile > 0) {
+      excl = lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
+      st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, LB_INCLUSIVE, excl + cnt));
+    }
+    s_gbase[tid] = digit_base[tid] + excl - tstart;
+  }
+  __syncthreads();
+
+#pragma unroll
+  for (int i = 0; i < ITEMS; i++) {
+    const uint64_t idx = wbase + (uint64_t)i * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = KeyOps<K>::digit(key[i], shift, RADIX_BITS);
+      const uint32_t p = s_tile_start[d] + s_whist[warp][d] + rank[i];
+      s_keys[p] = key[i];
+      if (HAS_VAL) s_vals[p] = val[i];
+    }
+  }
+  __syncthreads();
+  const uint32_t tile_n = (uint32_t)min((uint64_t)TILE, n - base);
+  for (uint32_t j = tid; j < tile_n; j += BLOCK) {
+    const K kk = s_keys[j];
+    const uint32_t d = KeyOps<K>::digit(kk, shift, RADIX_BITS);
+    const uint64_t dst = s_gbase[d] + j;
+    if (dst >= n) {  // only reachable if the digit counts were inconsistent
+      atomicOr(err, ERR_INTERNAL);
+      continue;
+    }
+    kout[dst] = kk;
+    if (HAS_VAL) vout[dst] = s_vals[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4 run-length reduce (STEP-2): unique keys of the sorted array and the
+// index of the first element of each run, by a single pass with look-back.
+// The last tile writes headpos[E] = n and E itself to *total.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_BLOCK = 256, SCAN_ITEMS = 16, SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+// Block-wide ranks of per-item flags in index order for the strided layout
+// (item i of thread t at i*BLOCK + t).  Returns the tile's flag count;
+// rank_out[i] = flags before item i of this thread within the tile.
+template <int BLOCK, int ITEMS>
+__device__ __forceinline__ uint32_t tile_flag_ranks(const bool (&flag)[ITEMS], uint32_t (&rank_out)[ITEMS],
+                                                    uint32_t *s_cnt /* ITEMS*WARPS */) {
+  constexpr int WARPS = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < ITEMS; i++) {
+    const unsigned b = __ballot_sync(0xffffffffu, flag[i]);
+    rank_out[i] = __popc(b & lt);
+    if (lane == 0) s_cnt[i * WARPS + warp] = __popc(b);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int PER = (ITEMS * WARPS + 31) / 32;
+    uint32_t v[PER];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+      const int idx = lane * PER + j;
+      v[j] = idx < ITEMS * WARPS ? s_cnt[idx] : 0;
+      s += v[j];
+    }
+    const uint32_t incl = warp_incl_scan(s);
+    uint32_t run = incl - s;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+      const int idx = lane * PER + j;
+      if (idx < ITEMS * WARPS) s_cnt[idx] = run;
+      run += v[j];
+    }
+    if (lane == 31) s_cnt[ITEMS * WARPS] = incl;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < ITEMS; i++) rank_out[i] += s_cnt[i * WARPS + warp];
+  return s_cnt[ITEMS * WARPS];
+}
+
+// warp 0 publishes the tile's count and looks back; returns the exclusive
+// prefix to every thread through shared memory
+__device__ __forceinline__ uint32_t tile_prefix(uint64_t *status, uint32_t tile, uint32_t count, uint32_t epoch,
+                                                uint32_t spin_limit, uint32_t *err, uint32_t *s_slot) {
+  if (threadIdx.x < 32) {
+    uint32_t excl = 0;
+    if (tile == 0) {
+      if (threadIdx.x == 0) st_relaxed(status, lb_word(epoch, LB_INCLUSIVE, count));
+    } else {
+      if (threadIdx.x == 0) st_relaxed(status + tile, lb_word(epoch, LB_AGGREGATE, count));
+      excl = lookback_exclusive_warp(status, tile, epoch, spin_limit, err);
+      if (threadIdx.x == 0) st_relaxed(status + tile, lb_word(epoch, LB_INCLUSIVE, excl + count));
+    }
+    if (threadIdx.x == 0) *s_slot = excl;
+  }
+  __syncthreads();
+  return *s_slot;
+}
+
+template <class K>
+__global__ __launch_bounds__(SCAN_BLOCK) void k_rle(const K *__restrict__ keys, uint64_t n, K *__restrict__ uniq,
+                                                    uint32_t *__restrict__ headpos, uint64_t *status,
+                                                    uint32_t *ticket, uint32_t epoch, uint32_t spin_limit,
+                                                    uint32_t *err, uint32_t *total) {
+  constexpr int WARPS = SCAN_BLOCK / 32;
+  __shared__ uint32_t s_cnt[SCAN_ITEMS * WARPS + 1];
+  __shared__ uint32_t s_tile, s_excl;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * SCAN_TILE;
+  K key[SCAN_ITEMS];
+  bool head[SCAN_ITEMS];
+  uint32_t rank[SCAN_ITEMS];
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; i++) {
+    const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
+    head[i] = false;
+    if (idx < n) {
+      key[i] = keys[idx];
+      head[i] = idx == 0 || !KeyOps<K>::eq(key[i], keys[idx - 1]);
+    }
+  }
+  const uint32_t count = tile_flag_ranks<SCAN_BLOCK, SCAN_ITEMS>(head, rank, s_cnt);
+  const uint32_t excl = tile_prefix(status, tile, count, epoch, spin_limit, err, &s_excl);
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; i++) {
+    if (head[i]) {
+      const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
+      const uint32_t pos = excl + rank[i];
+      uniq[pos] = key[i];
+      headpos[pos] = (uint32_t)idx;
+    }
+  }
+  if (base + SCAN_TILE >= n && threadIdx.x == 0) {
+    headpos[excl + count] = (uint32_t)n;
+    *total = excl + count;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K5 edge ends (STEP-1 decoding + STEP-3 collection).  The unique key z is
+// the canonical (k+1)-mer; x = its first k bases, y = its last k bases.
+// With x^, y^ their canonical forms and o = 1 where the k-mer is the
+// negative strand, STEP-1's table gives (x^, y^, o1, o2) if x^ <= y^ and
+// (y^, x^, not o2, not o1) otherwise.  Writes orient, mult, a copy of the
+// key into the graph, and two node records per edge (payload e<<1 | role),
+// and accumulates the digit histograms of the node sort.
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ uniq,
+                                                          const uint32_t *__restrict__ headpos, uint64_t E,
+                                                          uint32_t k, K *__restrict__ edge_keys,
+                                                          uint32_t *__restrict__ mult,
+                                                          uint8_t *__restrict__ orient, K *__restrict__ rkeys,
+                                                          uint32_t *__restrict__ rvals, int passes,
+                                                          unsigned long long *__restrict__ hist) {
+  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK) s_hist[i] = 0;
+  __syncthreads();
+  const int kk = (int)k;
+  for (uint64_t e = (uint64_t)blockIdx.x * EMIT_TILE + threadIdx.x; e < min(E, (uint64_t)(blockIdx.x + 1) * EMIT_TILE);
+       e += EMIT_BLOCK) {
+    const K z = uniq[e];
+    const K x = KeyOps<K>::shr(z, 2);
+    const K y = KeyOps<K>::mask_low(z, 2 * kk);
+    const K xh = kmin(x, revcomp(x, kk));
+    const K yh = kmin(y, revcomp(y, kk));
+    const uint32_t o1 = !KeyOps<K>::eq(x, xh), o2 = !KeyOps<K>::eq(y, yh);
+    K s, d;
+    uint32_t a, b;
+    if (!KeyOps<K>::less(yh, xh)) { s = xh; d = yh; a = o1; b = o2; }
+    else { s = yh; d = xh; a = !o2; b = !o1; }
+    edge_keys[e] = z;
+    orient[e] = (uint8_t)((a << 1) | b);
+    mult[e] = headpos[e + 1] - headpos[e];
+    rkeys[2 * e] = s;
+    rvals[2 * e] = (uint32_t)(e << 1);
+    rkeys[2 * e + 1] = d;
+    rvals[2 * e + 1] = (uint32_t)(e << 1) | 1u;
+    for (int ps = 0; ps < passes; ps++) {
+      atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(s, ps * RADIX_BITS, RADIX_BITS)], 1u);
+      atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(d, ps * RADIX_BITS, RADIX_BITS)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK)
+    if (s_hist[i]) atomicAdd(hist + i, (unsigned long long)s_hist[i]);
+}
+
+// Reads of length exactly k: their k-mer is a node with no edge (Section 2
+// takes every k-mer of the reads).  One record each, payload REC_NONE,
+// appended after the edge ends.
+template <class K>
+__global__ void k_isolated(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ base_off,
+                           const uint32_t *__restrict__ len, uint64_t n, uint32_t k, K *__restrict__ rkeys,
+                           uint32_t *__restrict__ rvals, uint32_t *slot, int passes,
+                           unsigned long long *__restrict__ hist) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+    if (len[r] != k) continue;
+    const K x = load_window<K>(packed, base_off[r], (int)k);
+    const K xh = kmin(x, revcomp(x, (int)k));
+    const uint32_t i = atomicAdd(slot, 1u);
+    rkeys[i] = xh;
+    rvals[i] = REC_NONE;
+    for (int ps = 0; ps < passes; ps++)
+      atomicAdd(hist + ps * RADIX + KeyOps<K>::digit(xh, ps * RADIX_BITS, RADIX_BITS), 1ull);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K6 node IDs (STEP-3) + adjacency rows (STEP-4).  Over the node records
+// sorted by key (stable, so edge ends precede isolated records within a
+// node and are in (e, role) order): node ID = number of run heads up to the
+// record minus one; adjacency slot = number of edge-end records before it.
+// Two look-back scans in one pass.  The last tile writes row_ptr[V] and the
+// totals {V, ends}.
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ __launch_bounds__(SCAN_BLOCK) void k_node_ids(
+    const K *__restrict__ rkeys, const uint32_t *__restrict__ rvals, uint64_t R, K *__restrict__ node_keys,
+    uint64_t *__restrict__ row_ptr, uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+    uint32_t *__restrict__ adj_edge, uint8_t *__restrict__ adj_role, uint64_t *status_h, uint64_t *status_e,
+    uint32_t *ticket, uint32_t epoch_h, uint32_t epoch_e, uint32_t spin_limit, uint32_t *err,
+    uint32_t *totals) {
+  constexpr int WARPS = SCAN_BLOCK / 32;
+  __shared__ uint32_t s_cnt_h[SCAN_ITEMS * WARPS + 1], s_cnt_e[SCAN_ITEMS * WARPS + 1];
+  __shared__ uint32_t s_tile, s_excl_h, s_excl_e;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * SCAN_TILE;
+  K key[SCAN_ITEMS];
+  uint32_t val[SCAN_ITEMS];
+  bool head[SCAN_ITEMS], end[SCAN_ITEMS];
+  uint32_t rh[SCAN_ITEMS], re[SCAN_ITEMS];
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; i++) {
+    const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
+    head[i] = end[i] = false;
+    val[i] = REC_NONE;
+    if (idx < R) {
+      key[i] = rkeys[idx];
+      val[i] = rvals[idx];
+      head[i] = idx == 0 || !KeyOps<K>::eq(key[i], rkeys[idx - 1]);
+      end[i] = val[i] != REC_NONE;
+    }
+  }
+  const uint32_t ch = tile_flag_ranks<SCAN_BLOCK, SCAN_ITEMS>(head, rh, s_cnt_h);
+  const uint32_t ce = tile_flag_ranks<SCAN_BLOCK, SCAN_ITEMS>(end, re, s_cnt_e);
+  // both look-backs: warp 0 for heads, then for edge ends
+  const uint32_t xh = tile_prefix(status_h, tile, ch, epoch_h, spin_limit, err, &s_excl_h);
+  const uint32_t xe = tile_prefix(status_e, tile, ce, epoch_e, spin_limit, err, &s_excl_e);
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; i++) {
+    const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
+    if (idx >= R) continue;
+    const uint32_t id = xh + rh[i] + (head[i] ? 1u : 0u) - 1u;
+    const uint32_t slot = xe + re[i];
+    if (head[i]) {
+      node_keys[id] = key[i];
+      row_ptr[id] = slot;
+    }
+    if (end[i]) {
+      const uint32_t e = val[i] >> 1, role = val[i] & 1u;
+      adj_edge[slot] = e;
+      adj_role[slot] = (uint8_t)role;
+      (role ? dst : src)[e] = id;
+    }
+  }
+  if (base + SCAN_TILE >= R && threadIdx.x == 0) {
+    row_ptr[xh + ch] = xe + ce;
+    totals[0] = xh + ch;
+    totals[1] = xe + ce;
+  }
+}
+
+// K7 neighbour of every adjacency slot: the edge's other end.
+static __global__ void k_adj_nbr(const uint32_t *__restrict__ adj_edge, const uint8_t *__restrict__ adj_role,
+                          const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst, uint64_t n,
+                          uint32_t *__restrict__ nbr) {
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = adj_edge[p];
+    nbr[p] = adj_role[p] ? __ldg(src + e) : __ldg(dst + e);
+  }
+}
+
+// node keys as 1 or 2 words; row_ptr shrink copies are plain memcpy
+
+}  // namespace dbg

@@ -1,0 +1,359 @@
+"""Thin ctypes binding of libdbg (include/dbg.h), with the same names.
+
+Only argument marshalling lives here: every step of graph construction and
+compaction runs in the library's CUDA kernels.  PyTorch supplies device
+memory (its caching allocator, through the library's allocator hooks) and
+streams.  There is no CPU fallback: if libdbg.so is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build_lib
+
+DBG_OK, DBG_EINVAL, DBG_ENOMEM, DBG_ECUDA, DBG_ETIMEOUT, DBG_ECANCELLED, DBG_EOVERFLOW = range(7)
+_STATUS = {0: "DBG_OK", 1: "DBG_EINVAL", 2: "DBG_ENOMEM", 3: "DBG_ECUDA", 4: "DBG_ETIMEOUT",
+           5: "DBG_ECANCELLED", 6: "DBG_EOVERFLOW"}
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class dbg_options(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("device", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("alloc", _ALLOC_FN),
+        ("free", _FREE_FN),
+        ("alloc_user", ctypes.c_void_p),
+        ("mem_budget", ctypes.c_uint64),
+        ("spin_limit", ctypes.c_uint32),
+        ("sort_block", ctypes.c_uint32),
+        ("sort_items", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 8),
+    ]
+
+
+class dbg_graph_view(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_uint32), ("key_words", ctypes.c_uint32),
+        ("num_nodes", ctypes.c_uint64), ("num_edges", ctypes.c_uint64), ("num_instances", ctypes.c_uint64),
+        ("node_keys", ctypes.c_void_p), ("edge_keys", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p),
+        ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("mult", ctypes.c_void_p),
+        ("adj_nbr", ctypes.c_void_p), ("adj_edge", ctypes.c_void_p),
+        ("orient", ctypes.c_void_p), ("adj_role", ctypes.c_void_p),
+    ]
+
+
+class dbg_stage_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+# (name, restype, argtypes) of every C entry point
+_P = ctypes.c_void_p
+_SIGNATURES = [
+    ("dbg_options_init", None, [_P]),
+    ("dbg_create", ctypes.c_int, [_P, _P]),
+    ("dbg_destroy", None, [_P]),
+    ("dbg_last_error", ctypes.c_char_p, []),
+    ("dbg_build", ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, ctypes.c_uint32, _P]),
+    ("dbg_graph_k", ctypes.c_uint32, [_P]),
+    ("dbg_graph_key_words", ctypes.c_uint32, [_P]),
+    ("dbg_graph_num_nodes", ctypes.c_uint64, [_P]),
+    ("dbg_graph_num_edges", ctypes.c_uint64, [_P]),
+    ("dbg_graph_num_instances", ctypes.c_uint64, [_P]),
+    ("dbg_graph_nodes", ctypes.c_int, [_P, _P]),
+    ("dbg_graph_edges", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("dbg_graph_csr", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("dbg_graph_device_view", ctypes.c_int, [_P, _P]),
+    ("dbg_graph_free", None, [_P]),
+    ("dbg_compact", ctypes.c_int, [_P, _P, _P]),
+    ("dbg_unitigs_count", ctypes.c_uint64, [_P]),
+    ("dbg_unitigs_total_bases", ctypes.c_uint64, [_P]),
+    ("dbg_unitigs_get", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("dbg_unitigs_free", None, [_P]),
+    ("dbg_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
+    ("dbg_profile_read", ctypes.c_uint32, [_P, _P, ctypes.c_uint32]),
+    ("dbg_launch_count", ctypes.c_uint64, [_P]),
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return build_lib.LIB_PATH
+
+
+def load(build: bool = False):
+    """Loads libdbg.so (building it first when `build`); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build_lib.build() if build else build_lib.LIB_PATH
+            if not os.path.exists(path):
+                raise RuntimeError(f"libdbg.so not built ({path}); run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            for name, res, args in _SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class DbgError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != DBG_OK:
+        msg = _lib.dbg_last_error()
+        raise DbgError(status, where, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# device memory from PyTorch's caching allocator
+# ---------------------------------------------------------------------------
+class _TorchAllocator:
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(user, nbytes, stream):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream or 0))
+            except Exception:  # out of memory: report NULL, the library returns DBG_ENOMEM
+                return None
+
+        def _free(user, ptr, nbytes, stream):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = _ALLOC_FN(_alloc)
+        self.free = _FREE_FN(_free)
+
+
+class Context:
+    """dbg_ctx: device, stream, allocator."""
+
+    def __init__(self, device: int | None = None, stream=None, torch_allocator: bool = True,
+                 mem_budget: int = 0, spin_limit: int = 0):
+        import torch
+        lib = load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        opt = dbg_options()
+        lib.dbg_options_init(ctypes.byref(opt))
+        opt.device = device
+        opt.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        opt.mem_budget = mem_budget
+        opt.spin_limit = spin_limit
+        self._alloc = None
+        if torch_allocator:
+            self._alloc = _TorchAllocator(device)
+            opt.alloc = self._alloc.alloc
+            opt.free = self._alloc.free
+        self._opt = opt
+        h = ctypes.c_void_p()
+        _check(lib.dbg_create(ctypes.byref(h), ctypes.byref(opt)), "dbg_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.dbg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def _ptr(x) -> tuple[int, object]:
+    """Data pointer of a numpy array, bytes or torch tensor (host or device)."""
+    if isinstance(x, (bytes, bytearray)):
+        x = np.frombuffer(bytes(x), dtype=np.uint8)
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x)
+        return x.ctypes.data, x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return x.data_ptr(), x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+class Graph:
+    """dbg_graph handle; holds its context so the context outlives it."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    def free(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.dbg_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.free()
+
+
+class Unitigs:
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    def free(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.dbg_unitigs_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.free()
+
+
+def dbg_create(**kw) -> Context:
+    return Context(**kw)
+
+
+def dbg_destroy(ctx: Context):
+    ctx.close()
+
+
+def dbg_build(ctx: Context, reads, lengths, k: int) -> Graph:
+    """reads: uint8 ASCII (numpy / bytes / torch, host or cuda); lengths: uint32."""
+    rp, rkeep = _ptr(reads)
+    if isinstance(lengths, np.ndarray) and lengths.dtype != np.uint32:
+        lengths = lengths.astype(np.uint32)
+    lp, lkeep = _ptr(lengths)
+    n = len(lengths) if not hasattr(lengths, "numel") else int(lengths.numel())
+    out = ctypes.c_void_p()
+    _check(_lib.dbg_build(ctx.handle, ctypes.c_void_p(rp), ctypes.c_void_p(lp), n, k, ctypes.byref(out)),
+           "dbg_build")
+    del rkeep, lkeep
+    return Graph(ctx, out)
+
+
+def dbg_graph_k(g: Graph) -> int:
+    return int(_lib.dbg_graph_k(g.handle))
+
+
+def dbg_graph_key_words(g: Graph) -> int:
+    return int(_lib.dbg_graph_key_words(g.handle))
+
+
+def dbg_graph_num_nodes(g: Graph) -> int:
+    return int(_lib.dbg_graph_num_nodes(g.handle))
+
+
+def dbg_graph_num_edges(g: Graph) -> int:
+    return int(_lib.dbg_graph_num_edges(g.handle))
+
+
+def dbg_graph_num_instances(g: Graph) -> int:
+    return int(_lib.dbg_graph_num_instances(g.handle))
+
+
+def _np_out(n, dtype):
+    return np.zeros(max(0, n), dtype=dtype)
+
+
+def dbg_graph_nodes(g: Graph) -> np.ndarray:
+    W = dbg_graph_key_words(g)
+    out = _np_out(dbg_graph_num_nodes(g) * W, np.uint64)
+    _check(_lib.dbg_graph_nodes(g.handle, ctypes.c_void_p(out.ctypes.data)), "dbg_graph_nodes")
+    return out.reshape(-1, W)
+
+
+def dbg_graph_edges(g: Graph) -> dict:
+    W, E = dbg_graph_key_words(g), dbg_graph_num_edges(g)
+    keys, src, dst = _np_out(E * W, np.uint64), _np_out(E, np.uint32), _np_out(E, np.uint32)
+    orient, mult = _np_out(E, np.uint8), _np_out(E, np.uint32)
+    _check(_lib.dbg_graph_edges(g.handle, *(ctypes.c_void_p(a.ctypes.data) for a in (keys, src, dst, orient, mult))),
+           "dbg_graph_edges")
+    return {"keys": keys.reshape(-1, W), "src": src, "dst": dst, "orient": orient, "mult": mult}
+
+
+def dbg_graph_csr(g: Graph) -> dict:
+    V, E = dbg_graph_num_nodes(g), dbg_graph_num_edges(g)
+    row_ptr, nbr = _np_out(V + 1, np.uint64), _np_out(2 * E, np.uint32)
+    edge, role = _np_out(2 * E, np.uint32), _np_out(2 * E, np.uint8)
+    _check(_lib.dbg_graph_csr(g.handle, *(ctypes.c_void_p(a.ctypes.data) for a in (row_ptr, nbr, edge, role))),
+           "dbg_graph_csr")
+    return {"row_ptr": row_ptr, "nbr": nbr, "edge": edge, "role": role}
+
+
+def dbg_graph_device_view(g: Graph) -> dbg_graph_view:
+    v = dbg_graph_view()
+    _check(_lib.dbg_graph_device_view(g.handle, ctypes.byref(v)), "dbg_graph_device_view")
+    return v
+
+
+def dbg_graph_free(g: Graph):
+    g.free()
+
+
+def dbg_compact(ctx: Context, g: Graph) -> Unitigs:
+    out = ctypes.c_void_p()
+    _check(_lib.dbg_compact(ctx.handle, g.handle, ctypes.byref(out)), "dbg_compact")
+    return Unitigs(ctx, out)
+
+
+def dbg_unitigs_count(u: Unitigs) -> int:
+    return int(_lib.dbg_unitigs_count(u.handle))
+
+
+def dbg_unitigs_total_bases(u: Unitigs) -> int:
+    return int(_lib.dbg_unitigs_total_bases(u.handle))
+
+
+def dbg_unitigs_get(u: Unitigs) -> dict:
+    U = dbg_unitigs_count(u)
+    node_off, seq_off = _np_out(U + 1, np.uint64), _np_out(U + 1, np.uint64)
+    n_nodes = 0
+    _check(_lib.dbg_unitigs_get(u.handle, ctypes.c_void_p(node_off.ctypes.data), None,
+                                None, None, None), "dbg_unitigs_get")
+    n_nodes = int(node_off[-1]) if U else 0
+    nodes = _np_out(n_nodes, np.uint64)
+    seq = _np_out(dbg_unitigs_total_bases(u), np.uint8)
+    circ = _np_out(U, np.uint8)
+    _check(_lib.dbg_unitigs_get(u.handle, None, ctypes.c_void_p(nodes.ctypes.data),
+                                ctypes.c_void_p(seq_off.ctypes.data), ctypes.c_void_p(seq.ctypes.data),
+                                ctypes.c_void_p(circ.ctypes.data)), "dbg_unitigs_get")
+    return {"node_off": node_off, "nodes": nodes, "seq_off": seq_off, "seq": seq.tobytes(), "circular": circ}
+
+
+def dbg_unitigs_free(u: Unitigs):
+    u.free()
+
+
+def dbg_profile_enable(ctx: Context, on: bool = True):
+    _check(_lib.dbg_profile_enable(ctx.handle, 1 if on else 0), "dbg_profile_enable")
+
+
+def dbg_profile_read(ctx: Context) -> dict:
+    """{stage: {"launches", "ms", "bytes"}} for the stages with launches."""
+    arr = (dbg_stage_stat * 32)()
+    n = _lib.dbg_profile_read(ctx.handle, arr, 32)
+    out = {}
+    for i in range(min(n, 32)):
+        st = arr[i]
+        if st.launches:
+            out[st.name.decode()] = {"launches": int(st.launches), "ms": float(st.ms), "bytes": float(st.bytes)}
+    return out
+
+
+def dbg_launch_count(ctx: Context) -> int:
+    return int(_lib.dbg_launch_count(ctx.handle))

@@ -149,25 +149,37 @@ def genome_codes(spec: ReadSetSpec, rng: np.random.Generator) -> tuple[np.ndarra
     return genome, covered / g
 
 
+def _substitute(block: np.ndarray, rate: float, rng: np.random.Generator) -> None:
+    """i.i.d. per-base substitutions in place: the number of errors is
+    Binomial(size, rate), their positions a uniform subset, and each new base
+    uniform over the other three."""
+    flat = block.reshape(-1)
+    count = int(rng.binomial(flat.size, rate))
+    if count == 0:
+        return
+    pos = rng.choice(flat.size, size=count, replace=False)
+    code_of = np.zeros(256, dtype=np.uint8)
+    code_of[ALPHABET] = np.arange(4, dtype=np.uint8)
+    shift = rng.integers(1, 4, size=count, dtype=np.uint8)
+    flat[pos] = ALPHABET[(code_of[flat[pos]] + shift) & 3]
+
+
 def sample_reads(spec: ReadSetSpec, genome_ascii: np.ndarray, rng: np.random.Generator,
                  chunk: int = 1 << 18) -> tuple[np.ndarray, np.ndarray]:
     """Reads of fixed length at uniform positions of a linear genome, each
     from the reverse strand with probability 1/2, with substitution errors."""
-    L, n, g = spec.read_len, spec.n_reads, genome_ascii.size
+    L, n = spec.read_len, spec.n_reads
     out = np.empty(n * L, dtype=np.uint8)
-    code_of = np.zeros(256, dtype=np.uint8)
-    code_of[ALPHABET] = np.arange(4, dtype=np.uint8)
-    offs = np.arange(L, dtype=np.int64)
+    windows = np.lib.stride_tricks.sliding_window_view(genome_ascii, L)
     for c0 in range(0, n, chunk):
         c1 = min(n, c0 + chunk)
         m = c1 - c0
-        starts = rng.integers(0, g - L + 1, size=m, dtype=np.int64)
-        block = genome_ascii[starts[:, None] + offs[None, :]]
+        starts = rng.integers(0, windows.shape[0], size=m, dtype=np.int64)
+        block = windows[starts]
         reverse = rng.random(m) < 0.5
         block[reverse] = _PAIR[block[reverse][:, ::-1]]
         if spec.error_rate > 0:
-            codes = code_of[block]
-            block = ALPHABET[_mutate(codes, spec.error_rate, rng)]
+            _substitute(block, spec.error_rate, rng)
         out[c0 * L:c1 * L] = block.reshape(-1)
     return out, np.full(n, L, dtype=np.uint32)
 

@@ -1,0 +1,151 @@
+"""Parity of the CUDA path (called through the C ABI) with the CPU oracle.
+
+Integer work: every comparison is bit-exact."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from golden_io import all_fixtures, load
+from parity import check_parity, gpu_graph
+from paper_1003_1940_gb300 import readgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dbg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1003_1940_gb300 import dbg as d
+    d.load()
+    return d
+
+
+@pytest.fixture(scope="module")
+def ctx(dbg):
+    return dbg.Context()
+
+
+def as_input(reads: list[str]):
+    lengths = np.array([len(r) for r in reads], dtype=np.uint32)
+    return np.frombuffer("".join(reads).encode(), dtype=np.uint8).copy(), lengths
+
+
+@pytest.mark.parametrize("name", all_fixtures())
+def test_worked_examples(dbg, ctx, name):
+    fx = load(name)
+    reads, lengths = as_input(fx["reads"])
+    check_parity(dbg, ctx, reads, lengths, fx["k"])
+
+
+def test_tiny_workload(dbg, ctx):
+    """The 10,000-read, 100 kbp, k = 21 workload in full."""
+    reads, lengths = readgen.generate(readgen.tiny_spec())
+    got = check_parity(dbg, ctx, reads, lengths, 21)
+    assert got["N"] == 10_000 * (36 - 21)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 15, 21, 31, 33, 45, 55, 63])
+def test_ragged_reads_all_widths(dbg, ctx, k):
+    """Ragged lengths around k (shorter, equal, one longer, much longer)."""
+    rng = np.random.default_rng(1000 + k)
+    spec = readgen.ReadSetSpec(4_000, 1, 10, 0.0, k, 7 + k)
+    reads_g, _ = readgen.generate(readgen.ReadSetSpec(3_000, 400, 2 * k + 40, 0.01, k, 9 + k))
+    lens = rng.integers(max(1, k - 3), 2 * k + 40, size=400).astype(np.uint32)
+    lens[:5] = [k, k, k + 1, max(1, k - 1), 2 * k + 39]
+    reads = reads_g[:int(lens.sum())]
+    check_parity(dbg, ctx, reads, lens, k)
+    del spec
+
+
+@pytest.mark.parametrize("k", [21, 55])
+def test_many_tiles_ragged_tail(dbg, ctx, k):
+    """Enough edge instances for several hundred sort tiles plus a partial one."""
+    L = 100 if k < 33 else 150
+    n = 7_777
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(60_000, n, L, 0.01, k, 11))
+    check_parity(dbg, ctx, reads, lengths, k, compact=True)
+
+
+def test_repeats_workload_scaled(dbg, ctx):
+    """The 50 Mbp repeat workload's recipe at 1/500 scale (k = 31)."""
+    spec = readgen.large_spec(scale=1 / 500)
+    reads, lengths = readgen.generate(spec)
+    check_parity(dbg, ctx, reads, lengths, 31)
+
+
+def test_long_k_workload_scaled(dbg, ctx):
+    """The long-k workload (tandem arrays, k = 55, 128-bit keys) at 1/400 scale."""
+    spec = readgen.long_k_spec(scale=1 / 400)
+    reads, lengths = readgen.generate(spec)
+    check_parity(dbg, ctx, reads, lengths, 55)
+
+
+def test_low_complexity(dbg, ctx):
+    """Homopolymers, dinucleotide repeats and palindromes: self-loops,
+    parallel edges with different orientations, cycles."""
+    reads = ["A" * 50, "T" * 40, "ACACACACACACACACAC", "ACGT" * 10, "GATC" * 12,
+             "AAAAACCCCCGGGGGTTTTT" * 3, "TGCA" * 9]
+    for k in (1, 3, 5, 7, 11):
+        r, l = as_input(reads)
+        check_parity(dbg, ctx, r, l, k)
+
+
+def test_empty_and_short(dbg, ctx):
+    r, l = as_input([])
+    got = check_parity(dbg, ctx, r, l, 21)
+    assert got["V"] == 0 and got["E"] == 0
+    r, l = as_input(["ACGT", "GG", "A" * 20])
+    got = check_parity(dbg, ctx, r, l, 21)
+    assert got["V"] == 0
+    # a read of exactly k bases: one node, no edge
+    r, l = as_input(["ACGTACGTACGTACGTACGTA"])
+    got = check_parity(dbg, ctx, r, l, 21)
+    assert got["V"] == 1 and got["E"] == 0
+
+
+def test_device_resident_input(dbg, ctx):
+    import torch
+    reads, lengths = readgen.generate(readgen.tiny_spec())
+    og = oracle.build_graph(reads, lengths, 21)
+    d_reads = torch.from_numpy(reads).cuda()
+    d_len = torch.from_numpy(lengths.view(np.int32)).cuda()
+    _, got = gpu_graph(dbg, ctx, d_reads, d_len, 21)
+    from parity import assert_graph_equal
+    assert_graph_equal(got, og)
+
+
+def test_unaligned_host_input(dbg, ctx):
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(5_000, 500, 50, 0.01, 15, 3))
+    buf = np.zeros(reads.size + 3, dtype=np.uint8)
+    buf[3:] = reads
+    check_parity(dbg, ctx, buf[3:], lengths, 15)
+
+
+@pytest.mark.parametrize("k", [0, 2, 64])
+def test_bad_k(dbg, ctx, k):
+    r, l = as_input(["ACGTACGT"])
+    with pytest.raises(dbg.DbgError) as e:
+        dbg.dbg_build(ctx, r, l, k)
+    assert e.value.status == dbg.DBG_EINVAL
+
+
+def test_bad_base_is_reported(dbg, ctx):
+    r, l = as_input(["ACGTACGTNACGT", "ACGT"])
+    with pytest.raises(dbg.DbgError) as e:
+        dbg.dbg_build(ctx, r, l, 3)
+    assert e.value.status == dbg.DBG_EINVAL
+    # the context stays usable
+    r, l = as_input(["ACGTACGTTACGT"])
+    check_parity(dbg, ctx, r, l, 3)
+
+
+def test_repeat_calls_identical(dbg, ctx):
+    reads, lengths = readgen.generate(readgen.tiny_spec())
+    _, a = gpu_graph(dbg, ctx, reads, lengths, 21)
+    _, b = gpu_graph(dbg, ctx, reads, lengths, 21)
+    for key in a:
+        if isinstance(a[key], np.ndarray):
+            np.testing.assert_array_equal(a[key], b[key])
