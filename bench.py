@@ -46,14 +46,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle sample time")
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (profiling captures only)")
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, scale=1.0):
+    tag = "" if scale == 1.0 else f" scaled x{scale:g}"
     if name == "large":
-        return readgen.large_spec(), "50Mbp-repeats 15Mx100bp 30x 0.5%err k=31 (build+compact)"
+        return (readgen.large_spec(scale), "50Mbp-repeats 15Mx100bp 30x 0.5%err k=31 (build+compact)" + tag)
     if name == "long_k":
-        return readgen.long_k_spec(), "20Mbp-repeats+tandem 4Mx150bp 30x 0.3%err k=55 (build+compact)"
+        return (readgen.long_k_spec(scale),
+                "20Mbp-repeats+tandem 4Mx150bp 30x 0.3%err k=55 (build+compact)" + tag)
     return readgen.tiny_spec(), "100kbp 10000x36bp 1%err k=21 (build+compact)"
 
 
@@ -175,7 +178,7 @@ def run_reference(args):
     ws, rank, _ = dist_setup(args)
     if rank != 0:
         return
-    spec, wl = workload(args.workload)
+    spec, wl = workload(args.workload, args.scale)
     reads, lengths = readgen.generate(spec)
     import oracle
     oracle.build()
@@ -218,7 +221,7 @@ def run_ours(args):
     from paper_1003_1940_gb300 import build_lib, dbg
     build_lib.build()
     dbg.load()
-    spec, wl = workload(args.workload)
+    spec, wl = workload(args.workload, args.scale)
     reads, lengths = readgen.generate(spec)
     k = spec.k
     N = int(np.maximum(lengths.astype(np.int64) - k, 0).sum())
