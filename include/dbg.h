@@ -176,6 +176,36 @@ dbg_status dbg_unitigs_get(const dbg_unitigs *u, uint64_t *node_off, uint64_t *n
 void dbg_unitigs_free(dbg_unitigs *u);
 
 /* ----------------------------------------------------------------------
+ * dbg_rle_u64_noalloc -- the run-length reduce that dbg_build runs on its
+ * sorted 64-bit edge keys (distinct keys and where each run starts), as a
+ * call that allocates no memory at all.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at call
+ * time -- a host program whose memory manager reserved the whole GPU up
+ * front, a plugin whose host framework forbids allocation after start-up,
+ * or a real-time loop that cannot take cudaMalloc's implicit device
+ * synchronisation.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   keys       device, n keys in ascending order
+ *   n          0 <= n <= 2^26 (67,108,864); larger n returns DBG_EINVAL
+ *   uniq       device, room for n keys: the distinct keys, ascending
+ *   run_start  device, room for n + 1 entries: index in `keys` of each
+ *              distinct key's first occurrence, then n; the multiplicity of
+ *              uniq[i] is run_start[i + 1] - run_start[i]
+ *   count      host: receives the number of distinct keys
+ *   stream     cudaStream_t to run on (NULL = the legacy default stream);
+ *              the call returns after the stream has finished its work
+ * Its scratch (per-tile look-back words, counters, error word: 128 KiB) is
+ * a fixed array in the library's device memory, which every GPU that loads
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the one array and
+ * clear it at their start, so calls that overlap on the GPU (other streams,
+ * other host threads) race: serialise them.
+ * -------------------------------------------------------------------- */
+dbg_status dbg_rle_u64_noalloc(const uint64_t *keys, uint64_t n, uint64_t *uniq, uint32_t *run_start,
+                               uint64_t *count, void *stream);
+
+/* ----------------------------------------------------------------------
  * Profiling (tracing).  When enabled, the context brackets every kernel it
  * launches with CUDA events on its stream and accumulates, per stage, the
  * launches, device time and algorithmic bytes (the bytes the stage must

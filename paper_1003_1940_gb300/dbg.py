@@ -81,6 +81,7 @@ _SIGNATURES = [
     ("dbg_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
     ("dbg_profile_read", ctypes.c_uint32, [_P, _P, ctypes.c_uint32]),
     ("dbg_launch_count", ctypes.c_uint64, [_P]),
+    ("dbg_rle_u64_noalloc", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, _P]),
 ]
 
 _lib = None
@@ -357,3 +358,14 @@ def dbg_profile_read(ctx: Context) -> dict:
 
 def dbg_launch_count(ctx: Context) -> int:
     return int(_lib.dbg_launch_count(ctx.handle))
+
+
+def dbg_rle_u64_noalloc(keys, n: int, uniq, run_start, stream=None) -> int:
+    """Run-length reduce of n sorted u64 keys with no allocation (device
+    tensors in, device tensors out); returns the number of distinct keys."""
+    count = ctypes.c_uint64(0)
+    s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(_lib.dbg_rle_u64_noalloc(ctypes.c_void_p(_ptr(keys)[0]), n, ctypes.c_void_p(_ptr(uniq)[0]),
+                                    ctypes.c_void_p(_ptr(run_start)[0]), ctypes.byref(count), ctypes.c_void_p(s)),
+           "dbg_rle_u64_noalloc")
+    return int(count.value)
