@@ -122,6 +122,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_traffic(workload_name, scale):
+    """DRAM bytes per onesweep launch from the committed ncu summary, or None
+    when the kernel source changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "onesweep_large_k31.md")
+    src = os.path.join(ROOT, "paper_1003_1940_gb300", "csrc", "k_build.cuh")
+    if scale != 1.0 or not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("    "):
+            key, _, val = line.strip().partition(":")
+            fields[key.strip()] = val.strip()
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if fields.get("source_sha256_16") != digest or fields.get("workload") != workload_name:
+        return None
+    return float(fields["bytes_per_launch"])
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -275,15 +294,7 @@ def run_ours(args):
     pass_ms = srt["ms"] / max(1, srt["launches"] - args.steps) if n_pass > 0 else 0.0
     pass_bytes = srt["bytes"] / max(1, n_pass)
     achieved = pass_bytes / (pass_ms / 1000.0) / 1e9 if pass_ms > 0 else 0.0
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "onesweep_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            tr = json.load(open(tr_path))
-            if tr.get("workload") == args.workload:
-                traffic = tr.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = measured_traffic(args.workload, args.scale)
 
     stages = {name: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
