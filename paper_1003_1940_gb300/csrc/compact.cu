@@ -39,168 +39,182 @@ __device__ __forceinline__ uint32_t end_side(uint8_t orient, uint32_t role) {
   return role == 0 ? (o1 ? 0u : 1u) : (o2 ? 1u : 0u);
 }
 
-// Per node: the single edge on each side, or NONE when the side has 0 or
-// >= 2 edge ends.  link[2v + side].
-__global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ adj_edge,
-                             const uint8_t *__restrict__ adj_role, const uint8_t *__restrict__ orient,
-                             uint64_t V, uint32_t *__restrict__ link) {
+// Per node and side: the edge end alone on that side, if exactly one is.
+// link_node[2v + side] = (w << 1) | side_at_w of the edge's other end, and
+// link_edge[2v + side] = the edge; NONE when the side has 0 or >= 2 ends.
+// The neighbour comes from the adjacency row, so only orient is gathered.
+__global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ adj_nbr,
+                             const uint32_t *__restrict__ adj_edge, const uint8_t *__restrict__ adj_role,
+                             const uint8_t *__restrict__ orient, uint64_t V, uint32_t *__restrict__ link_node,
+                             uint32_t *__restrict__ link_edge) {
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t cnt[2] = {0, 0}, e_at[2] = {NONE32, NONE32};
-    for (uint64_t p = row_ptr[v]; p < row_ptr[v + 1]; p++) {
-      const uint32_t e = adj_edge[p];
-      const uint32_t sd = end_side(orient[e], adj_role[p]);
+    uint32_t cnt[2] = {0, 0}, e_at[2] = {NONE32, NONE32}, far[2] = {NONE32, NONE32};
+    const uint64_t p0 = row_ptr[v], p1 = row_ptr[v + 1];
+    for (uint64_t p = p0; p < p1; p++) {
+      const uint32_t e = adj_edge[p], role = adj_role[p];
+      const uint8_t o = orient[e];
+      const uint32_t sd = end_side(o, role);
       cnt[sd]++;
       e_at[sd] = e;
+      far[sd] = (adj_nbr[p] << 1) | end_side(o, 1u - role);
     }
-    link[2 * v] = cnt[0] == 1 ? e_at[0] : NONE32;
-    link[2 * v + 1] = cnt[1] == 1 ? e_at[1] : NONE32;
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      link_node[2 * v + sd] = cnt[sd] == 1 ? far[sd] : NONE32;
+      link_edge[2 * v + sd] = cnt[sd] == 1 ? e_at[sd] : NONE32;
+    }
   }
 }
 
-// succ of strand-node x = 2v + s: leave v by its right side (s = 0) or left
-// side (s = 1); the far end w must have that edge alone on its side.
-__global__ void k_successors(const uint32_t *__restrict__ link, const uint32_t *__restrict__ src,
-                             const uint32_t *__restrict__ dst, const uint8_t *__restrict__ orient, uint64_t V,
-                             uint32_t *__restrict__ succ, uint32_t *__restrict__ pred) {
+// ListRankingTransform arcs.  Strand-node x = 2v + s leaves v by its right
+// side (s = 0) or its left side (s = 1); the arc exists when the edge there
+// joins two distinct nodes and is alone on the far node's side too.  It
+// enters w on side sw: strand 0 when that is w's left side, 1 otherwise.
+__global__ void k_successors(const uint32_t *__restrict__ link_node, const uint32_t *__restrict__ link_edge,
+                             uint64_t V, uint32_t *__restrict__ succ, uint32_t *__restrict__ pred) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * V; x += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t v = x >> 1;
-    const uint32_t s = (uint32_t)(x & 1);
-    const uint32_t leave_side = s ? 0u : 1u;
-    const uint32_t e = link[2 * v + leave_side];
+    const uint32_t leave = (x & 1) ? 0u : 1u;
+    const uint32_t ln = link_node[2 * v + leave];
     uint32_t out = NONE32;
-    if (e != NONE32) {
-      const uint32_t a = src[e], b = dst[e];
-      if (a != b) {
-        const uint32_t w = a == v ? b : a;
-        const uint32_t wrole = a == v ? 1u : 0u;
-        const uint32_t wside = end_side(orient[e], wrole);
-        if (link[2 * (uint64_t)w + wside] == e) out = 2 * w + (wside == 0 ? 0u : 1u);
-      }
+    if (ln != NONE32) {
+      const uint32_t w = ln >> 1, sw = ln & 1u;
+      if (w != (uint32_t)v && link_edge[2 * (uint64_t)w + sw] == link_edge[2 * v + leave])
+        out = 2 * w + (sw == 0 ? 0u : 1u);
     }
     succ[x] = out;
     if (out != NONE32) pred[out] = (uint32_t)x;
   }
 }
 
-// pointer-jumping state: P = current ancestor (itself for a list head),
-// D = distance to it
-__global__ void k_rank_init(const uint32_t *__restrict__ pred, uint64_t n, uint32_t *__restrict__ P,
-                            uint32_t *__restrict__ D) {
+// Ranking state of a strand-node, one 64-bit word: (ancestor << 32) |
+// distance.  A list head is (itself, 0).  Words are read and written whole,
+// so a thread that reads a neighbour mid-update sees either its old or its
+// new (ancestor, distance) pair, both valid.
+__device__ __forceinline__ uint64_t pk(uint32_t a, uint32_t d) { return ((uint64_t)a << 32) | d; }
+__device__ __forceinline__ uint32_t pk_a(uint64_t w) { return (uint32_t)(w >> 32); }
+__device__ __forceinline__ uint32_t pk_d(uint64_t w) { return (uint32_t)w; }
+__device__ __forceinline__ bool pk_root(uint64_t w, uint32_t x) { return pk_a(w) == x && pk_d(w) == 0; }
+constexpr uint64_t UNSET64 = ~0ull;
+
+// Every list head walks its list, writing (head, rank), for at most `cap`
+// strand-nodes; the rest of a longer list and all cycles stay UNSET.
+__global__ void k_walk_lists(const uint32_t *__restrict__ pred, const uint32_t *__restrict__ succ, uint64_t n,
+                             uint32_t cap, uint64_t *__restrict__ word) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+    if (pred[x] != NONE32) continue;
+    uint32_t y = (uint32_t)x;
+    for (uint32_t i = 0; i < cap; i++) {
+      word[y] = pk((uint32_t)x, i);
+      const uint32_t ny = succ[y];
+      if (ny == NONE32) break;
+      y = ny;
+    }
+  }
+}
+
+// Strand-nodes the walks did not reach go on an active list, pointing to
+// their predecessor at distance 1.
+__global__ void k_collect_active(const uint32_t *__restrict__ pred, uint64_t n, uint64_t *__restrict__ word,
+                                 uint32_t *__restrict__ active, uint32_t *count) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+    if (word[x] != UNSET64) continue;
     const uint32_t p = pred[x];
-    P[x] = p == NONE32 ? (uint32_t)x : p;
-    D[x] = p == NONE32 ? 0u : 1u;
+    word[x] = p == NONE32 ? pk((uint32_t)x, 0) : pk(p, 1);
+    active[atomicAdd(count, 1u)] = (uint32_t)x;
   }
 }
 
-// A list head points to itself at distance 0.  A strand-node on a cycle
-// can also come to point to itself (when the cycle length divides 2^r), but
-// always at a distance > 0, so (P == x, D == 0) identifies heads.
-__device__ __forceinline__ bool is_root(const uint32_t *P, const uint32_t *D, uint32_t x) {
-  return P[x] == x && D[x] == 0;
-}
-
-// One Wyllie round over all strand-nodes (or only those flagged in `only`).
-// Counts the strand-nodes whose ancestor is not yet a list head.  Distances
-// saturate, so on a cycle they never wrap back to 0.
-__global__ void k_rank_jump(const uint32_t *__restrict__ Pin, const uint32_t *__restrict__ Din, uint64_t n,
-                            uint32_t *__restrict__ Pout, uint32_t *__restrict__ Dout,
-                            const uint8_t *__restrict__ only, uint32_t *unfinished) {
+// One round of pointer jumping, in place, over the active strand-nodes.
+// Counts those whose ancestor was not yet a list head.  Distances saturate,
+// so on a cycle they never return to 0.
+__global__ void k_jump_active(const uint32_t *__restrict__ active, uint32_t A, uint64_t *word,
+                              uint32_t *jumped) {
   uint32_t local = 0;
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t p = Pin[x];
-    uint32_t d = Din[x];
-    uint32_t np = p;
-    if (!(p == (uint32_t)x && d == 0) && (!only || only[x]) && !is_root(Pin, Din, p)) {
-      d = (uint32_t)min((uint64_t)d + Din[p], (uint64_t)0x7fffffffu);
-      np = Pin[p];
-      local++;
-    }
-    Pout[x] = np;
-    Dout[x] = d;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A; i += gridDim.x * blockDim.x) {
+    const uint32_t x = active[i];
+    const uint64_t w = word[x];
+    if (pk_root(w, x)) continue;
+    const uint32_t p = pk_a(w);
+    const uint64_t wp = word[p];
+    if (pk_root(wp, p)) continue;
+    word[x] = pk(pk_a(wp), (uint32_t)min((uint64_t)pk_d(w) + pk_d(wp), (uint64_t)0x7fffffffu));
+    local++;
   }
   local = __reduce_add_sync(0xffffffffu, local);
-  if ((threadIdx.x & 31) == 0 && local) atomicAdd(unfinished, local);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(jumped, local);
 }
 
-// Strand-nodes whose ancestor is not a list head after convergence lie on
-// cycles.  Marks them and seeds the min-label propagation.
-__global__ void k_cycle_mark(const uint32_t *__restrict__ P, const uint32_t *__restrict__ D, uint64_t n,
-                             uint8_t *__restrict__ on_cycle, uint32_t *__restrict__ label, uint32_t *count) {
-  uint32_t local = 0;
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-    const bool c = !is_root(P, D, P[x]);
-    on_cycle[x] = c;
-    label[x] = (uint32_t)x;
-    local += c;
+// Active strand-nodes that never reached a head lie on cycles: list them and
+// seed (predecessor, own index) words for the min-label propagation.
+__global__ void k_collect_cycles(const uint32_t *__restrict__ active, uint32_t A, const uint64_t *__restrict__ word,
+                                 const uint32_t *__restrict__ pred, uint32_t *__restrict__ cyc_list,
+                                 uint64_t *__restrict__ lab, uint32_t *count) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A; i += gridDim.x * blockDim.x) {
+    const uint32_t x = active[i];
+    const uint64_t w = word[x];
+    if (pk_root(w, x) || pk_root(word[pk_a(w)], pk_a(w))) continue;
+    cyc_list[atomicAdd(count, 1u)] = x;
+    lab[x] = pk(pred[x], x);
   }
-  local = __reduce_add_sync(0xffffffffu, local);
-  if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
 }
 
-// One round of min-label propagation around cycles: M = min over 2^r preds.
-__global__ void k_cycle_min(const uint32_t *__restrict__ Qin, const uint32_t *__restrict__ Min, uint64_t n,
-                            const uint8_t *__restrict__ on_cycle, uint32_t *__restrict__ Qout,
-                            uint32_t *__restrict__ Mout) {
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t q = Qin[x], m = Min[x];
-    if (on_cycle[x]) {
-      m = min(m, Min[q]);
-      q = Qin[q];
-    }
-    Qout[x] = q;
-    Mout[x] = m;
+// Min-label propagation around the cycles, in place: lab[x] = (q, m) with m
+// the smallest strand-node index in the cycle stretch (q, x].
+__global__ void k_cycle_min(const uint32_t *__restrict__ cyc_list, uint32_t C, uint64_t *lab) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
+    const uint32_t x = cyc_list[i];
+    const uint64_t w = lab[x];
+    const uint64_t wq = lab[pk_a(w)];
+    lab[x] = pk(pk_a(wq), min(pk_d(w), pk_d(wq)));
   }
 }
 
 // A cycle whose smallest strand-node is 2v (positive strand) is the copy
-// kept; it is opened at that strand-node.  cyc: 0 path, 1 kept cycle, 2
-// mirror of a kept cycle.
-__global__ void k_cycle_break(const uint32_t *__restrict__ pred, const uint32_t *__restrict__ M,
-                              const uint8_t *__restrict__ on_cycle, uint64_t n, uint8_t *__restrict__ cyc,
-                              uint32_t *__restrict__ P, uint32_t *__restrict__ D) {
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-    if (!on_cycle[x]) {
-      cyc[x] = 0;
-      continue;
-    }
-    const uint32_t m = M[x];
+// kept (cyc = 1); its mirror is cyc = 2.  Both are opened at their smallest
+// strand-node and ranked again as lists.
+__global__ void k_cycle_break(const uint32_t *__restrict__ cyc_list, uint32_t C, const uint64_t *__restrict__ lab,
+                              const uint32_t *__restrict__ pred, uint8_t *__restrict__ cyc,
+                              uint64_t *__restrict__ word) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
+    const uint32_t x = cyc_list[i];
+    const uint32_t m = pk_d(lab[x]);
     cyc[x] = (m & 1u) ? 2 : 1;
-    if (m == (uint32_t)x) {
-      P[x] = (uint32_t)x;
-      D[x] = 0;
-    } else {
-      P[x] = pred[x];
-      D[x] = 1;
-    }
+    word[x] = m == x ? pk(x, 0) : pk(pred[x], 1);
   }
 }
 
-// Per node: the strand kept (canonical copy), its unitig's first node and
-// its rank there.
+// Per node: the strand kept (canonical copy), its unitig's first node, its
+// rank there; the last node of the kept copy records the unitig length at
+// the first node's slot.
 template <class K>
-__global__ void k_select(const uint32_t *__restrict__ P, const uint32_t *__restrict__ D,
+__global__ void k_select(const uint64_t *__restrict__ word, const uint32_t *__restrict__ succ,
                          const uint8_t *__restrict__ cyc, const uint64_t *__restrict__ node_keys, uint64_t V,
                          int k, uint8_t *__restrict__ strand, uint32_t *__restrict__ head,
-                         uint32_t *__restrict__ rank, uint32_t *__restrict__ is_head) {
+                         uint32_t *__restrict__ rank, uint32_t *__restrict__ is_head,
+                         uint32_t *__restrict__ len_at_head) {
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t x0 = 2 * v, x1 = 2 * v + 1;
+    const uint64_t w0 = word[x0], w1 = word[x1];
     uint32_t s;
-    if (cyc[x0] || cyc[x1]) {
-      s = cyc[x0] == 1 ? 0u : 1u;
+    const uint8_t c0 = cyc ? cyc[x0] : 0, c1 = cyc ? cyc[x1] : 0;
+    if (c0 || c1) {
+      s = c0 == 1 ? 0u : 1u;
     } else {
-      const uint32_t h0 = P[x0], h1 = P[x1];
+      const uint32_t h0 = pk_a(w0), h1 = pk_a(w1);
       K a = load_node_key<K>(node_keys, h0 >> 1), b = load_node_key<K>(node_keys, h1 >> 1);
       if (h0 & 1u) a = revcomp(a, k);
       if (h1 & 1u) b = revcomp(b, k);
       s = KeyOps<K>::less(a, b) ? 0u : 1u;
     }
-    const uint64_t x = 2 * v + s;
-    const uint32_t h = P[x] >> 1;
+    const uint64_t w = s ? w1 : w0;
+    const uint32_t hx = pk_a(w), r = pk_d(w), h = hx >> 1;
     strand[v] = (uint8_t)s;
     head[v] = h;
-    rank[v] = D[x];
+    rank[v] = r;
     is_head[v] = h == (uint32_t)v ? 1u : 0u;
+    const uint32_t nx = succ[2 * v + s];
+    if (nx == NONE32 || nx == hx) len_at_head[h] = r + 1;
   }
 }
 
@@ -247,51 +261,56 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_scan_excl(const uint32_t *__rest
   }
 }
 
-__global__ void k_unitig_len(const uint32_t *__restrict__ head, const uint64_t *__restrict__ uidx, uint64_t V,
-                             uint64_t U, uint32_t *__restrict__ len, uint8_t *__restrict__ circ,
-                             const uint8_t *__restrict__ cyc, const uint8_t *__restrict__ strand, uint32_t *err) {
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t u = uidx[head[v]];
-    if (u >= U) {
-      atomicOr(err, ERR_INTERNAL);
+// Unitig tables, one thread per node; the first node of each unitig writes
+// its entries.  off_by_v[h] = first output slot of the unitig headed by h.
+__global__ void k_unitig_offsets(const uint32_t *__restrict__ is_head, const uint64_t *__restrict__ uidx,
+                                 const uint64_t *__restrict__ off_by_v, const uint8_t *__restrict__ cyc,
+                                 const uint8_t *__restrict__ strand, uint64_t V, uint64_t U, int k,
+                                 uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
+                                 uint8_t *__restrict__ circular) {
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= V; v += (uint64_t)gridDim.x * blockDim.x) {
+    if (v == V) {
+      node_off[U] = V;
+      seq_off[U] = V + U * (uint64_t)(k - 1);
       continue;
     }
-    atomicAdd(len + u, 1u);
-    if (head[v] == (uint32_t)v) circ[u] = cyc[2 * v + strand[v]] == 1 ? 1 : 0;
+    if (!is_head[v]) continue;
+    const uint64_t u = uidx[v];
+    node_off[u] = off_by_v[v];
+    seq_off[u] = off_by_v[v] + u * (uint64_t)(k - 1);
+    circular[u] = cyc && cyc[2 * v + strand[v]] == 1 ? 1 : 0;
   }
 }
 
+// Node list and spelled string of every unitig: the node at rank r writes
+// its (ID, strand) entry and, for r = 0, the first k-mer, else the last base
+// of its k-mer as read on the kept strand.
 template <class K>
 __global__ void k_unitig_write(const uint32_t *__restrict__ head, const uint32_t *__restrict__ rank,
                                const uint8_t *__restrict__ strand, const uint64_t *__restrict__ uidx,
-                               const uint64_t *__restrict__ node_off, const uint64_t *__restrict__ node_keys,
-                               uint64_t V, int k, uint64_t *__restrict__ nodes_out, char *__restrict__ seq,
-                               uint32_t *err) {
+                               const uint64_t *__restrict__ off_by_v, const uint32_t *__restrict__ len_at_head,
+                               const uint64_t *__restrict__ node_keys, uint64_t V, int k,
+                               uint64_t *__restrict__ nodes_out, char *__restrict__ seq, uint32_t *err) {
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t u = uidx[head[v]];
+    const uint32_t h = head[v];
     const uint64_t r = rank[v];
-    const uint32_t s = strand[v];
-    if (node_off[u] + r >= node_off[u + 1]) {  // ranks must fit their unitig
+    if (r >= len_at_head[h]) {  // a rank must fall inside its unitig
       atomicOr(err, ERR_INTERNAL);
       continue;
     }
-    nodes_out[node_off[u] + r] = (v << 1) | s;
+    const uint64_t u = uidx[h];
+    const uint32_t s = strand[v];
+    nodes_out[off_by_v[h] + r] = (v << 1) | s;
     K km = load_node_key<K>(node_keys, v);
     if (s) km = revcomp(km, k);
-    const uint64_t so = node_off[u] + u * (uint64_t)(k - 1);
+    const uint64_t so = off_by_v[h] + u * (uint64_t)(k - 1);
     const char *acgt = "ACGT";
     if (r == 0) {
-      for (int i = 0; i < k; i++)
-        seq[so + i] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - i), 2)];
+      for (int i = 0; i < k; i++) seq[so + i] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - i), 2)];
     } else {
       seq[so + k - 1 + r] = acgt[KeyOps<K>::low2(km)];
     }
   }
-}
-
-__global__ void k_seq_off(const uint64_t *__restrict__ node_off, uint64_t U, int k, uint64_t *__restrict__ seq_off) {
-  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= U; u += (uint64_t)gridDim.x * blockDim.x)
-    seq_off[u] = node_off[u] + u * (uint64_t)(k - 1);
 }
 
 static unsigned grid_of(uint64_t n) {
@@ -312,36 +331,36 @@ static dbg_status scan_excl(dbg_ctx *ctx, const uint32_t *in, uint64_t n, uint64
   DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 2 * sizeof(uint32_t), s));
   DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 12.0 * n,
              k_scan_excl<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(in, n, out, ctx->d_status, ctx->d_counters, epoch,
-                                                     ctx->spin_limit, ctx->d_err, ctx->d_counters + 1));
+                                                                ctx->spin_limit, ctx->d_err, ctx->d_counters + 1));
   DBG_CUDA_TRY(cudaGetLastError());
   return read_small(ctx, ctx->d_counters + 1, sizeof(uint32_t), total);
 }
 
-// Runs pointer jumping until every strand-node that can reach a list head
-// has done so.  P/D hold the result on return (buffers may be swapped).
-static dbg_status rank_lists(dbg_ctx *ctx, uint32_t **P, uint32_t **D, uint32_t **P2, uint32_t **D2, uint64_t n,
-                             const uint8_t *only, int *rounds) {
+// Pointer jumping over a list of strand-nodes until every one that can
+// reach a list head has (a round without progress leaves only cycles: a list
+// always has one strand-node that finishes per round).
+static dbg_status jump_until_stable(dbg_ctx *ctx, const uint32_t *list, uint32_t A, uint64_t *word,
+                                    uint32_t *remaining) {
   cudaStream_t s = ctx->stream;
-  uint32_t prev = 0xffffffffu;
-  for (int r = 0; r < 64; r++) {
+  uint32_t prev = 0xffffffffu, jumped = 0;
+  for (int r = 0; r < 96; r++) {
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 3, 0, sizeof(uint32_t), s));
-    DBG_LAUNCH(ctx, ST_COMPACT_RANK, 24.0 * n,
-               k_rank_jump<<<grid_of(n), 256, 0, s>>>(*P, *D, n, *P2, *D2, only, ctx->d_counters + 3));
+    DBG_LAUNCH(ctx, ST_COMPACT_RANK, 24.0 * A,
+               k_jump_active<<<grid_of(A), 256, 0, s>>>(list, A, word, ctx->d_counters + 3));
     DBG_CUDA_TRY(cudaGetLastError());
-    std::swap(*P, *P2);
-    std::swap(*D, *D2);
-    uint32_t unfinished;
-    DBG_TRY(read_small(ctx, ctx->d_counters + 3, sizeof(uint32_t), &unfinished));
-    ++*rounds;
-    // no progress in a round: what is left lies on cycles (a list has a
-    // strand-node at every distance up to its length, so a longer list
-    // would still have shrunk the count)
-    if (unfinished == 0 || unfinished == prev) return DBG_OK;
-    prev = unfinished;
+    DBG_TRY(read_small(ctx, ctx->d_counters + 3, sizeof(uint32_t), &jumped));
+    if (jumped == 0 || jumped == prev) {
+      *remaining = jumped;
+      return DBG_OK;
+    }
+    prev = jumped;
   }
   set_error("list ranking did not converge");
   return DBG_ETIMEOUT;
 }
+
+// Lists of up to this many strand-nodes are ranked by one walking thread.
+constexpr uint32_t kWalkCap = 2048;
 
 template <class K>
 static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u) {
@@ -349,77 +368,103 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
   const uint64_t V = g->num_nodes, n = 2 * V, E2 = 2 * g->num_edges;
   const int k = (int)g->k;
   u->num_nodes = V;
-  DevBuf link, succ, pred, P, D, P2, D2, oncyc, cyc, label, strand, head, rank, is_head, uidx, len;
   const uint64_t V1 = std::max<uint64_t>(1, V), n1 = std::max<uint64_t>(1, n);
-  DBG_TRY(alloc_buf(ctx, link, n1 * 4));
-  DBG_TRY(alloc_buf(ctx, succ, n1 * 4));
-  DBG_TRY(alloc_buf(ctx, pred, n1 * 4));
-  DBG_TRY(alloc_buf(ctx, P, n1 * 4));
-  DBG_TRY(alloc_buf(ctx, D, n1 * 4));
-  DBG_TRY(alloc_buf(ctx, P2, n1 * 4));
-  DBG_TRY(alloc_buf(ctx, D2, n1 * 4));
-  DBG_TRY(alloc_buf(ctx, oncyc, n1));
-  DBG_TRY(alloc_buf(ctx, cyc, n1));
+  DevBuf link_node, link_edge, succ, pred, word, active, cycl, lab, cyc;
+  DevBuf strand, head, rank, is_head, len_at_head, uidx, off_by_v;
   uint64_t U = 0;
+  bool have_cycles = false;
   if (V > 0) {
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, (double)V * 8 + 4.0 * E2 * 5 + 8.0 * V,
-               k_side_links<<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_edge.as<uint32_t>(),
-                                            g->adj_role.as<uint8_t>(), g->orient.as<uint8_t>(), V,
-                                            link.as<uint32_t>()));
+    DBG_TRY(alloc_buf(ctx, link_node, n1 * 4));
+    DBG_TRY(alloc_buf(ctx, link_edge, n1 * 4));
+    DBG_TRY(alloc_buf(ctx, succ, n1 * 4));
+    DBG_TRY(alloc_buf(ctx, pred, n1 * 4));
+    DBG_TRY(alloc_buf(ctx, word, n1 * 8));
+    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + (double)E2 * 10 + 16.0 * V,
+               k_side_links<<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
+                                                       g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
+                                                       g->orient.as<uint8_t>(), V, link_node.as<uint32_t>(),
+                                                       link_edge.as<uint32_t>()));
     DBG_CUDA_TRY(cudaMemsetAsync(pred.p, 0xff, n * 4, s));
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 8.0 * n + 2.0 * n * (4 + 4 + 1 + 4) + 8.0 * n,
-               k_successors<<<grid_of(n), 256, 0, s>>>(link.as<uint32_t>(), g->src.as<uint32_t>(), g->dst.as<uint32_t>(),
-                                            g->orient.as<uint8_t>(), V, succ.as<uint32_t>(), pred.as<uint32_t>()));
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n,
-               k_rank_init<<<grid_of(n), 256, 0, s>>>(pred.as<uint32_t>(), n, P.as<uint32_t>(), D.as<uint32_t>()));
+    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 8.0 * n + 8.0 * n,
+               k_successors<<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint32_t>(), V,
+                                                       succ.as<uint32_t>(), pred.as<uint32_t>()));
+    link_node.release();
+    link_edge.release();
+    DBG_CUDA_TRY(cudaMemsetAsync(word.p, 0xff, n * 8, s));
+    DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 12.0 * n,
+               k_walk_lists<<<grid_of(n), 256, 0, s>>>(pred.as<uint32_t>(), succ.as<uint32_t>(), n, kWalkCap,
+                                                       word.as<uint64_t>()));
     DBG_CUDA_TRY(cudaGetLastError());
-    uint32_t *p = P.as<uint32_t>(), *d = D.as<uint32_t>(), *p2 = P2.as<uint32_t>(), *d2 = D2.as<uint32_t>();
-    int rounds = 0;
-    DBG_TRY(rank_lists(ctx, &p, &d, &p2, &d2, n, nullptr, &rounds));
-    // cycles
-    DBG_TRY(alloc_buf(ctx, label, n1 * 4));
+    // what the walks left: tails of very long lists, and cycles
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 4, 0, sizeof(uint32_t), s));
-    DBG_LAUNCH(ctx, ST_COMPACT_CYCLES, 13.0 * n,
-               k_cycle_mark<<<grid_of(n), 256, 0, s>>>(p, d, n, oncyc.as<uint8_t>(), label.as<uint32_t>(), ctx->d_counters + 4));
-    uint32_t ncyc;
-    DBG_TRY(read_small(ctx, ctx->d_counters + 4, sizeof(uint32_t), &ncyc));
-    if (ncyc > 0) {
-      // min label over each cycle: ceil(log2(ncyc)) + 1 doubling rounds
-      uint32_t *q = p2, *m = label.as<uint32_t>(), *q2 = d2;
-      DevBuf m2buf;
-      DBG_TRY(alloc_buf(ctx, m2buf, n1 * 4));
-      uint32_t *m2 = m2buf.as<uint32_t>();
-      DBG_CUDA_TRY(cudaMemcpyAsync(q, pred.p, n * 4, cudaMemcpyDeviceToDevice, s));
-      int R = 1;
-      while ((1ull << (R - 1)) < ncyc) R++;
-      for (int r = 0; r < R; r++) {
-        DBG_LAUNCH(ctx, ST_COMPACT_CYCLES, 25.0 * n,
-                   k_cycle_min<<<grid_of(n), 256, 0, s>>>(q, m, n, oncyc.as<uint8_t>(), q2, m2));
-        std::swap(q, q2);
-        std::swap(m, m2);
+    DBG_TRY(alloc_buf(ctx, active, n1 * 4));
+    DBG_LAUNCH(ctx, ST_COMPACT_RANK, 16.0 * n,
+               k_collect_active<<<grid_of(n), 256, 0, s>>>(pred.as<uint32_t>(), n, word.as<uint64_t>(),
+                                                           active.as<uint32_t>(), ctx->d_counters + 4));
+    uint32_t A = 0;
+    DBG_TRY(read_small(ctx, ctx->d_counters + 4, sizeof(uint32_t), &A));
+    if (A > 0) {
+      uint32_t left = 0;
+      DBG_TRY(jump_until_stable(ctx, active.as<uint32_t>(), A, word.as<uint64_t>(), &left));
+      if (left > 0) {
+        have_cycles = true;
+        DBG_TRY(alloc_buf(ctx, cycl, (uint64_t)A * 4));
+        DBG_TRY(alloc_buf(ctx, lab, n1 * 8));
+        DBG_TRY(alloc_buf(ctx, cyc, n1));
+        DBG_CUDA_TRY(cudaMemsetAsync(cyc.p, 0, n, s));
+        DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 5, 0, sizeof(uint32_t), s));
+        DBG_LAUNCH(ctx, ST_COMPACT_CYCLES, 24.0 * A,
+                   k_collect_cycles<<<grid_of(A), 256, 0, s>>>(active.as<uint32_t>(), A, word.as<uint64_t>(),
+                                                               pred.as<uint32_t>(), cycl.as<uint32_t>(),
+                                                               lab.as<uint64_t>(), ctx->d_counters + 5));
+        uint32_t C = 0;
+        DBG_TRY(read_small(ctx, ctx->d_counters + 5, sizeof(uint32_t), &C));
+        int R = 2;
+        while ((1ull << (R - 2)) < C) R++;
+        for (int r = 0; r < R; r++)
+          DBG_LAUNCH(ctx, ST_COMPACT_CYCLES, 20.0 * C,
+                     k_cycle_min<<<grid_of(C), 256, 0, s>>>(cycl.as<uint32_t>(), C, lab.as<uint64_t>()));
+        DBG_LAUNCH(ctx, ST_COMPACT_CYCLES, 25.0 * C,
+                   k_cycle_break<<<grid_of(C), 256, 0, s>>>(cycl.as<uint32_t>(), C, lab.as<uint64_t>(),
+                                                            pred.as<uint32_t>(), cyc.as<uint8_t>(),
+                                                            word.as<uint64_t>()));
+        DBG_CUDA_TRY(cudaGetLastError());
+        uint32_t still = 0;
+        DBG_TRY(jump_until_stable(ctx, cycl.as<uint32_t>(), C, word.as<uint64_t>(), &still));
+        if (still != 0) {
+          set_error("%u strand-nodes stayed on cycles after they were opened", still);
+          return DBG_ECUDA;
+        }
       }
-      DBG_LAUNCH(ctx, ST_COMPACT_CYCLES, 18.0 * n,
-                 k_cycle_break<<<grid_of(n), 256, 0, s>>>(pred.as<uint32_t>(), m, oncyc.as<uint8_t>(), n, cyc.as<uint8_t>(), p,
-                                               d));
-      DBG_CUDA_TRY(cudaGetLastError());
-      // rank the opened cycles (the other strand-nodes are already final)
-      DBG_TRY(rank_lists(ctx, &p, &d, &p2, &d2, n, oncyc.as<uint8_t>(), &rounds));
-    } else {
-      DBG_CUDA_TRY(cudaMemsetAsync(cyc.p, 0, n, s));
     }
-    label.release();
+    active.release();
+    cycl.release();
+    lab.release();
     DBG_TRY(alloc_buf(ctx, strand, V1));
     DBG_TRY(alloc_buf(ctx, head, V1 * 4));
     DBG_TRY(alloc_buf(ctx, rank, V1 * 4));
     DBG_TRY(alloc_buf(ctx, is_head, V1 * 4));
-    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 16.0 * n + 13.0 * V,
-               k_select<K><<<grid_of(V), 256, 0, s>>>(p, d, cyc.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
-                                           strand.as<uint8_t>(), head.as<uint32_t>(), rank.as<uint32_t>(),
-                                           is_head.as<uint32_t>()));
+    DBG_TRY(alloc_buf(ctx, len_at_head, V1 * 4));
+    DBG_CUDA_TRY(cudaMemsetAsync(len_at_head.p, 0, V1 * 4, s));
+    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 16.0 * n + 8.0 * V + 17.0 * V,
+               k_select<K><<<grid_of(V), 256, 0, s>>>(word.as<uint64_t>(), succ.as<uint32_t>(),
+                                                      have_cycles ? cyc.as<uint8_t>() : nullptr,
+                                                      g->node_keys.as<uint64_t>(), V, k, strand.as<uint8_t>(),
+                                                      head.as<uint32_t>(), rank.as<uint32_t>(),
+                                                      is_head.as<uint32_t>(), len_at_head.as<uint32_t>()));
     DBG_CUDA_TRY(cudaGetLastError());
+    word.release();
+    succ.release();
+    pred.release();
     DBG_TRY(alloc_buf(ctx, uidx, (V + 1) * 8));
-    uint32_t U32;
+    DBG_TRY(alloc_buf(ctx, off_by_v, (V + 1) * 8));
+    uint32_t U32 = 0, total = 0;
     DBG_TRY(scan_excl(ctx, is_head.as<uint32_t>(), V, uidx.as<uint64_t>(), &U32));
+    DBG_TRY(scan_excl(ctx, len_at_head.as<uint32_t>(), V, off_by_v.as<uint64_t>(), &total));
+    if (total != V) {
+      set_error("unitigs hold %u nodes, expected %llu", total, (unsigned long long)V);
+      return DBG_ECUDA;
+    }
     U = U32;
   }
   u->count = U;
@@ -431,25 +476,17 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
   u->total_bases = V + U * (uint64_t)(k - 1);
   DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
   if (V > 0) {
-    DBG_TRY(alloc_buf(ctx, len, U1 * 4));
-    DBG_CUDA_TRY(cudaMemsetAsync(len.p, 0, U1 * 4, s));
-    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 13.0 * V,
-               k_unitig_len<<<grid_of(V), 256, 0, s>>>(head.as<uint32_t>(), uidx.as<uint64_t>(), V, U, len.as<uint32_t>(),
-                                            u->circular.as<uint8_t>(), cyc.as<uint8_t>(), strand.as<uint8_t>(),
-                                            ctx->d_err));
-    uint32_t tot;
-    DBG_TRY(scan_excl(ctx, len.as<uint32_t>(), U, u->node_off.as<uint64_t>(), &tot));
-    if (tot != V) {
-      set_error("unitigs hold %u nodes, expected %llu", tot, (unsigned long long)V);
-      return DBG_ECUDA;
-    }
-    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 16.0 * U,
-               k_seq_off<<<grid_of(U + 1), 256, 0, s>>>(u->node_off.as<uint64_t>(), U, k, u->seq_off.as<uint64_t>()));
-    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)V * (4 + 4 + 1 + 8 + 8 + 8 * g->key_words + 8 + 1) + (double)U * k,
-               k_unitig_write<K><<<grid_of(V), 256, 0, s>>>(head.as<uint32_t>(), rank.as<uint32_t>(), strand.as<uint8_t>(),
-                                                 uidx.as<uint64_t>(), u->node_off.as<uint64_t>(),
-                                                 g->node_keys.as<uint64_t>(), V, k, u->nodes.as<uint64_t>(),
-                                                 u->seq.as<char>(), ctx->d_err));
+    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 4.0 * V + 16.0 * U * 3,
+               k_unitig_offsets<<<grid_of(V + 1), 256, 0, s>>>(
+                   is_head.as<uint32_t>(), uidx.as<uint64_t>(), off_by_v.as<uint64_t>(),
+                   have_cycles ? cyc.as<uint8_t>() : nullptr, strand.as<uint8_t>(), V, U, k,
+                   u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(), u->circular.as<uint8_t>()));
+    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT,
+               (double)V * (4 + 4 + 1 + 8 + 8 + 4 + 8 * g->key_words + 8 + 1) + (double)U * k,
+               k_unitig_write<K><<<grid_of(V), 256, 0, s>>>(
+                   head.as<uint32_t>(), rank.as<uint32_t>(), strand.as<uint8_t>(), uidx.as<uint64_t>(),
+                   off_by_v.as<uint64_t>(), len_at_head.as<uint32_t>(), g->node_keys.as<uint64_t>(), V, k,
+                   u->nodes.as<uint64_t>(), u->seq.as<char>(), ctx->d_err));
     DBG_CUDA_TRY(cudaGetLastError());
   } else {
     DBG_CUDA_TRY(cudaMemsetAsync(u->node_off.p, 0, 8, s));
