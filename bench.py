@@ -262,6 +262,8 @@ def run_ours(args):
         u.free()
         g.free()
 
+    tune_ms = dbg.dbg_autotune(ctx)
+    variants = {kd: dbg.dbg_sort_variant_name(kd, dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(4)}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -347,7 +349,9 @@ def run_ours(args):
             "config": {"workload": wl, "edge_instances": N, "reads": int(len(lengths)), "k": k,
                        "nodes": info.get("nodes"), "edges": info.get("edges"), "unitigs": info.get("unitigs"),
                        "l2": "inputs and sort buffers far larger than L2 (1.5 GB reads, 8.3 GB keys)",
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}",
+                       "sort_variants": variants,
+                       "autotune_pass_ms": {kd: [round(x, 4) for x in v] for kd, v in tune_ms.items()}},
             "roofline": {"bound": "hbm", "kernel": "k_onesweep (edge keys, one 8-bit digit pass)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "peak_kind": peak_kind,

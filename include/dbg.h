@@ -78,8 +78,8 @@ typedef struct dbg_options {
   void *alloc_user;
   uint64_t mem_budget;     /* bytes a request may hold on the device; 0 = no limit */
   uint32_t spin_limit;     /* iterations a device wait may spin before DBG_ETIMEOUT; 0 = default */
-  uint32_t sort_block;     /* radix sort tile shape, 0 = tuned default */
-  uint32_t sort_items;
+  uint32_t reserved0;      /* must be 0 */
+  uint32_t reserved1;      /* must be 0 */
   uint32_t reserved[8];
 } dbg_options;
 
@@ -204,6 +204,26 @@ void dbg_unitigs_free(dbg_unitigs *u);
  * -------------------------------------------------------------------- */
 dbg_status dbg_rle_u64_noalloc(const uint64_t *keys, uint64_t n, uint64_t *uniq, uint32_t *run_start,
                                uint64_t *count, void *stream);
+
+/* ----------------------------------------------------------------------
+ * Radix sort variants and the autotuner.  The onesweep sort of STEP-2/3 is
+ * compiled in several configurations per key kind (tile shape, TMA or
+ * register loads, ballot / atomicOr / match.any ranking); all sort
+ * identically.  Kinds: 0 = 64-bit keys, 1 = 64-bit keys + 32-bit payload,
+ * 2 = 128-bit keys, 3 = 128-bit keys + payload.  A context starts with
+ * variant 0 of every kind.
+ * dbg_autotune times one digit pass of every variant on n synthetic keys
+ * (0 = 2^25; 128-bit kinds use n / 2) and keeps the fastest of each kind in
+ * the context.  cache_path (may be NULL) names a text file of choices keyed
+ * by GPU name and SM count: a matching line is used instead of timing, and
+ * a new result is appended.  ms_out (may be NULL) receives 4 x 16 pass
+ * times in ms (kind-major).
+ * -------------------------------------------------------------------- */
+uint32_t dbg_sort_variant_count(uint32_t kind);
+const char *dbg_sort_variant_name(uint32_t kind, uint32_t variant);
+dbg_status dbg_sort_variant_set(dbg_ctx *ctx, uint32_t kind, uint32_t variant);
+int32_t dbg_sort_variant_get(const dbg_ctx *ctx, uint32_t kind);
+dbg_status dbg_autotune(dbg_ctx *ctx, uint64_t n, const char *cache_path, double *ms_out);
 
 /* ----------------------------------------------------------------------
  * Profiling (tracing).  When enabled, the context brackets every kernel it

@@ -458,4 +458,100 @@ void dbg_graph_free(dbg_graph *g) {
   delete g;  // DevBuf destructors release in stream order
 }
 
+static const char *variant_name_of(uint32_t kind, uint32_t v, uint32_t *count) {
+  *count = 0;
+  switch (kind) {
+    case 0: return sort_variant_name_u64(false, v, count);
+    case 1: return sort_variant_name_u64(true, v, count);
+    case 2: return sort_variant_name_u128(false, v, count);
+    case 3: return sort_variant_name_u128(true, v, count);
+    default: return nullptr;
+  }
+}
+
+uint32_t dbg_sort_variant_count(uint32_t kind) {
+  uint32_t c = 0;
+  variant_name_of(kind, 0, &c);
+  return c;
+}
+
+const char *dbg_sort_variant_name(uint32_t kind, uint32_t variant) {
+  uint32_t c = 0;
+  return variant_name_of(kind, variant, &c);
+}
+
+dbg_status dbg_sort_variant_set(dbg_ctx *ctx, uint32_t kind, uint32_t variant) {
+  if (!ctx || kind > 3 || variant >= dbg_sort_variant_count(kind)) {
+    set_error("bad sort variant %u of kind %u", variant, kind);
+    return DBG_EINVAL;
+  }
+  ctx->sort_variant[kind] = (int)variant;
+  return DBG_OK;
+}
+
+int32_t dbg_sort_variant_get(const dbg_ctx *ctx, uint32_t kind) {
+  return (ctx && kind <= 3) ? ctx->sort_variant[kind] : -1;
+}
+
+// cache line format: "<gpu name>|<SMs>" v0 v1 v2 v3
+static std::string tune_cache_key(int device) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string name = prop.name;
+  for (char &c : name)
+    if (c == ' ') c = '_';
+  return name + "|" + std::to_string(prop.multiProcessorCount);
+}
+
+static bool tune_cache_load(const char *path, const std::string &key, int out[4]) {
+  FILE *f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    char k[400];
+    int v[4];
+    if (std::sscanf(line, "%399s %d %d %d %d", k, &v[0], &v[1], &v[2], &v[3]) == 5 && key == k) {
+      for (int i = 0; i < 4; i++) out[i] = v[i];
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+static void tune_cache_store(const char *path, const std::string &key, const int v[4]) {
+  FILE *f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3]);
+  std::fclose(f);
+}
+
+dbg_status dbg_autotune(dbg_ctx *ctx, uint64_t n, const char *cache_path, double *ms_out) {
+  if (!ctx) return DBG_EINVAL;
+  DeviceScope scope(ctx->device);
+  const std::string key = tune_cache_key(ctx->device);
+  int cached[4];
+  if (cache_path && tune_cache_load(cache_path, key, cached)) {
+    bool ok = true;
+    for (uint32_t kd = 0; kd < 4; kd++) ok = ok && cached[kd] >= 0 && (uint32_t)cached[kd] < dbg_sort_variant_count(kd);
+    if (ok) {
+      for (int kd = 0; kd < 4; kd++) ctx->sort_variant[kd] = cached[kd];
+      return DBG_OK;
+    }
+  }
+  if (n == 0) n = 1ull << 25;
+  double *m = ms_out;
+  dbg_status st = autotune_u64(ctx, n, m ? m : nullptr, m ? m + 16 : nullptr);
+  if (st == DBG_OK) st = autotune_u128(ctx, n / 2, m ? m + 32 : nullptr, m ? m + 48 : nullptr);
+  cudaStreamSynchronize(ctx->stream);
+  prof_resolve(ctx);
+  if (st != DBG_OK) return st;
+  if (cache_path) tune_cache_store(cache_path, key, ctx->sort_variant);
+  return DBG_OK;
+}
+
 }  // extern "C"

@@ -11,18 +11,101 @@ namespace dbg {
 
 inline int passes_for_bits(int bits) { return (bits + RADIX_BITS - 1) / RADIX_BITS; }
 
-// Tile shape of the onesweep kernel for each key width; the shared-memory
-// staging area holds one tile of keys (and payloads).
-template <class K, bool HAS_VAL> struct SortCfg;
-template <> struct SortCfg<uint64_t, false> { static constexpr int BLOCK = 256, ITEMS = 16; };
-template <> struct SortCfg<uint64_t, true> { static constexpr int BLOCK = 256, ITEMS = 12; };
-template <> struct SortCfg<Key128, false> { static constexpr int BLOCK = 256, ITEMS = 8; };
-template <> struct SortCfg<Key128, true> { static constexpr int BLOCK = 256, ITEMS = 8; };
+// ---------------------------------------------------------------------------
+// Radix sort variants.  Every compiled onesweep configuration of a key kind
+// sorts identically; they differ in tile shape, load path and ranking
+// method.  The context keeps one choice per kind (default, set by the
+// caller, or picked by dbg_autotune).
+// ---------------------------------------------------------------------------
+using SortLaunchFn = void (*)(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *vin, uint32_t *vout,
+                              uint64_t n, int shift, const uint64_t *digit_base, uint32_t epoch);
 
-template <class K, bool HAS_VAL>
-constexpr size_t sort_smem_bytes() {
-  constexpr int TILE = SortCfg<K, HAS_VAL>::BLOCK * SortCfg<K, HAS_VAL>::ITEMS;
-  return (size_t)TILE * sizeof(K) + (HAS_VAL ? (size_t)TILE * sizeof(uint32_t) : 0);
+struct SortVariant {
+  const char *name;
+  int tile;
+  SortLaunchFn launch;
+};
+
+template <class K, bool V, int BLOCK, int ITEMS, int RANK, bool TMA, int MINB>
+void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *vin, uint32_t *vout, uint64_t n,
+                     int shift, const uint64_t *digit_base, uint32_t epoch) {
+  auto kern = k_onesweep<K, V, BLOCK, ITEMS, RANK, TMA, MINB>;
+  constexpr size_t smem = sizeof(OnesweepSmem<K, V, BLOCK, ITEMS>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint64_t tiles = (n + BLOCK * ITEMS - 1) / (BLOCK * ITEMS);
+  kern<<<(unsigned)tiles, BLOCK, smem, ctx->stream>>>(static_cast<const K *>(kin), static_cast<K *>(kout), vin,
+                                                      vout, n, shift, digit_base, ctx->d_status, ctx->d_counters,
+                                                      epoch, ctx->spin_limit, ctx->d_err);
+}
+
+#define DBG_SV(K, V, B, I, R, T, M, NAME) \
+  SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M> }
+
+// kinds: 0 = 64-bit keys, 1 = 64-bit keys + payload, 2 = 128-bit keys,
+// 3 = 128-bit keys + payload
+template <class K, bool V> struct SortKind;
+template <> struct SortKind<uint64_t, false> {
+  static constexpr int kind = 0;
+  static const SortVariant *table(int *count) {
+    static const SortVariant t[] = {
+        DBG_SV(uint64_t, false, 256, 16, RANK_BALLOT, false, 1, "256x16 ballot ldg"),
+        DBG_SV(uint64_t, false, 256, 16, RANK_MATCH, false, 1, "256x16 match ldg"),
+        DBG_SV(uint64_t, false, 256, 16, RANK_MATCH, true, 1, "256x16 match tma"),
+        DBG_SV(uint64_t, false, 256, 12, RANK_MATCH, true, 3, "256x12 match tma occ3"),
+        DBG_SV(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, "256x12 atomic tma occ3"),
+        DBG_SV(uint64_t, false, 256, 8, RANK_MATCH, true, 4, "256x8 match tma occ4"),
+        DBG_SV(uint64_t, false, 512, 8, RANK_MATCH, true, 2, "512x8 match tma occ2"),
+    };
+    *count = sizeof(t) / sizeof(t[0]);
+    return t;
+  }
+};
+template <> struct SortKind<uint64_t, true> {
+  static constexpr int kind = 1;
+  static const SortVariant *table(int *count) {
+    static const SortVariant t[] = {
+        DBG_SV(uint64_t, true, 256, 12, RANK_BALLOT, false, 1, "256x12 ballot ldg"),
+        DBG_SV(uint64_t, true, 256, 12, RANK_MATCH, true, 1, "256x12 match tma"),
+        DBG_SV(uint64_t, true, 256, 8, RANK_MATCH, true, 3, "256x8 match tma occ3"),
+        DBG_SV(uint64_t, true, 256, 8, RANK_ATOMIC, true, 3, "256x8 atomic tma occ3"),
+    };
+    *count = sizeof(t) / sizeof(t[0]);
+    return t;
+  }
+};
+template <> struct SortKind<Key128, false> {
+  static constexpr int kind = 2;
+  static const SortVariant *table(int *count) {
+    static const SortVariant t[] = {
+        DBG_SV(Key128, false, 256, 8, RANK_BALLOT, false, 1, "256x8 ballot ldg"),
+        DBG_SV(Key128, false, 256, 8, RANK_MATCH, true, 1, "256x8 match tma"),
+        DBG_SV(Key128, false, 256, 6, RANK_MATCH, true, 3, "256x6 match tma occ3"),
+    };
+    *count = sizeof(t) / sizeof(t[0]);
+    return t;
+  }
+};
+template <> struct SortKind<Key128, true> {
+  static constexpr int kind = 3;
+  static const SortVariant *table(int *count) {
+    static const SortVariant t[] = {
+        DBG_SV(Key128, true, 256, 8, RANK_BALLOT, false, 1, "256x8 ballot ldg"),
+        DBG_SV(Key128, true, 256, 8, RANK_MATCH, true, 1, "256x8 match tma"),
+        DBG_SV(Key128, true, 256, 6, RANK_MATCH, true, 3, "256x6 match tma occ3"),
+    };
+    *count = sizeof(t) / sizeof(t[0]);
+    return t;
+  }
+};
+#undef DBG_SV
+
+template <class K, bool V>
+const SortVariant &chosen_variant(dbg_ctx *ctx) {
+  int count = 0;
+  const SortVariant *t = SortKind<K, V>::table(&count);
+  int v = ctx->sort_variant[SortKind<K, V>::kind];
+  if (v < 0 || v >= count) v = 0;
+  return t[v];
 }
 
 // Ascending LSD radix sort of n keys (with optional u32 payloads) whose
@@ -34,30 +117,22 @@ template <class K, bool HAS_VAL>
 dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uint32_t **alt_vals, uint64_t n,
                       int bits, const unsigned long long *d_hist, uint64_t *d_digit_base) {
   if (n <= 1) return DBG_OK;
-  using C = SortCfg<K, HAS_VAL>;
-  constexpr int TILE = C::BLOCK * C::ITEMS;
+  const SortVariant &sv = chosen_variant<K, HAS_VAL>(ctx);
   const int passes = passes_for_bits(bits);
-  const uint64_t tiles = (n + TILE - 1) / TILE;
+  const uint64_t tiles = (n + sv.tile - 1) / sv.tile;
   if (tiles > 0x7fffffffull) return DBG_EOVERFLOW;
   DBG_TRY(ensure_status(ctx, (size_t)tiles * RADIX));
   cudaStream_t s = ctx->stream;
-  {
-    DBG_LAUNCH(ctx, HAS_VAL ? ST_SORT_NODES : ST_SORT_EDGES, 0.0,
-               k_digit_base<<<passes, RADIX, 0, s>>>(d_hist, d_digit_base));
-  }
-  auto kern = k_onesweep<K, HAS_VAL, C::BLOCK, C::ITEMS>;
-  constexpr size_t smem = sort_smem_bytes<K, HAS_VAL>();
-  DBG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DBG_LAUNCH(ctx, HAS_VAL ? ST_SORT_NODES : ST_SORT_EDGES, 0.0,
+             k_digit_base<<<passes, RADIX, 0, s>>>(d_hist, d_digit_base));
   for (int p = 0; p < passes; p++) {
     uint32_t epoch;
     DBG_TRY(next_epoch(ctx, &epoch));
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), s));
-    Span sp(ctx, HAS_VAL ? ST_SORT_NODES : ST_SORT_EDGES,
-            2.0 * (double)n * (double)(sizeof(K) + (HAS_VAL ? sizeof(uint32_t) : 0)));
-    kern<<<(unsigned)tiles, C::BLOCK, smem, s>>>(*keys, *alt_keys, HAS_VAL ? *vals : nullptr,
-                                                 HAS_VAL ? *alt_vals : nullptr, n, p * RADIX_BITS,
-                                                 d_digit_base + p * RADIX, ctx->d_status, ctx->d_counters,
-                                                 epoch, ctx->spin_limit, ctx->d_err);
+    DBG_LAUNCH(ctx, HAS_VAL ? ST_SORT_NODES : ST_SORT_EDGES,
+               2.0 * (double)n * (double)(sizeof(K) + (HAS_VAL ? sizeof(uint32_t) : 0)),
+               sv.launch(ctx, *keys, *alt_keys, HAS_VAL ? *vals : nullptr, HAS_VAL ? *alt_vals : nullptr, n,
+                         p * RADIX_BITS, d_digit_base + p * RADIX, epoch));
     std::swap(*keys, *alt_keys);
     if (HAS_VAL) std::swap(*vals, *alt_vals);
   }
@@ -265,6 +340,114 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   }
   DBG_CUDA_TRY(cudaStreamSynchronize(s));
   return check_device_error(ctx);
+}
+
+}  // namespace dbg
+
+namespace dbg {
+
+// ---------------------------------------------------------------------------
+// Autotuner: times one digit pass of every variant of a key kind on n
+// synthetic keys (a counter-based hash of the index, so all digits vary) and
+// keeps the fastest.  ms_out[v] receives each variant's pass time.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t tune_hash(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+template <class K>
+__global__ void k_tune_fill(K *keys, uint32_t *vals, uint64_t n) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    K k;
+    if constexpr (sizeof(K) == 8) {
+      k = tune_hash(i);
+    } else {
+      k = Key128{tune_hash(2 * i), tune_hash(2 * i + 1)};
+    }
+    keys[i] = k;
+    if (vals) vals[i] = (uint32_t)i;
+  }
+}
+
+// digit histogram of one 8-bit digit position of arbitrary keys
+template <class K>
+__global__ void k_tune_hist(const K *keys, uint64_t n, int shift, unsigned long long *hist) {
+  __shared__ uint32_t h[RADIX];
+  for (int i = threadIdx.x; i < RADIX; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[KeyOps<K>::digit(keys[i], shift, RADIX_BITS)], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < RADIX; i += blockDim.x)
+    if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
+}
+
+template <class K, bool V>
+dbg_status autotune_kind(dbg_ctx *ctx, uint64_t n, double *ms_out) {
+  cudaStream_t s = ctx->stream;
+  int count = 0;
+  const SortVariant *t = SortKind<K, V>::table(&count);
+  DevBuf ka, kb, va, vb, small;
+  DBG_TRY(alloc_buf(ctx, ka, n * sizeof(K)));
+  DBG_TRY(alloc_buf(ctx, kb, n * sizeof(K)));
+  if (V) {
+    DBG_TRY(alloc_buf(ctx, va, n * 4));
+    DBG_TRY(alloc_buf(ctx, vb, n * 4));
+  }
+  DBG_TRY(alloc_buf(ctx, small, RADIX * 16));
+  unsigned long long *hist = small.as<unsigned long long>();
+  uint64_t *dbase = reinterpret_cast<uint64_t *>(hist + RADIX);
+  k_tune_fill<K><<<1024, 256, 0, s>>>(ka.as<K>(), V ? va.as<uint32_t>() : nullptr, n);
+  DBG_CUDA_TRY(cudaMemsetAsync(hist, 0, RADIX * 8, s));
+  k_tune_hist<K><<<1024, 256, 0, s>>>(ka.as<K>(), n, 8, hist);
+  k_digit_base<<<1, RADIX, 0, s>>>(hist, dbase);
+  int min_tile = t[0].tile;
+  for (int v = 0; v < count; v++) min_tile = std::min(min_tile, t[v].tile);
+  DBG_TRY(ensure_status(ctx, ((n + min_tile - 1) / min_tile) * RADIX));
+  cudaEvent_t e0, e1;
+  DBG_CUDA_TRY(cudaEventCreate(&e0));
+  DBG_CUDA_TRY(cudaEventCreate(&e1));
+  int best = 0;
+  double best_ms = 1e30;
+  for (int v = 0; v < count; v++) {
+    float total = 0.f;
+    for (int rep = 0; rep < 4; rep++) {
+      uint32_t epoch;
+      DBG_TRY(next_epoch(ctx, &epoch));
+      DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), s));
+      cudaEventRecord(e0, s);
+      t[v].launch(ctx, ka.p, kb.p, V ? va.as<uint32_t>() : nullptr, V ? vb.as<uint32_t>() : nullptr, n, 8, dbase,
+                  epoch);
+      cudaEventRecord(e1, s);
+      DBG_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) total += ms;  // the first launch is a warm-up
+    }
+    const double ms = total / 3.0;
+    if (ms_out) ms_out[v] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  DBG_CUDA_TRY(cudaGetLastError());
+  DBG_TRY(check_device_error(ctx));
+  ctx->sort_variant[SortKind<K, V>::kind] = best;
+  return DBG_OK;
+}
+
+template <class K, bool V>
+const char *variant_name(uint32_t v, uint32_t *count) {
+  int c = 0;
+  const SortVariant *t = SortKind<K, V>::table(&c);
+  *count = (uint32_t)c;
+  return v < (uint32_t)c ? t[v].name : nullptr;
 }
 
 }  // namespace dbg

@@ -64,12 +64,6 @@ struct ProfRecord {
   uint32_t launches;
 };
 
-// Radix sort tile shape.
-struct SortShape {
-  int block = 256;
-  int items = 16;
-};
-
 }  // namespace dbg
 
 struct dbg_ctx {
@@ -79,7 +73,7 @@ struct dbg_ctx {
   dbg::Allocator al;
   uint64_t mem_budget = 0;
   uint32_t spin_limit = 1u << 22;
-  dbg::SortShape shape;
+  int sort_variant[4] = {0, 0, 0, 0};  // per key kind (0: u64, 1: u64+payload, 2: u128, 3: u128+payload)
   int num_sms = 0;
   // persistent scratch: the look-back status words of every scan and sort
   // pass, tagged by epoch so they never need clearing between uses
@@ -176,6 +170,10 @@ struct BuildInput {
 };
 
 dbg_status build_graph_u64(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g);
+dbg_status autotune_u64(dbg_ctx *ctx, uint64_t n, double *ms_keys, double *ms_pairs);
+dbg_status autotune_u128(dbg_ctx *ctx, uint64_t n, double *ms_keys, double *ms_pairs);
+const char *sort_variant_name_u64(bool pairs, uint32_t v, uint32_t *count);
+const char *sort_variant_name_u128(bool pairs, uint32_t v, uint32_t *count);
 dbg_status build_graph_u128(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g);
 
 }  // namespace dbg

@@ -310,53 +310,140 @@ static __global__ void k_digit_base(const unsigned long long *__restrict__ hist,
 }
 
 // ---------------------------------------------------------------------------
-// K3 onesweep radix pass (Adinets & Merrill): one launch per 8-bit digit.
-// Tiles are taken in launch order from an atomic ticket, so every tile that
-// a tile waits for is already running.  Per tile:
-//   1. load keys warp-striped (coalesced), rank each key among equal digits
-//      of its warp (stable: item order, then lane order) with a ballot-based
-//      match and warp-private shared-memory digit counters;
-//   2. publish the tile's per-digit counts, look back over predecessor tiles
-//      for the exclusive prefix of each digit, publish the inclusive prefix;
-//   3. stage the keys in shared memory in digit order and write each digit's
-//      run to digit_base[d] + prefix (contiguous, coalesced writes).
+// TMA bulk copies and mbarriers (inline PTX)
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// generic-proxy writes to shared memory before an async-proxy (TMA) write
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// one bulk copy global -> shared, completing `bytes` on the mbarrier
+__device__ __forceinline__ void tma_load_bulk(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// bounded wait on an mbarrier phase; false when the limit was reached
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t spin_limit) {
+  for (uint32_t i = 0; i <= spin_limit; i++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// K3 onesweep radix pass (Adinets & Merrill): one launch per 8-bit digit,
+// one CTA per tile.  Tiles are taken in launch order from an atomic ticket,
+// so every tile a tile waits for belongs to a CTA that is already running.
+// Per tile:
+//   1. load the keys (and payloads) -- LOAD_TMA: one TMA bulk copy into
+//      shared memory completing on an mbarrier; else warp-striped coalesced
+//      loads -- and rank each key among the equal digits of its warp, stably
+//      (item order, then lane order), with warp-private digit counters.  The
+//      peer lanes holding the same digit come from RANK_BALLOT (one ballot
+//      per digit bit), RANK_ATOMIC (shared-memory atomicOr of lane bits) or
+//      RANK_MATCH (the hardware match.any instruction);
+//   2. publish the tile's per-digit counts, look back over predecessor tiles
+//      for each digit's exclusive prefix, publish the inclusive prefix;
+//   3. stage the keys in shared memory in digit order and write each digit's
+//      run to digit_base[d] + prefix (contiguous, coalesced).
+// ---------------------------------------------------------------------------
+enum : int { RANK_BALLOT = 0, RANK_ATOMIC = 1, RANK_MATCH = 2 };
+
 template <class K, bool HAS_VAL, int BLOCK, int ITEMS>
-__global__ __launch_bounds__(BLOCK) void k_onesweep(const K *__restrict__ kin, K *__restrict__ kout,
-                                                    const uint32_t *__restrict__ vin,
-                                                    uint32_t *__restrict__ vout, uint64_t n, int shift,
-                                                    const uint64_t *__restrict__ digit_base,
-                                                    uint64_t *__restrict__ status, uint32_t *ticket,
-                                                    uint32_t epoch, uint32_t spin_limit, uint32_t *err) {
-  constexpr int WARPS = BLOCK / 32;
-  constexpr int TILE = BLOCK * ITEMS;
+struct OnesweepSmem {
+  static constexpr int WARPS = BLOCK / 32;
+  static constexpr int TILE = BLOCK * ITEMS;
+  K keys[TILE];
+  uint32_t vals[HAS_VAL ? TILE : 1];
+  uint32_t whist[WARPS][RADIX];
+  uint32_t match[WARPS][RADIX + 1];
+  uint32_t tile_start[RADIX];
+  uint64_t gbase[RADIX];
+  uint64_t bar;
+  uint32_t tmp[8];
+  uint32_t tile;
+};
+
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, bool LOAD_TMA, int MIN_BLOCKS>
+__global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
+    const K *__restrict__ kin, K *__restrict__ kout, const uint32_t *__restrict__ vin, uint32_t *__restrict__ vout,
+    uint64_t n, int shift, const uint64_t *__restrict__ digit_base, uint64_t *__restrict__ status,
+    uint32_t *ticket, uint32_t epoch, uint32_t spin_limit, uint32_t *err) {
+  using S = OnesweepSmem<K, HAS_VAL, BLOCK, ITEMS>;
+  constexpr int WARPS = S::WARPS;
+  constexpr int TILE = S::TILE;
   static_assert(BLOCK >= RADIX, "one thread per digit");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  K *s_keys = reinterpret_cast<K *>(smem_raw);
-  uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + TILE);
-  __shared__ uint32_t s_whist[WARPS][RADIX];
-  __shared__ uint32_t s_tile_start[RADIX];
-  __shared__ uint64_t s_gbase[RADIX];
-  __shared__ uint32_t s_tmp[8];
-  __shared__ uint32_t s_tile;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  S &sm = *reinterpret_cast<S *>(smem_raw);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < WARPS * RADIX; i += BLOCK) (&s_whist[0][0])[i] = 0;
-  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+  for (int i = tid; i < WARPS * RADIX; i += BLOCK) (&sm.whist[0][0])[i] = 0;
+  if (RANK == RANK_ATOMIC)
+    for (int i = tid; i < WARPS * (RADIX + 1); i += BLOCK) (&sm.match[0][0])[i] = 0;
+  if (tid == 0) {
+    sm.tile = atomicAdd(ticket, 1u);
+    if (LOAD_TMA) {
+      mbar_init(&sm.bar, 1);
+      mbar_init_fence();
+    }
+  }
   __syncthreads();
-  const uint32_t tile = s_tile;
+  const uint32_t tile = sm.tile;
   const uint64_t base = (uint64_t)tile * TILE;
-  const uint64_t wbase = base + (uint64_t)warp * 32 * ITEMS;
+  const uint32_t tile_n = (uint32_t)min((uint64_t)TILE, n - base);
+  // a full tile of 16-byte aligned data arrives by one bulk copy
+  const bool bulk = LOAD_TMA && tile_n == TILE &&
+                    ((reinterpret_cast<uintptr_t>(kin) | (HAS_VAL ? reinterpret_cast<uintptr_t>(vin) : 0)) & 15) == 0;
+  if (bulk) {
+    if (tid == 0) {
+      const uint32_t kb = TILE * sizeof(K), vb = HAS_VAL ? TILE * sizeof(uint32_t) : 0;
+      mbar_expect_tx(&sm.bar, kb + vb);
+      tma_load_bulk(sm.keys, kin + base, kb, &sm.bar);
+      if (HAS_VAL) tma_load_bulk(sm.vals, vin + base, vb, &sm.bar);
+    }
+    if (!__syncthreads_and(mbar_wait(&sm.bar, 0, spin_limit))) {
+      if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+      return;
+    }
+  }
 
+  const int wofs = warp * 32 * ITEMS;
   K key[ITEMS];
   uint32_t val[ITEMS];
   uint32_t rank[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; i++) {
-    const uint64_t idx = wbase + (uint64_t)i * 32 + lane;
-    if (idx < n) {
-      key[i] = kin[idx];
-      if (HAS_VAL) val[i] = vin[idx];
+    const uint32_t li = wofs + i * 32 + lane;
+    if (bulk) {
+      key[i] = sm.keys[li];
+      if (HAS_VAL) val[i] = sm.vals[li];
+    } else if (li < tile_n) {
+      key[i] = kin[base + li];
+      if (HAS_VAL) val[i] = vin[base + li];
     } else {
       key[i] = KeyOps<K>::zero();
       val[i] = 0;
@@ -365,21 +452,32 @@ __global__ __launch_bounds__(BLOCK) void k_onesweep(const K *__restrict__ kin, K
   const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < ITEMS; i++) {
-    const uint64_t idx = wbase + (uint64_t)i * 32 + lane;
-    // digit, with bit 8 set for slots past the end of the input
-    const uint32_t d = idx < n ? KeyOps<K>::digit(key[i], shift, RADIX_BITS) : (uint32_t)RADIX;
-    unsigned peers = 0xffffffffu;
+    const bool valid = (uint32_t)(wofs + i * 32 + lane) < tile_n;
+    // digit, or RADIX for slots past the end of the input
+    const uint32_t d = valid ? KeyOps<K>::digit(key[i], shift, RADIX_BITS) : (uint32_t)RADIX;
+    unsigned peers;
+    if (RANK == RANK_MATCH) {
+      peers = __match_any_sync(0xffffffffu, d);
+    } else if (RANK == RANK_ATOMIC) {
+      atomicOr(&sm.match[warp][d], 1u << lane);
+      __syncwarp();
+      peers = sm.match[warp][d];
+      __syncwarp();
+      if (lane == __ffs(peers) - 1) sm.match[warp][d] = 0;
+    } else {
+      peers = 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b <= RADIX_BITS; b++) {
-      const bool bit = (d >> b) & 1u;
-      const unsigned bal = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? bal : ~bal;
+      for (int bt = 0; bt <= RADIX_BITS; bt++) {
+        const bool bit = (d >> bt) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+      }
     }
     const int leader = __ffs(peers) - 1;
     uint32_t before = 0;
-    if (lane == leader && d < RADIX) {
-      before = s_whist[warp][d];
-      s_whist[warp][d] = before + __popc(peers);
+    if (lane == leader && valid) {
+      before = sm.whist[warp][d];
+      sm.whist[warp][d] = before + __popc(peers);
     }
     before = __shfl_sync(0xffffffffu, before, leader);
     rank[i] = before + __popc(peers & lt_mask);
@@ -389,48 +487,47 @@ __global__ __launch_bounds__(BLOCK) void k_onesweep(const K *__restrict__ kin, K
 
   uint32_t cnt = 0;
   if (tid < RADIX) {
+#pragma unroll
     for (int w = 0; w < WARPS; w++) {
-      const uint32_t c = s_whist[w][tid];
-      s_whist[w][tid] = cnt;
+      const uint32_t c = sm.whist[w][tid];
+      sm.whist[w][tid] = cnt;
       cnt += c;
     }
-    st_relaxed(status + (size_t)tile * RADIX + tid,
-               lb_word(epoch, tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE, cnt));
+    st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE, cnt));
   }
-  const uint32_t tstart = block_excl_scan_256(cnt, s_tmp);
+  const uint32_t tstart = block_excl_scan_256(cnt, sm.tmp);
   if (tid < RADIX) {
-    s_tile_start[tid] = tstart;
+    sm.tile_start[tid] = tstart;
     uint32_t excl = 0;
     if (tile > 0) {
       excl = lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
       st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, LB_INCLUSIVE, excl + cnt));
     }
-    s_gbase[tid] = digit_base[tid] + excl - tstart;
+    sm.gbase[tid] = digit_base[tid] + excl - tstart;
   }
   __syncthreads();
 
+  // stage in digit order (the tile's keys are all in registers now)
 #pragma unroll
   for (int i = 0; i < ITEMS; i++) {
-    const uint64_t idx = wbase + (uint64_t)i * 32 + lane;
-    if (idx < n) {
+    if ((uint32_t)(wofs + i * 32 + lane) < tile_n) {
       const uint32_t d = KeyOps<K>::digit(key[i], shift, RADIX_BITS);
-      const uint32_t p = s_tile_start[d] + s_whist[warp][d] + rank[i];
-      s_keys[p] = key[i];
-      if (HAS_VAL) s_vals[p] = val[i];
+      const uint32_t p = sm.tile_start[d] + sm.whist[warp][d] + rank[i];
+      sm.keys[p] = key[i];
+      if (HAS_VAL) sm.vals[p] = val[i];
     }
   }
   __syncthreads();
-  const uint32_t tile_n = (uint32_t)min((uint64_t)TILE, n - base);
   for (uint32_t j = tid; j < tile_n; j += BLOCK) {
-    const K kk = s_keys[j];
+    const K kk = sm.keys[j];
     const uint32_t d = KeyOps<K>::digit(kk, shift, RADIX_BITS);
-    const uint64_t dst = s_gbase[d] + j;
+    const uint64_t dst = sm.gbase[d] + j;
     if (dst >= n) {  // only reachable if the digit counts were inconsistent
       atomicOr(err, ERR_INTERNAL);
       continue;
     }
     kout[dst] = kk;
-    if (HAS_VAL) vout[dst] = s_vals[j];
+    if (HAS_VAL) vout[dst] = sm.vals[j];
   }
 }
 

@@ -33,8 +33,8 @@ class dbg_options(ctypes.Structure):
         ("alloc_user", ctypes.c_void_p),
         ("mem_budget", ctypes.c_uint64),
         ("spin_limit", ctypes.c_uint32),
-        ("sort_block", ctypes.c_uint32),
-        ("sort_items", ctypes.c_uint32),
+        ("reserved0", ctypes.c_uint32),
+        ("reserved1", ctypes.c_uint32),
         ("reserved", ctypes.c_uint32 * 8),
     ]
 
@@ -82,6 +82,11 @@ _SIGNATURES = [
     ("dbg_profile_read", ctypes.c_uint32, [_P, _P, ctypes.c_uint32]),
     ("dbg_launch_count", ctypes.c_uint64, [_P]),
     ("dbg_rle_u64_noalloc", ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("dbg_sort_variant_count", ctypes.c_uint32, [ctypes.c_uint32]),
+    ("dbg_sort_variant_name", ctypes.c_char_p, [ctypes.c_uint32, ctypes.c_uint32]),
+    ("dbg_sort_variant_set", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32]),
+    ("dbg_sort_variant_get", ctypes.c_int32, [_P, ctypes.c_uint32]),
+    ("dbg_autotune", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_char_p, _P]),
 ]
 
 _lib = None
@@ -369,3 +374,27 @@ def dbg_rle_u64_noalloc(keys, n: int, uniq, run_start, stream=None) -> int:
                                     ctypes.c_void_p(_ptr(run_start)[0]), ctypes.byref(count), ctypes.c_void_p(s)),
            "dbg_rle_u64_noalloc")
     return int(count.value)
+
+
+def dbg_sort_variant_count(kind: int) -> int:
+    return int(_lib.dbg_sort_variant_count(kind))
+
+
+def dbg_sort_variant_name(kind: int, variant: int) -> str:
+    r = _lib.dbg_sort_variant_name(kind, variant)
+    return r.decode() if r else ""
+
+
+def dbg_sort_variant_set(ctx: Context, kind: int, variant: int):
+    _check(_lib.dbg_sort_variant_set(ctx.handle, kind, variant), "dbg_sort_variant_set")
+
+
+def dbg_sort_variant_get(ctx: Context, kind: int) -> int:
+    return int(_lib.dbg_sort_variant_get(ctx.handle, kind))
+
+
+def dbg_autotune(ctx: Context, n: int = 0, cache_path: str | None = None) -> dict:
+    """Times every radix-sort variant; returns {kind: [ms per variant]}."""
+    ms = (ctypes.c_double * 64)()
+    _check(_lib.dbg_autotune(ctx.handle, n, cache_path.encode() if cache_path else None, ms), "dbg_autotune")
+    return {kd: [ms[kd * 16 + v] for v in range(dbg_sort_variant_count(kd))] for kd in range(4)}

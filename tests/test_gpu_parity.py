@@ -149,3 +149,40 @@ def test_repeat_calls_identical(dbg, ctx):
     for key in a:
         if isinstance(a[key], np.ndarray):
             np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_every_sort_variant_sorts_identically(dbg, ctx):
+    """Each compiled radix-sort configuration gives the oracle's graph."""
+    small64 = readgen.generate(readgen.ReadSetSpec(40_000, 3_000, 100, 0.01, 31, 41))
+    small128 = readgen.generate(readgen.ReadSetSpec(30_000, 1_500, 120, 0.01, 55, 42))
+    og64 = oracle.build_graph(*small64, 31)
+    og128 = oracle.build_graph(*small128, 55)
+    counts = [dbg.dbg_sort_variant_count(kd) for kd in range(4)]
+    from parity import assert_graph_equal
+    try:
+        for v in range(max(counts)):
+            for kd in range(4):
+                dbg.dbg_sort_variant_set(ctx, kd, min(v, counts[kd] - 1))
+            _, got = gpu_graph(dbg, ctx, *small64, 31)
+            assert_graph_equal(got, og64)
+            _, got = gpu_graph(dbg, ctx, *small128, 55)
+            assert_graph_equal(got, og128)
+    finally:
+        for kd in range(4):
+            dbg.dbg_sort_variant_set(ctx, kd, 0)
+
+
+def test_autotune_and_cache(dbg, tmp_path):
+    c = dbg.Context()
+    cache = str(tmp_path / "tune.txt")
+    ms = dbg.dbg_autotune(c, 1 << 20, cache)
+    chosen = [dbg.dbg_sort_variant_get(c, kd) for kd in range(4)]
+    for kd in range(4):
+        assert 0 <= chosen[kd] < dbg.dbg_sort_variant_count(kd)
+        assert all(t > 0 for t in ms[kd])
+        assert ms[kd][chosen[kd]] == min(ms[kd])
+    c2 = dbg.Context()
+    dbg.dbg_autotune(c2, 1 << 20, cache)  # answered from the cache file
+    assert [dbg.dbg_sort_variant_get(c2, kd) for kd in range(4)] == chosen
+    reads, lengths = readgen.generate(readgen.tiny_spec())
+    check_parity(dbg, c2, reads, lengths, 21)
