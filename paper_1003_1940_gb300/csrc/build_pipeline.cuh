@@ -11,6 +11,10 @@ namespace dbg {
 
 inline int passes_for_bits(int bits) { return (bits + RADIX_BITS - 1) / RADIX_BITS; }
 
+// items per thread of the build's run-length reduce and node-ID scans
+constexpr int BUILD_SCAN_ITEMS = 8;
+constexpr int BUILD_SCAN_TILE = SCAN_BLOCK * BUILD_SCAN_ITEMS;
+
 // ---------------------------------------------------------------------------
 // Radix sort variants.  Every compiled onesweep configuration of a key kind
 // sorts identically; they differ in tile shape, load path and ranking
@@ -26,10 +30,10 @@ struct SortVariant {
   SortLaunchFn launch;
 };
 
-template <class K, bool V, int BLOCK, int ITEMS, int RANK, bool TMA, int MINB>
+template <class K, bool V, int BLOCK, int ITEMS, int RANK, bool TMA, int MINB, bool EARLY>
 void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *vin, uint32_t *vout, uint64_t n,
                      int shift, const uint64_t *digit_base, uint32_t epoch) {
-  auto kern = k_onesweep<K, V, BLOCK, ITEMS, RANK, TMA, MINB>;
+  auto kern = k_onesweep<K, V, BLOCK, ITEMS, RANK, TMA, MINB, EARLY>;
   constexpr size_t smem = sizeof(OnesweepSmem<K, V, BLOCK, ITEMS>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const uint64_t tiles = (n + BLOCK * ITEMS - 1) / (BLOCK * ITEMS);
@@ -39,7 +43,9 @@ void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *
 }
 
 #define DBG_SV(K, V, B, I, R, T, M, NAME) \
-  SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M> }
+  SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, false> }
+#define DBG_SVE(K, V, B, I, R, T, M, NAME) \
+  SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, true> }
 
 // kinds: 0 = 64-bit keys, 1 = 64-bit keys + payload, 2 = 128-bit keys,
 // 3 = 128-bit keys + payload
@@ -55,6 +61,10 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SV(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, "256x12 atomic tma occ3"),
         DBG_SV(uint64_t, false, 256, 8, RANK_MATCH, true, 4, "256x8 match tma occ4"),
         DBG_SV(uint64_t, false, 512, 8, RANK_MATCH, true, 2, "512x8 match tma occ2"),
+        DBG_SVE(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, "256x12 atomic tma occ3 early"),
+        DBG_SVE(uint64_t, false, 256, 12, RANK_MATCH, true, 3, "256x12 match tma occ3 early"),
+        DBG_SVE(uint64_t, false, 256, 8, RANK_ATOMIC, true, 4, "256x8 atomic tma occ4 early"),
+        DBG_SVE(uint64_t, false, 256, 16, RANK_ATOMIC, true, 2, "256x16 atomic tma occ2 early"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -68,6 +78,8 @@ template <> struct SortKind<uint64_t, true> {
         DBG_SV(uint64_t, true, 256, 12, RANK_MATCH, true, 1, "256x12 match tma"),
         DBG_SV(uint64_t, true, 256, 8, RANK_MATCH, true, 3, "256x8 match tma occ3"),
         DBG_SV(uint64_t, true, 256, 8, RANK_ATOMIC, true, 3, "256x8 atomic tma occ3"),
+        DBG_SVE(uint64_t, true, 256, 8, RANK_ATOMIC, true, 3, "256x8 atomic tma occ3 early"),
+        DBG_SVE(uint64_t, true, 256, 12, RANK_ATOMIC, true, 2, "256x12 atomic tma occ2 early"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -80,6 +92,8 @@ template <> struct SortKind<Key128, false> {
         DBG_SV(Key128, false, 256, 8, RANK_BALLOT, false, 1, "256x8 ballot ldg"),
         DBG_SV(Key128, false, 256, 8, RANK_MATCH, true, 1, "256x8 match tma"),
         DBG_SV(Key128, false, 256, 6, RANK_MATCH, true, 3, "256x6 match tma occ3"),
+        DBG_SVE(Key128, false, 256, 6, RANK_ATOMIC, true, 3, "256x6 atomic tma occ3 early"),
+        DBG_SVE(Key128, false, 256, 8, RANK_ATOMIC, true, 2, "256x8 atomic tma occ2 early"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -92,12 +106,14 @@ template <> struct SortKind<Key128, true> {
         DBG_SV(Key128, true, 256, 8, RANK_BALLOT, false, 1, "256x8 ballot ldg"),
         DBG_SV(Key128, true, 256, 8, RANK_MATCH, true, 1, "256x8 match tma"),
         DBG_SV(Key128, true, 256, 6, RANK_MATCH, true, 3, "256x6 match tma occ3"),
+        DBG_SVE(Key128, true, 256, 6, RANK_ATOMIC, true, 3, "256x6 atomic tma occ3 early"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
   }
 };
 #undef DBG_SV
+#undef DBG_SVE
 
 template <class K, bool V>
 const SortVariant &chosen_variant(dbg_ctx *ctx) {
@@ -211,9 +227,9 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
     {
       DBG_LAUNCH(ctx, ST_EMIT, 8.0 * nwords + 16.0 * n + (double)N * sizeof(K),
-                 k_emit<K><<<grid_for(N, EMIT_TILE), EMIT_BLOCK, 0, s>>>(packed.as<uint64_t>(), base_off.as<uint64_t>(),
-                                                              edge_off.as<uint64_t>(), n, N, k, keys_a.as<K>(),
-                                                              kpasses, d_hist));
+                 k_emit<K><<<(unsigned)std::min<uint64_t>(grid_for(n, EMIT_BLOCK / 32), 152ull * 64), EMIT_BLOCK, 0, s>>>(
+                     packed.as<uint64_t>(), base_off.as<uint64_t>(), edge_off.as<uint64_t>(), n, k, keys_a.as<K>(),
+                     kpasses, d_hist));
     }
     DBG_CUDA_TRY(cudaGetLastError());
     K *kp = keys_a.as<K>(), *alt = keys_b.as<K>();
@@ -222,14 +238,14 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     sorted = kp;
     // run-length reduce into the other buffer
     DBG_TRY(alloc_buf(ctx, headpos, (N + 1) * sizeof(uint32_t)));
-    const uint64_t tiles = (N + SCAN_TILE - 1) / SCAN_TILE;
+    const uint64_t tiles = (N + BUILD_SCAN_TILE - 1) / BUILD_SCAN_TILE;
     DBG_TRY(ensure_status(ctx, tiles));
     uint32_t epoch;
     DBG_TRY(next_epoch(ctx, &epoch));
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(uint32_t), s));
     {
       DBG_LAUNCH(ctx, ST_RLE, (double)N * sizeof(K),
-                 k_rle<K><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(sorted, N, alt, headpos.as<uint32_t>(), ctx->d_status,
+                 k_rle<K, BUILD_SCAN_ITEMS><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(sorted, N, alt, headpos.as<uint32_t>(), ctx->d_status,
                                                      ctx->d_counters, epoch, ctx->spin_limit, ctx->d_err,
                                                      ctx->d_counters + 1));
     }
@@ -297,7 +313,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   DBG_TRY(alloc_buf(ctx, g->adj_nbr, std::max<uint64_t>(1, 2 * E) * sizeof(uint32_t)));
   uint64_t V = 0;
   if (R > 0) {
-    const uint64_t tiles = (R + SCAN_TILE - 1) / SCAN_TILE;
+    const uint64_t tiles = (R + BUILD_SCAN_TILE - 1) / BUILD_SCAN_TILE;
     DBG_TRY(ensure_status(ctx, 2 * tiles));
     uint32_t eh, ee;
     DBG_TRY(next_epoch(ctx, &eh));
@@ -306,7 +322,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     // node keys go to the free record buffer first (|V| is known only after)
     {
       DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (sizeof(K) + 4) + (double)E * (2 * 5 + 8),
-                 k_node_ids<K><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
+                 k_node_ids<K, BUILD_SCAN_ITEMS><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
           rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g->src.as<uint32_t>(), g->dst.as<uint32_t>(),
           g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), ctx->d_status, ctx->d_status + tiles,
           ctx->d_counters, eh, ee, ctx->spin_limit, ctx->d_err, ctx->d_counters + 1));

@@ -264,10 +264,10 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_scan_excl(const uint32_t *__rest
 // Unitig tables, one thread per node; the first node of each unitig writes
 // its entries.  off_by_v[h] = first output slot of the unitig headed by h.
 __global__ void k_unitig_offsets(const uint32_t *__restrict__ is_head, const uint64_t *__restrict__ uidx,
-                                 const uint64_t *__restrict__ off_by_v, const uint8_t *__restrict__ cyc,
-                                 const uint8_t *__restrict__ strand, uint64_t V, uint64_t U, int k,
-                                 uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
-                                 uint8_t *__restrict__ circular) {
+                                 const uint64_t *__restrict__ off_by_v, const uint32_t *__restrict__ len_at_head,
+                                 const uint8_t *__restrict__ cyc, const uint8_t *__restrict__ strand, uint64_t V,
+                                 uint64_t U, int k, uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
+                                 uint8_t *__restrict__ circular, uint4 *__restrict__ hinfo) {
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= V; v += (uint64_t)gridDim.x * blockDim.x) {
     if (v == V) {
       node_off[U] = V;
@@ -279,6 +279,8 @@ __global__ void k_unitig_offsets(const uint32_t *__restrict__ is_head, const uin
     node_off[u] = off_by_v[v];
     seq_off[u] = off_by_v[v] + u * (uint64_t)(k - 1);
     circular[u] = cyc && cyc[2 * v + strand[v]] == 1 ? 1 : 0;
+    // everything a node of this unitig needs, in one 16-byte gather
+    hinfo[v] = make_uint4((uint32_t)off_by_v[v], (uint32_t)u, len_at_head[v], 0u);
   }
 }
 
@@ -287,23 +289,23 @@ __global__ void k_unitig_offsets(const uint32_t *__restrict__ is_head, const uin
 // of its k-mer as read on the kept strand.
 template <class K>
 __global__ void k_unitig_write(const uint32_t *__restrict__ head, const uint32_t *__restrict__ rank,
-                               const uint8_t *__restrict__ strand, const uint64_t *__restrict__ uidx,
-                               const uint64_t *__restrict__ off_by_v, const uint32_t *__restrict__ len_at_head,
+                               const uint8_t *__restrict__ strand, const uint4 *__restrict__ hinfo,
                                const uint64_t *__restrict__ node_keys, uint64_t V, int k,
                                uint64_t *__restrict__ nodes_out, char *__restrict__ seq, uint32_t *err) {
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t h = head[v];
     const uint64_t r = rank[v];
-    if (r >= len_at_head[h]) {  // a rank must fall inside its unitig
+    const uint4 hi = hinfo[h];  // (first slot, unitig index, length, -)
+    if (r >= hi.z) {  // a rank must fall inside its unitig
       atomicOr(err, ERR_INTERNAL);
       continue;
     }
-    const uint64_t u = uidx[h];
+    const uint64_t u = hi.y;
     const uint32_t s = strand[v];
-    nodes_out[off_by_v[h] + r] = (v << 1) | s;
+    nodes_out[hi.x + r] = (v << 1) | s;
     K km = load_node_key<K>(node_keys, v);
     if (s) km = revcomp(km, k);
-    const uint64_t so = off_by_v[h] + u * (uint64_t)(k - 1);
+    const uint64_t so = hi.x + u * (uint64_t)(k - 1);
     const char *acgt = "ACGT";
     if (r == 0) {
       for (int i = 0; i < k; i++) seq[so + i] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - i), 2)];
@@ -476,17 +478,20 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
   u->total_bases = V + U * (uint64_t)(k - 1);
   DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
   if (V > 0) {
-    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 4.0 * V + 16.0 * U * 3,
+    DevBuf hinfo;
+    DBG_TRY(alloc_buf(ctx, hinfo, V1 * sizeof(uint4)));
+    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 4.0 * V + 16.0 * U * 5,
                k_unitig_offsets<<<grid_of(V + 1), 256, 0, s>>>(
-                   is_head.as<uint32_t>(), uidx.as<uint64_t>(), off_by_v.as<uint64_t>(),
+                   is_head.as<uint32_t>(), uidx.as<uint64_t>(), off_by_v.as<uint64_t>(), len_at_head.as<uint32_t>(),
                    have_cycles ? cyc.as<uint8_t>() : nullptr, strand.as<uint8_t>(), V, U, k,
-                   u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(), u->circular.as<uint8_t>()));
+                   u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(), u->circular.as<uint8_t>(),
+                   hinfo.as<uint4>()));
     DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT,
-               (double)V * (4 + 4 + 1 + 8 + 8 + 4 + 8 * g->key_words + 8 + 1) + (double)U * k,
-               k_unitig_write<K><<<grid_of(V), 256, 0, s>>>(
-                   head.as<uint32_t>(), rank.as<uint32_t>(), strand.as<uint8_t>(), uidx.as<uint64_t>(),
-                   off_by_v.as<uint64_t>(), len_at_head.as<uint32_t>(), g->node_keys.as<uint64_t>(), V, k,
-                   u->nodes.as<uint64_t>(), u->seq.as<char>(), ctx->d_err));
+               (double)V * (4 + 4 + 1 + 16 + 8 * g->key_words + 8 + 1) + (double)U * k,
+               k_unitig_write<K><<<grid_of(V), 256, 0, s>>>(head.as<uint32_t>(), rank.as<uint32_t>(),
+                                                            strand.as<uint8_t>(), hinfo.as<uint4>(),
+                                                            g->node_keys.as<uint64_t>(), V, k,
+                                                            u->nodes.as<uint64_t>(), u->seq.as<char>(), ctx->d_err));
     DBG_CUDA_TRY(cudaGetLastError());
   } else {
     DBG_CUDA_TRY(cudaMemsetAsync(u->node_off.p, 0, 8, s));

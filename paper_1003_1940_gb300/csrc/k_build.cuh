@@ -241,10 +241,10 @@ __device__ __forceinline__ Key128 load_window<Key128>(const uint64_t *packed, ui
 }
 
 // ---------------------------------------------------------------------------
-// K2 emit (STEP-1): key e of read r at position j = e - edge_off[r] is the
-// canonical (k+1)-mer min(z, revcomp z) of z = r[j .. j+k].  The block also
-// accumulates the digit histograms of every radix pass of the sort that
-// follows (one upfront histogram for all passes, as in onesweep).
+// K2 emit (STEP-1): key edge_off[r] + j of read r is the canonical (k+1)-mer
+// min(z, revcomp z) of z = r[j .. j+k].  The block also accumulates the
+// digit histograms of every radix pass of the sort that follows (one
+// upfront histogram for all passes, as in onesweep).
 // ---------------------------------------------------------------------------
 constexpr int EMIT_BLOCK = 256, EMIT_ITEMS = 8, EMIT_TILE = EMIT_BLOCK * EMIT_ITEMS;
 
@@ -262,29 +262,25 @@ template <class K>
 __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict__ packed,
                                                      const uint64_t *__restrict__ base_off,
                                                      const uint64_t *__restrict__ edge_off, uint64_t n_reads,
-                                                     uint64_t n_keys, uint32_t k, K *__restrict__ keys,
-                                                     int passes, unsigned long long *__restrict__ hist) {
+                                                     uint32_t k, K *__restrict__ keys, int passes,
+                                                     unsigned long long *__restrict__ hist) {
+  // one warp per read: lanes take consecutive positions, so every warp-wide
+  // store writes 32 consecutive keys
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
-  __shared__ uint64_t s_r0, s_r1;
   for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK) s_hist[i] = 0;
-  const uint64_t t0 = (uint64_t)blockIdx.x * EMIT_TILE;
-  const uint64_t t1 = min(n_keys, t0 + EMIT_TILE);
-  if (threadIdx.x == 0) {
-    s_r0 = last_le(edge_off, 0, n_reads, t0);
-    s_r1 = last_le(edge_off, s_r0, n_reads, t1 - 1) + 1;
-  }
   __syncthreads();
-  const uint64_t r0 = s_r0, r1 = s_r1;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (EMIT_BLOCK / 32);
   const int m = (int)k + 1;
-  uint64_t r = r0;
-  for (uint64_t e = t0 + threadIdx.x; e < t1; e += EMIT_BLOCK) {
-    r = last_le(edge_off, r, r1, e);
-    const uint64_t p = __ldg(base_off + r) + (e - __ldg(edge_off + r));
-    const K z = load_window<K>(packed, p, m);
-    const K key = kmin(z, revcomp(z, m));
-    keys[e] = key;
-    for (int ps = 0; ps < passes; ps++)
-      atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(key, ps * RADIX_BITS, RADIX_BITS)], 1u);
+  for (uint64_t r = (uint64_t)blockIdx.x * (EMIT_BLOCK / 32) + (threadIdx.x >> 5); r < n_reads; r += warps) {
+    const uint64_t e0 = __ldg(edge_off + r), cnt = __ldg(edge_off + r + 1) - e0, p0 = __ldg(base_off + r);
+    for (uint64_t j = lane; j < cnt; j += 32) {
+      const K z = load_window<K>(packed, p0 + j, m);
+      const K key = kmin(z, revcomp(z, m));
+      keys[e0 + j] = key;
+      for (int ps = 0; ps < passes; ps++)
+        atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(key, ps * RADIX_BITS, RADIX_BITS)], 1u);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK)
@@ -382,13 +378,14 @@ struct OnesweepSmem {
   uint32_t whist[WARPS][RADIX];
   uint32_t match[WARPS][RADIX + 1];
   uint32_t tile_start[RADIX];
+  uint32_t early[RADIX];
   uint64_t gbase[RADIX];
   uint64_t bar;
   uint32_t tmp[8];
   uint32_t tile;
 };
 
-template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, bool LOAD_TMA, int MIN_BLOCKS>
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, bool LOAD_TMA, int MIN_BLOCKS, bool EARLY>
 __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
     const K *__restrict__ kin, K *__restrict__ kout, const uint32_t *__restrict__ vin, uint32_t *__restrict__ vout,
     uint64_t n, int shift, const uint64_t *__restrict__ digit_base, uint64_t *__restrict__ status,
@@ -404,6 +401,7 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
   for (int i = tid; i < WARPS * RADIX; i += BLOCK) (&sm.whist[0][0])[i] = 0;
   if (RANK == RANK_ATOMIC)
     for (int i = tid; i < WARPS * (RADIX + 1); i += BLOCK) (&sm.match[0][0])[i] = 0;
+  if (EARLY && tid < RADIX) sm.early[tid] = 0;
   if (tid == 0) {
     sm.tile = atomicAdd(ticket, 1u);
     if (LOAD_TMA) {
@@ -447,6 +445,28 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
     } else {
       key[i] = KeyOps<K>::zero();
       val[i] = 0;
+    }
+  }
+  // EARLY: count the tile's digits, publish, look back and publish the
+  // inclusive prefix before ranking, so that successors never wait for
+  // this tile's ranking
+  uint32_t excl_early = 0;
+  if (EARLY) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++)
+      if ((uint32_t)(wofs + i * 32 + lane) < tile_n)
+        atomicAdd(&sm.early[KeyOps<K>::digit(key[i], shift, RADIX_BITS)], 1u);
+    __syncthreads();
+    if (tid < RADIX) {
+      const uint32_t c = sm.early[tid];
+      uint64_t *st = status + (size_t)tile * RADIX + tid;
+      if (tile == 0) {
+        st_relaxed(st, lb_word(epoch, LB_INCLUSIVE, c));
+      } else {
+        st_relaxed(st, lb_word(epoch, LB_AGGREGATE, c));
+        excl_early = lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
+        st_relaxed(st, lb_word(epoch, LB_INCLUSIVE, excl_early + c));
+      }
     }
   }
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -493,13 +513,14 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
       sm.whist[w][tid] = cnt;
       cnt += c;
     }
-    st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE, cnt));
+    if (!EARLY)
+      st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE, cnt));
   }
   const uint32_t tstart = block_excl_scan_256(cnt, sm.tmp);
   if (tid < RADIX) {
     sm.tile_start[tid] = tstart;
-    uint32_t excl = 0;
-    if (tile > 0) {
+    uint32_t excl = excl_early;
+    if (!EARLY && tile > 0) {
       excl = lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
       st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, LB_INCLUSIVE, excl + cnt));
     }
@@ -599,23 +620,24 @@ __device__ __forceinline__ uint32_t tile_prefix(uint64_t *status, uint32_t tile,
   return *s_slot;
 }
 
-template <class K>
+template <class K, int ITEMS = SCAN_ITEMS>
 __global__ __launch_bounds__(SCAN_BLOCK) void k_rle(const K *__restrict__ keys, uint64_t n, K *__restrict__ uniq,
                                                     uint32_t *__restrict__ headpos, uint64_t *status,
                                                     uint32_t *ticket, uint32_t epoch, uint32_t spin_limit,
                                                     uint32_t *err, uint32_t *total) {
   constexpr int WARPS = SCAN_BLOCK / 32;
-  __shared__ uint32_t s_cnt[SCAN_ITEMS * WARPS + 1];
+  constexpr int TILE = SCAN_BLOCK * ITEMS;
+  __shared__ uint32_t s_cnt[ITEMS * WARPS + 1];
   __shared__ uint32_t s_tile, s_excl;
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * SCAN_TILE;
-  K key[SCAN_ITEMS];
-  bool head[SCAN_ITEMS];
-  uint32_t rank[SCAN_ITEMS];
+  const uint64_t base = (uint64_t)tile * TILE;
+  K key[ITEMS];
+  bool head[ITEMS];
+  uint32_t rank[ITEMS];
 #pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; i++) {
+  for (int i = 0; i < ITEMS; i++) {
     const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
     head[i] = false;
     if (idx < n) {
@@ -623,10 +645,10 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_rle(const K *__restrict__ keys, 
       head[i] = idx == 0 || !KeyOps<K>::eq(key[i], keys[idx - 1]);
     }
   }
-  const uint32_t count = tile_flag_ranks<SCAN_BLOCK, SCAN_ITEMS>(head, rank, s_cnt);
+  const uint32_t count = tile_flag_ranks<SCAN_BLOCK, ITEMS>(head, rank, s_cnt);
   const uint32_t excl = tile_prefix(status, tile, count, epoch, spin_limit, err, &s_excl);
 #pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; i++) {
+  for (int i = 0; i < ITEMS; i++) {
     if (head[i]) {
       const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
       const uint32_t pos = excl + rank[i];
@@ -634,7 +656,7 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_rle(const K *__restrict__ keys, 
       headpos[pos] = (uint32_t)idx;
     }
   }
-  if (base + SCAN_TILE >= n && threadIdx.x == 0) {
+  if (base + TILE >= n && threadIdx.x == 0) {
     headpos[excl + count] = (uint32_t)n;
     *total = excl + count;
   }
@@ -718,7 +740,7 @@ __global__ void k_isolated(const uint64_t *__restrict__ packed, const uint64_t *
 // Two look-back scans in one pass.  The last tile writes row_ptr[V] and the
 // totals {V, ends}.
 // ---------------------------------------------------------------------------
-template <class K>
+template <class K, int ITEMS>
 __global__ __launch_bounds__(SCAN_BLOCK) void k_node_ids(
     const K *__restrict__ rkeys, const uint32_t *__restrict__ rvals, uint64_t R, K *__restrict__ node_keys,
     uint64_t *__restrict__ row_ptr, uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
@@ -726,18 +748,19 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_node_ids(
     uint32_t *ticket, uint32_t epoch_h, uint32_t epoch_e, uint32_t spin_limit, uint32_t *err,
     uint32_t *totals) {
   constexpr int WARPS = SCAN_BLOCK / 32;
-  __shared__ uint32_t s_cnt_h[SCAN_ITEMS * WARPS + 1], s_cnt_e[SCAN_ITEMS * WARPS + 1];
+  constexpr int TILE = SCAN_BLOCK * ITEMS;
+  __shared__ uint32_t s_cnt_h[ITEMS * WARPS + 1], s_cnt_e[ITEMS * WARPS + 1];
   __shared__ uint32_t s_tile, s_excl_h, s_excl_e;
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * SCAN_TILE;
-  K key[SCAN_ITEMS];
-  uint32_t val[SCAN_ITEMS];
-  bool head[SCAN_ITEMS], end[SCAN_ITEMS];
-  uint32_t rh[SCAN_ITEMS], re[SCAN_ITEMS];
+  const uint64_t base = (uint64_t)tile * TILE;
+  K key[ITEMS];
+  uint32_t val[ITEMS];
+  bool head[ITEMS], end[ITEMS];
+  uint32_t rh[ITEMS], re[ITEMS];
 #pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; i++) {
+  for (int i = 0; i < ITEMS; i++) {
     const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
     head[i] = end[i] = false;
     val[i] = REC_NONE;
@@ -748,13 +771,13 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_node_ids(
       end[i] = val[i] != REC_NONE;
     }
   }
-  const uint32_t ch = tile_flag_ranks<SCAN_BLOCK, SCAN_ITEMS>(head, rh, s_cnt_h);
-  const uint32_t ce = tile_flag_ranks<SCAN_BLOCK, SCAN_ITEMS>(end, re, s_cnt_e);
+  const uint32_t ch = tile_flag_ranks<SCAN_BLOCK, ITEMS>(head, rh, s_cnt_h);
+  const uint32_t ce = tile_flag_ranks<SCAN_BLOCK, ITEMS>(end, re, s_cnt_e);
   // both look-backs: warp 0 for heads, then for edge ends
   const uint32_t xh = tile_prefix(status_h, tile, ch, epoch_h, spin_limit, err, &s_excl_h);
   const uint32_t xe = tile_prefix(status_e, tile, ce, epoch_e, spin_limit, err, &s_excl_e);
 #pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; i++) {
+  for (int i = 0; i < ITEMS; i++) {
     const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
     if (idx >= R) continue;
     const uint32_t id = xh + rh[i] + (head[i] ? 1u : 0u) - 1u;
@@ -770,7 +793,7 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_node_ids(
       (role ? dst : src)[e] = id;
     }
   }
-  if (base + SCAN_TILE >= R && threadIdx.x == 0) {
+  if (base + TILE >= R && threadIdx.x == 0) {
     row_ptr[xh + ch] = xe + ce;
     totals[0] = xh + ch;
     totals[1] = xe + ce;
