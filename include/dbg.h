@@ -57,7 +57,8 @@ typedef enum dbg_status {
   DBG_ECUDA = 3,       /* a CUDA runtime call failed */
   DBG_ETIMEOUT = 4,    /* a bounded device-side wait reached its limit */
   DBG_ECANCELLED = 5,  /* request cancelled (serving) */
-  DBG_EOVERFLOW = 6    /* more than 2^32 - 1 edge instances, edges or nodes in one build */
+  DBG_EOVERFLOW = 6,   /* more than 2^32 - 1 edge instances, edges or nodes in one build */
+  DBG_EAGAIN = 7       /* dbg_poll without waiting: the request has not finished */
 } dbg_status;
 
 typedef struct dbg_ctx dbg_ctx;
@@ -174,6 +175,84 @@ uint64_t dbg_unitigs_total_bases(const dbg_unitigs *u);
 dbg_status dbg_unitigs_get(const dbg_unitigs *u, uint64_t *node_off, uint64_t *nodes,
                            uint64_t *seq_off, char *seq, uint8_t *circular);
 void dbg_unitigs_free(dbg_unitigs *u);
+
+/* ----------------------------------------------------------------------
+ * Many constructions at once (batched builds and a request server).
+ *
+ * A read set as dbg_build takes it.  The buffers are borrowed until the
+ * request has finished (dbg_poll returned it, or dbg_build_batch returned).
+ * flags: DBG_REQ_BUCKETED forces the key-range bucket path.
+ * -------------------------------------------------------------------- */
+typedef struct dbg_readset {
+  const char *reads;
+  const uint32_t *lengths;
+  uint64_t n;
+  uint32_t k;
+  uint32_t flags;
+} dbg_readset;
+enum { DBG_REQ_BUCKETED = 1u };
+
+typedef struct dbg_server dbg_server;
+
+typedef struct dbg_server_options {
+  uint32_t struct_size;     /* sizeof(dbg_server_options) */
+  int32_t device;           /* -1 = the current device */
+  uint32_t workers;         /* concurrent builds (each its own stream), 1..64; default 4 */
+  uint32_t spin_limit;      /* as in dbg_options; 0 = default */
+  uint64_t mem_budget;      /* device bytes all running requests may hold; 0 = 80 % of free memory */
+  uint32_t sort_variant[4]; /* radix sort variant per key kind (see dbg_sort_variant_set) */
+  uint32_t reserved[8];
+} dbg_server_options;
+
+typedef struct dbg_request_stats {
+  double queue_s;      /* submission to start */
+  double run_s;        /* start to finish */
+  double latency_s;    /* submission to finish */
+  uint64_t footprint;  /* estimated device bytes charged to the budget */
+  uint32_t bucketed;   /* 1 if built by the key-range bucket path */
+} dbg_request_stats;
+
+void dbg_server_options_init(dbg_server_options *opt);
+
+/* Starts `workers` worker threads, each with its own context and stream.
+ * Requests are admitted in submission order as soon as a worker is free and
+ * their estimated footprint fits the budget next to the running ones
+ * (continuous admission); their kernels overlap on the device.  A request
+ * whose footprint exceeds the whole budget runs on the bucket path.
+ * Results are the same graphs dbg_build returns for the same read set. */
+dbg_status dbg_server_create(dbg_server **srv, const dbg_server_options *opt);
+/* Waits for running requests; frees results nobody polled. */
+void dbg_server_destroy(dbg_server *srv);
+uint64_t dbg_server_budget(const dbg_server *srv);
+dbg_status dbg_submit(dbg_server *srv, const dbg_readset *req, uint64_t *ticket);
+/* wait != 0 blocks until the request has finished; otherwise returns
+ * DBG_EAGAIN while it runs.  On success *out is the graph (the caller frees
+ * it, before destroying the server) and the ticket is retired; an error
+ * status of the build is returned here.  stats may be NULL. */
+dbg_status dbg_poll(dbg_server *srv, uint64_t ticket, int wait, dbg_graph **out, dbg_request_stats *stats);
+
+/* Builds nsets read sets concurrently (a transient server with `workers`
+ * workers, 0 = 4) and returns one graph per set in outs; identical to
+ * calling dbg_build on each.  On error every outs[i] is NULL. */
+dbg_status dbg_build_batch(dbg_ctx *ctx, const dbg_readset *sets, uint32_t nsets, uint32_t workers,
+                           dbg_graph **outs);
+
+/* ----------------------------------------------------------------------
+ * dbg_build_bucketed -- dbg_build for inputs whose edge keys do not fit the
+ * device: the out-of-core construction of Section 5, with the external
+ * R-way merge replaced by key-range partitioning.  The reads are packed
+ * once on the device (host reads are streamed in chunks); the canonical
+ * (k+1)-mer key space is cut into ranges that each fit mem_budget, and for
+ * each range in ascending order only its keys are emitted, sorted and
+ * reduced, so the concatenated results are the sorted edge list.  Nodes are
+ * handled the same way over node-key ranges.  The result is bit-identical
+ * to dbg_build's.  Packed reads, per-read offsets and the final graph must
+ * fit on the device.  mem_budget = 0 uses half the free device memory.
+ * -------------------------------------------------------------------- */
+dbg_status dbg_build_bucketed(dbg_ctx *ctx, const char *reads, const uint32_t *lengths, uint64_t n, uint32_t k,
+                              uint64_t mem_budget, dbg_graph **out);
+/* Key ranges the build used (1 and 1 for dbg_build). */
+void dbg_graph_buckets(const dbg_graph *g, uint32_t *edge_ranges, uint32_t *node_ranges);
 
 /* ----------------------------------------------------------------------
  * dbg_rle_u64_noalloc -- the run-length reduce that dbg_build runs on its

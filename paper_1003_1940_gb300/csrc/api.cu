@@ -392,6 +392,78 @@ dbg_status dbg_build(dbg_ctx *ctx, const char *reads, const uint32_t *lengths, u
   return DBG_OK;
 }
 
+dbg_status dbg_build_bucketed(dbg_ctx *ctx, const char *reads, const uint32_t *lengths, uint64_t n, uint32_t k,
+                              uint64_t mem_budget, dbg_graph **out) {
+  if (!out) {
+    set_error("out is NULL");
+    return DBG_EINVAL;
+  }
+  *out = nullptr;
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return DBG_EINVAL;
+  }
+  if (k < 1 || k > 63 || (k % 2) == 0) {
+    set_error("k = %u: k must be odd and in [1, 63]", k);
+    return DBG_EINVAL;
+  }
+  if (n > 0 && (!reads || !lengths)) {
+    set_error("reads or lengths is NULL");
+    return DBG_EINVAL;
+  }
+  if (n >= 0xffffffffull) {
+    set_error("n = %llu reads exceed one build", (unsigned long long)n);
+    return DBG_EOVERFLOW;
+  }
+  DeviceScope scope(ctx->device);
+  cudaStream_t s = ctx->stream;
+  if (mem_budget == 0) {
+    size_t free_b = 0, total_b = 0;
+    DBG_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    mem_budget = free_b / 2;
+  }
+  dbg_graph *g = new (std::nothrow) dbg_graph();
+  if (!g) return DBG_ENOMEM;
+  g->al = ctx->al;
+  g->device = ctx->device;
+  dbg_status st = DBG_OK;
+  DevBuf d_len;
+  const uint32_t *len_dev = lengths;
+  const bool reads_on_dev = n > 0 && is_device_ptr(reads);
+  if (n > 0 && !is_device_ptr(lengths)) {
+    st = alloc_buf(ctx, d_len, n * sizeof(uint32_t));
+    if (st == DBG_OK && cudaMemcpyAsync(d_len.p, lengths, n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_error("copy of the read lengths to the device failed");
+      st = DBG_ECUDA;
+    }
+    len_dev = d_len.as<uint32_t>();
+  }
+  if (st == DBG_OK) {
+    BucketInput in{reads, reads_on_dev, len_dev, n, k};
+    st = k <= 31 ? build_bucketed_u64(ctx, in, mem_budget, g, &g->edge_buckets, &g->node_buckets)
+                 : build_bucketed_u128(ctx, in, mem_budget, g, &g->edge_buckets, &g->node_buckets);
+  }
+  for (DevBuf *b : {&g->node_keys, &g->edge_keys, &g->src, &g->dst, &g->orient, &g->mult, &g->row_ptr,
+                    &g->adj_nbr, &g->adj_edge, &g->adj_role})
+    b->al = &g->al;
+  d_len.release();
+  cudaStreamSynchronize(s);
+  prof_resolve(ctx);
+  if (st != DBG_OK) {
+    cudaGetLastError();
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s);
+    dbg_graph_free(g);
+    return st;
+  }
+  *out = g;
+  return DBG_OK;
+}
+
+void dbg_graph_buckets(const dbg_graph *g, uint32_t *edge_ranges, uint32_t *node_ranges) {
+  if (edge_ranges) *edge_ranges = g ? g->edge_buckets : 0;
+  if (node_ranges) *node_ranges = g ? g->node_buckets : 0;
+}
+
 uint32_t dbg_graph_k(const dbg_graph *g) { return g ? g->k : 0; }
 uint32_t dbg_graph_key_words(const dbg_graph *g) { return g ? g->key_words : 0; }
 uint64_t dbg_graph_num_nodes(const dbg_graph *g) { return g ? g->num_nodes : 0; }

@@ -325,7 +325,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
                  k_node_ids<K, BUILD_SCAN_ITEMS><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
           rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g->src.as<uint32_t>(), g->dst.as<uint32_t>(),
           g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), ctx->d_status, ctx->d_status + tiles,
-          ctx->d_counters, eh, ee, ctx->spin_limit, ctx->d_err, ctx->d_counters + 1));
+          ctx->d_counters, eh, ee, ctx->spin_limit, ctx->d_err, ctx->d_counters + 1, 0u, 0ull));
     }
     DBG_CUDA_TRY(cudaGetLastError());
     uint32_t tot[2];
@@ -464,6 +464,336 @@ const char *variant_name(uint32_t v, uint32_t *count) {
   const SortVariant *t = SortKind<K, V>::table(&c);
   *count = (uint32_t)c;
   return v < (uint32_t)c ? t[v].name : nullptr;
+}
+
+}  // namespace dbg
+
+namespace dbg {
+
+// ---------------------------------------------------------------------------
+// The bucket path (dbg_build_bucketed): Section 5's out-of-core
+// construction with key-range partitioning in place of the external merge.
+// ---------------------------------------------------------------------------
+// Cuts the prefix bins into consecutive ranges of at most `cap` items (a
+// single bin above cap gets a range of its own).
+inline std::vector<std::pair<uint32_t, uint32_t>> plan_ranges(const uint64_t *hist, uint64_t cap,
+                                                              std::vector<uint64_t> *sizes) {
+  std::vector<std::pair<uint32_t, uint32_t>> out;
+  uint32_t lo = 0;
+  uint64_t acc = 0;
+  for (uint32_t b = 0; b < (uint32_t)PREFIX_BINS; b++) {
+    if (acc > 0 && acc + hist[b] > cap) {
+      out.emplace_back(lo, b);
+      sizes->push_back(acc);
+      lo = b;
+      acc = 0;
+    }
+    acc += hist[b];
+  }
+  out.emplace_back(lo, (uint32_t)PREFIX_BINS);
+  sizes->push_back(acc);
+  return out;
+}
+
+static dbg_status scan_flags(dbg_ctx *ctx, const uint32_t *in, uint64_t n, uint64_t *out, uint32_t *total) {
+  cudaStream_t s = ctx->stream;
+  const uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  DBG_TRY(ensure_status(ctx, tiles));
+  uint32_t epoch;
+  DBG_TRY(next_epoch(ctx, &epoch));
+  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 2 * sizeof(uint32_t), s));
+  DBG_LAUNCH(ctx, ST_NODE_IDS, 12.0 * n,
+             k_scan_excl<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(in, n, out, ctx->d_status, ctx->d_counters, epoch,
+                                                                ctx->spin_limit, ctx->d_err, ctx->d_counters + 1));
+  DBG_CUDA_TRY(cudaGetLastError());
+  return read_small(ctx, ctx->d_counters + 1, sizeof(uint32_t), total);
+}
+
+template <class K>
+dbg_status concat_chunks(dbg_ctx *ctx, std::vector<DevBuf> &chunks, const std::vector<uint64_t> &counts,
+                         size_t elem, void *dst) {
+  uint64_t at = 0;
+  for (size_t i = 0; i < chunks.size(); i++) {
+    if (counts[i])
+      DBG_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(dst) + at * elem, chunks[i].p, counts[i] * elem,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+    at += counts[i];
+    chunks[i].release();
+  }
+  return DBG_OK;
+}
+
+template <class K>
+dbg_status build_bucketed_impl(dbg_ctx *ctx, const BucketInput &in, uint64_t budget, dbg_graph *g,
+                               uint32_t *n_edge_buckets, uint32_t *n_node_buckets) {
+  cudaStream_t s = ctx->stream;
+  const uint32_t k = in.k;
+  const uint64_t n = in.n;
+  const int m = (int)k + 1;
+  const uint64_t w = sizeof(K);
+  g->k = k;
+  g->key_words = sizeof(K) / 8;
+  DBG_CUDA_TRY(cudaStreamSynchronize(s));  // the pinned mirror is free
+
+  // ---- per-read offsets ----
+  DevBuf base_off, edge_off, tile_sums, small;
+  const uint64_t off_tiles = (n + OFF_TILE - 1) / OFF_TILE;
+  DBG_TRY(alloc_buf(ctx, base_off, (n + 1) * 8));
+  DBG_TRY(alloc_buf(ctx, edge_off, (n + 1) * 8));
+  DBG_TRY(alloc_buf(ctx, tile_sums, std::max<uint64_t>(1, off_tiles) * sizeof(Sum3)));
+  DBG_TRY(alloc_buf(ctx, small, 64 * 8 + MAX_PASSES * RADIX * 16 + PREFIX_BINS * 8));
+  uint64_t *d_totals = small.as<uint64_t>();
+  unsigned long long *d_hist = reinterpret_cast<unsigned long long *>(d_totals + 64);
+  uint64_t *d_digit_base = reinterpret_cast<uint64_t *>(d_hist + MAX_PASSES * RADIX);
+  unsigned long long *d_phist = reinterpret_cast<unsigned long long *>(d_digit_base + MAX_PASSES * RADIX);
+  if (n > 0)
+    DBG_LAUNCH(ctx, ST_OFFSETS, 4.0 * n,
+               k_read_tile_sums<<<(unsigned)off_tiles, OFF_BLOCK, 0, s>>>(in.d_lengths, n, k, tile_sums.as<Sum3>()));
+  DBG_LAUNCH(ctx, ST_OFFSETS, 0.0,
+             k_scan_tile_sums<<<1, 1024, 0, s>>>(tile_sums.as<Sum3>(), (uint32_t)off_tiles, d_totals,
+                                                 base_off.as<uint64_t>(), edge_off.as<uint64_t>(), n));
+  if (n > 0)
+    DBG_LAUNCH(ctx, ST_OFFSETS, 20.0 * n,
+               k_read_offsets<<<(unsigned)off_tiles, OFF_BLOCK, 0, s>>>(in.d_lengths, n, k, tile_sums.as<Sum3>(),
+                                                                        base_off.as<uint64_t>(),
+                                                                        edge_off.as<uint64_t>()));
+  DBG_CUDA_TRY(cudaGetLastError());
+  uint64_t totals[3];
+  DBG_TRY(read_small(ctx, d_totals, sizeof(totals), totals));
+  const uint64_t total_bases = totals[0], N = totals[1], I = totals[2];
+  tile_sums.release();
+  g->num_instances = N;
+
+  // ---- pack the reads once; host reads stream through a staging buffer ----
+  DevBuf packed;
+  const uint64_t nwords = (total_bases + 31) / 32;
+  DBG_TRY(alloc_buf(ctx, packed, (nwords + 3) * 8));
+  DBG_CUDA_TRY(cudaMemsetAsync(packed.as<uint64_t>() + nwords, 0, 3 * 8, s));
+  if (nwords > 0) {
+    if (in.reads_on_device) {
+      DBG_LAUNCH(ctx, ST_PACK, (double)total_bases * 1.25,
+                 k_pack<<<grid_for(nwords, 256), 256, 0, s>>>(reinterpret_cast<const uint8_t *>(in.reads),
+                                                              total_bases, packed.as<uint64_t>(), nwords, ctx->d_err));
+    } else {
+      const uint64_t chunk = 256ull << 20;  // bases per staged copy (a multiple of 32)
+      DevBuf stage;
+      DBG_TRY(alloc_buf(ctx, stage, std::min(chunk, total_bases)));
+      for (uint64_t off = 0; off < total_bases; off += chunk) {
+        const uint64_t len = std::min(chunk, total_bases - off);
+        DBG_CUDA_TRY(cudaMemcpyAsync(stage.p, in.reads + off, len, cudaMemcpyHostToDevice, s));
+        DBG_LAUNCH(ctx, ST_PACK, (double)len * 1.25,
+                   k_pack_at<<<grid_for((len + 31) / 32, 256), 256, 0, s>>>(stage.as<uint8_t>(), len,
+                                                                          packed.as<uint64_t>(), off / 32,
+                                                                          ctx->d_err));
+      }
+      DBG_CUDA_TRY(cudaStreamSynchronize(s));  // the staging buffer is released next
+    }
+  }
+  DBG_CUDA_TRY(cudaGetLastError());
+  DBG_TRY(check_device_error(ctx));
+
+  // ---- edge-key ranges ----
+  const unsigned emit_grid = (unsigned)std::min<uint64_t>(grid_for(n, EMIT_BLOCK / 32), 152ull * 64);
+  std::vector<uint64_t> hist(PREFIX_BINS, 0);
+  if (N > 0) {
+    DBG_CUDA_TRY(cudaMemsetAsync(d_phist, 0, PREFIX_BINS * 8, s));
+    DBG_LAUNCH(ctx, ST_EMIT, 8.0 * nwords + 16.0 * n,
+               k_emit_prefix_hist<K><<<emit_grid, EMIT_BLOCK, 0, s>>>(packed.as<uint64_t>(), base_off.as<uint64_t>(),
+                                                                      edge_off.as<uint64_t>(), n, k, d_phist));
+    DBG_CUDA_TRY(cudaMemcpyAsync(hist.data(), d_phist, PREFIX_BINS * 8, cudaMemcpyDeviceToHost, s));
+    DBG_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  const uint64_t persistent = (nwords + 3) * 8 + (n + 1) * 16;
+  const uint64_t room = budget > persistent ? budget - persistent : 0;
+  const uint64_t key_cap = std::max<uint64_t>(1ull << 16, room / (2 * w + 4 + 4));
+  std::vector<uint64_t> sizes;
+  auto ranges = plan_ranges(hist.data(), key_cap, &sizes);
+  *n_edge_buckets = (uint32_t)ranges.size();
+
+  const int kbits = 2 * m;
+  const int kpasses = passes_for_bits(kbits);
+  std::vector<DevBuf> ck, cm, co;
+  std::vector<uint64_t> ce;
+  uint64_t E = 0;
+  for (size_t b = 0; b < ranges.size(); b++) {
+    const uint64_t cnt = sizes[b];
+    if (cnt == 0) continue;
+    DevBuf ka, kb, headpos;
+    DBG_TRY(alloc_buf(ctx, ka, cnt * w));
+    DBG_TRY(alloc_buf(ctx, kb, cnt * w));
+    DBG_TRY(alloc_buf(ctx, headpos, (cnt + 1) * 4));
+    DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * 8, s));
+    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 8, 0, 4, s));
+    DBG_LAUNCH(ctx, ST_EMIT, 8.0 * nwords + 16.0 * n + (double)cnt * w,
+               k_emit_range<K><<<emit_grid, EMIT_BLOCK, 0, s>>>(packed.as<uint64_t>(), base_off.as<uint64_t>(),
+                                                                edge_off.as<uint64_t>(), n, k, ranges[b].first,
+                                                                ranges[b].second, ka.as<K>(), ctx->d_counters + 8,
+                                                                kpasses, d_hist));
+    DBG_CUDA_TRY(cudaGetLastError());
+    K *kp = ka.as<K>(), *alt = kb.as<K>();
+    uint32_t *vn = nullptr, *van = nullptr;
+    DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, cnt, kbits, d_hist, d_digit_base)));
+    const uint64_t tiles = (cnt + BUILD_SCAN_TILE - 1) / BUILD_SCAN_TILE;
+    DBG_TRY(ensure_status(ctx, tiles));
+    uint32_t epoch;
+    DBG_TRY(next_epoch(ctx, &epoch));
+    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(uint32_t), s));
+    DBG_LAUNCH(ctx, ST_RLE, (double)cnt * w,
+               k_rle<K, BUILD_SCAN_ITEMS><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
+                   kp, cnt, alt, headpos.as<uint32_t>(), ctx->d_status, ctx->d_counters, epoch, ctx->spin_limit,
+                   ctx->d_err, ctx->d_counters + 1));
+    uint32_t eb = 0;
+    DBG_TRY(read_small(ctx, ctx->d_counters + 1, 4, &eb));
+    DBG_TRY(check_device_error(ctx));
+    DevBuf k1, m1, o1;
+    DBG_TRY(alloc_buf(ctx, k1, std::max<uint64_t>(1, eb) * w));
+    DBG_TRY(alloc_buf(ctx, m1, std::max<uint64_t>(1, eb) * 4));
+    DBG_TRY(alloc_buf(ctx, o1, std::max<uint64_t>(1, eb)));
+    if (eb)
+      DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)eb * (2 * w + 9),
+                 k_edge_finish<K><<<grid_for(eb, 256), 256, 0, s>>>(alt, headpos.as<uint32_t>(), eb, k, k1.as<K>(),
+                                                                   m1.as<uint32_t>(), o1.as<uint8_t>()));
+    ck.push_back(std::move(k1));
+    cm.push_back(std::move(m1));
+    co.push_back(std::move(o1));
+    ce.push_back(eb);
+    E += eb;
+  }
+  if (E >= 0x80000000ull) {
+    set_error("%llu unique edges exceed one build (2^31 - 1)", (unsigned long long)E);
+    return DBG_EOVERFLOW;
+  }
+  g->num_edges = E;
+  const uint64_t E1 = std::max<uint64_t>(1, E);
+  DBG_TRY(alloc_buf(ctx, g->edge_keys, E1 * w));
+  DBG_TRY(alloc_buf(ctx, g->mult, E1 * 4));
+  DBG_TRY(alloc_buf(ctx, g->orient, E1));
+  DBG_TRY(concat_chunks<K>(ctx, ck, ce, w, g->edge_keys.p));
+  DBG_TRY(concat_chunks<K>(ctx, cm, ce, 4, g->mult.p));
+  DBG_TRY(concat_chunks<K>(ctx, co, ce, 1, g->orient.p));
+
+  // ---- node-key ranges ----
+  DBG_TRY(alloc_buf(ctx, g->src, E1 * 4));
+  DBG_TRY(alloc_buf(ctx, g->dst, E1 * 4));
+  DBG_TRY(alloc_buf(ctx, g->adj_edge, 2 * E1 * 4));
+  DBG_TRY(alloc_buf(ctx, g->adj_role, 2 * E1));
+  DBG_TRY(alloc_buf(ctx, g->adj_nbr, 2 * E1 * 4));
+  std::fill(hist.begin(), hist.end(), 0);
+  if (E > 0) {
+    DBG_CUDA_TRY(cudaMemsetAsync(d_phist, 0, PREFIX_BINS * 8, s));
+    DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)E * w,
+               k_node_prefix_hist<K><<<grid_for(E, 256 * 8), 256, 0, s>>>(g->edge_keys.as<K>(), E, k, d_phist));
+    DBG_CUDA_TRY(cudaMemcpyAsync(hist.data(), d_phist, PREFIX_BINS * 8, cudaMemcpyDeviceToHost, s));
+    DBG_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  const uint64_t held = persistent + E1 * (w + 4 + 1 + 4 + 4 + 2 * 9);
+  const uint64_t room2 = budget > held ? budget - held : 0;
+  const uint64_t rec_cap = std::max<uint64_t>(1ull << 16, room2 / (2 * (w + 4) + 16));
+  sizes.clear();
+  auto nranges = plan_ranges(hist.data(), rec_cap, &sizes);
+  *n_node_buckets = (uint32_t)nranges.size();
+  DevBuf flags, pos;
+  if (E > 0) {
+    DBG_TRY(alloc_buf(ctx, flags, 2 * E * 4));
+    DBG_TRY(alloc_buf(ctx, pos, (2 * E + 1) * 8));
+  }
+  const int nbits = 2 * (int)k;
+  const int npasses = passes_for_bits(nbits);
+  std::vector<DevBuf> cnk, crp;
+  std::vector<uint64_t> cv;
+  uint64_t base_v = 0, base_slot = 0;
+  for (size_t c = 0; c < nranges.size(); c++) {
+    const uint32_t lo = nranges[c].first, hi = nranges[c].second;
+    uint32_t Rc = 0;
+    if (E > 0) {
+      DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)E * w + 8.0 * E,
+                 k_flag_ends<K><<<grid_for(E, 256 * 8), 256, 0, s>>>(g->edge_keys.as<K>(), E, k, lo, hi,
+                                                                    flags.as<uint32_t>()));
+      DBG_TRY(scan_flags(ctx, flags.as<uint32_t>(), 2 * E, pos.as<uint64_t>(), &Rc));
+    }
+    const uint64_t cap = (uint64_t)Rc + I;
+    if (cap == 0) continue;
+    DevBuf ra, rb, va, vb, row_tmp;
+    DBG_TRY(alloc_buf(ctx, ra, cap * w));
+    DBG_TRY(alloc_buf(ctx, rb, cap * w));
+    DBG_TRY(alloc_buf(ctx, va, cap * 4));
+    DBG_TRY(alloc_buf(ctx, vb, cap * 4));
+    DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * 8, s));
+    if (Rc > 0)
+      DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)E * (w + 8) + (double)Rc * (w + 4),
+                 k_gather_ends<K><<<grid_for(E, 256 * 8), 256, 0, s>>>(g->edge_keys.as<K>(), E, k,
+                                                                      flags.as<uint32_t>(), pos.as<uint64_t>(),
+                                                                      ra.as<K>(), va.as<uint32_t>(), npasses,
+                                                                      d_hist));
+    uint64_t R = Rc;
+    if (I > 0) {
+      DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 9, 0, 4, s));
+      DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)n * 4,
+                 k_isolated_range<K><<<grid_for(n, 256), 256, 0, s>>>(packed.as<uint64_t>(), base_off.as<uint64_t>(),
+                                                                     in.d_lengths, n, k, lo, hi, ra.as<K>() + Rc,
+                                                                     va.as<uint32_t>() + Rc, ctx->d_counters + 9,
+                                                                     npasses, d_hist));
+      uint32_t iso = 0;
+      DBG_TRY(read_small(ctx, ctx->d_counters + 9, 4, &iso));
+      R += iso;
+    }
+    if (R == 0) continue;
+    K *rk = ra.as<K>(), *rk_alt = rb.as<K>();
+    uint32_t *rv = va.as<uint32_t>(), *rv_alt = vb.as<uint32_t>();
+    DBG_TRY((radix_sort<K, true>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, d_hist, d_digit_base)));
+    DBG_TRY(alloc_buf(ctx, row_tmp, (R + 1) * 8));
+    const uint64_t tiles = (R + BUILD_SCAN_TILE - 1) / BUILD_SCAN_TILE;
+    DBG_TRY(ensure_status(ctx, 2 * tiles));
+    uint32_t eh, ee;
+    DBG_TRY(next_epoch(ctx, &eh));
+    DBG_TRY(next_epoch(ctx, &ee));
+    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(uint32_t), s));
+    DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (w + 4),
+               k_node_ids<K, BUILD_SCAN_ITEMS><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
+                   rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g->src.as<uint32_t>(), g->dst.as<uint32_t>(),
+                   g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), ctx->d_status, ctx->d_status + tiles,
+                   ctx->d_counters, eh, ee, ctx->spin_limit, ctx->d_err, ctx->d_counters + 1, (uint32_t)base_v,
+                   base_slot));
+    DBG_CUDA_TRY(cudaGetLastError());
+    uint32_t tot[2];
+    DBG_TRY(read_small(ctx, ctx->d_counters + 1, sizeof(tot), tot));
+    DBG_TRY(check_device_error(ctx));
+    const uint64_t Vc = tot[0];
+    DevBuf nk, rp;
+    DBG_TRY(alloc_buf(ctx, nk, std::max<uint64_t>(1, Vc) * w));
+    DBG_TRY(alloc_buf(ctx, rp, std::max<uint64_t>(1, Vc) * 8));
+    if (Vc) {
+      DBG_CUDA_TRY(cudaMemcpyAsync(nk.p, rk_alt, Vc * w, cudaMemcpyDeviceToDevice, s));
+      DBG_CUDA_TRY(cudaMemcpyAsync(rp.p, row_tmp.p, Vc * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    cnk.push_back(std::move(nk));
+    crp.push_back(std::move(rp));
+    cv.push_back(Vc);
+    base_v += Vc;
+    base_slot += tot[1];
+  }
+  if (base_slot != 2 * E) {
+    set_error("adjacency holds %llu edge ends, expected %llu", (unsigned long long)base_slot,
+              (unsigned long long)(2 * E));
+    return DBG_ECUDA;
+  }
+  const uint64_t V = base_v;
+  g->num_nodes = V;
+  DBG_TRY(alloc_buf(ctx, g->node_keys, std::max<uint64_t>(1, V) * w));
+  DBG_TRY(alloc_buf(ctx, g->row_ptr, (V + 1) * 8));
+  DBG_TRY(concat_chunks<K>(ctx, cnk, cv, w, g->node_keys.p));
+  DBG_TRY(concat_chunks<K>(ctx, crp, cv, 8, g->row_ptr.p));
+  uint64_t *last = reinterpret_cast<uint64_t *>(ctx->h_pinned + 64);  // pinned: safe for an async copy
+  *last = 2 * E;
+  DBG_CUDA_TRY(cudaMemcpyAsync(g->row_ptr.as<uint64_t>() + V, last, 8, cudaMemcpyHostToDevice, s));
+  if (E > 0)
+    DBG_LAUNCH(ctx, ST_ADJACENCY, 2.0 * E * 13,
+               k_adj_nbr<<<grid_for(2 * E, 256 * 8), 256, 0, s>>>(g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
+                                                                 g->src.as<uint32_t>(), g->dst.as<uint32_t>(), 2 * E,
+                                                                 g->adj_nbr.as<uint32_t>()));
+  DBG_CUDA_TRY(cudaGetLastError());
+  DBG_CUDA_TRY(cudaStreamSynchronize(s));
+  return check_device_error(ctx);
 }
 
 }  // namespace dbg

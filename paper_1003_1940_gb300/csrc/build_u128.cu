@@ -16,3 +16,10 @@ const char *sort_variant_name_u128(bool pairs, uint32_t v, uint32_t *count) {
   return pairs ? variant_name<Key128, true>(v, count) : variant_name<Key128, false>(v, count);
 }
 }  // namespace dbg
+
+namespace dbg {
+dbg_status build_bucketed_u128(dbg_ctx *ctx, const BucketInput &in, uint64_t budget, dbg_graph *g, uint32_t *eb,
+                               uint32_t *nb) {
+  return build_bucketed_impl<Key128>(ctx, in, budget, g, eb, nb);
+}
+}  // namespace dbg

@@ -16,3 +16,10 @@ const char *sort_variant_name_u64(bool pairs, uint32_t v, uint32_t *count) {
   return pairs ? variant_name<uint64_t, true>(v, count) : variant_name<uint64_t, false>(v, count);
 }
 }  // namespace dbg
+
+namespace dbg {
+dbg_status build_bucketed_u64(dbg_ctx *ctx, const BucketInput &in, uint64_t budget, dbg_graph *g, uint32_t *eb,
+                              uint32_t *nb) {
+  return build_bucketed_impl<uint64_t>(ctx, in, budget, g, eb, nb);
+}
+}  // namespace dbg

@@ -218,49 +218,6 @@ __global__ void k_select(const uint64_t *__restrict__ word, const uint32_t *__re
   }
 }
 
-// Exclusive scan of u32 values with decoupled look-back; out is 64-bit.
-// The last tile writes out[n] = total and *total.
-__global__ __launch_bounds__(SCAN_BLOCK) void k_scan_excl(const uint32_t *__restrict__ in, uint64_t n,
-                                                          uint64_t *__restrict__ out, uint64_t *status,
-                                                          uint32_t *ticket, uint32_t epoch, uint32_t spin_limit,
-                                                          uint32_t *err, uint32_t *total) {
-  constexpr int WARPS = SCAN_BLOCK / 32;
-  __shared__ uint32_t s_w[WARPS * SCAN_ITEMS + 1];
-  __shared__ uint32_t s_tile, s_excl;
-  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  // blocked per thread: thread t owns [base + t*ITEMS, +ITEMS)
-  const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
-  uint32_t v[SCAN_ITEMS];
-  uint32_t sum = 0;
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; i++) {
-    v[i] = base + i < n ? in[base + i] : 0u;
-    sum += v[i];
-  }
-  const uint32_t incl = warp_incl_scan(sum);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 31) s_w[warp] = incl;
-  __syncthreads();
-  uint32_t wadd = 0, tile_total = 0;
-  for (int w = 0; w < WARPS; w++) {
-    if (w < warp) wadd += s_w[w];
-    tile_total += s_w[w];
-  }
-  const uint32_t excl_tile = tile_prefix(status, tile, tile_total, epoch, spin_limit, err, &s_excl);
-  uint64_t run = (uint64_t)excl_tile + wadd + incl - sum;
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; i++) {
-    if (base + i < n) out[base + i] = run;
-    run += v[i];
-  }
-  if ((uint64_t)(tile + 1) * SCAN_TILE >= n && threadIdx.x == 0) {
-    out[n] = (uint64_t)excl_tile + tile_total;
-    *total = excl_tile + tile_total;
-  }
-}
-
 // Unitig tables, one thread per node; the first node of each unitig writes
 // its entries.  off_by_v[h] = first output slot of the unitig headed by h.
 __global__ void k_unitig_offsets(const uint32_t *__restrict__ is_head, const uint64_t *__restrict__ uidx,

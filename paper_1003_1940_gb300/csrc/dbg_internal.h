@@ -97,6 +97,7 @@ struct dbg_graph {
   uint64_t num_nodes = 0, num_edges = 0, num_instances = 0;
   dbg::Allocator al;  // copy of the creating context's allocator
   int device = 0;
+  uint32_t edge_buckets = 1, node_buckets = 1;  // key ranges used (bucket path)
   dbg::DevBuf node_keys, edge_keys, src, dst, orient, mult, row_ptr, adj_nbr, adj_edge, adj_role;
 };
 
@@ -168,6 +169,21 @@ struct BuildInput {
   uint64_t total_bases;
   uint32_t k;
 };
+
+// Input of the bucket path (dbg_build_bucketed).
+struct BucketInput {
+  const char *reads;  // host or device
+  bool reads_on_device;
+  const uint32_t *d_lengths;
+  uint64_t n;
+  uint32_t k;
+};
+dbg_status build_bucketed_u64(dbg_ctx *ctx, const BucketInput &in, uint64_t budget, dbg_graph *g, uint32_t *eb,
+                              uint32_t *nb);
+dbg_status build_bucketed_u128(dbg_ctx *ctx, const BucketInput &in, uint64_t budget, dbg_graph *g, uint32_t *eb,
+                               uint32_t *nb);
+// estimated peak device bytes of one in-memory build
+uint64_t build_footprint(const uint32_t *lengths, uint64_t n, uint32_t k, bool lengths_on_host);
 
 dbg_status build_graph_u64(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g);
 dbg_status autotune_u64(dbg_ctx *ctx, uint64_t n, double *ms_keys, double *ms_pairs);

@@ -662,6 +662,49 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_rle(const K *__restrict__ keys, 
   }
 }
 
+// Exclusive scan of u32 values with decoupled look-back; out is 64-bit.
+// The last tile writes out[n] = total and *total.
+static __global__ __launch_bounds__(SCAN_BLOCK) void k_scan_excl(const uint32_t *__restrict__ in, uint64_t n,
+                                                          uint64_t *__restrict__ out, uint64_t *status,
+                                                          uint32_t *ticket, uint32_t epoch, uint32_t spin_limit,
+                                                          uint32_t *err, uint32_t *total) {
+  constexpr int WARPS = SCAN_BLOCK / 32;
+  __shared__ uint32_t s_w[WARPS * SCAN_ITEMS + 1];
+  __shared__ uint32_t s_tile, s_excl;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  // blocked per thread: thread t owns [base + t*ITEMS, +ITEMS)
+  const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; i++) {
+    v[i] = base + i < n ? in[base + i] : 0u;
+    sum += v[i];
+  }
+  const uint32_t incl = warp_incl_scan(sum);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  uint32_t wadd = 0, tile_total = 0;
+  for (int w = 0; w < WARPS; w++) {
+    if (w < warp) wadd += s_w[w];
+    tile_total += s_w[w];
+  }
+  const uint32_t excl_tile = tile_prefix(status, tile, tile_total, epoch, spin_limit, err, &s_excl);
+  uint64_t run = (uint64_t)excl_tile + wadd + incl - sum;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; i++) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+  if ((uint64_t)(tile + 1) * SCAN_TILE >= n && threadIdx.x == 0) {
+    out[n] = (uint64_t)excl_tile + tile_total;
+    *total = excl_tile + tile_total;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K5 edge ends (STEP-1 decoding + STEP-3 collection).  The unique key z is
 // the canonical (k+1)-mer; x = its first k bases, y = its last k bases.
@@ -733,7 +776,9 @@ __global__ void k_isolated(const uint64_t *__restrict__ packed, const uint64_t *
 }
 
 // ---------------------------------------------------------------------------
-// K6 node IDs (STEP-3) + adjacency rows (STEP-4).  Over the node records
+// K6 node IDs (STEP-3) + adjacency rows (STEP-4).  (base_v, base_slot) are
+// added to the IDs and adjacency slots written to src/dst and the adjacency
+// arrays, for a node-key range built after others.  Over the node records
 // sorted by key (stable, so edge ends precede isolated records within a
 // node and are in (e, role) order): node ID = number of run heads up to the
 // record minus one; adjacency slot = number of edge-end records before it.
@@ -746,7 +791,7 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_node_ids(
     uint64_t *__restrict__ row_ptr, uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
     uint32_t *__restrict__ adj_edge, uint8_t *__restrict__ adj_role, uint64_t *status_h, uint64_t *status_e,
     uint32_t *ticket, uint32_t epoch_h, uint32_t epoch_e, uint32_t spin_limit, uint32_t *err,
-    uint32_t *totals) {
+    uint32_t *totals, uint32_t base_v, uint64_t base_slot) {
   constexpr int WARPS = SCAN_BLOCK / 32;
   constexpr int TILE = SCAN_BLOCK * ITEMS;
   __shared__ uint32_t s_cnt_h[ITEMS * WARPS + 1], s_cnt_e[ITEMS * WARPS + 1];
@@ -784,17 +829,17 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_node_ids(
     const uint32_t slot = xe + re[i];
     if (head[i]) {
       node_keys[id] = key[i];
-      row_ptr[id] = slot;
+      row_ptr[id] = base_slot + slot;
     }
     if (end[i]) {
       const uint32_t e = val[i] >> 1, role = val[i] & 1u;
-      adj_edge[slot] = e;
-      adj_role[slot] = (uint8_t)role;
-      (role ? dst : src)[e] = id;
+      adj_edge[base_slot + slot] = e;
+      adj_role[base_slot + slot] = (uint8_t)role;
+      (role ? dst : src)[e] = base_v + id;
     }
   }
   if (base + TILE >= R && threadIdx.x == 0) {
-    row_ptr[xh + ch] = xe + ce;
+    row_ptr[xh + ch] = base_slot + xe + ce;
     totals[0] = xh + ch;
     totals[1] = xe + ce;
   }
@@ -811,5 +856,229 @@ static __global__ void k_adj_nbr(const uint32_t *__restrict__ adj_edge, const ui
 }
 
 // node keys as 1 or 2 words; row_ptr shrink copies are plain memcpy
+
+}  // namespace dbg
+
+namespace dbg {
+
+// ---------------------------------------------------------------------------
+// Key-range buckets (the bucket path of dbg_build_bucketed).  A key's prefix
+// is its top PREFIX_BITS bits (all its bits when it is shorter).
+// ---------------------------------------------------------------------------
+constexpr int PREFIX_BITS = 12;
+constexpr int PREFIX_BINS = 1 << PREFIX_BITS;
+
+template <class K>
+__device__ __forceinline__ uint32_t key_prefix(const K &key, int key_bits) {
+  const int pb = key_bits < PREFIX_BITS ? key_bits : PREFIX_BITS;
+  return KeyOps<K>::digit(key, key_bits - pb, pb);
+}
+
+// Histogram of the prefixes of the canonical (k+1)-mer keys (one warp per read).
+template <class K>
+__global__ __launch_bounds__(EMIT_BLOCK) void k_emit_prefix_hist(const uint64_t *__restrict__ packed,
+                                                                 const uint64_t *__restrict__ base_off,
+                                                                 const uint64_t *__restrict__ edge_off,
+                                                                 uint64_t n_reads, uint32_t k,
+                                                                 unsigned long long *__restrict__ hist) {
+  __shared__ uint32_t s_hist[PREFIX_BINS];
+  for (int i = threadIdx.x; i < PREFIX_BINS; i += EMIT_BLOCK) s_hist[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, m = (int)k + 1;
+  const uint64_t warps = (uint64_t)gridDim.x * (EMIT_BLOCK / 32);
+  for (uint64_t r = (uint64_t)blockIdx.x * (EMIT_BLOCK / 32) + (threadIdx.x >> 5); r < n_reads; r += warps) {
+    const uint64_t e0 = __ldg(edge_off + r), cnt = __ldg(edge_off + r + 1) - e0, p0 = __ldg(base_off + r);
+    for (uint64_t j = lane; j < cnt; j += 32) {
+      const K z = load_window<K>(packed, p0 + j, m);
+      atomicAdd(&s_hist[key_prefix(kmin(z, revcomp(z, m)), 2 * m)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < PREFIX_BINS; i += EMIT_BLOCK)
+    if (s_hist[i]) atomicAdd(hist + i, (unsigned long long)s_hist[i]);
+}
+
+// STEP-1 restricted to keys whose prefix lies in [lo, hi): the keys of one
+// bucket, appended in any order (the sort that follows orders them), with
+// the digit histograms of its radix passes.
+template <class K>
+__global__ __launch_bounds__(EMIT_BLOCK) void k_emit_range(const uint64_t *__restrict__ packed,
+                                                           const uint64_t *__restrict__ base_off,
+                                                           const uint64_t *__restrict__ edge_off, uint64_t n_reads,
+                                                           uint32_t k, uint32_t lo, uint32_t hi,
+                                                           K *__restrict__ keys, uint32_t *count, int passes,
+                                                           unsigned long long *__restrict__ hist) {
+  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK) s_hist[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, m = (int)k + 1;
+  const uint64_t warps = (uint64_t)gridDim.x * (EMIT_BLOCK / 32);
+  for (uint64_t r = (uint64_t)blockIdx.x * (EMIT_BLOCK / 32) + (threadIdx.x >> 5); r < n_reads; r += warps) {
+    const uint64_t e0 = __ldg(edge_off + r), cnt = __ldg(edge_off + r + 1) - e0, p0 = __ldg(base_off + r);
+    for (uint64_t j0 = 0; j0 < cnt; j0 += 32) {
+      const uint64_t j = j0 + lane;
+      K key = KeyOps<K>::zero();
+      bool in = false;
+      if (j < cnt) {
+        const K z = load_window<K>(packed, p0 + j, m);
+        key = kmin(z, revcomp(z, m));
+        const uint32_t pf = key_prefix(key, 2 * m);
+        in = pf >= lo && pf < hi;
+      }
+      const unsigned b = __ballot_sync(0xffffffffu, in);
+      if (!b) continue;
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(b));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (in) {
+        keys[base + __popc(b & ((1u << lane) - 1u))] = key;
+        for (int ps = 0; ps < passes; ps++)
+          atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(key, ps * RADIX_BITS, RADIX_BITS)], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK)
+    if (s_hist[i]) atomicAdd(hist + i, (unsigned long long)s_hist[i]);
+}
+
+// The two node keys (x^, y^) of an edge key, by STEP-1's table; orient.
+template <class K>
+__device__ __forceinline__ void edge_ends(const K &z, int k, K &s, K &d, uint32_t &orient) {
+  const K x = KeyOps<K>::shr(z, 2);
+  const K y = KeyOps<K>::mask_low(z, 2 * k);
+  const K xh = kmin(x, revcomp(x, k));
+  const K yh = kmin(y, revcomp(y, k));
+  const uint32_t o1 = !KeyOps<K>::eq(x, xh), o2 = !KeyOps<K>::eq(y, yh);
+  if (!KeyOps<K>::less(yh, xh)) {
+    s = xh; d = yh; orient = (o1 << 1) | o2;
+  } else {
+    s = yh; d = xh; orient = ((!o2) << 1) | (!o1);
+  }
+}
+
+// Edges of one bucket: key, multiplicity and orientation at offset e_base.
+template <class K>
+__global__ void k_edge_finish(const K *__restrict__ uniq, const uint32_t *__restrict__ headpos, uint64_t E, uint32_t k,
+                              K *__restrict__ edge_keys, uint32_t *__restrict__ mult, uint8_t *__restrict__ orient) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x) {
+    const K z = uniq[e];
+    K s, d;
+    uint32_t o;
+    edge_ends(z, (int)k, s, d, o);
+    edge_keys[e] = z;
+    orient[e] = (uint8_t)o;
+    mult[e] = headpos[e + 1] - headpos[e];
+  }
+}
+
+// Histogram of the prefixes of both node keys of every edge, and of the
+// k-mers of reads of length exactly k.
+template <class K>
+__global__ void k_node_prefix_hist(const K *__restrict__ edge_keys, uint64_t E, uint32_t k,
+                                   unsigned long long *__restrict__ hist) {
+  __shared__ uint32_t s_hist[PREFIX_BINS];
+  for (int i = threadIdx.x; i < PREFIX_BINS; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x) {
+    K s, d;
+    uint32_t o;
+    edge_ends(edge_keys[e], (int)k, s, d, o);
+    atomicAdd(&s_hist[key_prefix(s, 2 * (int)k)], 1u);
+    atomicAdd(&s_hist[key_prefix(d, 2 * (int)k)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < PREFIX_BINS; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(hist + i, (unsigned long long)s_hist[i]);
+}
+
+// 1 for every edge end (slot 2e + role) whose node key prefix is in [lo, hi).
+template <class K>
+__global__ void k_flag_ends(const K *__restrict__ edge_keys, uint64_t E, uint32_t k, uint32_t lo, uint32_t hi,
+                            uint32_t *__restrict__ flags) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x) {
+    K s, d;
+    uint32_t o;
+    edge_ends(edge_keys[e], (int)k, s, d, o);
+    const uint32_t ps = key_prefix(s, 2 * (int)k), pd = key_prefix(d, 2 * (int)k);
+    flags[2 * e] = ps >= lo && ps < hi;
+    flags[2 * e + 1] = pd >= lo && pd < hi;
+  }
+}
+
+// The flagged edge ends as node records, in (e, role) order (positions from
+// an exclusive scan of the flags), with the node-sort digit histograms.
+template <class K>
+__global__ void k_gather_ends(const K *__restrict__ edge_keys, uint64_t E, uint32_t k,
+                              const uint32_t *__restrict__ flags, const uint64_t *__restrict__ pos,
+                              K *__restrict__ rkeys, uint32_t *__restrict__ rvals, int passes,
+                              unsigned long long *__restrict__ hist) {
+  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t f0 = flags[2 * e], f1 = flags[2 * e + 1];
+    if (!f0 && !f1) continue;
+    K s, d;
+    uint32_t o;
+    edge_ends(edge_keys[e], (int)k, s, d, o);
+    for (int role = 0; role < 2; role++) {
+      if (!(role ? f1 : f0)) continue;
+      const K nk = role ? d : s;
+      const uint64_t p = pos[2 * e + role];
+      rkeys[p] = nk;
+      rvals[p] = (uint32_t)(e << 1) | (uint32_t)role;
+      for (int ps = 0; ps < passes; ps++)
+        atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(nk, ps * RADIX_BITS, RADIX_BITS)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(hist + i, (unsigned long long)s_hist[i]);
+}
+
+// Reads of length exactly k whose k-mer prefix is in [lo, hi): one record
+// each (payload REC_NONE), appended at rkeys + *slot.
+template <class K>
+__global__ void k_isolated_range(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ base_off,
+                                 const uint32_t *__restrict__ len, uint64_t n, uint32_t k, uint32_t lo, uint32_t hi,
+                                 K *__restrict__ rkeys, uint32_t *__restrict__ rvals, uint32_t *slot, int passes,
+                                 unsigned long long *__restrict__ hist) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+    if (len[r] != k) continue;
+    const K x = load_window<K>(packed, base_off[r], (int)k);
+    const K xh = kmin(x, revcomp(x, (int)k));
+    const uint32_t pf = key_prefix(xh, 2 * (int)k);
+    if (pf < lo || pf >= hi) continue;
+    const uint32_t i = atomicAdd(slot, 1u);
+    rkeys[i] = xh;
+    rvals[i] = REC_NONE;
+    for (int ps = 0; ps < passes; ps++)
+      atomicAdd(hist + ps * RADIX + KeyOps<K>::digit(xh, ps * RADIX_BITS, RADIX_BITS), 1ull);
+  }
+}
+
+// Copies a chunk of ASCII reads and packs it into the packed array at base
+// position `at` (a multiple of 32).
+static __global__ void k_pack_at(const uint8_t *__restrict__ ascii, uint64_t total, uint64_t *__restrict__ packed,
+                          uint64_t word0, uint32_t *err) {
+  const uint64_t nwords = (total + 31) / 32;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t word = 0;
+    bool ok = true;
+    for (int i = 0; i < 32; i++) {
+      const uint64_t b = w * 32 + i;
+      uint32_t code = 0;
+      if (b < total) {
+        const uint8_t c = ascii[b];
+        ok = ok && (c == 'A' || c == 'C' || c == 'G' || c == 'T');
+        code = ((c >> 1) ^ (c >> 2)) & 3u;
+      }
+      word = (word << 2) | code;
+    }
+    packed[word0 + w] = word;
+    if (!ok) atomicOr(err, ERR_BAD_BASE);
+  }
+}
 
 }  // namespace dbg

@@ -15,9 +15,9 @@ import numpy as np
 
 from . import build_lib
 
-DBG_OK, DBG_EINVAL, DBG_ENOMEM, DBG_ECUDA, DBG_ETIMEOUT, DBG_ECANCELLED, DBG_EOVERFLOW = range(7)
+DBG_OK, DBG_EINVAL, DBG_ENOMEM, DBG_ECUDA, DBG_ETIMEOUT, DBG_ECANCELLED, DBG_EOVERFLOW, DBG_EAGAIN = range(8)
 _STATUS = {0: "DBG_OK", 1: "DBG_EINVAL", 2: "DBG_ENOMEM", 3: "DBG_ECUDA", 4: "DBG_ETIMEOUT",
-           5: "DBG_ECANCELLED", 6: "DBG_EOVERFLOW"}
+           5: "DBG_ECANCELLED", 6: "DBG_EOVERFLOW", 7: "DBG_EAGAIN"}
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -398,3 +398,147 @@ def dbg_autotune(ctx: Context, n: int = 0, cache_path: str | None = None) -> dic
     ms = (ctypes.c_double * 64)()
     _check(_lib.dbg_autotune(ctx.handle, n, cache_path.encode() if cache_path else None, ms), "dbg_autotune")
     return {kd: [ms[kd * 16 + v] for v in range(dbg_sort_variant_count(kd))] for kd in range(4)}
+
+
+# ---------------------------------------------------------------------------
+# many constructions at once: batch, server, bucket path
+# ---------------------------------------------------------------------------
+class dbg_readset(ctypes.Structure):
+    _fields_ = [("reads", ctypes.c_void_p), ("lengths", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("k", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class dbg_server_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("device", ctypes.c_int32), ("workers", ctypes.c_uint32),
+                ("spin_limit", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
+                ("sort_variant", ctypes.c_uint32 * 4), ("reserved", ctypes.c_uint32 * 8)]
+
+
+class dbg_request_stats(ctypes.Structure):
+    _fields_ = [("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("latency_s", ctypes.c_double),
+                ("footprint", ctypes.c_uint64), ("bucketed", ctypes.c_uint32)]
+
+
+DBG_REQ_BUCKETED = 1
+_SIGNATURES += [
+    ("dbg_server_options_init", None, [_P]),
+    ("dbg_server_create", ctypes.c_int, [_P, _P]),
+    ("dbg_server_destroy", None, [_P]),
+    ("dbg_server_budget", ctypes.c_uint64, [_P]),
+    ("dbg_submit", ctypes.c_int, [_P, _P, _P]),
+    ("dbg_poll", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P, _P]),
+    ("dbg_build_batch", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint32, _P]),
+    ("dbg_build_bucketed", ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _P]),
+    ("dbg_graph_buckets", None, [_P, _P, _P]),
+]
+
+
+def _bind_late():
+    lib = load()
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def _readset(reads, lengths, k, flags=0):
+    rp, rkeep = _ptr(reads)
+    lp, lkeep = _ptr(lengths)
+    n = len(lengths) if not hasattr(lengths, "numel") else int(lengths.numel())
+    rs = dbg_readset(ctypes.c_void_p(rp), ctypes.c_void_p(lp), n, k, flags)
+    return rs, (rkeep, lkeep)
+
+
+class Server:
+    """dbg_server: worker threads with one context and stream each."""
+
+    def __init__(self, device=None, workers=4, mem_budget=0, spin_limit=0, sort_variant=(0, 0, 0, 0)):
+        import torch
+        lib = _bind_late()
+        o = dbg_server_options()
+        lib.dbg_server_options_init(ctypes.byref(o))
+        o.device = torch.cuda.current_device() if device is None else device
+        o.workers = workers
+        o.mem_budget = mem_budget
+        o.spin_limit = spin_limit
+        for i, v in enumerate(sort_variant):
+            o.sort_variant[i] = v
+        h = ctypes.c_void_p()
+        _check(lib.dbg_server_create(ctypes.byref(h), ctypes.byref(o)), "dbg_server_create")
+        self.handle = h
+        self._inputs = {}
+
+    def budget(self) -> int:
+        return int(_lib.dbg_server_budget(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.dbg_server_destroy(self.handle)
+            self.handle = None
+            self._inputs.clear()
+
+    def __del__(self):
+        self.close()
+
+
+def dbg_server_create(**kw) -> Server:
+    return Server(**kw)
+
+
+def dbg_server_destroy(srv: Server):
+    srv.close()
+
+
+def dbg_submit(srv: Server, reads, lengths, k: int, flags: int = 0) -> int:
+    rs, keep = _readset(reads, lengths, k, flags)
+    t = ctypes.c_uint64(0)
+    _check(_lib.dbg_submit(srv.handle, ctypes.byref(rs), ctypes.byref(t)), "dbg_submit")
+    srv._inputs[int(t.value)] = keep  # borrowed by the library until polled
+    return int(t.value)
+
+
+def dbg_poll(srv: Server, ticket: int, wait: bool = True):
+    """(Graph, stats dict), or None while the request runs (wait=False)."""
+    out = ctypes.c_void_p()
+    st = dbg_request_stats()
+    rc = _lib.dbg_poll(srv.handle, ticket, 1 if wait else 0, ctypes.byref(out), ctypes.byref(st))
+    if rc == DBG_EAGAIN:
+        return None
+    srv._inputs.pop(ticket, None)
+    _check(rc, "dbg_poll")
+    stats = {"queue_s": st.queue_s, "run_s": st.run_s, "latency_s": st.latency_s,
+             "footprint": int(st.footprint), "bucketed": bool(st.bucketed)}
+    return Graph(srv, out), stats
+
+
+def dbg_build_batch(ctx: Context, sets, workers: int = 0) -> list:
+    """sets: list of (reads, lengths, k); one Graph per set."""
+    _bind_late()
+    arr = (dbg_readset * max(1, len(sets)))()
+    keep = []
+    for i, (r, l, k) in enumerate(sets):
+        rs, kp = _readset(r, l, k)
+        arr[i] = rs
+        keep.append(kp)
+    outs = (ctypes.c_void_p * max(1, len(sets)))()
+    _check(_lib.dbg_build_batch(ctx.handle, arr, len(sets), workers, outs), "dbg_build_batch")
+    return [Graph(ctx, ctypes.c_void_p(outs[i])) for i in range(len(sets))]
+
+
+def dbg_build_bucketed(ctx: Context, reads, lengths, k: int, mem_budget: int = 0) -> Graph:
+    _bind_late()
+    rp, rkeep = _ptr(reads)
+    lp, lkeep = _ptr(lengths)
+    n = len(lengths) if not hasattr(lengths, "numel") else int(lengths.numel())
+    out = ctypes.c_void_p()
+    _check(_lib.dbg_build_bucketed(ctx.handle, ctypes.c_void_p(rp), ctypes.c_void_p(lp), n, k, mem_budget,
+                                   ctypes.byref(out)), "dbg_build_bucketed")
+    del rkeep, lkeep
+    return Graph(ctx, out)
+
+
+def dbg_graph_buckets(g: Graph) -> tuple[int, int]:
+    a, b = ctypes.c_uint32(0), ctypes.c_uint32(0)
+    _lib.dbg_graph_buckets(g.handle, ctypes.byref(a), ctypes.byref(b))
+    return int(a.value), int(b.value)
