@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle sample time")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (profiling captures only)")
+    ap.add_argument("--mode", choices=["build", "batched", "served"], default="build",
+                    help="build: the large workload (default); batched: 256 read sets, batch vs one at a "
+                         "time; served: Poisson request stream through the server")
+    ap.add_argument("--sets", type=int, default=256, help="read sets of the batched/served workloads")
+    ap.add_argument("--workers", type=int, default=8)
     return ap.parse_args()
 
 
@@ -368,10 +373,148 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# batched and served modes (reported beside the main line)
+# ---------------------------------------------------------------------------
+def batched_inputs(args):
+    import torch
+    specs = readgen.batched_specs(args.sets)
+    sets = []
+    for sp in specs:
+        r, l = readgen.generate(sp)
+        sets.append((torch.from_numpy(r).cuda(), torch.from_numpy(l.view(np.int32)).cuda(), sp.k,
+                     int(np.maximum(l.astype(np.int64) - sp.k, 0).sum())))
+    torch.cuda.synchronize()
+    return specs, sets
+
+
+def run_batched(args):
+    import torch
+    from paper_1003_1940_gb300 import build_lib, dbg
+    build_lib.build()
+    dbg.load()
+    specs, sets = batched_inputs(args)
+    N = sum(s[3] for s in sets)
+    ctx = dbg.Context()
+    dbg.dbg_autotune(ctx)
+    trip = [(r, l, k) for r, l, k, _ in sets]
+    # warm-up: a few sets both ways
+    for g in dbg.dbg_build_batch(ctx, trip[:8], workers=args.workers):
+        g.free()
+    for r, l, k in trip[:8]:
+        dbg.dbg_build(ctx, r, l, k).free()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for r, l, k in trip:
+        dbg.dbg_build(ctx, r, l, k).free()
+    torch.cuda.synchronize()
+    one = time.perf_counter() - t
+    t = time.perf_counter()
+    graphs = dbg.dbg_build_batch(ctx, trip, workers=args.workers)
+    torch.cuda.synchronize()
+    bat = time.perf_counter() - t
+    for g in graphs:
+        g.free()
+    print(json.dumps({
+        "metric": METRIC + " (batched vs one-at-a-time)", "value": N / bat, "unit": UNIT,
+        "one_at_a_time": N / one, "speedup": one / bat, "batched_s": bat, "one_at_a_time_s": one,
+        "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": f"{len(sets)} read sets: genome log-uniform 10 kbp-5 Mbp, coverage U[10,60], "
+                               f"L in {{36,75,100,150}}, errors U[0,1%], k in {{21,31}}",
+                   "edge_instances": N, "workers": args.workers,
+                   "largest_set_instances": max(s[3] for s in sets)}}))
+
+
+def run_served(args):
+    import threading as th
+    import torch
+    from paper_1003_1940_gb300 import build_lib, dbg
+    build_lib.build()
+    dbg.load()
+    specs, sets = batched_inputs(args)
+    ctx = dbg.Context()
+    dbg.dbg_autotune(ctx)
+    variants = [dbg.dbg_sort_variant_get(ctx, kd) for kd in range(4)]
+    # capacity: a closed loop over the whole set list
+    srv = dbg.Server(workers=args.workers, sort_variant=variants)
+    t = time.perf_counter()
+    ts = [dbg.dbg_submit(srv, r, l, k) for r, l, k, _ in sets]
+    for x in ts:
+        dbg.dbg_poll(srv, x)[0].free()
+    cap = len(sets) / (time.perf_counter() - t)
+    # one larger request: the 15 M-read workload, through the bucket path
+    big_spec = readgen.large_spec(args.scale)
+    big_r, big_l = readgen.generate(big_spec)
+    big_r, big_l = torch.from_numpy(big_r).cuda(), torch.from_numpy(big_l.view(np.int32)).cuda()
+    out = {}
+    for load in (0.5, 0.8, 1.0):
+        rate = load * cap
+        arrivals = readgen.poisson_arrivals(rate, 2 * len(sets), seed=4)
+        order = np.random.default_rng(4).integers(0, len(sets), size=len(arrivals))
+        lat, tickets = [], []
+        done_n = [0]
+        t0 = time.perf_counter()
+        lock = th.Lock()
+
+        def poller():
+            while True:
+                with lock:
+                    if not tickets:
+                        if done_n[0] < 0:
+                            return
+                        item = None
+                    else:
+                        item = tickets.pop(0)
+                if item is None:
+                    time.sleep(0.0005)
+                    continue
+                g, st = dbg.dbg_poll(srv, item)
+                lat.append(st["latency_s"])
+                g.free()
+
+        pt = th.Thread(target=poller)
+        pt.start()
+        N = 0
+        big_t = None
+        for i, (a, j) in enumerate(zip(arrivals, order)):
+            while time.perf_counter() - t0 < a:
+                time.sleep(0.0002)
+            r, l, k, ni = sets[j]
+            tk = dbg.dbg_submit(srv, r, l, k)
+            N += ni
+            with lock:
+                tickets.append(tk)
+            if load == 0.8 and i == len(arrivals) // 2:
+                big_t = dbg.dbg_submit(srv, big_r, big_l, big_spec.k, flags=dbg.DBG_REQ_BUCKETED)
+        with lock:
+            done_n[0] = -1
+        pt.join()
+        big = None
+        if big_t is not None:
+            g, st = dbg.dbg_poll(srv, big_t)
+            big = {"latency_s": st["latency_s"], "bucketed": st["bucketed"],
+                   "edge_instances": big_spec.raw_edges, "edge_ranges": dbg.dbg_graph_buckets(g)[0]}
+            g.free()
+            N += big_spec.raw_edges
+        span = time.perf_counter() - t0
+        lat = np.array(lat)
+        out[str(load)] = {"rate_per_s": rate, "requests": len(arrivals), "throughput": N / span,
+                          "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                          "big_request": big}
+    srv.close()
+    print(json.dumps({"metric": METRIC + " (served, Poisson arrivals)", "unit": UNIT,
+                      "capacity_sets_per_s": cap, "loads": out, "workers": args.workers,
+                      "data": "synthetic", "n_gpus": 1}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "batched":
+        run_batched(args)
+    elif args.mode == "served":
+        run_served(args)
     else:
         run_ours(args)
 
