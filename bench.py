@@ -158,14 +158,29 @@ def dist_setup(args):
     return ws, rank, local
 
 
-def max_over_ranks(x, ws):
+def _reduce(x, ws, op):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, ws):
+    import torch.distributed as dist
+    return x if ws == 1 else _reduce(x, ws, dist.ReduceOp.MAX)
+
+
+def job_rate(units_per_rank, ms_per_rank, ws):
+    """Whole-job throughput of replicas: all units of all ranks over the
+    slowest rank's time (weak scaling; no data-path collective)."""
+    import torch.distributed as dist
+    units = units_per_rank if ws == 1 else _reduce(units_per_rank, ws, dist.ReduceOp.SUM)
+    ms = max_over_ranks(ms_per_rank, ws)
+    return units / (ms / 1000.0), ms
 
 
 def barrier(ws):
@@ -290,8 +305,7 @@ def run_ours(args):
     launches = dbg.dbg_launch_count(ctx) - launches0
     prof = dbg.dbg_profile_read(ctx)
     dbg.dbg_profile_enable(ctx, False)
-    ms_max = max_over_ranks(ms, ws)
-    value = N * args.steps * ws / (ms_max / 1000.0)
+    value, ms_max = job_rate(N * args.steps, ms, ws)
 
     peak, peak_kind = load_peaks()
     srt = prof.get("sort_edges", {"launches": 0, "ms": 0.0, "bytes": 0.0})

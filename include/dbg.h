@@ -305,6 +305,16 @@ int32_t dbg_sort_variant_get(const dbg_ctx *ctx, uint32_t kind);
 dbg_status dbg_autotune(dbg_ctx *ctx, uint64_t n, const char *cache_path, double *ms_out);
 
 /* ----------------------------------------------------------------------
+ * Failure detection.  Every device-side wait of the library (decoupled
+ * look-back, TMA completion) spins at most spin_limit times, then records
+ * DBG_ETIMEOUT in the context's device error word and returns; the call
+ * reports it and the context stays usable.  dbg_selftest_wait runs one such
+ * wait on a status word that nothing writes, with the given limit
+ * (1..2^20), so the path can be tested: it returns DBG_ETIMEOUT.
+ * -------------------------------------------------------------------- */
+dbg_status dbg_selftest_wait(dbg_ctx *ctx, uint32_t spin_limit);
+
+/* ----------------------------------------------------------------------
  * Profiling (tracing).  When enabled, the context brackets every kernel it
  * launches with CUDA events on its stream and accumulates, per stage, the
  * launches, device time and algorithmic bytes (the bytes the stage must

@@ -464,6 +464,29 @@ void dbg_graph_buckets(const dbg_graph *g, uint32_t *edge_ranges, uint32_t *node
   if (node_ranges) *node_ranges = g ? g->node_buckets : 0;
 }
 
+namespace dbg {
+// one look-back wait on tile 0's word, which nothing writes in this epoch
+__global__ void k_selftest_wait(uint64_t *status, uint32_t epoch, uint32_t spin_limit, uint32_t *err) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) lookback_exclusive(status, 1, 1, epoch, spin_limit, err);
+}
+}  // namespace dbg
+
+dbg_status dbg_selftest_wait(dbg_ctx *ctx, uint32_t spin_limit) {
+  if (!ctx || spin_limit == 0 || spin_limit > (1u << 20)) {
+    set_error("spin_limit must be in [1, 2^20]");
+    return DBG_EINVAL;
+  }
+  DeviceScope scope(ctx->device);
+  DBG_TRY(ensure_status(ctx, 2));
+  uint32_t epoch;
+  DBG_TRY(next_epoch(ctx, &epoch));
+  DBG_LAUNCH(ctx, ST_COPIES, 0.0, k_selftest_wait<<<1, 32, 0, ctx->stream>>>(ctx->d_status, epoch, spin_limit, ctx->d_err));
+  DBG_CUDA_TRY(cudaGetLastError());
+  DBG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  prof_resolve(ctx);
+  return check_device_error(ctx);
+}
+
 uint32_t dbg_graph_k(const dbg_graph *g) { return g ? g->k : 0; }
 uint32_t dbg_graph_key_words(const dbg_graph *g) { return g ? g->key_words : 0; }
 uint64_t dbg_graph_num_nodes(const dbg_graph *g) { return g ? g->num_nodes : 0; }

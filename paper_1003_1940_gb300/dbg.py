@@ -430,6 +430,7 @@ _SIGNATURES += [
     ("dbg_build_batch", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint32, _P]),
     ("dbg_build_bucketed", ctypes.c_int, [_P, _P, _P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _P]),
     ("dbg_graph_buckets", None, [_P, _P, _P]),
+    ("dbg_selftest_wait", ctypes.c_int, [_P, ctypes.c_uint32]),
 ]
 
 
@@ -542,3 +543,24 @@ def dbg_graph_buckets(g: Graph) -> tuple[int, int]:
     a, b = ctypes.c_uint32(0), ctypes.c_uint32(0)
     _lib.dbg_graph_buckets(g.handle, ctypes.byref(a), ctypes.byref(b))
     return int(a.value), int(b.value)
+
+
+class _DeviceArray:
+    """Zero-copy view of one of a graph's device arrays (for torch.as_tensor)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+def device_tensor(g: Graph, field: str, n: int, typestr: str):
+    """torch view of the graph array `field` of dbg_graph_view (no copy;
+    valid while the graph lives).  typestr: numpy-style, e.g. '<u8', '<u4', '|u1'."""
+    import torch
+    v = dbg_graph_device_view(g)
+    return torch.as_tensor(_DeviceArray(int(getattr(v, field)), n, typestr), device="cuda")
+
+
+def dbg_selftest_wait(ctx: Context, spin_limit: int) -> int:
+    """Runs one bounded device wait that cannot succeed; returns the status."""
+    _bind_late()
+    return int(_lib.dbg_selftest_wait(ctx.handle, spin_limit))

@@ -1,0 +1,148 @@
+"""Parity at the benchmark's full size: the 50 Mbp repeat workload (15 M
+reads x 100 bp, k = 31, 1.035 G edge instances), built with the autotuned
+launch configuration the benchmark uses.
+
+The oracle cannot build this graph in seconds, so: every output is checked
+against properties that hold at any size (on the GPU), and the multiplicities
+of sampled edges -- and the absence of sampled non-edges -- are computed one
+by one by the oracle's scan over all reads."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import strings_model as sm
+from paper_1003_1940_gb300 import readgen
+
+pytestmark = pytest.mark.gpu
+
+K = 31
+
+
+def kmer_int(s: str) -> int:
+    v = 0
+    for c in s:
+        v = (v << 2) | "ACGT".index(c)
+    return v
+
+
+@pytest.fixture(scope="module")
+def built():
+    import torch
+    from paper_1003_1940_gb300 import dbg
+    dbg.load()
+    spec = readgen.large_spec()
+    reads, lengths = readgen.generate(spec)
+    ctx = dbg.Context()
+    dbg.dbg_autotune(ctx)
+    g = dbg.dbg_build(ctx, torch.from_numpy(reads).cuda(), torch.from_numpy(lengths.view(np.int32)).cuda(), K)
+    return dbg, ctx, g, reads, lengths
+
+
+def test_full_size_invariants(built):
+    import torch
+    dbg, ctx, g, reads, lengths = built
+    V, E, N = dbg.dbg_graph_num_nodes(g), dbg.dbg_graph_num_edges(g), dbg.dbg_graph_num_instances(g)
+    assert N == 15_000_000 * (100 - K)
+    t = lambda f, n, ty: dbg.device_tensor(g, f, n, ty)
+    keys = t("edge_keys", E, "<u8").view(torch.int64)
+    nodes = t("node_keys", V, "<u8").view(torch.int64)
+    mult = t("mult", E, "<u4").to(torch.int64)
+    src = t("src", E, "<u4").to(torch.int64)
+    dst = t("dst", E, "<u4").to(torch.int64)
+    orient = t("orient", E, "|u1").to(torch.int64)
+    row = t("row_ptr", V + 1, "<u8").view(torch.int64)
+    nbr = t("adj_nbr", 2 * E, "<u4").to(torch.int64)
+    aed = t("adj_edge", 2 * E, "<u4").to(torch.int64)
+    aro = t("adj_role", 2 * E, "|u1").to(torch.int64)
+    # multiplicities add up to the edge instances; every edge occurs
+    assert int(mult.sum()) == N and int(mult.min()) >= 1
+    # keys (64 bits used at k = 31: compare as unsigned by flipping the sign bit)
+    flip = lambda x: x ^ torch.iinfo(torch.int64).min
+    assert bool((flip(keys[1:]) > flip(keys[:-1])).all())
+    assert bool((nodes[1:] > nodes[:-1]).all())  # 62-bit node keys are non-negative
+    assert bool((src <= dst).all()) and int(dst.max()) < V
+    # each edge joins the canonical forms of its key's first and last k
+    # bases; o = 1 where the k-mer read there is the reverse complement
+    mask = (1 << (2 * K)) - 1
+    x = (keys >> 2) & mask
+    y = keys & mask
+
+    def revcomp(v):
+        r = v ^ mask
+        for sh, m in ((2, 0x3333333333333333), (4, 0x0F0F0F0F0F0F0F0F), (8, 0x00FF00FF00FF00FF),
+                      (16, 0x0000FFFF0000FFFF), (32, 0x00000000FFFFFFFF)):
+            r = ((r >> sh) & m) | ((r & m) << sh)
+        return (r >> (64 - 2 * K)) & mask
+
+    xh, yh = torch.minimum(x, revcomp(x)), torch.minimum(y, revcomp(y))
+    a1, a2 = (x != xh).to(torch.int64), (y != yh).to(torch.int64)
+    fwd = xh <= yh
+    want_s = torch.where(fwd, xh, yh)
+    want_d = torch.where(fwd, yh, xh)
+    want_o = torch.where(fwd, a1 * 2 + a2, (1 - a2) * 2 + (1 - a1))
+    assert bool((nodes[src] == want_s).all()) and bool((nodes[dst] == want_d).all())
+    assert bool((orient == want_o).all())
+    del x, y, xh, yh, a1, a2, fwd, want_s, want_d, want_o
+    # adjacency rows: the edge ends of each node, in (edge, role) order
+    assert int(row[0]) == 0 and int(row[-1]) == 2 * E
+    deg = row[1:] - row[:-1]
+    owner = torch.repeat_interleave(torch.arange(V, device="cuda"), deg)
+    assert bool((torch.where(aro == 0, src[aed], dst[aed]) == owner).all())
+    assert bool((torch.where(aro == 0, dst[aed], src[aed]) == nbr).all())
+    order = aed * 2 + aro
+    same_row = owner[1:] == owner[:-1]
+    assert bool((order[1:][same_row] > order[:-1][same_row]).all())
+    # every node is an edge end (all reads are longer than k)
+    assert bool((deg > 0).all())
+
+
+def test_full_size_sampled_multiplicities(built):
+    dbg, ctx, g, reads, lengths = built
+    rng = np.random.default_rng(2024)
+    E = dbg.dbg_graph_num_edges(g)
+    keys = dbg.dbg_graph_edges(g)
+    ekeys, mult = keys["keys"][:, 0], keys["mult"]
+    # sampled instances: (read, position) pairs of the input
+    picks = rng.integers(0, len(lengths), size=1500)
+    offs = rng.integers(0, 100 - K, size=1500)
+    queries = [reads[r * 100 + j:r * 100 + j + K + 1].tobytes().decode() for r, j in zip(picks, offs)]
+    # and random (k+1)-mers, nearly all absent from the reads
+    letters = np.frombuffer(b"ACGT", dtype=np.uint8)
+    queries += [letters[rng.integers(0, 4, size=K + 1)].tobytes().decode() for _ in range(500)]
+    want = oracle.count_kplus1(reads, lengths, K, queries)
+    can = np.array([kmer_int(sm.canonical(q)) for q in queries], dtype=np.uint64)
+    pos = np.searchsorted(ekeys, can)
+    found = (pos < E) & (ekeys[np.minimum(pos, E - 1)] == can)
+    got = np.where(found, mult[np.minimum(pos, E - 1)], 0).astype(np.uint64)
+    np.testing.assert_array_equal(got, want)
+    assert int((want[:1500] > 0).sum()) == 1500
+
+
+def test_full_size_compaction_invariants(built):
+    import torch
+    dbg, ctx, g, reads, lengths = built
+    V = dbg.dbg_graph_num_nodes(g)
+    u = dbg.dbg_compact(ctx, g)
+    U = dbg.dbg_unitigs_count(u)
+    res = dbg.dbg_unitigs_get(u)
+    node_off, nodes = res["node_off"], res["nodes"]
+    assert int(node_off[-1]) == V
+    ids = torch.from_numpy(nodes.view(np.int64) >> 1).cuda()
+    counts = torch.bincount(ids, minlength=V)
+    assert bool((counts == 1).all())  # every node in exactly one unitig
+    assert len(res["seq"]) == V + U * (K - 1)
+    heads = ids[torch.from_numpy(node_off[:-1].view(np.int64)).cuda()]
+    assert bool((heads[1:] > heads[:-1]).all())  # ordered by first node
+    # spelled strings: sample unitigs and check them against the node keys
+    rng = np.random.default_rng(7)
+    nk = dbg.dbg_graph_nodes(g)[:, 0]
+    for ui in rng.integers(0, U, size=300):
+        s = res["seq"][res["seq_off"][ui]:res["seq_off"][ui + 1]].decode()
+        lst = nodes[node_off[ui]:node_off[ui + 1]]
+        assert len(s) == len(lst) + K - 1
+        for i, x in enumerate(lst):
+            km = s[i:i + K]
+            assert kmer_int(sm.canonical(km)) == int(nk[int(x) >> 1])
+            assert (km == sm.canonical(km)) == ((int(x) & 1) == 0)

@@ -186,3 +186,14 @@ def test_autotune_and_cache(dbg, tmp_path):
     assert [dbg.dbg_sort_variant_get(c2, kd) for kd in range(4)] == chosen
     reads, lengths = readgen.generate(readgen.tiny_spec())
     check_parity(dbg, c2, reads, lengths, 21)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(dbg, ctx):
+    """A device wait on a flag that nothing sets gives up after its spin
+    limit with DBG_ETIMEOUT; the same context then builds normally."""
+    import time
+    t = time.perf_counter()
+    assert dbg.dbg_selftest_wait(ctx, 2000) == dbg.DBG_ETIMEOUT
+    assert time.perf_counter() - t < 5.0
+    reads, lengths = readgen.generate(readgen.tiny_spec())
+    check_parity(dbg, ctx, reads, lengths, 21)

@@ -1,0 +1,38 @@
+"""The multi-GPU bench path runs independent replicas: each rank builds its
+own graph and the job's value is all ranks' edge instances over the slowest
+rank's time.  Checked with two gloo ranks on the CPU."""
+import os
+import socket
+
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import bench
+    # rank r built 1000 * (r + 1) units in 100 * (r + 1) ms
+    rate, ms = bench.job_rate(1000.0 * (rank + 1), 100.0 * (rank + 1), ws)
+    out[rank] = (rate, ms, bench.max_over_ranks(float(rank), ws))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_aggregation_two_ranks():
+    ws, port = 2, _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(ws, port, out), nprocs=ws, join=True)
+        for r in range(ws):
+            rate, ms, mx = out[r]
+            assert ms == 200.0 and mx == 1.0
+            assert abs(rate - 3000.0 / 0.2) < 1e-6
