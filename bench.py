@@ -52,6 +52,8 @@ def parse():
                          "time; served: Poisson request stream through the server")
     ap.add_argument("--sets", type=int, default=256, help="read sets of the batched/served workloads")
     ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--sort-variant", default="", help="a,b,c,d: fixed radix variants per key kind instead "
+                                                        "of the autotuner (profiling captures)")
     return ap.parse_args()
 
 
@@ -282,7 +284,12 @@ def run_ours(args):
         u.free()
         g.free()
 
-    tune_ms = dbg.dbg_autotune(ctx)
+    if args.sort_variant:
+        tune_ms = {}
+        for kd, v in enumerate(int(x) for x in args.sort_variant.split(",")):
+            dbg.dbg_sort_variant_set(ctx, kd, v)
+    else:
+        tune_ms = dbg.dbg_autotune(ctx)
     variants = {kd: dbg.dbg_sort_variant_name(kd, dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(4)}
     for _ in range(args.warmup):
         step()

@@ -295,8 +295,8 @@ dbg_status dbg_rle_u64_noalloc(const uint64_t *keys, uint64_t n, uint64_t *uniq,
  * (0 = 2^25; 128-bit kinds use n / 2) and keeps the fastest of each kind in
  * the context.  cache_path (may be NULL) names a text file of choices keyed
  * by GPU name and SM count: a matching line is used instead of timing, and
- * a new result is appended.  ms_out (may be NULL) receives 4 x 16 pass
- * times in ms (kind-major).
+ * a new result is appended.  ms_out (may be NULL) receives 4 x 32 pass
+ * times in ms (kind-major; at most 32 variants per kind).
  * -------------------------------------------------------------------- */
 uint32_t dbg_sort_variant_count(uint32_t kind);
 const char *dbg_sort_variant_name(uint32_t kind, uint32_t variant);

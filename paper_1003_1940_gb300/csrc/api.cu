@@ -640,8 +640,8 @@ dbg_status dbg_autotune(dbg_ctx *ctx, uint64_t n, const char *cache_path, double
   }
   if (n == 0) n = 1ull << 25;
   double *m = ms_out;
-  dbg_status st = autotune_u64(ctx, n, m ? m : nullptr, m ? m + 16 : nullptr);
-  if (st == DBG_OK) st = autotune_u128(ctx, n / 2, m ? m + 32 : nullptr, m ? m + 48 : nullptr);
+  dbg_status st = autotune_u64(ctx, n, m ? m : nullptr, m ? m + 32 : nullptr);
+  if (st == DBG_OK) st = autotune_u128(ctx, n / 2, m ? m + 64 : nullptr, m ? m + 96 : nullptr);
   cudaStreamSynchronize(ctx->stream);
   prof_resolve(ctx);
   if (st != DBG_OK) return st;

@@ -30,12 +30,13 @@ struct SortVariant {
   SortLaunchFn launch;
 };
 
-template <class K, bool V, int BLOCK, int ITEMS, int RANK, bool TMA, int MINB, bool EARLY>
+template <class K, bool V, int BLOCK, int ITEMS, int RANK, bool TMA, int MINB, bool EARLY, bool DIRECT = false>
 void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *vin, uint32_t *vout, uint64_t n,
                      int shift, const uint64_t *digit_base, uint32_t epoch) {
-  auto kern = k_onesweep<K, V, BLOCK, ITEMS, RANK, TMA, MINB, EARLY>;
+  auto kern = k_onesweep<K, V, BLOCK, ITEMS, RANK, TMA, MINB, EARLY, DIRECT>;
   constexpr size_t smem = sizeof(OnesweepSmem<K, V, BLOCK, ITEMS>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   const uint64_t tiles = (n + BLOCK * ITEMS - 1) / (BLOCK * ITEMS);
   kern<<<(unsigned)tiles, BLOCK, smem, ctx->stream>>>(static_cast<const K *>(kin), static_cast<K *>(kout), vin,
                                                       vout, n, shift, digit_base, ctx->d_status, ctx->d_counters,
@@ -46,6 +47,8 @@ void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *
   SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, false> }
 #define DBG_SVE(K, V, B, I, R, T, M, NAME) \
   SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, true> }
+#define DBG_SVD(K, V, B, I, R, T, M, E, NAME) \
+  SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, E, true> }
 
 // kinds: 0 = 64-bit keys, 1 = 64-bit keys + payload, 2 = 128-bit keys,
 // 3 = 128-bit keys + payload
@@ -65,6 +68,14 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SVE(uint64_t, false, 256, 12, RANK_MATCH, true, 3, "256x12 match tma occ3 early"),
         DBG_SVE(uint64_t, false, 256, 8, RANK_ATOMIC, true, 4, "256x8 atomic tma occ4 early"),
         DBG_SVE(uint64_t, false, 256, 16, RANK_ATOMIC, true, 2, "256x16 atomic tma occ2 early"),
+        DBG_SV(uint64_t, false, 256, 8, RANK_ATOMIC, true, 4, "256x8 atomic tma occ4"),
+        DBG_SV(uint64_t, false, 256, 10, RANK_ATOMIC, true, 3, "256x10 atomic tma occ3"),
+        DBG_SV(uint64_t, false, 384, 8, RANK_ATOMIC, true, 2, "384x8 atomic tma occ2"),
+        DBG_SV(uint64_t, false, 512, 6, RANK_ATOMIC, true, 2, "512x6 atomic tma occ2"),
+        DBG_SVD(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, false, "256x12 atomic tma occ3 direct"),
+        DBG_SVD(uint64_t, false, 256, 12, RANK_ATOMIC, false, 3, false, "256x12 atomic ldg occ3 direct"),
+        DBG_SVD(uint64_t, false, 256, 16, RANK_ATOMIC, false, 2, false, "256x16 atomic ldg occ2 direct"),
+        DBG_SVD(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, true, "256x12 atomic tma occ3 early direct"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -80,6 +91,10 @@ template <> struct SortKind<uint64_t, true> {
         DBG_SV(uint64_t, true, 256, 8, RANK_ATOMIC, true, 3, "256x8 atomic tma occ3"),
         DBG_SVE(uint64_t, true, 256, 8, RANK_ATOMIC, true, 3, "256x8 atomic tma occ3 early"),
         DBG_SVE(uint64_t, true, 256, 12, RANK_ATOMIC, true, 2, "256x12 atomic tma occ2 early"),
+        DBG_SV(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, "256x10 atomic tma occ3"),
+        DBG_SV(uint64_t, true, 384, 8, RANK_ATOMIC, true, 2, "384x8 atomic tma occ2"),
+        DBG_SVD(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, false, "256x10 atomic tma occ3 direct"),
+        DBG_SVD(uint64_t, true, 256, 8, RANK_ATOMIC, false, 3, false, "256x8 atomic ldg occ3 direct"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -94,6 +109,7 @@ template <> struct SortKind<Key128, false> {
         DBG_SV(Key128, false, 256, 6, RANK_MATCH, true, 3, "256x6 match tma occ3"),
         DBG_SVE(Key128, false, 256, 6, RANK_ATOMIC, true, 3, "256x6 atomic tma occ3 early"),
         DBG_SVE(Key128, false, 256, 8, RANK_ATOMIC, true, 2, "256x8 atomic tma occ2 early"),
+        DBG_SVD(Key128, false, 256, 8, RANK_ATOMIC, true, 2, true, "256x8 atomic tma occ2 early direct"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -107,6 +123,7 @@ template <> struct SortKind<Key128, true> {
         DBG_SV(Key128, true, 256, 8, RANK_MATCH, true, 1, "256x8 match tma"),
         DBG_SV(Key128, true, 256, 6, RANK_MATCH, true, 3, "256x6 match tma occ3"),
         DBG_SVE(Key128, true, 256, 6, RANK_ATOMIC, true, 3, "256x6 atomic tma occ3 early"),
+        DBG_SVD(Key128, true, 256, 6, RANK_ATOMIC, true, 3, true, "256x6 atomic tma occ3 early direct"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -114,6 +131,7 @@ template <> struct SortKind<Key128, true> {
 };
 #undef DBG_SV
 #undef DBG_SVE
+#undef DBG_SVD
 
 template <class K, bool V>
 const SortVariant &chosen_variant(dbg_ctx *ctx) {
@@ -159,6 +177,70 @@ dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uin
 inline unsigned grid_for(uint64_t n, int per_block) {
   uint64_t g = (n + per_block - 1) / per_block;
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 0x7fffffffull));
+}
+
+// Exclusive scan of n u32 values into n + 1 u64 (the last is the total).
+inline dbg_status scan_u32(dbg_ctx *ctx, const uint32_t *in, uint64_t n, uint64_t *out, uint32_t *total, int stage) {
+  cudaStream_t s = ctx->stream;
+  const uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  DBG_TRY(ensure_status(ctx, tiles));
+  uint32_t epoch;
+  DBG_TRY(next_epoch(ctx, &epoch));
+  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 2 * sizeof(uint32_t), s));
+  DBG_LAUNCH(ctx, stage, 12.0 * n,
+             k_scan_excl<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(in, n, out, ctx->d_status, ctx->d_counters, epoch,
+                                                                ctx->spin_limit, ctx->d_err, ctx->d_counters + 1));
+  DBG_CUDA_TRY(cudaGetLastError());
+  return read_small(ctx, ctx->d_counters + 1, sizeof(uint32_t), total);
+}
+
+// K4 by reduce-then-scan: unique keys into `uniq`, run heads into headpos
+// (E + 1 entries, the last = n); returns E.
+template <class K>
+dbg_status run_length_reduce(dbg_ctx *ctx, const K *sorted, uint64_t n, K *uniq, uint32_t *headpos, uint64_t *E) {
+  cudaStream_t s = ctx->stream;
+  const uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+  DevBuf counts, toff;
+  DBG_TRY(alloc_buf(ctx, counts, tiles * 4));
+  DBG_TRY(alloc_buf(ctx, toff, (tiles + 1) * 8));
+  DBG_LAUNCH(ctx, ST_RLE, (double)n * sizeof(K),
+             k_count_heads<K><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(sorted, nullptr, n, counts.as<uint32_t>(),
+                                                                   nullptr));
+  uint32_t total = 0;
+  DBG_TRY(scan_u32(ctx, counts.as<uint32_t>(), tiles, toff.as<uint64_t>(), &total, ST_RLE));
+  DBG_LAUNCH(ctx, ST_RLE, (double)n * sizeof(K) + (double)total * (sizeof(K) + 4),
+             k_write_heads<K><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(sorted, n, toff.as<uint64_t>(), uniq, headpos));
+  DBG_CUDA_TRY(cudaGetLastError());
+  *E = total;
+  return DBG_OK;
+}
+
+// K6 by reduce-then-scan over R sorted node records; returns the node count
+// and the number of edge ends.
+template <class K>
+dbg_status assign_node_ids(dbg_ctx *ctx, const K *rk, const uint32_t *rv, uint64_t R, K *node_keys,
+                           uint64_t *row_ptr, dbg_graph *g, uint32_t base_v, uint64_t base_slot, uint64_t *V,
+                           uint64_t *ends) {
+  cudaStream_t s = ctx->stream;
+  const uint64_t tiles = (R + RS_TILE - 1) / RS_TILE;
+  DevBuf hc, ec, ho, eo;
+  DBG_TRY(alloc_buf(ctx, hc, tiles * 4));
+  DBG_TRY(alloc_buf(ctx, ec, tiles * 4));
+  DBG_TRY(alloc_buf(ctx, ho, (tiles + 1) * 8));
+  DBG_TRY(alloc_buf(ctx, eo, (tiles + 1) * 8));
+  DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (sizeof(K) + 4),
+             k_count_heads<K><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(rk, rv, R, hc.as<uint32_t>(), ec.as<uint32_t>()));
+  uint32_t nv = 0, ne = 0;
+  DBG_TRY(scan_u32(ctx, hc.as<uint32_t>(), tiles, ho.as<uint64_t>(), &nv, ST_NODE_IDS));
+  DBG_TRY(scan_u32(ctx, ec.as<uint32_t>(), tiles, eo.as<uint64_t>(), &ne, ST_NODE_IDS));
+  DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (sizeof(K) + 4) + (double)nv * (sizeof(K) + 8) + (double)ne * 9,
+             k_write_nodes<K><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
+                 rk, rv, R, ho.as<uint64_t>(), eo.as<uint64_t>(), node_keys, row_ptr, g->src.as<uint32_t>(),
+                 g->dst.as<uint32_t>(), g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), base_v, base_slot));
+  DBG_CUDA_TRY(cudaGetLastError());
+  *V = nv;
+  *ends = ne;
+  return DBG_OK;
 }
 
 template <class K>
@@ -238,22 +320,8 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     sorted = kp;
     // run-length reduce into the other buffer
     DBG_TRY(alloc_buf(ctx, headpos, (N + 1) * sizeof(uint32_t)));
-    const uint64_t tiles = (N + BUILD_SCAN_TILE - 1) / BUILD_SCAN_TILE;
-    DBG_TRY(ensure_status(ctx, tiles));
-    uint32_t epoch;
-    DBG_TRY(next_epoch(ctx, &epoch));
-    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(uint32_t), s));
-    {
-      DBG_LAUNCH(ctx, ST_RLE, (double)N * sizeof(K),
-                 k_rle<K, BUILD_SCAN_ITEMS><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(sorted, N, alt, headpos.as<uint32_t>(), ctx->d_status,
-                                                     ctx->d_counters, epoch, ctx->spin_limit, ctx->d_err,
-                                                     ctx->d_counters + 1));
-    }
-    DBG_CUDA_TRY(cudaGetLastError());
-    uint32_t e32;
-    DBG_TRY(read_small(ctx, ctx->d_counters + 1, sizeof(uint32_t), &e32));
+    DBG_TRY(run_length_reduce<K>(ctx, sorted, N, alt, headpos.as<uint32_t>(), &E));
     DBG_TRY(check_device_error(ctx));
-    E = e32;
     // keep the buffer holding the unique keys; the sorted keys are done
     if (sorted == keys_a.as<K>()) { uniq = std::move(keys_b); keys_a.release(); }
     else { uniq = std::move(keys_a); keys_b.release(); }
@@ -313,27 +381,13 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   DBG_TRY(alloc_buf(ctx, g->adj_nbr, std::max<uint64_t>(1, 2 * E) * sizeof(uint32_t)));
   uint64_t V = 0;
   if (R > 0) {
-    const uint64_t tiles = (R + BUILD_SCAN_TILE - 1) / BUILD_SCAN_TILE;
-    DBG_TRY(ensure_status(ctx, 2 * tiles));
-    uint32_t eh, ee;
-    DBG_TRY(next_epoch(ctx, &eh));
-    DBG_TRY(next_epoch(ctx, &ee));
-    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(uint32_t), s));
     // node keys go to the free record buffer first (|V| is known only after)
-    {
-      DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (sizeof(K) + 4) + (double)E * (2 * 5 + 8),
-                 k_node_ids<K, BUILD_SCAN_ITEMS><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
-          rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g->src.as<uint32_t>(), g->dst.as<uint32_t>(),
-          g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), ctx->d_status, ctx->d_status + tiles,
-          ctx->d_counters, eh, ee, ctx->spin_limit, ctx->d_err, ctx->d_counters + 1, 0u, 0ull));
-    }
-    DBG_CUDA_TRY(cudaGetLastError());
-    uint32_t tot[2];
-    DBG_TRY(read_small(ctx, ctx->d_counters + 1, sizeof(tot), tot));
+    uint64_t ends = 0;
+    DBG_TRY(assign_node_ids<K>(ctx, rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g, 0u, 0ull, &V, &ends));
     DBG_TRY(check_device_error(ctx));
-    V = tot[0];
-    if (tot[1] != 2 * E) {
-      set_error("adjacency holds %u edge ends, expected %llu", tot[1], (unsigned long long)(2 * E));
+    if (ends != 2 * E) {
+      set_error("adjacency holds %llu edge ends, expected %llu", (unsigned long long)ends,
+                (unsigned long long)(2 * E));
       return DBG_ECUDA;
     }
   }
@@ -633,18 +687,10 @@ dbg_status build_bucketed_impl(dbg_ctx *ctx, const BucketInput &in, uint64_t bud
     K *kp = ka.as<K>(), *alt = kb.as<K>();
     uint32_t *vn = nullptr, *van = nullptr;
     DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, cnt, kbits, d_hist, d_digit_base)));
-    const uint64_t tiles = (cnt + BUILD_SCAN_TILE - 1) / BUILD_SCAN_TILE;
-    DBG_TRY(ensure_status(ctx, tiles));
-    uint32_t epoch;
-    DBG_TRY(next_epoch(ctx, &epoch));
-    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(uint32_t), s));
-    DBG_LAUNCH(ctx, ST_RLE, (double)cnt * w,
-               k_rle<K, BUILD_SCAN_ITEMS><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
-                   kp, cnt, alt, headpos.as<uint32_t>(), ctx->d_status, ctx->d_counters, epoch, ctx->spin_limit,
-                   ctx->d_err, ctx->d_counters + 1));
-    uint32_t eb = 0;
-    DBG_TRY(read_small(ctx, ctx->d_counters + 1, 4, &eb));
+    uint64_t eb64 = 0;
+    DBG_TRY(run_length_reduce<K>(ctx, kp, cnt, alt, headpos.as<uint32_t>(), &eb64));
     DBG_TRY(check_device_error(ctx));
+    const uint32_t eb = (uint32_t)eb64;
     DevBuf k1, m1, o1;
     DBG_TRY(alloc_buf(ctx, k1, std::max<uint64_t>(1, eb) * w));
     DBG_TRY(alloc_buf(ctx, m1, std::max<uint64_t>(1, eb) * 4));
@@ -742,21 +788,9 @@ dbg_status build_bucketed_impl(dbg_ctx *ctx, const BucketInput &in, uint64_t bud
     uint32_t *rv = va.as<uint32_t>(), *rv_alt = vb.as<uint32_t>();
     DBG_TRY((radix_sort<K, true>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, d_hist, d_digit_base)));
     DBG_TRY(alloc_buf(ctx, row_tmp, (R + 1) * 8));
-    const uint64_t tiles = (R + BUILD_SCAN_TILE - 1) / BUILD_SCAN_TILE;
-    DBG_TRY(ensure_status(ctx, 2 * tiles));
-    uint32_t eh, ee;
-    DBG_TRY(next_epoch(ctx, &eh));
-    DBG_TRY(next_epoch(ctx, &ee));
-    DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(uint32_t), s));
-    DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (w + 4),
-               k_node_ids<K, BUILD_SCAN_ITEMS><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
-                   rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g->src.as<uint32_t>(), g->dst.as<uint32_t>(),
-                   g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), ctx->d_status, ctx->d_status + tiles,
-                   ctx->d_counters, eh, ee, ctx->spin_limit, ctx->d_err, ctx->d_counters + 1, (uint32_t)base_v,
-                   base_slot));
-    DBG_CUDA_TRY(cudaGetLastError());
-    uint32_t tot[2];
-    DBG_TRY(read_small(ctx, ctx->d_counters + 1, sizeof(tot), tot));
+    uint64_t tot[2] = {0, 0};
+    DBG_TRY(assign_node_ids<K>(ctx, rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g, (uint32_t)base_v, base_slot,
+                               &tot[0], &tot[1]));
     DBG_TRY(check_device_error(ctx));
     const uint64_t Vc = tot[0];
     DevBuf nk, rp;

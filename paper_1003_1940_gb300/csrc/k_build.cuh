@@ -385,7 +385,8 @@ struct OnesweepSmem {
   uint32_t tile;
 };
 
-template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, bool LOAD_TMA, int MIN_BLOCKS, bool EARLY>
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, bool LOAD_TMA, int MIN_BLOCKS, bool EARLY,
+          bool DIRECT = false>
 __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
     const K *__restrict__ kin, K *__restrict__ kout, const uint32_t *__restrict__ vin, uint32_t *__restrict__ vout,
     uint64_t n, int shift, const uint64_t *__restrict__ digit_base, uint64_t *__restrict__ status,
@@ -500,7 +501,8 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
       sm.whist[warp][d] = before + __popc(peers);
     }
     before = __shfl_sync(0xffffffffu, before, leader);
-    rank[i] = before + __popc(peers & lt_mask);
+    // rank within the tile's digit run so far, with the digit in the low 9 bits
+    rank[i] = ((before + __popc(peers & lt_mask)) << 9) | d;
     __syncwarp();
   }
   __syncthreads();
@@ -508,17 +510,20 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
   uint32_t cnt = 0;
   if (tid < RADIX) {
 #pragma unroll
-    for (int w = 0; w < WARPS; w++) {
-      const uint32_t c = sm.whist[w][tid];
-      sm.whist[w][tid] = cnt;
-      cnt += c;
-    }
+    for (int w = 0; w < WARPS; w++) cnt += sm.whist[w][tid];
     if (!EARLY)
       st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE, cnt));
   }
   const uint32_t tstart = block_excl_scan_256(cnt, sm.tmp);
   if (tid < RADIX) {
-    sm.tile_start[tid] = tstart;
+    // each warp's first slot for this digit in the tile's digit-ordered staging
+    uint32_t run = tstart;
+#pragma unroll
+    for (int w = 0; w < WARPS; w++) {
+      const uint32_t c = sm.whist[w][tid];
+      sm.whist[w][tid] = run;
+      run += c;
+    }
     uint32_t excl = excl_early;
     if (!EARLY && tile > 0) {
       excl = lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
@@ -528,12 +533,30 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
   }
   __syncthreads();
 
+  if (DIRECT) {
+    // each key straight from its register to its final position; the L2
+    // merges the partial sectors of neighbouring keys before DRAM sees them
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const uint32_t d = rank[i] & 0x1ffu;
+      if (d < RADIX) {
+        const uint64_t dst = sm.gbase[d] + sm.whist[warp][d] + (rank[i] >> 9);
+        if (dst >= n) {  // only reachable if the digit counts were inconsistent
+          atomicOr(err, ERR_INTERNAL);
+          continue;
+        }
+        kout[dst] = key[i];
+        if (HAS_VAL) vout[dst] = val[i];
+      }
+    }
+    return;
+  }
   // stage in digit order (the tile's keys are all in registers now)
 #pragma unroll
   for (int i = 0; i < ITEMS; i++) {
-    if ((uint32_t)(wofs + i * 32 + lane) < tile_n) {
-      const uint32_t d = KeyOps<K>::digit(key[i], shift, RADIX_BITS);
-      const uint32_t p = sm.tile_start[d] + sm.whist[warp][d] + rank[i];
+    const uint32_t d = rank[i] & 0x1ffu;
+    if (d < RADIX) {
+      const uint32_t p = sm.whist[warp][d] + (rank[i] >> 9);
       sm.keys[p] = key[i];
       if (HAS_VAL) sm.vals[p] = val[i];
     }
@@ -1079,6 +1102,150 @@ static __global__ void k_pack_at(const uint8_t *__restrict__ ascii, uint64_t tot
     packed[word0 + w] = word;
     if (!ok) atomicOr(err, ERR_BAD_BASE);
   }
+}
+
+}  // namespace dbg
+
+namespace dbg {
+
+// ---------------------------------------------------------------------------
+// Reduce-then-scan forms of K4 and K6 (no look-back): a counting pass per
+// tile, an exclusive scan of the tile counts, and a writing pass that
+// recomputes the flags.  Layout of a tile: item i of thread t at
+// i * SCAN_BLOCK + t.
+// ---------------------------------------------------------------------------
+constexpr int RS_ITEMS = 16, RS_TILE = SCAN_BLOCK * RS_ITEMS;
+
+// previous element of item (i, t) in the strided layout: (i, t - 1), from
+// the neighbouring lane or, for lane 0, from memory
+template <class K>
+__device__ __forceinline__ K prev_key(const K *keys, uint64_t idx, uint64_t n, const K &mine) {
+  const int lane = threadIdx.x & 31;
+  K p;
+  if constexpr (sizeof(K) == 8) {
+    p = __shfl_up_sync(0xffffffffu, mine, 1);
+  } else {
+    p.hi = __shfl_up_sync(0xffffffffu, mine.hi, 1);
+    p.lo = __shfl_up_sync(0xffffffffu, mine.lo, 1);
+  }
+  if (lane == 0 && idx > 0 && idx <= n) p = keys[idx - 1];
+  return p;
+}
+
+// heads per tile: counts[t] (and, when `vals` is given, edge-end records
+// per tile in counts2[t])
+template <class K>
+__global__ __launch_bounds__(SCAN_BLOCK) void k_count_heads(const K *__restrict__ keys, const uint32_t *__restrict__ vals,
+                                                            uint64_t n, uint32_t *__restrict__ counts,
+                                                            uint32_t *__restrict__ counts2) {
+  __shared__ uint32_t s_red[2][SCAN_BLOCK / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+  uint32_t c = 0, c2 = 0;
+#pragma unroll 4
+  for (int i = 0; i < RS_ITEMS; i++) {
+    const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
+    const bool in = idx < n;
+    const K k = in ? keys[idx] : KeyOps<K>::zero();
+    const K p = prev_key(keys, idx, n, k);
+    if (in && (idx == 0 || !KeyOps<K>::eq(k, p))) c++;
+    if (vals && in && vals[idx] != REC_NONE) c2++;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  c2 = __reduce_add_sync(0xffffffffu, c2);
+  if ((threadIdx.x & 31) == 0) {
+    s_red[0][threadIdx.x >> 5] = c;
+    s_red[1][threadIdx.x >> 5] = c2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t a = 0, b = 0;
+    for (int w = 0; w < SCAN_BLOCK / 32; w++) {
+      a += s_red[0][w];
+      b += s_red[1][w];
+    }
+    counts[blockIdx.x] = a;
+    if (counts2) counts2[blockIdx.x] = b;
+  }
+}
+
+// K4 writing pass: unique keys and run heads at the scanned tile offsets;
+// the last tile writes headpos[E] = n.
+template <class K>
+__global__ __launch_bounds__(SCAN_BLOCK) void k_write_heads(const K *__restrict__ keys, uint64_t n,
+                                                            const uint64_t *__restrict__ tile_off,
+                                                            K *__restrict__ uniq, uint32_t *__restrict__ headpos) {
+  constexpr int WARPS = SCAN_BLOCK / 32;
+  __shared__ uint32_t s_cnt[RS_ITEMS * WARPS + 1];
+  const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+  K key[RS_ITEMS];
+  bool head[RS_ITEMS];
+  uint32_t rank[RS_ITEMS];
+#pragma unroll
+  for (int i = 0; i < RS_ITEMS; i++) {
+    const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
+    const bool in = idx < n;
+    key[i] = in ? keys[idx] : KeyOps<K>::zero();
+    const K p = prev_key(keys, idx, n, key[i]);
+    head[i] = in && (idx == 0 || !KeyOps<K>::eq(key[i], p));
+  }
+  const uint32_t count = tile_flag_ranks<SCAN_BLOCK, RS_ITEMS>(head, rank, s_cnt);
+  const uint64_t off = tile_off[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < RS_ITEMS; i++) {
+    if (head[i]) {
+      uniq[off + rank[i]] = key[i];
+      headpos[off + rank[i]] = (uint32_t)(base + (uint64_t)i * SCAN_BLOCK + threadIdx.x);
+    }
+  }
+  if (base + RS_TILE >= n && threadIdx.x == 0) headpos[off + count] = (uint32_t)n;
+}
+
+// K6 writing pass: node IDs and adjacency slots from the scanned tile
+// offsets of run heads (hoff) and edge-end records (eoff).
+template <class K>
+__global__ __launch_bounds__(SCAN_BLOCK) void k_write_nodes(
+    const K *__restrict__ rkeys, const uint32_t *__restrict__ rvals, uint64_t R, const uint64_t *__restrict__ hoff,
+    const uint64_t *__restrict__ eoff, K *__restrict__ node_keys, uint64_t *__restrict__ row_ptr,
+    uint32_t *__restrict__ src, uint32_t *__restrict__ dst, uint32_t *__restrict__ adj_edge,
+    uint8_t *__restrict__ adj_role, uint32_t base_v, uint64_t base_slot) {
+  constexpr int WARPS = SCAN_BLOCK / 32;
+  __shared__ uint32_t s_cnt_h[RS_ITEMS * WARPS + 1], s_cnt_e[RS_ITEMS * WARPS + 1];
+  const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+  K key[RS_ITEMS];
+  uint32_t val[RS_ITEMS];
+  bool head[RS_ITEMS], end[RS_ITEMS];
+  uint32_t rh[RS_ITEMS], re[RS_ITEMS];
+#pragma unroll
+  for (int i = 0; i < RS_ITEMS; i++) {
+    const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
+    const bool in = idx < R;
+    key[i] = in ? rkeys[idx] : KeyOps<K>::zero();
+    val[i] = in ? rvals[idx] : REC_NONE;
+    const K p = prev_key(rkeys, idx, R, key[i]);
+    head[i] = in && (idx == 0 || !KeyOps<K>::eq(key[i], p));
+    end[i] = val[i] != REC_NONE;
+  }
+  tile_flag_ranks<SCAN_BLOCK, RS_ITEMS>(head, rh, s_cnt_h);
+  tile_flag_ranks<SCAN_BLOCK, RS_ITEMS>(end, re, s_cnt_e);
+  const uint64_t xh = hoff[blockIdx.x], xe = eoff[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < RS_ITEMS; i++) {
+    const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
+    if (idx >= R) continue;
+    const uint64_t id = xh + rh[i] + (head[i] ? 1u : 0u) - 1u;
+    const uint64_t slot = xe + re[i];
+    if (head[i]) {
+      node_keys[id] = key[i];
+      row_ptr[id] = base_slot + slot;
+    }
+    if (end[i]) {
+      const uint32_t e = val[i] >> 1, role = val[i] & 1u;
+      adj_edge[base_slot + slot] = e;
+      adj_role[base_slot + slot] = (uint8_t)role;
+      (role ? dst : src)[e] = base_v + (uint32_t)id;
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) row_ptr[hoff[gridDim.x]] = base_slot + eoff[gridDim.x];
 }
 
 }  // namespace dbg

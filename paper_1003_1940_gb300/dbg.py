@@ -395,9 +395,9 @@ def dbg_sort_variant_get(ctx: Context, kind: int) -> int:
 
 def dbg_autotune(ctx: Context, n: int = 0, cache_path: str | None = None) -> dict:
     """Times every radix-sort variant; returns {kind: [ms per variant]}."""
-    ms = (ctypes.c_double * 64)()
+    ms = (ctypes.c_double * 128)()
     _check(_lib.dbg_autotune(ctx.handle, n, cache_path.encode() if cache_path else None, ms), "dbg_autotune")
-    return {kd: [ms[kd * 16 + v] for v in range(dbg_sort_variant_count(kd))] for kd in range(4)}
+    return {kd: [ms[kd * 32 + v] for v in range(dbg_sort_variant_count(kd))] for kd in range(4)}
 
 
 # ---------------------------------------------------------------------------
