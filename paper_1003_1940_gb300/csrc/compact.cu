@@ -71,7 +71,7 @@ __global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_
 // joins two distinct nodes and is alone on the far node's side too.  It
 // enters w on side sw: strand 0 when that is w's left side, 1 otherwise.
 __global__ void k_successors(const uint32_t *__restrict__ link_node, const uint32_t *__restrict__ link_edge,
-                             uint64_t V, uint32_t *__restrict__ succ, uint32_t *__restrict__ pred) {
+                             uint64_t V, uint32_t *__restrict__ succ) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * V; x += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t v = x >> 1;
     const uint32_t leave = (x & 1) ? 0u : 1u;
@@ -83,8 +83,14 @@ __global__ void k_successors(const uint32_t *__restrict__ link_node, const uint3
         out = 2 * w + (sw == 0 ? 0u : 1u);
     }
     succ[x] = out;
-    if (out != NONE32) pred[out] = (uint32_t)x;
   }
+}
+
+// The predecessor of a strand-node, from the mirror symmetry of the
+// transform: an arc y -> x exists exactly when x^1 -> y^1 does.
+__device__ __forceinline__ uint32_t pred_of(const uint32_t *__restrict__ succ, uint64_t x) {
+  const uint32_t m = succ[x ^ 1];
+  return m == NONE32 ? NONE32 : (m ^ 1u);
 }
 
 // Ranking state of a strand-node, one 64-bit word: (ancestor << 32) |
@@ -99,10 +105,9 @@ constexpr uint64_t UNSET64 = ~0ull;
 
 // Every list head walks its list, writing (head, rank), for at most `cap`
 // strand-nodes; the rest of a longer list and all cycles stay UNSET.
-__global__ void k_walk_lists(const uint32_t *__restrict__ pred, const uint32_t *__restrict__ succ, uint64_t n,
-                             uint32_t cap, uint64_t *__restrict__ word) {
+__global__ void k_walk_lists(const uint32_t *__restrict__ succ, uint64_t n, uint32_t cap, uint64_t *__restrict__ word) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-    if (pred[x] != NONE32) continue;
+    if (succ[x ^ 1] != NONE32) continue;  // not a list head
     uint32_t y = (uint32_t)x;
     for (uint32_t i = 0; i < cap; i++) {
       word[y] = pk((uint32_t)x, i);
@@ -115,11 +120,11 @@ __global__ void k_walk_lists(const uint32_t *__restrict__ pred, const uint32_t *
 
 // Strand-nodes the walks did not reach go on an active list, pointing to
 // their predecessor at distance 1.
-__global__ void k_collect_active(const uint32_t *__restrict__ pred, uint64_t n, uint64_t *__restrict__ word,
+__global__ void k_collect_active(const uint32_t *__restrict__ succ, uint64_t n, uint64_t *__restrict__ word,
                                  uint32_t *__restrict__ active, uint32_t *count) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
     if (word[x] != UNSET64) continue;
-    const uint32_t p = pred[x];
+    const uint32_t p = pred_of(succ, x);
     word[x] = p == NONE32 ? pk((uint32_t)x, 0) : pk(p, 1);
     active[atomicAdd(count, 1u)] = (uint32_t)x;
   }
@@ -148,14 +153,14 @@ __global__ void k_jump_active(const uint32_t *__restrict__ active, uint32_t A, u
 // Active strand-nodes that never reached a head lie on cycles: list them and
 // seed (predecessor, own index) words for the min-label propagation.
 __global__ void k_collect_cycles(const uint32_t *__restrict__ active, uint32_t A, const uint64_t *__restrict__ word,
-                                 const uint32_t *__restrict__ pred, uint32_t *__restrict__ cyc_list,
+                                 const uint32_t *__restrict__ succ, uint32_t *__restrict__ cyc_list,
                                  uint64_t *__restrict__ lab, uint32_t *count) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A; i += gridDim.x * blockDim.x) {
     const uint32_t x = active[i];
     const uint64_t w = word[x];
     if (pk_root(w, x) || pk_root(word[pk_a(w)], pk_a(w))) continue;
     cyc_list[atomicAdd(count, 1u)] = x;
-    lab[x] = pk(pred[x], x);
+    lab[x] = pk(pred_of(succ, x), x);
   }
 }
 
@@ -174,13 +179,13 @@ __global__ void k_cycle_min(const uint32_t *__restrict__ cyc_list, uint32_t C, u
 // kept (cyc = 1); its mirror is cyc = 2.  Both are opened at their smallest
 // strand-node and ranked again as lists.
 __global__ void k_cycle_break(const uint32_t *__restrict__ cyc_list, uint32_t C, const uint64_t *__restrict__ lab,
-                              const uint32_t *__restrict__ pred, uint8_t *__restrict__ cyc,
+                              const uint32_t *__restrict__ succ, uint8_t *__restrict__ cyc,
                               uint64_t *__restrict__ word) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
     const uint32_t x = cyc_list[i];
     const uint32_t m = pk_d(lab[x]);
     cyc[x] = (m & 1u) ? 2 : 1;
-    word[x] = m == x ? pk(x, 0) : pk(pred[x], 1);
+    word[x] = m == x ? pk(x, 0) : pk(pred_of(succ, x), 1);
   }
 }
 
@@ -272,6 +277,88 @@ __global__ void k_unitig_write(const uint32_t *__restrict__ head, const uint32_t
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fast path, for graphs whose lists are all at most `cap` strand-nodes long
+// and acyclic (the usual case): one walk per list head measures the list
+// and picks the copy to keep; a second walk writes each kept unitig's nodes
+// and bases in order.  No per-strand-node ranking state is written.
+// ---------------------------------------------------------------------------
+template <class K>
+__device__ __forceinline__ K strand_kmer(const uint64_t *node_keys, uint32_t x, int k) {
+  K km = load_node_key<K>(node_keys, x >> 1);
+  return (x & 1u) ? revcomp(km, k) : km;
+}
+
+template <class K>
+__global__ void k_fast_measure(const uint32_t *__restrict__ succ, uint64_t n, const uint64_t *__restrict__ node_keys,
+                               int k, uint32_t cap, uint32_t *__restrict__ is_head, uint32_t *__restrict__ len_at_head,
+                               uint8_t *__restrict__ hstrand, uint32_t *covered, uint32_t *too_long) {
+  uint32_t cov = 0, lng = 0;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+    if (succ[x ^ 1] != NONE32) continue;  // not a list head
+    uint32_t y = (uint32_t)x, L = 1;
+    for (; L < cap; L++) {
+      const uint32_t ny = succ[y];
+      if (ny == NONE32) break;
+      y = ny;
+    }
+    if (succ[y] != NONE32) {
+      lng++;
+      continue;
+    }
+    // the mirror copy starts at the tail on the other strand; the copy whose
+    // first k-mer is smaller spells the smaller string
+    if (KeyOps<K>::less(strand_kmer<K>(node_keys, (uint32_t)x, k), strand_kmer<K>(node_keys, y ^ 1u, k))) {
+      const uint64_t v = x >> 1;
+      is_head[v] = 1;
+      len_at_head[v] = L;
+      hstrand[v] = (uint8_t)(x & 1);
+      cov += 2 * L;
+    }
+  }
+  cov = __reduce_add_sync(0xffffffffu, cov);
+  lng = __reduce_add_sync(0xffffffffu, lng);
+  if ((threadIdx.x & 31) == 0) {
+    if (cov) atomicAdd(covered, cov);
+    if (lng) atomicAdd(too_long, lng);
+  }
+}
+
+template <class K>
+__global__ void k_fast_write(const uint32_t *__restrict__ succ, const uint32_t *__restrict__ is_head,
+                             const uint8_t *__restrict__ hstrand, const uint64_t *__restrict__ uidx,
+                             const uint64_t *__restrict__ off_by_v, const uint64_t *__restrict__ node_keys, uint64_t V,
+                             uint64_t U, int k, uint64_t *__restrict__ nodes_out, char *__restrict__ seq,
+                             uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
+                             uint8_t *__restrict__ circular) {
+  const char *acgt = "ACGT";
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
+    if (v == 0) {
+      node_off[U] = V;
+      seq_off[U] = V + U * (uint64_t)(k - 1);
+    }
+    if (!is_head[v]) continue;
+    const uint64_t u = uidx[v], off = off_by_v[v];
+    const uint64_t so = off + u * (uint64_t)(k - 1);
+    node_off[u] = off;
+    seq_off[u] = so;
+    circular[u] = 0;
+    uint32_t y = (uint32_t)(2 * v + hstrand[v]);
+    for (uint64_t i = 0;; i++) {
+      nodes_out[off + i] = y;  // (node ID << 1) | strand
+      const K km = strand_kmer<K>(node_keys, y, k);
+      if (i == 0) {
+        for (int j = 0; j < k; j++) seq[so + j] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - j), 2)];
+      } else {
+        seq[so + k - 1 + i] = acgt[KeyOps<K>::low2(km)];
+      }
+      const uint32_t ny = succ[y];
+      if (ny == NONE32) break;
+      y = ny;
+    }
+  }
+}
+
 static unsigned grid_of(uint64_t n) {
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, 152ull * 64));
 }
@@ -328,7 +415,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
   const int k = (int)g->k;
   u->num_nodes = V;
   const uint64_t V1 = std::max<uint64_t>(1, V), n1 = std::max<uint64_t>(1, n);
-  DevBuf link_node, link_edge, succ, pred, word, active, cycl, lab, cyc;
+  DevBuf link_node, link_edge, succ, word, active, cycl, lab, cyc;
   DevBuf strand, head, rank, is_head, len_at_head, uidx, off_by_v;
   uint64_t U = 0;
   bool have_cycles = false;
@@ -336,29 +423,74 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
     DBG_TRY(alloc_buf(ctx, link_node, n1 * 4));
     DBG_TRY(alloc_buf(ctx, link_edge, n1 * 4));
     DBG_TRY(alloc_buf(ctx, succ, n1 * 4));
-    DBG_TRY(alloc_buf(ctx, pred, n1 * 4));
     DBG_TRY(alloc_buf(ctx, word, n1 * 8));
     DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + (double)E2 * 10 + 16.0 * V,
                k_side_links<<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
                                                        g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
                                                        g->orient.as<uint8_t>(), V, link_node.as<uint32_t>(),
                                                        link_edge.as<uint32_t>()));
-    DBG_CUDA_TRY(cudaMemsetAsync(pred.p, 0xff, n * 4, s));
     DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 8.0 * n + 8.0 * n,
                k_successors<<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint32_t>(), V,
-                                                       succ.as<uint32_t>(), pred.as<uint32_t>()));
+                                                       succ.as<uint32_t>()));
     link_node.release();
     link_edge.release();
+    // ---- fast path: short acyclic lists only ----
+    {
+      DevBuf f_is_head, f_len, f_strand, f_uidx, f_off;
+      DBG_TRY(alloc_buf(ctx, f_is_head, V1 * 4));
+      DBG_TRY(alloc_buf(ctx, f_len, V1 * 4));
+      DBG_TRY(alloc_buf(ctx, f_strand, V1));
+      DBG_CUDA_TRY(cudaMemsetAsync(f_is_head.p, 0, V1 * 4, s));
+      DBG_CUDA_TRY(cudaMemsetAsync(f_len.p, 0, V1 * 4, s));
+      DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 10, 0, 2 * sizeof(uint32_t), s));
+      DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 32.0 * n + 16.0 * V,
+                 k_fast_measure<K><<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n, g->node_keys.as<uint64_t>(), k,
+                                                              kWalkCap, f_is_head.as<uint32_t>(),
+                                                              f_len.as<uint32_t>(), f_strand.as<uint8_t>(),
+                                                              ctx->d_counters + 10, ctx->d_counters + 11));
+      DBG_CUDA_TRY(cudaGetLastError());
+      uint32_t cnt[2] = {0, 0};
+      DBG_TRY(read_small(ctx, ctx->d_counters + 10, sizeof(cnt), cnt));
+      if (cnt[1] == 0 && cnt[0] == n) {
+        DBG_TRY(alloc_buf(ctx, f_uidx, (V + 1) * 8));
+        DBG_TRY(alloc_buf(ctx, f_off, (V + 1) * 8));
+        uint32_t U32 = 0, total = 0;
+        DBG_TRY(scan_excl(ctx, f_is_head.as<uint32_t>(), V, f_uidx.as<uint64_t>(), &U32));
+        DBG_TRY(scan_excl(ctx, f_len.as<uint32_t>(), V, f_off.as<uint64_t>(), &total));
+        if (total != V) {
+          set_error("unitigs hold %u nodes, expected %llu", total, (unsigned long long)V);
+          return DBG_ECUDA;
+        }
+        const uint64_t Uf = U32;
+        u->count = Uf;
+        DBG_TRY(alloc_buf(ctx, u->node_off, (Uf + 1) * 8));
+        DBG_TRY(alloc_buf(ctx, u->seq_off, (Uf + 1) * 8));
+        DBG_TRY(alloc_buf(ctx, u->circular, std::max<uint64_t>(1, Uf)));
+        DBG_TRY(alloc_buf(ctx, u->nodes, V1 * 8));
+        u->total_bases = V + Uf * (uint64_t)(k - 1);
+        DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
+        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)V * (4 + 1 + 16 + 8 + 8 * g->key_words + 1) + (double)Uf * (k + 17),
+                   k_fast_write<K><<<grid_of(V), 256, 0, s>>>(
+                       succ.as<uint32_t>(), f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_uidx.as<uint64_t>(),
+                       f_off.as<uint64_t>(), g->node_keys.as<uint64_t>(), V, Uf, k, u->nodes.as<uint64_t>(),
+                       u->seq.as<char>(), u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(),
+                       u->circular.as<uint8_t>()));
+        DBG_CUDA_TRY(cudaGetLastError());
+        DBG_CUDA_TRY(cudaStreamSynchronize(s));
+        return check_device_error(ctx);
+      }
+    }
+    // ---- general path: long lists or cycles present ----
     DBG_CUDA_TRY(cudaMemsetAsync(word.p, 0xff, n * 8, s));
     DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 12.0 * n,
-               k_walk_lists<<<grid_of(n), 256, 0, s>>>(pred.as<uint32_t>(), succ.as<uint32_t>(), n, kWalkCap,
+               k_walk_lists<<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n, kWalkCap,
                                                        word.as<uint64_t>()));
     DBG_CUDA_TRY(cudaGetLastError());
     // what the walks left: tails of very long lists, and cycles
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 4, 0, sizeof(uint32_t), s));
     DBG_TRY(alloc_buf(ctx, active, n1 * 4));
     DBG_LAUNCH(ctx, ST_COMPACT_RANK, 16.0 * n,
-               k_collect_active<<<grid_of(n), 256, 0, s>>>(pred.as<uint32_t>(), n, word.as<uint64_t>(),
+               k_collect_active<<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n, word.as<uint64_t>(),
                                                            active.as<uint32_t>(), ctx->d_counters + 4));
     uint32_t A = 0;
     DBG_TRY(read_small(ctx, ctx->d_counters + 4, sizeof(uint32_t), &A));
@@ -374,7 +506,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
         DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 5, 0, sizeof(uint32_t), s));
         DBG_LAUNCH(ctx, ST_COMPACT_CYCLES, 24.0 * A,
                    k_collect_cycles<<<grid_of(A), 256, 0, s>>>(active.as<uint32_t>(), A, word.as<uint64_t>(),
-                                                               pred.as<uint32_t>(), cycl.as<uint32_t>(),
+                                                               succ.as<uint32_t>(), cycl.as<uint32_t>(),
                                                                lab.as<uint64_t>(), ctx->d_counters + 5));
         uint32_t C = 0;
         DBG_TRY(read_small(ctx, ctx->d_counters + 5, sizeof(uint32_t), &C));
@@ -385,7 +517,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
                      k_cycle_min<<<grid_of(C), 256, 0, s>>>(cycl.as<uint32_t>(), C, lab.as<uint64_t>()));
         DBG_LAUNCH(ctx, ST_COMPACT_CYCLES, 25.0 * C,
                    k_cycle_break<<<grid_of(C), 256, 0, s>>>(cycl.as<uint32_t>(), C, lab.as<uint64_t>(),
-                                                            pred.as<uint32_t>(), cyc.as<uint8_t>(),
+                                                            succ.as<uint32_t>(), cyc.as<uint8_t>(),
                                                             word.as<uint64_t>()));
         DBG_CUDA_TRY(cudaGetLastError());
         uint32_t still = 0;
@@ -414,7 +546,6 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
     DBG_CUDA_TRY(cudaGetLastError());
     word.release();
     succ.release();
-    pred.release();
     DBG_TRY(alloc_buf(ctx, uidx, (V + 1) * 8));
     DBG_TRY(alloc_buf(ctx, off_by_v, (V + 1) * 8));
     uint32_t U32 = 0, total = 0;

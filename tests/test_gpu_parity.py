@@ -197,3 +197,14 @@ def test_bounded_wait_reports_timeout_and_context_survives(dbg, ctx):
     assert time.perf_counter() - t < 5.0
     reads, lengths = readgen.generate(readgen.tiny_spec())
     check_parity(dbg, ctx, reads, lengths, 21)
+
+
+def test_unitig_longer_than_walk_cap(dbg, ctx):
+    """One 6,000-node unitig (longer than the walkers' cap) plus a cycle:
+    the general ranking path, against the oracle."""
+    rng = np.random.default_rng(99)
+    gnm = rng.integers(0, 4, size=6_000 + 40).astype(np.uint8)
+    reads = ["".join("ACGT"[c] for c in gnm[s:s + 100]) for s in range(0, 6_000, 40)]
+    reads += ["ACACACACACACACACACACAC" * 2]  # a circular unitig as well
+    r, l = as_input(reads)
+    check_parity(dbg, ctx, r, l, 21)
