@@ -30,10 +30,11 @@ struct SortVariant {
   SortLaunchFn launch;
 };
 
-template <class K, bool V, int BLOCK, int ITEMS, int RANK, bool TMA, int MINB, bool EARLY, bool DIRECT = false>
+template <class K, bool V, int BLOCK, int ITEMS, int RANK, bool TMA, int MINB, bool EARLY, bool DIRECT = false,
+          int LB = 1>
 void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *vin, uint32_t *vout, uint64_t n,
                      int shift, const uint64_t *digit_base, uint32_t epoch) {
-  auto kern = k_onesweep<K, V, BLOCK, ITEMS, RANK, TMA, MINB, EARLY, DIRECT>;
+  auto kern = k_onesweep<K, V, BLOCK, ITEMS, RANK, TMA, MINB, EARLY, DIRECT, LB>;
   constexpr size_t smem = sizeof(OnesweepSmem<K, V, BLOCK, ITEMS>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
@@ -47,6 +48,8 @@ void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *
   SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, false> }
 #define DBG_SVE(K, V, B, I, R, T, M, NAME) \
   SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, true> }
+#define DBG_SVL(K, V, B, I, R, T, M, E, L, NAME) \
+  SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, E, false, L> }
 #define DBG_SVD(K, V, B, I, R, T, M, E, NAME) \
   SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, E, true> }
 
@@ -76,6 +79,10 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SVD(uint64_t, false, 256, 12, RANK_ATOMIC, false, 3, false, "256x12 atomic ldg occ3 direct"),
         DBG_SVD(uint64_t, false, 256, 16, RANK_ATOMIC, false, 2, false, "256x16 atomic ldg occ2 direct"),
         DBG_SVD(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, true, "256x12 atomic tma occ3 early direct"),
+        DBG_SVL(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, false, 4, "256x12 atomic tma occ3 lb4"),
+        DBG_SVL(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, true, 4, "256x12 atomic tma occ3 early lb4"),
+        DBG_SVL(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, true, 8, "256x12 atomic tma occ3 early lb8"),
+        DBG_SVL(uint64_t, false, 256, 16, RANK_ATOMIC, true, 2, true, 8, "256x16 atomic tma occ2 early lb8"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -95,6 +102,8 @@ template <> struct SortKind<uint64_t, true> {
         DBG_SV(uint64_t, true, 384, 8, RANK_ATOMIC, true, 2, "384x8 atomic tma occ2"),
         DBG_SVD(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, false, "256x10 atomic tma occ3 direct"),
         DBG_SVD(uint64_t, true, 256, 8, RANK_ATOMIC, false, 3, false, "256x8 atomic ldg occ3 direct"),
+        DBG_SVL(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, true, 4, "256x10 atomic tma occ3 early lb4"),
+        DBG_SVL(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, false, 4, "256x10 atomic tma occ3 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -110,6 +119,7 @@ template <> struct SortKind<Key128, false> {
         DBG_SVE(Key128, false, 256, 6, RANK_ATOMIC, true, 3, "256x6 atomic tma occ3 early"),
         DBG_SVE(Key128, false, 256, 8, RANK_ATOMIC, true, 2, "256x8 atomic tma occ2 early"),
         DBG_SVD(Key128, false, 256, 8, RANK_ATOMIC, true, 2, true, "256x8 atomic tma occ2 early direct"),
+        DBG_SVL(Key128, false, 256, 8, RANK_ATOMIC, true, 2, true, 4, "256x8 atomic tma occ2 early lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -124,6 +134,7 @@ template <> struct SortKind<Key128, true> {
         DBG_SV(Key128, true, 256, 6, RANK_MATCH, true, 3, "256x6 match tma occ3"),
         DBG_SVE(Key128, true, 256, 6, RANK_ATOMIC, true, 3, "256x6 atomic tma occ3 early"),
         DBG_SVD(Key128, true, 256, 6, RANK_ATOMIC, true, 3, true, "256x6 atomic tma occ3 early direct"),
+        DBG_SVL(Key128, true, 256, 6, RANK_ATOMIC, true, 3, true, 4, "256x6 atomic tma occ3 early lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -132,6 +143,7 @@ template <> struct SortKind<Key128, true> {
 #undef DBG_SV
 #undef DBG_SVE
 #undef DBG_SVD
+#undef DBG_SVL
 
 template <class K, bool V>
 const SortVariant &chosen_variant(dbg_ctx *ctx) {

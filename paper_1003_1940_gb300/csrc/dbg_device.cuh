@@ -160,6 +160,39 @@ __device__ __forceinline__ uint32_t lookback_exclusive(uint64_t *status, size_t 
   return sum;
 }
 
+// As lookback_exclusive, but loads BATCH predecessors' words at once, so a
+// run of tiles that have published only their aggregates costs one memory
+// round trip per BATCH tiles instead of one per tile.
+template <int BATCH>
+__device__ __forceinline__ uint32_t lookback_exclusive_batched(uint64_t *status, size_t stride, uint32_t tile,
+                                                               uint32_t epoch, uint32_t spin_limit, uint32_t *err) {
+  uint32_t sum = 0;
+  int64_t t = (int64_t)tile - 1;
+  const uint32_t ep = epoch & 0x3fffffffu;
+  while (t >= 0) {
+    uint64_t w[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; j++) w[j] = t - j >= 0 ? ld_relaxed(status + (size_t)(t - j) * stride) : 0;
+#pragma unroll
+    for (int j = 0; j < BATCH; j++) {
+      if (t - j < 0) return sum;
+      uint32_t spins = 0;
+      while (!(lb_epoch(w[j]) == ep && lb_flag(w[j]) != 0)) {
+        if (++spins > spin_limit) {
+          atomicOr(err, ERR_TIMEOUT);
+          return sum;
+        }
+        __nanosleep(32);
+        w[j] = ld_relaxed(status + (size_t)(t - j) * stride);
+      }
+      sum += lb_count(w[j]);
+      if (lb_flag(w[j]) == LB_INCLUSIVE) return sum;
+    }
+    t -= BATCH;
+  }
+  return sum;
+}
+
 // Warp-wide exclusive prefix of one counter: all 32 lanes look back over 32
 // predecessors at a time.  Returns the same value in every lane.
 __device__ __forceinline__ uint32_t lookback_exclusive_warp(uint64_t *status, uint32_t tile,

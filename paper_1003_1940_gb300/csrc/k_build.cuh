@@ -386,7 +386,7 @@ struct OnesweepSmem {
 };
 
 template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, bool LOAD_TMA, int MIN_BLOCKS, bool EARLY,
-          bool DIRECT = false>
+          bool DIRECT = false, int LB = 1>
 __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
     const K *__restrict__ kin, K *__restrict__ kout, const uint32_t *__restrict__ vin, uint32_t *__restrict__ vout,
     uint64_t n, int shift, const uint64_t *__restrict__ digit_base, uint64_t *__restrict__ status,
@@ -465,7 +465,8 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
         st_relaxed(st, lb_word(epoch, LB_INCLUSIVE, c));
       } else {
         st_relaxed(st, lb_word(epoch, LB_AGGREGATE, c));
-        excl_early = lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
+        excl_early = LB > 1 ? lookback_exclusive_batched<LB>(status + tid, RADIX, tile, epoch, spin_limit, err)
+                            : lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
         st_relaxed(st, lb_word(epoch, LB_INCLUSIVE, excl_early + c));
       }
     }
@@ -526,7 +527,8 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
     }
     uint32_t excl = excl_early;
     if (!EARLY && tile > 0) {
-      excl = lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
+      excl = LB > 1 ? lookback_exclusive_batched<LB>(status + tid, RADIX, tile, epoch, spin_limit, err)
+                    : lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
       st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, LB_INCLUSIVE, excl + cnt));
     }
     sm.gbase[tid] = digit_base[tid] + excl - tstart;
