@@ -129,9 +129,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def measured_traffic(workload_name, scale):
+def measured_traffic(workload_name, scale, variant):
     """DRAM bytes per onesweep launch from the committed ncu summary, or None
-    when the kernel source changed since those counters were taken."""
+    when the kernel source or the chosen variant differs from the capture's."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "onesweep_large_k31.md")
     src = os.path.join(ROOT, "paper_1003_1940_gb300", "csrc", "k_build.cuh")
@@ -139,11 +139,14 @@ def measured_traffic(workload_name, scale):
         return None
     fields = {}
     for line in open(path):
-        if ":" in line and line.startswith("    "):
-            key, _, val = line.strip().partition(":")
+        if line.startswith("    ") and ": " in line and not line.strip().startswith(("ncu", "python")):
+            key, _, val = line.strip().partition(": ")
             fields[key.strip()] = val.strip()
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if fields.get("source_sha256_16") != digest or fields.get("workload") != workload_name:
+    text = open(src).read()
+    section = text[text.index("// K3 onesweep radix pass"):text.index("// K4 run-length reduce")]
+    digest = hashlib.sha256(section.encode()).hexdigest()[:16]
+    if (fields.get("source_sha256_16") != digest or fields.get("workload") != workload_name
+            or fields.get("variant") != variant):
         return None
     return float(fields["bytes_per_launch"])
 
@@ -322,7 +325,7 @@ def run_ours(args):
     pass_ms = srt["ms"] / max(1, srt["launches"] - args.steps) if n_pass > 0 else 0.0
     pass_bytes = srt["bytes"] / max(1, n_pass)
     achieved = pass_bytes / (pass_ms / 1000.0) / 1e9 if pass_ms > 0 else 0.0
-    traffic = measured_traffic(args.workload, args.scale)
+    traffic = measured_traffic(args.workload, args.scale, variants.get(0))
 
     stages = {name: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
