@@ -83,6 +83,11 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SVL(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, true, 4, "256x12 atomic tma occ3 early lb4"),
         DBG_SVL(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, true, 8, "256x12 atomic tma occ3 early lb8"),
         DBG_SVL(uint64_t, false, 256, 16, RANK_ATOMIC, true, 2, true, 8, "256x16 atomic tma occ2 early lb8"),
+        DBG_SVL(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, false, 8, "256x12 atomic tma occ3 lb8"),
+        DBG_SVL(uint64_t, false, 256, 12, RANK_ATOMIC, true, 3, false, 16, "256x12 atomic tma occ3 lb16"),
+        DBG_SVL(uint64_t, false, 256, 16, RANK_ATOMIC, true, 2, false, 4, "256x16 atomic tma occ2 lb4"),
+        DBG_SVL(uint64_t, false, 256, 8, RANK_ATOMIC, true, 4, false, 4, "256x8 atomic tma occ4 lb4"),
+        DBG_SVL(uint64_t, false, 256, 10, RANK_ATOMIC, true, 3, false, 8, "256x10 atomic tma occ3 lb8"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -104,6 +109,8 @@ template <> struct SortKind<uint64_t, true> {
         DBG_SVD(uint64_t, true, 256, 8, RANK_ATOMIC, false, 3, false, "256x8 atomic ldg occ3 direct"),
         DBG_SVL(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, true, 4, "256x10 atomic tma occ3 early lb4"),
         DBG_SVL(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, false, 4, "256x10 atomic tma occ3 lb4"),
+        DBG_SVL(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, false, 8, "256x10 atomic tma occ3 lb8"),
+        DBG_SVL(uint64_t, true, 256, 8, RANK_ATOMIC, true, 3, false, 8, "256x8 atomic tma occ3 lb8"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -120,6 +127,8 @@ template <> struct SortKind<Key128, false> {
         DBG_SVE(Key128, false, 256, 8, RANK_ATOMIC, true, 2, "256x8 atomic tma occ2 early"),
         DBG_SVD(Key128, false, 256, 8, RANK_ATOMIC, true, 2, true, "256x8 atomic tma occ2 early direct"),
         DBG_SVL(Key128, false, 256, 8, RANK_ATOMIC, true, 2, true, 4, "256x8 atomic tma occ2 early lb4"),
+        DBG_SVL(Key128, false, 256, 8, RANK_ATOMIC, true, 2, false, 8, "256x8 atomic tma occ2 lb8"),
+        DBG_SVL(Key128, false, 256, 6, RANK_ATOMIC, true, 3, false, 8, "256x6 atomic tma occ3 lb8"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -135,6 +144,7 @@ template <> struct SortKind<Key128, true> {
         DBG_SVE(Key128, true, 256, 6, RANK_ATOMIC, true, 3, "256x6 atomic tma occ3 early"),
         DBG_SVD(Key128, true, 256, 6, RANK_ATOMIC, true, 3, true, "256x6 atomic tma occ3 early direct"),
         DBG_SVL(Key128, true, 256, 6, RANK_ATOMIC, true, 3, true, 4, "256x6 atomic tma occ3 early lb4"),
+        DBG_SVL(Key128, true, 256, 6, RANK_ATOMIC, true, 3, false, 8, "256x6 atomic tma occ3 lb8"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;

@@ -289,62 +289,118 @@ __device__ __forceinline__ K strand_kmer(const uint64_t *node_keys, uint32_t x, 
   return (x & 1u) ? revcomp(km, k) : km;
 }
 
+// Walk scheduling: each warp takes a chunk of WALK_CHUNK indices, queues the
+// list heads it finds there in shared memory (ballots), and its lanes then
+// take heads from the queue one at a time, so no lane idles while another
+// finishes a long list.
+constexpr int WALK_BLOCK = 256, WALK_WARPS = WALK_BLOCK / 32, WALK_CHUNK = 1024;
+
+template <class IsHead>
+__device__ __forceinline__ uint32_t queue_heads(uint64_t base, uint64_t n, uint32_t *q, IsHead is_head) {
+  const int lane = threadIdx.x & 31;
+  uint32_t cnt = 0;
+  for (int r = 0; r < WALK_CHUNK / 32; r++) {
+    const uint64_t x = base + r * 32 + lane;
+    const bool h = x < n && is_head(x);
+    const unsigned b = __ballot_sync(0xffffffffu, h);
+    if (h) q[cnt + __popc(b & ((1u << lane) - 1u))] = (uint32_t)x;
+    cnt += __popc(b);
+  }
+  __syncwarp();
+  return cnt;
+}
+
 template <class K>
-__global__ void k_fast_measure(const uint32_t *__restrict__ succ, uint64_t n, const uint64_t *__restrict__ node_keys,
-                               int k, uint32_t cap, uint32_t *__restrict__ is_head, uint32_t *__restrict__ len_at_head,
-                               uint8_t *__restrict__ hstrand, uint32_t *covered, uint32_t *too_long) {
+__global__ __launch_bounds__(WALK_BLOCK) void k_fast_measure(const uint32_t *__restrict__ succ, uint64_t n,
+                                                             const uint64_t *__restrict__ node_keys, int k,
+                                                             uint32_t cap, uint32_t *__restrict__ is_head,
+                                                             uint32_t *__restrict__ len_at_head,
+                                                             uint8_t *__restrict__ hstrand, uint32_t *covered,
+                                                             uint32_t *too_long) {
+  __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
+  __shared__ uint32_t s_next[WALK_WARPS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
   uint32_t cov = 0, lng = 0;
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-    if (succ[x ^ 1] != NONE32) continue;  // not a list head
-    uint32_t y = (uint32_t)x, L = 1;
-    for (; L < cap; L++) {
+  for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
+    const uint32_t cnt = queue_heads(c * WALK_CHUNK, n, s_q[w], [&](uint64_t x) { return succ[x ^ 1] == NONE32; });
+    if (lane == 0) s_next[w] = 0;
+    __syncwarp();
+    uint32_t head = NONE32, y = 0, L = 0;
+    for (;;) {
+      if (head == NONE32) {
+        const uint32_t qi = atomicAdd(&s_next[w], 1u);
+        if (qi >= cnt) break;
+        head = s_q[w][qi];
+        y = head;
+        L = 1;
+      }
       const uint32_t ny = succ[y];
-      if (ny == NONE32) break;
-      y = ny;
+      if (ny != NONE32 && L < cap) {
+        y = ny;
+        L++;
+        continue;
+      }
+      if (ny != NONE32) {
+        lng++;
+      } else if (KeyOps<K>::less(strand_kmer<K>(node_keys, head, k), strand_kmer<K>(node_keys, y ^ 1u, k))) {
+        // the mirror copy starts at the tail on the other strand; the copy
+        // whose first k-mer is smaller spells the smaller string
+        const uint32_t v = head >> 1;
+        is_head[v] = 1;
+        len_at_head[v] = L;
+        hstrand[v] = (uint8_t)(head & 1u);
+        cov += 2 * L;
+      }
+      head = NONE32;
     }
-    if (succ[y] != NONE32) {
-      lng++;
-      continue;
-    }
-    // the mirror copy starts at the tail on the other strand; the copy whose
-    // first k-mer is smaller spells the smaller string
-    if (KeyOps<K>::less(strand_kmer<K>(node_keys, (uint32_t)x, k), strand_kmer<K>(node_keys, y ^ 1u, k))) {
-      const uint64_t v = x >> 1;
-      is_head[v] = 1;
-      len_at_head[v] = L;
-      hstrand[v] = (uint8_t)(x & 1);
-      cov += 2 * L;
-    }
+    __syncwarp();
   }
   cov = __reduce_add_sync(0xffffffffu, cov);
   lng = __reduce_add_sync(0xffffffffu, lng);
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     if (cov) atomicAdd(covered, cov);
     if (lng) atomicAdd(too_long, lng);
   }
 }
 
 template <class K>
-__global__ void k_fast_write(const uint32_t *__restrict__ succ, const uint32_t *__restrict__ is_head,
-                             const uint8_t *__restrict__ hstrand, const uint64_t *__restrict__ uidx,
-                             const uint64_t *__restrict__ off_by_v, const uint64_t *__restrict__ node_keys, uint64_t V,
-                             uint64_t U, int k, uint64_t *__restrict__ nodes_out, char *__restrict__ seq,
-                             uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
-                             uint8_t *__restrict__ circular) {
+__global__ __launch_bounds__(WALK_BLOCK) void k_fast_write(
+    const uint32_t *__restrict__ succ, const uint32_t *__restrict__ is_head, const uint8_t *__restrict__ hstrand,
+    const uint64_t *__restrict__ uidx, const uint64_t *__restrict__ off_by_v, const uint64_t *__restrict__ node_keys,
+    uint64_t V, uint64_t U, int k, uint64_t *__restrict__ nodes_out, char *__restrict__ seq,
+    uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off, uint8_t *__restrict__ circular) {
+  __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
+  __shared__ uint32_t s_next[WALK_WARPS];
   const char *acgt = "ACGT";
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
-    if (v == 0) {
-      node_off[U] = V;
-      seq_off[U] = V + U * (uint64_t)(k - 1);
-    }
-    if (!is_head[v]) continue;
-    const uint64_t u = uidx[v], off = off_by_v[v];
-    const uint64_t so = off + u * (uint64_t)(k - 1);
-    node_off[u] = off;
-    seq_off[u] = so;
-    circular[u] = 0;
-    uint32_t y = (uint32_t)(2 * v + hstrand[v]);
-    for (uint64_t i = 0;; i++) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    node_off[U] = V;
+    seq_off[U] = V + U * (uint64_t)(k - 1);
+  }
+  const uint64_t chunks = (V + WALK_CHUNK - 1) / WALK_CHUNK;
+  for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
+    const uint32_t cnt = queue_heads(c * WALK_CHUNK, V, s_q[w], [&](uint64_t v) { return is_head[v] != 0; });
+    if (lane == 0) s_next[w] = 0;
+    __syncwarp();
+    bool busy = false;
+    uint32_t y = 0;
+    uint64_t i = 0, off = 0, so = 0;
+    for (;;) {
+      if (!busy) {
+        const uint32_t qi = atomicAdd(&s_next[w], 1u);
+        if (qi >= cnt) break;
+        const uint32_t v = s_q[w][qi];
+        const uint64_t u = uidx[v];
+        off = off_by_v[v];
+        so = off + u * (uint64_t)(k - 1);
+        node_off[u] = off;
+        seq_off[u] = so;
+        circular[u] = 0;
+        y = 2 * v + hstrand[v];
+        i = 0;
+        busy = true;
+      }
       nodes_out[off + i] = y;  // (node ID << 1) | strand
       const K km = strand_kmer<K>(node_keys, y, k);
       if (i == 0) {
@@ -353,10 +409,22 @@ __global__ void k_fast_write(const uint32_t *__restrict__ succ, const uint32_t *
         seq[so + k - 1 + i] = acgt[KeyOps<K>::low2(km)];
       }
       const uint32_t ny = succ[y];
-      if (ny == NONE32) break;
-      y = ny;
+      if (ny == NONE32) {
+        busy = false;
+      } else {
+        y = ny;
+        i++;
+      }
     }
+    __syncwarp();
   }
+}
+
+// enough warps to fill the device, at most one per chunk
+static unsigned walk_grid(const dbg_ctx *ctx, uint64_t n) {
+  const uint64_t chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
+  const uint64_t blocks = (chunks + WALK_WARPS - 1) / WALK_WARPS;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)std::max(1, ctx->num_sms) * 6));
 }
 
 static unsigned grid_of(uint64_t n) {
@@ -444,7 +512,8 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
       DBG_CUDA_TRY(cudaMemsetAsync(f_len.p, 0, V1 * 4, s));
       DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 10, 0, 2 * sizeof(uint32_t), s));
       DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 32.0 * n + 16.0 * V,
-                 k_fast_measure<K><<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n, g->node_keys.as<uint64_t>(), k,
+                 k_fast_measure<K><<<walk_grid(ctx, n), WALK_BLOCK, 0, s>>>(succ.as<uint32_t>(), n,
+                                                                            g->node_keys.as<uint64_t>(), k,
                                                               kWalkCap, f_is_head.as<uint32_t>(),
                                                               f_len.as<uint32_t>(), f_strand.as<uint8_t>(),
                                                               ctx->d_counters + 10, ctx->d_counters + 11));
@@ -470,7 +539,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
         u->total_bases = V + Uf * (uint64_t)(k - 1);
         DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
         DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)V * (4 + 1 + 16 + 8 + 8 * g->key_words + 1) + (double)Uf * (k + 17),
-                   k_fast_write<K><<<grid_of(V), 256, 0, s>>>(
+                   k_fast_write<K><<<walk_grid(ctx, V), WALK_BLOCK, 0, s>>>(
                        succ.as<uint32_t>(), f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_uidx.as<uint64_t>(),
                        f_off.as<uint64_t>(), g->node_keys.as<uint64_t>(), V, Uf, k, u->nodes.as<uint64_t>(),
                        u->seq.as<char>(), u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(),
