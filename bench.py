@@ -52,6 +52,8 @@ def parse():
                          "time; served: Poisson request stream through the server")
     ap.add_argument("--sets", type=int, default=256, help="read sets of the batched/served workloads")
     ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--local-variant", type=int, default=-1,
+                    help="ranking method of the hybrid sort's local pass (sort kinds 4 and 5)")
     ap.add_argument("--sort-variant", default="", help="a,b,c,d: fixed radix variants per key kind instead "
                                                         "of the autotuner (profiling captures)")
     return ap.parse_args()
@@ -293,7 +295,10 @@ def run_ours(args):
             dbg.dbg_sort_variant_set(ctx, kd, v)
     else:
         tune_ms = dbg.dbg_autotune(ctx)
-    variants = {kd: dbg.dbg_sort_variant_name(kd, dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(4)}
+    if args.local_variant >= 0:
+        for kd in (4, 5):
+            dbg.dbg_sort_variant_set(ctx, kd, args.local_variant)
+    variants = {kd: dbg.dbg_sort_variant_name(kd, dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(6)}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

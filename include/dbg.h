@@ -289,10 +289,12 @@ dbg_status dbg_rle_u64_noalloc(const uint64_t *keys, uint64_t n, uint64_t *uniq,
  * compiled in several configurations per key kind (tile shape, TMA or
  * register loads, ballot / atomicOr / match.any ranking); all sort
  * identically.  Kinds: 0 = 64-bit keys, 1 = 64-bit keys + 32-bit payload,
- * 2 = 128-bit keys, 3 = 128-bit keys + payload.  A context starts with
- * variant 0 of every kind.
+ * 2 = 128-bit keys, 3 = 128-bit keys + payload; kinds 4 (64-bit keys) and
+ * 5 (128-bit keys) select the ranking method of the hybrid sort's local
+ * pass (0 = match.any, 1 = shared-memory atomicOr, 2 = ballots).  A context
+ * starts with variant 0 of every kind.
  * dbg_autotune times one digit pass of every variant on n synthetic keys
- * (0 = 2^25; 128-bit kinds use n / 2) and keeps the fastest of each kind in
+ * (0 = 2^25; 128-bit kinds use n / 2) and keeps the fastest of kinds 0-3 in
  * the context.  cache_path (may be NULL) names a text file of choices keyed
  * by GPU name and SM count: a matching line is used instead of timing, and
  * a new result is appended.  ms_out (may be NULL) receives 4 x 32 pass
@@ -303,6 +305,19 @@ const char *dbg_sort_variant_name(uint32_t kind, uint32_t variant);
 dbg_status dbg_sort_variant_set(dbg_ctx *ctx, uint32_t kind, uint32_t variant);
 int32_t dbg_sort_variant_get(const dbg_ctx *ctx, uint32_t kind);
 dbg_status dbg_autotune(dbg_ctx *ctx, uint64_t n, const char *cache_path, double *ms_out);
+
+/* ----------------------------------------------------------------------
+ * Hybrid sort switch.  With it on (the default) the sorts of STEP-2 and
+ * STEP-3 run the onesweep passes only over the high digits, which groups
+ * keys with equal high bits, and finish each run of whole groups in shared
+ * memory (for the edge keys fused with STEP-2's duplicate removal).  A group
+ * longer than the local sort's window (2048 keys for k <= 31, 1024 above)
+ * makes that sort fall back to the remaining global passes; the result is
+ * the same either way.  dbg_sort_fallbacks counts those fallbacks in the
+ * context.  on = 0 sorts every digit globally.
+ * -------------------------------------------------------------------- */
+dbg_status dbg_sort_hybrid_set(dbg_ctx *ctx, int on);
+uint64_t dbg_sort_fallbacks(const dbg_ctx *ctx);
 
 /* ----------------------------------------------------------------------
  * Failure detection.  Every device-side wait of the library (decoupled

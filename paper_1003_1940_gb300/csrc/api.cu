@@ -101,7 +101,8 @@ dbg_status check_device_error(dbg_ctx *ctx) {
 
 const char *const kStageNames[ST_COUNT] = {
     "offsets", "pack", "emit", "sort_edges", "rle", "endpoints", "sort_nodes", "node_ids",
-    "adjacency", "copies", "compact_links", "compact_rank", "compact_cycles", "compact_output"};
+    "adjacency", "copies", "compact_links", "compact_rank", "compact_cycles", "compact_output",
+    "local_sort_edges", "local_sort_nodes"};
 
 static cudaEvent_t pool_event(dbg_ctx *ctx) {
   if (!ctx->ev_pool.empty()) {
@@ -560,6 +561,13 @@ static const char *variant_name_of(uint32_t kind, uint32_t v, uint32_t *count) {
     case 1: return sort_variant_name_u64(true, v, count);
     case 2: return sort_variant_name_u128(false, v, count);
     case 3: return sort_variant_name_u128(true, v, count);
+    case 4:
+    case 5: {
+      // the local sort's ranking methods (same order as local_rank_method)
+      static const char *const names[] = {"local match", "local atomic", "local ballot"};
+      *count = 3;
+      return v < 3 ? names[v] : nullptr;
+    }
     default: return nullptr;
   }
 }
@@ -576,7 +584,7 @@ const char *dbg_sort_variant_name(uint32_t kind, uint32_t variant) {
 }
 
 dbg_status dbg_sort_variant_set(dbg_ctx *ctx, uint32_t kind, uint32_t variant) {
-  if (!ctx || kind > 3 || variant >= dbg_sort_variant_count(kind)) {
+  if (!ctx || kind > 5 || variant >= dbg_sort_variant_count(kind)) {
     set_error("bad sort variant %u of kind %u", variant, kind);
     return DBG_EINVAL;
   }
@@ -585,8 +593,19 @@ dbg_status dbg_sort_variant_set(dbg_ctx *ctx, uint32_t kind, uint32_t variant) {
 }
 
 int32_t dbg_sort_variant_get(const dbg_ctx *ctx, uint32_t kind) {
-  return (ctx && kind <= 3) ? ctx->sort_variant[kind] : -1;
+  return (ctx && kind <= 5) ? ctx->sort_variant[kind] : -1;
 }
+
+dbg_status dbg_sort_hybrid_set(dbg_ctx *ctx, int on) {
+  if (!ctx) {
+    set_error("null context");
+    return DBG_EINVAL;
+  }
+  ctx->hybrid_sort = on ? 1 : 0;
+  return DBG_OK;
+}
+
+uint64_t dbg_sort_fallbacks(const dbg_ctx *ctx) { return ctx ? ctx->local_sort_fallbacks : 0; }
 
 // cache line format: "<gpu name>|<SMs>" v0 v1 v2 v3
 static std::string tune_cache_key(int device) {

@@ -3,9 +3,11 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "k_build.cuh"
+#include "k_segsort.cuh"
 
 namespace dbg {
 
@@ -167,11 +169,12 @@ const SortVariant &chosen_variant(dbg_ctx *ctx) {
 // Ascending LSD radix sort of n keys (with optional u32 payloads) whose
 // significant bits are the low `bits`.  `hist` holds the per-pass digit
 // histograms (passes x 256), already accumulated by the producer kernel.
-// On return the sorted data is in *keys / *vals (the buffers may have been
-// swapped with *alt_keys / *alt_vals).
+// Passes below first_pass are skipped: the keys are then sorted by their
+// bits from 8 * first_pass up (stably).  On return the data is in *keys /
+// *vals (the buffers may have been swapped with *alt_keys / *alt_vals).
 template <class K, bool HAS_VAL>
 dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uint32_t **alt_vals, uint64_t n,
-                      int bits, const unsigned long long *d_hist, uint64_t *d_digit_base) {
+                      int bits, const unsigned long long *d_hist, uint64_t *d_digit_base, int first_pass = 0) {
   if (n <= 1) return DBG_OK;
   const SortVariant &sv = chosen_variant<K, HAS_VAL>(ctx);
   const int passes = passes_for_bits(bits);
@@ -181,7 +184,7 @@ dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uin
   cudaStream_t s = ctx->stream;
   DBG_LAUNCH(ctx, HAS_VAL ? ST_SORT_NODES : ST_SORT_EDGES, 0.0,
              k_digit_base<<<passes, RADIX, 0, s>>>(d_hist, d_digit_base));
-  for (int p = 0; p < passes; p++) {
+  for (int p = first_pass; p < passes; p++) {
     uint32_t epoch;
     DBG_TRY(next_epoch(ctx, &epoch));
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), s));
@@ -194,6 +197,104 @@ dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uin
   }
   DBG_CUDA_TRY(cudaGetLastError());
   return DBG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Hybrid sort: global onesweep passes over the high digits, then one local
+// pass (k_seg_sort) that finishes each group-aligned tile in shared memory.
+// ---------------------------------------------------------------------------
+template <class K> struct SegShape;
+template <> struct SegShape<uint64_t> {
+  static constexpr int ITEMS = 24, TILE = 4096;  // capacity 6144: groups of up to 2048 keys
+  static constexpr double MAX_MEAN = 128.0;
+};
+template <> struct SegShape<Key128> {
+  static constexpr int ITEMS = 12, TILE = 2048;  // capacity 3072: groups of up to 1024 keys
+  static constexpr double MAX_MEAN = 64.0;
+};
+
+// The first global pass of the hybrid sort of n keys of `bits` bits: the
+// largest p >= 2 for which keys sharing their bits from 8p up form groups of
+// at most MAX_MEAN keys on average (for uniform keys); 0 = no hybrid.
+template <class K>
+int hybrid_first_pass(uint64_t n, int bits) {
+  const int P = passes_for_bits(bits);
+  for (int p = P; p >= 2; p--) {
+    const int hi = bits - RADIX_BITS * p;
+    if (hi <= 0) {
+      if (n <= (uint64_t)SegShape<K>::TILE) return p;  // one tile holds every key
+      continue;
+    }
+    if ((double)n <= SegShape<K>::MAX_MEAN * std::ldexp(1.0, hi)) return p;
+  }
+  return 0;
+}
+
+// ranking method of the local sort, by variant number (kinds 4 and 5)
+inline int local_rank_method(dbg_ctx *ctx, bool wide) {
+  static const int methods[] = {RANK_MATCH, RANK_ATOMIC, RANK_BALLOT};
+  const int v = ctx->sort_variant[wide ? 5 : 4];
+  return methods[(v >= 0 && v < 3) ? v : 0];
+}
+
+template <class F>
+inline void set_smem_attrs(F kern, size_t smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
+// The local pass over node records sorted by their bits from low_bits up:
+// k_seg_sort writes the fully sorted records to kout / vout.  *oversize is
+// set if a group did not fit a tile (the output is then incomplete).
+template <class K>
+dbg_status seg_sort_records(dbg_ctx *ctx, const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, uint64_t n,
+                            int low_bits, int key_bits, uint32_t *oversize) {
+  using Sh = SegShape<K>;
+  const int rank = local_rank_method(ctx, sizeof(K) == 16);
+  auto kern = rank == RANK_MATCH    ? k_seg_sort<K, true, Sh::ITEMS, Sh::TILE, RANK_MATCH>
+              : rank == RANK_ATOMIC ? k_seg_sort<K, true, Sh::ITEMS, Sh::TILE, RANK_ATOMIC>
+                                    : k_seg_sort<K, true, Sh::ITEMS, Sh::TILE, RANK_BALLOT>;
+  constexpr size_t smem = sizeof(SegSortSmem<K, true, Sh::ITEMS>);
+  set_smem_attrs(kern, smem);
+  cudaStream_t s = ctx->stream;
+  const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
+  if (tiles > 0x7fffffffull) return DBG_EOVERFLOW;
+  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 13, 0, sizeof(uint32_t), s));
+  DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 2.0 * (double)n * (sizeof(K) + 4),
+             kern<<<(unsigned)tiles, SEG_BLOCK, smem, s>>>(kin, vin, kout, vout, n, low_bits, key_bits,
+                                                           ctx->d_counters + 13));
+  DBG_CUDA_TRY(cudaGetLastError());
+  return read_small(ctx, ctx->d_counters + 13, sizeof(uint32_t), oversize);
+}
+
+// The local pass of STEP-2 over edge keys sorted by their bits from
+// low_bits up: k_seg_rle writes the distinct keys to uniq and their
+// multiplicities to mult.  res[0] = the number of distinct keys, res[1] =
+// nonzero if a group did not fit a tile (the output is then incomplete).
+template <class K>
+dbg_status seg_rle(dbg_ctx *ctx, const K *kin, K *uniq, uint32_t *mult, uint64_t n, int low_bits, int key_bits,
+                   uint32_t res[2]) {
+  using Sh = SegShape<K>;
+  const int rank = local_rank_method(ctx, sizeof(K) == 16);
+  auto kern = rank == RANK_MATCH    ? k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_MATCH>
+              : rank == RANK_ATOMIC ? k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_ATOMIC>
+                                    : k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_BALLOT>;
+  constexpr size_t smem = sizeof(SegSortSmem<K, false, Sh::ITEMS>);
+  set_smem_attrs(kern, smem);
+  cudaStream_t s = ctx->stream;
+  const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
+  if (tiles > 0x7fffffffull) return DBG_EOVERFLOW;
+  DBG_TRY(ensure_status(ctx, tiles));
+  uint32_t epoch;
+  DBG_TRY(next_epoch(ctx, &epoch));
+  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), s));
+  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 12, 0, 2 * sizeof(uint32_t), s));
+  DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, (double)n * sizeof(K),
+             kern<<<(unsigned)tiles, SEG_BLOCK, smem, s>>>(kin, uniq, mult, n, low_bits, key_bits, ctx->d_status,
+                                                           ctx->d_counters, epoch, ctx->spin_limit, ctx->d_err,
+                                                           ctx->d_counters + 13, ctx->d_counters + 12));
+  DBG_CUDA_TRY(cudaGetLastError());
+  return read_small(ctx, ctx->d_counters + 12, 2 * sizeof(uint32_t), res);
 }
 
 inline unsigned grid_for(uint64_t n, int per_block) {
@@ -214,6 +315,28 @@ inline dbg_status scan_u32(dbg_ctx *ctx, const uint32_t *in, uint64_t n, uint64_
                                                                 ctx->spin_limit, ctx->d_err, ctx->d_counters + 1));
   DBG_CUDA_TRY(cudaGetLastError());
   return read_small(ctx, ctx->d_counters + 1, sizeof(uint32_t), total);
+}
+
+// STEP-3's stable sort of R node records: hybrid when the keys allow it,
+// falling back to the remaining global passes if a group does not fit.
+template <class K>
+dbg_status sort_records(dbg_ctx *ctx, K **rk, K **rk_alt, uint32_t **rv, uint32_t **rv_alt, uint64_t R, int nbits,
+                        const unsigned long long *d_hist, uint64_t *d_digit_base) {
+  const int q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(R, nbits) : 0;
+  if (q0 > 0 && R > 1) {
+    DBG_TRY((radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base, q0)));
+    uint32_t oversize = 0;
+    DBG_TRY(seg_sort_records<K>(ctx, *rk, *rv, *rk_alt, *rv_alt, R, RADIX_BITS * q0, nbits, &oversize));
+    if (oversize == 0) {
+      std::swap(*rk, *rk_alt);
+      std::swap(*rv, *rv_alt);
+      return DBG_OK;
+    }
+    ctx->local_sort_fallbacks++;
+    // the records are sorted by their high digits, stably; a full stable
+    // sort of them keeps equal keys in their original (payload) order
+  }
+  return radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base);
 }
 
 // K4 by reduce-then-scan: unique keys into `uniq`, run heads into headpos
@@ -322,7 +445,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   // ---- K2 emit + digit histograms, K3 sort, K4 run-length reduce ----
   const int kbits = 2 * ((int)k + 1);
   const int kpasses = passes_for_bits(kbits);
-  DevBuf keys_a, keys_b, headpos, uniq;
+  DevBuf keys_a, keys_b, headpos, mult_tmp, uniq;
   uint64_t E = 0;
   K *sorted = nullptr;
   if (N > 0) {
@@ -338,14 +461,32 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     DBG_CUDA_TRY(cudaGetLastError());
     K *kp = keys_a.as<K>(), *alt = keys_b.as<K>();
     uint32_t *vn = nullptr, *van = nullptr;
-    DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, N, kbits, d_hist, d_digit_base)));
-    sorted = kp;
-    // run-length reduce into the other buffer
-    DBG_TRY(alloc_buf(ctx, headpos, (N + 1) * sizeof(uint32_t)));
-    DBG_TRY(run_length_reduce<K>(ctx, sorted, N, alt, headpos.as<uint32_t>(), &E));
+    const int p0 = ctx->hybrid_sort ? hybrid_first_pass<K>(N, kbits) : 0;
+    bool reduced = false;
+    if (p0 > 0) {
+      // high digits globally, then the local sort with the run-length
+      // reduce: distinct keys into alt, multiplicities into mult_tmp
+      DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, N, kbits, d_hist, d_digit_base, p0)));
+      DBG_TRY(alloc_buf(ctx, mult_tmp, N * sizeof(uint32_t)));
+      uint32_t res[2] = {0, 0};
+      DBG_TRY(seg_rle<K>(ctx, kp, alt, mult_tmp.as<uint32_t>(), N, RADIX_BITS * p0, kbits, res));
+      if (res[1] == 0) {
+        E = res[0];
+        reduced = true;
+      } else {
+        mult_tmp.release();
+        ctx->local_sort_fallbacks++;
+      }
+    }
+    if (!reduced) {
+      DBG_TRY(alloc_buf(ctx, headpos, (N + 1) * sizeof(uint32_t)));
+      // every digit globally (keys only: any input order sorts the same)
+      DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, N, kbits, d_hist, d_digit_base)));
+      DBG_TRY(run_length_reduce<K>(ctx, kp, N, alt, headpos.as<uint32_t>(), &E));
+    }
     DBG_TRY(check_device_error(ctx));
-    // keep the buffer holding the unique keys; the sorted keys are done
-    if (sorted == keys_a.as<K>()) { uniq = std::move(keys_b); keys_a.release(); }
+    // keep the buffer holding the unique keys (alt); the sorted keys are done
+    if (alt == keys_b.as<K>()) { uniq = std::move(keys_b); keys_a.release(); }
     else { uniq = std::move(keys_a); keys_b.release(); }
   }
   if (E >= 0x80000000ull) {
@@ -370,7 +511,8 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   if (E > 0) {
     DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)E * (3 * sizeof(K) + 4 + 4 + 1 + 8),
                k_endpoints<K><<<grid_for(E, EMIT_TILE), EMIT_BLOCK, 0, s>>>(
-        uniq.as<K>(), headpos.as<uint32_t>(), E, k, g->edge_keys.as<K>(), g->mult.as<uint32_t>(),
+        uniq.as<K>(), headpos.p ? headpos.as<uint32_t>() : nullptr, mult_tmp.as<uint32_t>(), E, k,
+        g->edge_keys.as<K>(), g->mult.as<uint32_t>(),
         g->orient.as<uint8_t>(), rk_a.as<K>(), rv_a.as<uint32_t>(), npasses, d_hist));
   }
   if (I > 0) {
@@ -384,6 +526,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   DBG_CUDA_TRY(cudaGetLastError());
   uniq.release();
   headpos.release();
+  mult_tmp.release();
   packed.release();
   base_off.release();
   edge_off.release();
@@ -391,7 +534,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   // ---- STEP-3 sort of the node records (stable: payload order kept) ----
   K *rk = rk_a.as<K>(), *rk_alt = rk_b.as<K>();
   uint32_t *rv = rv_a.as<uint32_t>(), *rv_alt = rv_b.as<uint32_t>();
-  DBG_TRY((radix_sort<K, true>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, d_hist, d_digit_base)));
+  DBG_TRY((sort_records<K>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, d_hist, d_digit_base)));
 
   // ---- K6 node IDs + adjacency rows, K7 neighbours ----
   DevBuf row_tmp;

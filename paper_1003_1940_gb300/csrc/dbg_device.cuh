@@ -44,6 +44,10 @@ template <> struct KeyOps<uint64_t> {
   __device__ static uint64_t low2(uint64_t a) { return a & 3ull; }
   __device__ static uint64_t words_hi(uint64_t) { return 0; }
   __device__ static uint64_t words_lo(uint64_t a) { return a; }
+  __device__ static uint64_t sub(uint64_t a, uint64_t b) { return a - b; }
+  __device__ static uint64_t add(uint64_t a, uint64_t b) { return a + b; }
+  // number of significant bits (0 for 0)
+  __device__ static int bitlen(uint64_t a) { return a ? 64 - __clzll((long long)a) : 0; }
 };
 
 template <> struct KeyOps<Key128> {
@@ -74,6 +78,16 @@ template <> struct KeyOps<Key128> {
   __device__ static uint64_t low2(Key128 a) { return a.lo & 3ull; }
   __device__ static uint64_t words_hi(Key128 a) { return a.hi; }
   __device__ static uint64_t words_lo(Key128 a) { return a.lo; }
+  __device__ static Key128 sub(Key128 a, Key128 b) {
+    return Key128{a.hi - b.hi - (a.lo < b.lo ? 1ull : 0ull), a.lo - b.lo};
+  }
+  __device__ static Key128 add(Key128 a, Key128 b) {
+    const uint64_t lo = a.lo + b.lo;
+    return Key128{a.hi + b.hi + (lo < a.lo ? 1ull : 0ull), lo};
+  }
+  __device__ static int bitlen(Key128 a) {
+    return a.hi ? 128 - __clzll((long long)a.hi) : (a.lo ? 64 - __clzll((long long)a.lo) : 0);
+  }
 };
 
 // Swap the two bits of every 2-bit group.

@@ -53,7 +53,7 @@ struct DevBuf {
 enum Stage {
   ST_OFFSETS, ST_PACK, ST_EMIT, ST_SORT_EDGES, ST_RLE, ST_ENDPOINTS, ST_SORT_NODES, ST_NODE_IDS,
   ST_ADJACENCY, ST_COPIES, ST_COMPACT_LINKS, ST_COMPACT_RANK, ST_COMPACT_CYCLES, ST_COMPACT_OUTPUT,
-  ST_COUNT
+  ST_LOCAL_SORT_EDGES, ST_LOCAL_SORT_NODES, ST_COUNT
 };
 extern const char *const kStageNames[ST_COUNT];
 
@@ -73,7 +73,11 @@ struct dbg_ctx {
   dbg::Allocator al;
   uint64_t mem_budget = 0;
   uint32_t spin_limit = 1u << 22;
-  int sort_variant[4] = {0, 0, 0, 0};  // per key kind (0: u64, 1: u64+payload, 2: u128, 3: u128+payload)
+  // per sort kind: onesweep passes over 0: u64, 1: u64+payload, 2: u128,
+  // 3: u128+payload keys; the local sort's ranking for 4: u64, 5: u128 keys
+  int sort_variant[6] = {0, 0, 0, 0, 0, 0};
+  int hybrid_sort = 1;                 // high digits globally + local sort of group-aligned tiles
+  uint64_t local_sort_fallbacks = 0;   // local sorts that met a group longer than their window
   int num_sms = 0;
   // persistent scratch: the look-back status words of every scan and sort
   // pass, tagged by epoch so they never need clearing between uses

@@ -737,11 +737,13 @@ static __global__ __launch_bounds__(SCAN_BLOCK) void k_scan_excl(const uint32_t 
 // negative strand, STEP-1's table gives (x^, y^, o1, o2) if x^ <= y^ and
 // (y^, x^, not o2, not o1) otherwise.  Writes orient, mult, a copy of the
 // key into the graph, and two node records per edge (payload e<<1 | role),
-// and accumulates the digit histograms of the node sort.
+// and accumulates the digit histograms of the node sort.  The multiplicity
+// comes from the run heads (headpos) or directly from mult_in.
 // ---------------------------------------------------------------------------
 template <class K>
 __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ uniq,
-                                                          const uint32_t *__restrict__ headpos, uint64_t E,
+                                                          const uint32_t *__restrict__ headpos,
+                                                          const uint32_t *__restrict__ mult_in, uint64_t E,
                                                           uint32_t k, K *__restrict__ edge_keys,
                                                           uint32_t *__restrict__ mult,
                                                           uint8_t *__restrict__ orient, K *__restrict__ rkeys,
@@ -765,7 +767,7 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ 
     else { s = yh; d = xh; a = !o2; b = !o1; }
     edge_keys[e] = z;
     orient[e] = (uint8_t)((a << 1) | b);
-    mult[e] = headpos[e + 1] - headpos[e];
+    mult[e] = headpos ? headpos[e + 1] - headpos[e] : mult_in[e];
     rkeys[2 * e] = s;
     rvals[2 * e] = (uint32_t)(e << 1);
     rkeys[2 * e + 1] = d;

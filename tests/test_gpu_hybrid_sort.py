@@ -1,0 +1,80 @@
+"""The hybrid sort (global passes over the high digits, then a local sort of
+group-aligned tiles in shared memory, fused with the run-length reduce for the
+edge keys) gives bit-for-bit the graph of the all-global sort and the oracle's,
+including when a group is too long for a tile and the sort falls back."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import assert_graph_equal, check_parity, gpu_graph
+from paper_1003_1940_gb300 import readgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dbg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1003_1940_gb300 import dbg as d
+    d.load()
+    return d
+
+
+def same(a: dict, b: dict):
+    assert a.keys() == b.keys()
+    for key in a:
+        if isinstance(a[key], np.ndarray):
+            np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+        else:
+            assert a[key] == b[key], key
+
+
+@pytest.mark.parametrize("k,n_reads,L", [(15, 20_000, 60), (21, 30_000, 100), (31, 40_000, 100),
+                                         (33, 15_000, 120), (55, 12_000, 150), (63, 8_000, 150)])
+def test_hybrid_equals_global_sort(dbg, k, n_reads, L):
+    """Hundreds of local tiles with a ragged last one, for every key width."""
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(200_000, n_reads, L, 0.01, k, 500 + k))
+    lengths = lengths.copy()
+    lengths[-1] = L - 7  # a ragged tail
+    reads = reads[:int(lengths.sum())]
+    ctx = dbg.Context()
+    _, hyb = gpu_graph(dbg, ctx, reads, lengths, k)
+    assert dbg.dbg_sort_fallbacks(ctx) == 0
+    dbg.dbg_sort_hybrid_set(ctx, False)
+    _, glob = gpu_graph(dbg, ctx, reads, lengths, k)
+    same(hyb, glob)
+    assert_graph_equal(hyb, oracle.build_graph(reads, lengths, k))
+
+
+def test_group_longer_than_window_falls_back(dbg):
+    """10,000 copies of one (k+1)-mer form a group longer than a tile can
+    hold (6,144 keys): the edge sort falls back to the global passes."""
+    k = 21
+    rng = np.random.default_rng(7)
+    rep = "".join("ACGT"[c] for c in rng.integers(0, 4, size=k + 1))
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(50_000, 2_000, 60, 0.01, k, 71))
+    reads = np.concatenate([reads, np.frombuffer((rep * 10_000).encode(), dtype=np.uint8)])
+    lengths = np.concatenate([lengths, np.full(10_000, k + 1, dtype=np.uint32)])
+    ctx = dbg.Context()
+    got = check_parity(dbg, ctx, reads, lengths, k)
+    assert dbg.dbg_sort_fallbacks(ctx) >= 1
+    assert got["e_mult"].max() >= 10_000
+
+
+def test_node_records_fall_back(dbg):
+    """8,000 reads of exactly k bases that share their first seven: 8,000
+    node records with equal high bits, a group longer than a tile of the
+    node-record sort can hold, which falls back; plus ordinary reads."""
+    k = 15
+    rng = np.random.default_rng(8)
+    tails = rng.integers(0, 4, size=(8_000, k - 7))
+    reads = ["AAAAAAA" + "".join("ACGT"[c] for c in t) for t in tails]
+    r2, l2 = readgen.generate(readgen.ReadSetSpec(20_000, 300, 50, 0.01, k, 81))
+    data = np.concatenate([np.frombuffer("".join(reads).encode(), dtype=np.uint8), r2])
+    lengths = np.concatenate([np.full(8_000, k, dtype=np.uint32), l2])
+    ctx = dbg.Context()
+    check_parity(dbg, ctx, data, lengths, k)
+    assert dbg.dbg_sort_fallbacks(ctx) >= 1

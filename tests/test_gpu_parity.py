@@ -152,23 +152,24 @@ def test_repeat_calls_identical(dbg, ctx):
 
 
 def test_every_sort_variant_sorts_identically(dbg, ctx):
-    """Each compiled radix-sort configuration gives the oracle's graph."""
+    """Each compiled radix-sort configuration (onesweep passes and the local
+    sort's ranking methods) gives the oracle's graph."""
     small64 = readgen.generate(readgen.ReadSetSpec(40_000, 3_000, 100, 0.01, 31, 41))
     small128 = readgen.generate(readgen.ReadSetSpec(30_000, 1_500, 120, 0.01, 55, 42))
     og64 = oracle.build_graph(*small64, 31)
     og128 = oracle.build_graph(*small128, 55)
-    counts = [dbg.dbg_sort_variant_count(kd) for kd in range(4)]
+    counts = [dbg.dbg_sort_variant_count(kd) for kd in range(6)]
     from parity import assert_graph_equal
     try:
         for v in range(max(counts)):
-            for kd in range(4):
+            for kd in range(6):
                 dbg.dbg_sort_variant_set(ctx, kd, min(v, counts[kd] - 1))
             _, got = gpu_graph(dbg, ctx, *small64, 31)
             assert_graph_equal(got, og64)
             _, got = gpu_graph(dbg, ctx, *small128, 55)
             assert_graph_equal(got, og128)
     finally:
-        for kd in range(4):
+        for kd in range(6):
             dbg.dbg_sort_variant_set(ctx, kd, 0)
 
 
