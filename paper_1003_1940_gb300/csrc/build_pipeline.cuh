@@ -319,10 +319,11 @@ inline dbg_status scan_u32(dbg_ctx *ctx, const uint32_t *in, uint64_t n, uint64_
 
 // STEP-3's stable sort of R node records: hybrid when the keys allow it,
 // falling back to the remaining global passes if a group does not fit.
+// q0 = the first global pass (the producers accumulated only the
+// histograms of passes q0 and up), 0 for a full global sort.
 template <class K>
 dbg_status sort_records(dbg_ctx *ctx, K **rk, K **rk_alt, uint32_t **rv, uint32_t **rv_alt, uint64_t R, int nbits,
-                        const unsigned long long *d_hist, uint64_t *d_digit_base) {
-  const int q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(R, nbits) : 0;
+                        int q0, unsigned long long *d_hist, uint64_t *d_digit_base) {
   if (q0 > 0 && R > 1) {
     DBG_TRY((radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base, q0)));
     uint32_t oversize = 0;
@@ -336,6 +337,9 @@ dbg_status sort_records(dbg_ctx *ctx, K **rk, K **rk_alt, uint32_t **rv, uint32_
     // the records are sorted by their high digits, stably; a full stable
     // sort of them keeps equal keys in their original (payload) order
   }
+  if (q0 > 0 && R > 1)
+    DBG_LAUNCH(ctx, ST_SORT_NODES, (double)R * sizeof(K),
+               k_digit_hist<K><<<std::min(grid_for(R, 256 * 16), 152u * 8), 256, 0, ctx->stream>>>(*rk, R, 0, q0, d_hist));
   return radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base);
 }
 
@@ -452,16 +456,17 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     DBG_TRY(alloc_buf(ctx, keys_a, N * sizeof(K)));
     DBG_TRY(alloc_buf(ctx, keys_b, N * sizeof(K)));
     DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
+    // the hybrid sort needs the histograms of its global passes only
+    const int p0 = ctx->hybrid_sort ? hybrid_first_pass<K>(N, kbits) : 0;
     {
       DBG_LAUNCH(ctx, ST_EMIT, 8.0 * nwords + 16.0 * n + (double)N * sizeof(K),
                  k_emit<K><<<(unsigned)std::min<uint64_t>(grid_for(n, EMIT_BLOCK / 32), 152ull * 64), EMIT_BLOCK, 0, s>>>(
                      packed.as<uint64_t>(), base_off.as<uint64_t>(), edge_off.as<uint64_t>(), n, k, keys_a.as<K>(),
-                     kpasses, d_hist));
+                     p0, kpasses, d_hist));
     }
     DBG_CUDA_TRY(cudaGetLastError());
     K *kp = keys_a.as<K>(), *alt = keys_b.as<K>();
     uint32_t *vn = nullptr, *van = nullptr;
-    const int p0 = ctx->hybrid_sort ? hybrid_first_pass<K>(N, kbits) : 0;
     bool reduced = false;
     if (p0 > 0) {
       // high digits globally, then the local sort with the run-length
@@ -481,6 +486,9 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     if (!reduced) {
       DBG_TRY(alloc_buf(ctx, headpos, (N + 1) * sizeof(uint32_t)));
       // every digit globally (keys only: any input order sorts the same)
+      if (p0 > 0)
+        DBG_LAUNCH(ctx, ST_SORT_EDGES, (double)N * sizeof(K),
+                   k_digit_hist<K><<<std::min(grid_for(N, 256 * 16), 152u * 8), 256, 0, s>>>(kp, N, 0, p0, d_hist));
       DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, N, kbits, d_hist, d_digit_base)));
       DBG_TRY(run_length_reduce<K>(ctx, kp, N, alt, headpos.as<uint32_t>(), &E));
     }
@@ -508,19 +516,20 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   DBG_TRY(alloc_buf(ctx, rv_a, std::max<uint64_t>(1, R) * sizeof(uint32_t)));
   DBG_TRY(alloc_buf(ctx, rv_b, std::max<uint64_t>(1, R) * sizeof(uint32_t)));
   DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
+  const int q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(R, nbits) : 0;
   if (E > 0) {
     DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)E * (3 * sizeof(K) + 4 + 4 + 1 + 8),
                k_endpoints<K><<<grid_for(E, EMIT_TILE), EMIT_BLOCK, 0, s>>>(
         uniq.as<K>(), headpos.p ? headpos.as<uint32_t>() : nullptr, mult_tmp.as<uint32_t>(), E, k,
         g->edge_keys.as<K>(), g->mult.as<uint32_t>(),
-        g->orient.as<uint8_t>(), rk_a.as<K>(), rv_a.as<uint32_t>(), npasses, d_hist));
+        g->orient.as<uint8_t>(), rk_a.as<K>(), rv_a.as<uint32_t>(), q0, npasses, d_hist));
   }
   if (I > 0) {
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 2, 0, sizeof(uint32_t), s));
     DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)n * 4 + (double)I * (sizeof(K) + 4),
                k_isolated<K><<<grid_for(n, 256), 256, 0, s>>>(packed.as<uint64_t>(), base_off.as<uint64_t>(),
                                                    in.d_lengths, n, k, rk_a.as<K>() + 2 * E,
-                                                   rv_a.as<uint32_t>() + 2 * E, ctx->d_counters + 2, npasses,
+                                                   rv_a.as<uint32_t>() + 2 * E, ctx->d_counters + 2, q0, npasses,
                                                    d_hist));
   }
   DBG_CUDA_TRY(cudaGetLastError());
@@ -534,7 +543,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   // ---- STEP-3 sort of the node records (stable: payload order kept) ----
   K *rk = rk_a.as<K>(), *rk_alt = rk_b.as<K>();
   uint32_t *rv = rv_a.as<uint32_t>(), *rv_alt = rv_b.as<uint32_t>();
-  DBG_TRY((sort_records<K>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, d_hist, d_digit_base)));
+  DBG_TRY((sort_records<K>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, q0, d_hist, d_digit_base)));
 
   // ---- K6 node IDs + adjacency rows, K7 neighbours ----
   DevBuf row_tmp;

@@ -262,10 +262,11 @@ template <class K>
 __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict__ packed,
                                                      const uint64_t *__restrict__ base_off,
                                                      const uint64_t *__restrict__ edge_off, uint64_t n_reads,
-                                                     uint32_t k, K *__restrict__ keys, int passes,
+                                                     uint32_t k, K *__restrict__ keys, int first, int passes,
                                                      unsigned long long *__restrict__ hist) {
   // one warp per read: lanes take consecutive positions, so every warp-wide
-  // store writes 32 consecutive keys
+  // store writes 32 consecutive keys; the digit histograms of passes
+  // [first, passes) are accumulated on the way
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK) s_hist[i] = 0;
   __syncthreads();
@@ -278,13 +279,31 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict_
       const K z = load_window<K>(packed, p0 + j, m);
       const K key = kmin(z, revcomp(z, m));
       keys[e0 + j] = key;
-      for (int ps = 0; ps < passes; ps++)
+      for (int ps = first; ps < passes; ps++)
         atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(key, ps * RADIX_BITS, RADIX_BITS)], 1u);
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK)
     if (s_hist[i]) atomicAdd(hist + i, (unsigned long long)s_hist[i]);
+}
+
+// Digit histograms of passes [first, last) of n keys (any order): what the
+// producer kernels skipped when only the high digits were to be sorted
+// globally.
+template <class K>
+__global__ void k_digit_hist(const K *__restrict__ keys, uint64_t n, int first, int last,
+                             unsigned long long *__restrict__ hist) {
+  __shared__ uint32_t h[MAX_PASSES * RADIX];
+  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const K key = keys[i];
+    for (int ps = first; ps < last; ps++) atomicAdd(&h[ps * RADIX + KeyOps<K>::digit(key, ps * RADIX_BITS, RADIX_BITS)], 1u);
+  }
+  __syncthreads();
+  for (int i = first * RADIX + threadIdx.x; i < last * RADIX; i += blockDim.x)
+    if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
 }
 
 // digit_base[p][d] = number of keys whose digit p is below d
@@ -747,7 +766,7 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ 
                                                           uint32_t k, K *__restrict__ edge_keys,
                                                           uint32_t *__restrict__ mult,
                                                           uint8_t *__restrict__ orient, K *__restrict__ rkeys,
-                                                          uint32_t *__restrict__ rvals, int passes,
+                                                          uint32_t *__restrict__ rvals, int first, int passes,
                                                           unsigned long long *__restrict__ hist) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK) s_hist[i] = 0;
@@ -772,7 +791,7 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ 
     rvals[2 * e] = (uint32_t)(e << 1);
     rkeys[2 * e + 1] = d;
     rvals[2 * e + 1] = (uint32_t)(e << 1) | 1u;
-    for (int ps = 0; ps < passes; ps++) {
+    for (int ps = first; ps < passes; ps++) {
       atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(s, ps * RADIX_BITS, RADIX_BITS)], 1u);
       atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(d, ps * RADIX_BITS, RADIX_BITS)], 1u);
     }
@@ -788,7 +807,7 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ 
 template <class K>
 __global__ void k_isolated(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ base_off,
                            const uint32_t *__restrict__ len, uint64_t n, uint32_t k, K *__restrict__ rkeys,
-                           uint32_t *__restrict__ rvals, uint32_t *slot, int passes,
+                           uint32_t *__restrict__ rvals, uint32_t *slot, int first, int passes,
                            unsigned long long *__restrict__ hist) {
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
     if (len[r] != k) continue;
@@ -797,7 +816,7 @@ __global__ void k_isolated(const uint64_t *__restrict__ packed, const uint64_t *
     const uint32_t i = atomicAdd(slot, 1u);
     rkeys[i] = xh;
     rvals[i] = REC_NONE;
-    for (int ps = 0; ps < passes; ps++)
+    for (int ps = first; ps < passes; ps++)
       atomicAdd(hist + ps * RADIX + KeyOps<K>::digit(xh, ps * RADIX_BITS, RADIX_BITS), 1ull);
   }
 }
