@@ -310,11 +310,12 @@ dbg_status dbg_autotune(dbg_ctx *ctx, uint64_t n, const char *cache_path, double
  * Hybrid sort switch.  With it on (the default) the sorts of STEP-2 and
  * STEP-3 run the onesweep passes only over the high digits, which groups
  * keys with equal high bits, and finish each run of whole groups in shared
- * memory (for the edge keys fused with STEP-2's duplicate removal).  A group
- * longer than the local sort's window (2048 keys for k <= 31, 1024 above)
- * makes that sort fall back to the remaining global passes; the result is
- * the same either way.  dbg_sort_fallbacks counts those fallbacks in the
- * context.  on = 0 sorts every digit globally.
+ * memory (for the edge keys fused with STEP-2's duplicate removal).  Runs
+ * longer than shared memory holds (6144 keys for k <= 31, 3072 above; e.g.
+ * the (k+1)-mers of a tandem repeat) are gathered and sorted over every
+ * digit globally instead; the result is the same either way.
+ * dbg_sort_fallbacks counts the sorts of the context that had such runs.
+ * on = 0 sorts every digit globally.
  * -------------------------------------------------------------------- */
 dbg_status dbg_sort_hybrid_set(dbg_ctx *ctx, int on);
 uint64_t dbg_sort_fallbacks(const dbg_ctx *ctx);

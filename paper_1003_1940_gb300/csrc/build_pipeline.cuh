@@ -243,60 +243,6 @@ inline void set_smem_attrs(F kern, size_t smem) {
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
-// The local pass over node records sorted by their bits from low_bits up:
-// k_seg_sort writes the fully sorted records to kout / vout.  *oversize is
-// set if a group did not fit a tile (the output is then incomplete).
-template <class K>
-dbg_status seg_sort_records(dbg_ctx *ctx, const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, uint64_t n,
-                            int low_bits, int key_bits, uint32_t *oversize) {
-  using Sh = SegShape<K>;
-  const int rank = local_rank_method(ctx, sizeof(K) == 16);
-  auto kern = rank == RANK_MATCH    ? k_seg_sort<K, true, Sh::ITEMS, Sh::TILE, RANK_MATCH>
-              : rank == RANK_ATOMIC ? k_seg_sort<K, true, Sh::ITEMS, Sh::TILE, RANK_ATOMIC>
-                                    : k_seg_sort<K, true, Sh::ITEMS, Sh::TILE, RANK_BALLOT>;
-  constexpr size_t smem = sizeof(SegSortSmem<K, true, Sh::ITEMS>);
-  set_smem_attrs(kern, smem);
-  cudaStream_t s = ctx->stream;
-  const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
-  if (tiles > 0x7fffffffull) return DBG_EOVERFLOW;
-  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 13, 0, sizeof(uint32_t), s));
-  DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 2.0 * (double)n * (sizeof(K) + 4),
-             kern<<<(unsigned)tiles, SEG_BLOCK, smem, s>>>(kin, vin, kout, vout, n, low_bits, key_bits,
-                                                           ctx->d_counters + 13));
-  DBG_CUDA_TRY(cudaGetLastError());
-  return read_small(ctx, ctx->d_counters + 13, sizeof(uint32_t), oversize);
-}
-
-// The local pass of STEP-2 over edge keys sorted by their bits from
-// low_bits up: k_seg_rle writes the distinct keys to uniq and their
-// multiplicities to mult.  res[0] = the number of distinct keys, res[1] =
-// nonzero if a group did not fit a tile (the output is then incomplete).
-template <class K>
-dbg_status seg_rle(dbg_ctx *ctx, const K *kin, K *uniq, uint32_t *mult, uint64_t n, int low_bits, int key_bits,
-                   uint32_t res[2]) {
-  using Sh = SegShape<K>;
-  const int rank = local_rank_method(ctx, sizeof(K) == 16);
-  auto kern = rank == RANK_MATCH    ? k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_MATCH>
-              : rank == RANK_ATOMIC ? k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_ATOMIC>
-                                    : k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_BALLOT>;
-  constexpr size_t smem = sizeof(SegSortSmem<K, false, Sh::ITEMS>);
-  set_smem_attrs(kern, smem);
-  cudaStream_t s = ctx->stream;
-  const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
-  if (tiles > 0x7fffffffull) return DBG_EOVERFLOW;
-  DBG_TRY(ensure_status(ctx, tiles));
-  uint32_t epoch;
-  DBG_TRY(next_epoch(ctx, &epoch));
-  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), s));
-  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 12, 0, 2 * sizeof(uint32_t), s));
-  DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, (double)n * sizeof(K),
-             kern<<<(unsigned)tiles, SEG_BLOCK, smem, s>>>(kin, uniq, mult, n, low_bits, key_bits, ctx->d_status,
-                                                           ctx->d_counters, epoch, ctx->spin_limit, ctx->d_err,
-                                                           ctx->d_counters + 13, ctx->d_counters + 12));
-  DBG_CUDA_TRY(cudaGetLastError());
-  return read_small(ctx, ctx->d_counters + 12, 2 * sizeof(uint32_t), res);
-}
-
 inline unsigned grid_for(uint64_t n, int per_block) {
   uint64_t g = (n + per_block - 1) / per_block;
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, 0x7fffffffull));
@@ -315,32 +261,6 @@ inline dbg_status scan_u32(dbg_ctx *ctx, const uint32_t *in, uint64_t n, uint64_
                                                                 ctx->spin_limit, ctx->d_err, ctx->d_counters + 1));
   DBG_CUDA_TRY(cudaGetLastError());
   return read_small(ctx, ctx->d_counters + 1, sizeof(uint32_t), total);
-}
-
-// STEP-3's stable sort of R node records: hybrid when the keys allow it,
-// falling back to the remaining global passes if a group does not fit.
-// q0 = the first global pass (the producers accumulated only the
-// histograms of passes q0 and up), 0 for a full global sort.
-template <class K>
-dbg_status sort_records(dbg_ctx *ctx, K **rk, K **rk_alt, uint32_t **rv, uint32_t **rv_alt, uint64_t R, int nbits,
-                        int q0, unsigned long long *d_hist, uint64_t *d_digit_base) {
-  if (q0 > 0 && R > 1) {
-    DBG_TRY((radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base, q0)));
-    uint32_t oversize = 0;
-    DBG_TRY(seg_sort_records<K>(ctx, *rk, *rv, *rk_alt, *rv_alt, R, RADIX_BITS * q0, nbits, &oversize));
-    if (oversize == 0) {
-      std::swap(*rk, *rk_alt);
-      std::swap(*rv, *rv_alt);
-      return DBG_OK;
-    }
-    ctx->local_sort_fallbacks++;
-    // the records are sorted by their high digits, stably; a full stable
-    // sort of them keeps equal keys in their original (payload) order
-  }
-  if (q0 > 0 && R > 1)
-    DBG_LAUNCH(ctx, ST_SORT_NODES, (double)R * sizeof(K),
-               k_digit_hist<K><<<std::min(grid_for(R, 256 * 16), 152u * 8), 256, 0, ctx->stream>>>(*rk, R, 0, q0, d_hist));
-  return radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base);
 }
 
 // K4 by reduce-then-scan: unique keys into `uniq`, run heads into headpos
@@ -362,6 +282,142 @@ dbg_status run_length_reduce(dbg_ctx *ctx, const K *sorted, uint64_t n, K *uniq,
   DBG_CUDA_TRY(cudaGetLastError());
   *E = total;
   return DBG_OK;
+}
+
+// Tile bounds of the local pass over n keys sorted by their bits from
+// low_bits up, and the oversize tiles (longer than the shared-memory
+// capacity) gathered into *gk / *gv and sorted over every digit.  Returns the
+// number of gathered keys in *G (0: none).
+template <class K, bool HAS_VAL>
+dbg_status seg_prepare(dbg_ctx *ctx, const K *kin, const uint32_t *vin, uint64_t n, int low_bits, int key_bits,
+                       DevBuf &bound, DevBuf &osize, DevBuf &ooff, DevBuf &gk, DevBuf &gv, uint32_t *G, int stage) {
+  using Sh = SegShape<K>;
+  cudaStream_t s = ctx->stream;
+  const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
+  if (tiles > 0x7fffffffull) return DBG_EOVERFLOW;
+  DBG_TRY(alloc_buf(ctx, bound, (tiles + 1) * 8));
+  DBG_TRY(alloc_buf(ctx, osize, tiles * 4));
+  DBG_TRY(alloc_buf(ctx, ooff, (tiles + 1) * 8));
+  DBG_LAUNCH(ctx, stage, 0.0,
+             k_seg_bounds<K><<<grid_for(tiles + 1, 256), 256, 0, s>>>(kin, n, low_bits, Sh::TILE, tiles,
+                                                                     bound.as<uint64_t>()));
+  DBG_LAUNCH(ctx, stage, 0.0,
+             k_seg_oversize<<<grid_for(tiles, 256), 256, 0, s>>>(bound.as<uint64_t>(), tiles,
+                                                                 (uint32_t)(SEG_BLOCK * Sh::ITEMS),
+                                                                 osize.as<uint32_t>()));
+  DBG_TRY(scan_u32(ctx, osize.as<uint32_t>(), tiles, ooff.as<uint64_t>(), G, stage));
+  if (*G == 0) return DBG_OK;
+  // the oversize tiles, gathered in order and sorted over every digit
+  const uint64_t g = *G;
+  DevBuf galt, gvalt, small;
+  DBG_TRY(alloc_buf(ctx, gk, g * sizeof(K)));
+  DBG_TRY(alloc_buf(ctx, galt, g * sizeof(K)));
+  if (HAS_VAL) {
+    DBG_TRY(alloc_buf(ctx, gv, g * 4));
+    DBG_TRY(alloc_buf(ctx, gvalt, g * 4));
+  }
+  DBG_TRY(alloc_buf(ctx, small, MAX_PASSES * RADIX * 16));
+  unsigned long long *hist = small.as<unsigned long long>();
+  uint64_t *dbase = reinterpret_cast<uint64_t *>(hist + MAX_PASSES * RADIX);
+  const int passes = passes_for_bits(key_bits);
+  DBG_LAUNCH(ctx, stage, 2.0 * g * (sizeof(K) + (HAS_VAL ? 4 : 0)),
+             k_seg_gather<K, HAS_VAL><<<(unsigned)std::min<uint64_t>(tiles, 152ull * 8), 256, 0, s>>>(
+                 kin, vin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), tiles, gk.as<K>(),
+                 HAS_VAL ? gv.as<uint32_t>() : nullptr));
+  DBG_CUDA_TRY(cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 8, s));
+  DBG_LAUNCH(ctx, stage, (double)g * sizeof(K),
+             k_digit_hist<K><<<std::min(grid_for(g, 256 * 16), 152u * 8), 256, 0, s>>>(gk.as<K>(), g, 0, passes,
+                                                                                       hist));
+  K *kp = gk.as<K>(), *ka = galt.as<K>();
+  uint32_t *vp = HAS_VAL ? gv.as<uint32_t>() : nullptr, *va = HAS_VAL ? gvalt.as<uint32_t>() : nullptr;
+  DBG_TRY((radix_sort<K, HAS_VAL>(ctx, &kp, &ka, &vp, &va, g, key_bits, hist, dbase)));
+  if (kp != gk.as<K>()) std::swap(gk, galt);
+  if (HAS_VAL && vp != gv.as<uint32_t>()) std::swap(gv, gvalt);
+  ctx->local_sort_fallbacks++;
+  return DBG_OK;
+}
+
+// The local pass over node records sorted by their bits from low_bits up:
+// k_seg_sort writes the fully sorted records to kout / vout.
+template <class K>
+dbg_status seg_sort_records(dbg_ctx *ctx, const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, uint64_t n,
+                            int low_bits, int key_bits) {
+  using Sh = SegShape<K>;
+  DevBuf bound, osize, ooff, gk, gv;
+  uint32_t G = 0;
+  DBG_TRY((seg_prepare<K, true>(ctx, kin, vin, n, low_bits, key_bits, bound, osize, ooff, gk, gv, &G,
+                                ST_LOCAL_SORT_NODES)));
+  const int rank = local_rank_method(ctx, sizeof(K) == 16);
+  auto kern = rank == RANK_MATCH    ? k_seg_sort<K, Sh::ITEMS, RANK_MATCH>
+              : rank == RANK_ATOMIC ? k_seg_sort<K, Sh::ITEMS, RANK_ATOMIC>
+                                    : k_seg_sort<K, Sh::ITEMS, RANK_BALLOT>;
+  constexpr size_t smem = sizeof(SegSortSmem<K, true, Sh::ITEMS>);
+  set_smem_attrs(kern, smem);
+  const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
+  DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 2.0 * (double)n * (sizeof(K) + 4),
+             kern<<<(unsigned)tiles, SEG_BLOCK, smem, ctx->stream>>>(
+                 kin, vin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), gk.as<K>(),
+                 gv.as<uint32_t>(), kout, vout, low_bits, key_bits));
+  DBG_CUDA_TRY(cudaGetLastError());
+  return DBG_OK;
+}
+
+// The local pass of STEP-2 over edge keys sorted by their bits from
+// low_bits up: k_seg_rle writes the distinct keys to uniq and their
+// multiplicities to mult; *E = the number of distinct keys.
+template <class K>
+dbg_status seg_rle(dbg_ctx *ctx, const K *kin, K *uniq, uint32_t *mult, uint64_t n, int low_bits, int key_bits,
+                   uint64_t *E) {
+  using Sh = SegShape<K>;
+  cudaStream_t s = ctx->stream;
+  DevBuf bound, osize, ooff, gk, gv, gheads, guniq;
+  uint32_t G = 0;
+  DBG_TRY((seg_prepare<K, false>(ctx, kin, nullptr, n, low_bits, key_bits, bound, osize, ooff, gk, gv, &G,
+                                 ST_LOCAL_SORT_EDGES)));
+  uint64_t H = 0;
+  if (G > 0) {
+    DBG_TRY(alloc_buf(ctx, guniq, (uint64_t)G * sizeof(K)));
+    DBG_TRY(alloc_buf(ctx, gheads, ((uint64_t)G + 1) * 4));
+    DBG_TRY(run_length_reduce<K>(ctx, gk.as<K>(), G, guniq.as<K>(), gheads.as<uint32_t>(), &H));
+  }
+  const int rank = local_rank_method(ctx, sizeof(K) == 16);
+  auto kern = rank == RANK_MATCH    ? k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_MATCH>
+              : rank == RANK_ATOMIC ? k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_ATOMIC>
+                                    : k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_BALLOT>;
+  constexpr size_t smem = sizeof(SegSortSmem<K, false, Sh::ITEMS>);
+  set_smem_attrs(kern, smem);
+  const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
+  DBG_TRY(ensure_status(ctx, tiles));
+  uint32_t epoch;
+  DBG_TRY(next_epoch(ctx, &epoch));
+  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), s));
+  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 12, 0, sizeof(uint32_t), s));
+  DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, (double)n * sizeof(K),
+             kern<<<(unsigned)tiles, SEG_BLOCK, smem, s>>>(
+                 kin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), guniq.as<K>(),
+                 gheads.as<uint32_t>(), (uint32_t)H, uniq, mult, n, low_bits, key_bits, ctx->d_status,
+                 ctx->d_counters, epoch, ctx->spin_limit, ctx->d_err, ctx->d_counters + 12));
+  DBG_CUDA_TRY(cudaGetLastError());
+  uint32_t total = 0;
+  DBG_TRY(read_small(ctx, ctx->d_counters + 12, sizeof(uint32_t), &total));
+  *E = total;
+  return DBG_OK;
+}
+
+// STEP-3's stable sort of R node records: hybrid (global passes from q0
+// up, then the local pass) when q0 > 0, else every digit globally.  The
+// producers accumulated the histograms of passes q0 and up only.
+template <class K>
+dbg_status sort_records(dbg_ctx *ctx, K **rk, K **rk_alt, uint32_t **rv, uint32_t **rv_alt, uint64_t R, int nbits,
+                        int q0, unsigned long long *d_hist, uint64_t *d_digit_base) {
+  if (q0 > 0 && R > 1) {
+    DBG_TRY((radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base, q0)));
+    DBG_TRY(seg_sort_records<K>(ctx, *rk, *rv, *rk_alt, *rv_alt, R, RADIX_BITS * q0, nbits));
+    std::swap(*rk, *rk_alt);
+    std::swap(*rv, *rv_alt);
+    return DBG_OK;
+  }
+  return radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base);
 }
 
 // K6 by reduce-then-scan over R sorted node records; returns the node count
@@ -467,28 +523,15 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     DBG_CUDA_TRY(cudaGetLastError());
     K *kp = keys_a.as<K>(), *alt = keys_b.as<K>();
     uint32_t *vn = nullptr, *van = nullptr;
-    bool reduced = false;
     if (p0 > 0) {
       // high digits globally, then the local sort with the run-length
       // reduce: distinct keys into alt, multiplicities into mult_tmp
       DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, N, kbits, d_hist, d_digit_base, p0)));
       DBG_TRY(alloc_buf(ctx, mult_tmp, N * sizeof(uint32_t)));
-      uint32_t res[2] = {0, 0};
-      DBG_TRY(seg_rle<K>(ctx, kp, alt, mult_tmp.as<uint32_t>(), N, RADIX_BITS * p0, kbits, res));
-      if (res[1] == 0) {
-        E = res[0];
-        reduced = true;
-      } else {
-        mult_tmp.release();
-        ctx->local_sort_fallbacks++;
-      }
-    }
-    if (!reduced) {
+      DBG_TRY(seg_rle<K>(ctx, kp, alt, mult_tmp.as<uint32_t>(), N, RADIX_BITS * p0, kbits, &E));
+    } else {
+      // every digit globally, then the run-length reduce
       DBG_TRY(alloc_buf(ctx, headpos, (N + 1) * sizeof(uint32_t)));
-      // every digit globally (keys only: any input order sorts the same)
-      if (p0 > 0)
-        DBG_LAUNCH(ctx, ST_SORT_EDGES, (double)N * sizeof(K),
-                   k_digit_hist<K><<<std::min(grid_for(N, 256 * 16), 152u * 8), 256, 0, s>>>(kp, N, 0, p0, d_hist));
       DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, N, kbits, d_hist, d_digit_base)));
       DBG_TRY(run_length_reduce<K>(ctx, kp, N, alt, headpos.as<uint32_t>(), &E));
     }

@@ -2,11 +2,18 @@
 // STEP-3).  The global onesweep passes sort the keys by their high bits only
 // (the digits at and above bit `low_bits`), which leaves every group of keys
 // with equal high bits contiguous.  One CTA then finishes a run of whole
-// groups in shared memory: the tile of nominal size TILE_T is stretched to
-// start and end on group boundaries, so no group is split between CTAs, and
-// the keys are sorted by their remaining bits with an in-shared-memory LSD
-// radix sort.  Because the global passes are stable and the local passes are
-// stable, the result equals a full stable LSD sort.
+// groups in shared memory: tile t covers [bound[t], bound[t+1]), where
+// bound[t] is the start of the group holding position t * TILE_T (found by
+// binary search, the high bits being sorted), so no group is split between
+// CTAs, and the keys are sorted by their remaining bits with an in-shared-
+// memory LSD radix sort.  Because the global passes are stable and the local
+// passes are stable, the result equals a full stable LSD sort.
+//
+// A tile longer than the shared-memory capacity (it holds a group of more
+// keys than that, e.g. a tandem repeat's (k+1)-mer) is "oversize": the host
+// gathers all oversize tiles into one buffer, sorts it with the global
+// passes over every digit, and the local kernels copy those results into
+// place instead of sorting.
 //
 // k_seg_sort sorts (key, payload) records (STEP-3's node records).
 // k_seg_rle finishes STEP-2 on the edge keys: it sorts them and writes each
@@ -14,10 +21,6 @@
 // offset found by decoupled look-back over the tiles' distinct-key counts.
 // Equal keys share their high bits, so no run of equal keys crosses a tile
 // boundary.
-//
-// A group longer than the window TILE_CAP - TILE_T cannot be aligned; the
-// tiles around it set *oversize and do nothing, and the host then finishes
-// with the remaining global passes instead.
 #pragma once
 
 #include "k_build.cuh"
@@ -39,69 +42,95 @@ struct SegSortSmem {
   uint32_t tmp[8];
   uint64_t bound[2];
   K base;
-  uint32_t tile, passes, fail, excl, total;
+  uint32_t tile, passes, excl, total;
 };
 
-// First index q in [pos, pos + window) that starts a group (q >= n counts as
-// a start); false if there is none.  Called by one whole warp; pos >= 1.
+// bound[t] for t in [0, tiles]: the first index of the group holding
+// position t * tile_keys (n for positions past the end).  The high bits are
+// sorted, so a binary search finds it; it starts in the last 8192 keys
+// before the position unless the group is longer.
 template <class K>
-__device__ __forceinline__ bool find_group_start(const K *__restrict__ keys, uint64_t n, uint64_t pos,
-                                                 uint64_t window, int low_bits, uint64_t *out) {
-  const int lane = threadIdx.x & 31;
-  for (uint64_t q0 = pos; q0 < pos + window; q0 += 32) {
-    const uint64_t q = q0 + lane;
-    bool start = false;
-    if (q < pos + window) {
-      if (q >= n)
-        start = true;
-      else
-        start = !KeyOps<K>::eq(KeyOps<K>::shr(keys[q], low_bits), KeyOps<K>::shr(keys[q - 1], low_bits));
+__global__ void k_seg_bounds(const K *__restrict__ keys, uint64_t n, int low_bits, uint64_t tile_keys,
+                             uint64_t tiles, uint64_t *__restrict__ bound) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= tiles; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t pos = t * tile_keys;
+    uint64_t b;
+    if (t == tiles || pos >= n) {
+      b = n;
+    } else if (pos == 0) {
+      b = 0;
+    } else {
+      const K target = KeyOps<K>::shr(keys[pos], low_bits);
+      uint64_t lo = pos > 8192 ? pos - 8192 : 0, hi = pos;
+      if (lo > 0 && !KeyOps<K>::less(KeyOps<K>::shr(keys[lo], low_bits), target)) lo = 0;
+      while (lo < hi) {  // first index whose high bits are not below target
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (KeyOps<K>::less(KeyOps<K>::shr(keys[mid], low_bits), target)) lo = mid + 1;
+        else hi = mid;
+      }
+      b = lo;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, start);
-    if (m) {
-      *out = q0 + (uint64_t)(__ffs(m) - 1);
-      return true;
-    }
+    bound[t] = b;
   }
-  return false;
 }
 
-// The tile's group-aligned range [s, e) into sm.bound, its base (the first
-// key with the low bits cleared) and the number of local passes.  Returns
-// false (after flagging *oversize) if the range could not be aligned.
-template <class K, int TILE_T, class S>
-__device__ __forceinline__ bool seg_setup(S &sm, const K *__restrict__ kin, uint64_t n, int low_bits, int key_bits,
-                                          uint32_t tile, uint32_t *oversize) {
-  constexpr uint64_t WINDOW = S::CAP - TILE_T;
-  static_assert(TILE_T < S::CAP && WINDOW <= TILE_T, "tile shape");
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp < 2) {
-    const uint64_t pos = (uint64_t)(tile + warp) * TILE_T;
-    uint64_t b = 0;
-    bool ok = true;
-    if (pos == 0) b = 0;
-    else if (pos >= n) b = n;
-    else ok = find_group_start(kin, n, pos, WINDOW, low_bits, &b);
-    if (lane == 0) {
-      sm.bound[warp] = b;
-      if (!ok) atomicOr(&sm.fail, 1u);
+// osize[t] = the tile's length if it exceeds cap (an oversize tile), else 0.
+static __global__ void k_seg_oversize(const uint64_t *__restrict__ bound, uint64_t tiles, uint32_t cap,
+                                      uint32_t *__restrict__ osize) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t sz = bound[t + 1] - bound[t];
+    osize[t] = sz > cap ? (uint32_t)sz : 0u;
+  }
+}
+
+// Copies every oversize tile to gk[ooff[t] ...] (and its payloads), in tile
+// order, so that one sort of the gathered keys sorts each of them.
+template <class K, bool HAS_VAL>
+__global__ void k_seg_gather(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+                             const uint64_t *__restrict__ bound, const uint32_t *__restrict__ osize,
+                             const uint64_t *__restrict__ ooff, uint64_t tiles, K *__restrict__ gk,
+                             uint32_t *__restrict__ gv) {
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint32_t sz = osize[t];
+    if (sz == 0) continue;
+    const uint64_t s = bound[t], o = ooff[t];
+    for (uint32_t j = threadIdx.x; j < sz; j += blockDim.x) {
+      gk[o + j] = kin[s + j];
+      if (HAS_VAL) gv[o + j] = vin[s + j];
+    }
+  }
+}
+
+// The tile's range, its base (the first key with the low bits cleared) and
+// the number of local passes, into shared memory.  The caller checks that
+// the tile is not oversize.
+template <class K, class S>
+__device__ __forceinline__ void seg_setup(S &sm, const K *__restrict__ kin, const uint64_t *__restrict__ bound,
+                                          uint32_t tile, int low_bits, int key_bits) {
+  if (threadIdx.x == 0) {
+    const uint64_t s = bound[tile], e = bound[tile + 1];
+    sm.bound[0] = s;
+    sm.bound[1] = e;
+    if (e > s) {
+      const K first = kin[s], last = kin[e - 1];
+      sm.base = KeyOps<K>::sub(first, KeyOps<K>::mask_low(first, low_bits));
+      const int spread_bits =
+          KeyOps<K>::bitlen(KeyOps<K>::sub(KeyOps<K>::shr(last, low_bits), KeyOps<K>::shr(first, low_bits)));
+      sm.passes = (uint32_t)((min(low_bits + spread_bits, key_bits) + RADIX_BITS - 1) / RADIX_BITS);
     }
   }
   __syncthreads();
-  const uint64_t s = sm.bound[0], e = sm.bound[1];
-  if (sm.fail || e < s || e - s > (uint64_t)S::CAP) {
-    if (threadIdx.x == 0) atomicOr(oversize, 1u);
-    return false;
+}
+
+// first index in sorted a[0, m) whose value is >= x
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *__restrict__ a, uint32_t m, uint64_t x) {
+  uint32_t lo = 0, hi = m;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if ((uint64_t)a[mid] < x) lo = mid + 1;
+    else hi = mid;
   }
-  if (threadIdx.x == 0 && e > s) {
-    const K first = kin[s], last = kin[e - 1];
-    sm.base = KeyOps<K>::sub(first, KeyOps<K>::mask_low(first, low_bits));
-    const int spread_bits =
-        KeyOps<K>::bitlen(KeyOps<K>::sub(KeyOps<K>::shr(last, low_bits), KeyOps<K>::shr(first, low_bits)));
-    sm.passes = (uint32_t)((min(low_bits + spread_bits, key_bits) + RADIX_BITS - 1) / RADIX_BITS);
-  }
-  __syncthreads();
-  return true;
+  return lo;
 }
 
 // One stable ranking step: item i of this warp gets its rank among the
@@ -209,19 +238,30 @@ __device__ __forceinline__ void reload_items(S &sm, K (&key)[ITEMS], uint32_t (&
   for (int i = threadIdx.x; i < S::WARPS * RADIX; i += SEG_BLOCK) (&sm.whist[0][0])[i] = 0;
 }
 
-template <class K, bool HAS_VAL, int ITEMS, int TILE_T, int RANK>
+// Records: tile t sorted in shared memory into kout / vout at its own range;
+// an oversize tile copies its slice of the gathered, globally sorted records
+// (gk / gv at ooff[t]).
+template <class K, int ITEMS, int RANK>
 __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_sort(
-    const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout, uint32_t *__restrict__ vout,
-    uint64_t n, int low_bits, int key_bits, uint32_t *oversize) {
-  using S = SegSortSmem<K, HAS_VAL, ITEMS>;
+    const K *__restrict__ kin, const uint32_t *__restrict__ vin, const uint64_t *__restrict__ bound,
+    const uint32_t *__restrict__ osize, const uint64_t *__restrict__ ooff, const K *__restrict__ gk,
+    const uint32_t *__restrict__ gv, K *__restrict__ kout, uint32_t *__restrict__ vout, int low_bits, int key_bits) {
+  using S = SegSortSmem<K, true, ITEMS>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   S &sm = *reinterpret_cast<S *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t tile = blockIdx.x;
+  if (osize[tile]) {
+    const uint64_t s = bound[tile], o = ooff[tile];
+    for (uint32_t j = tid; j < osize[tile]; j += SEG_BLOCK) {
+      kout[s + j] = gk[o + j];
+      vout[s + j] = gv[o + j];
+    }
+    return;
+  }
   for (int i = tid; i < S::WARPS * RADIX; i += SEG_BLOCK) (&sm.whist[0][0])[i] = 0;
   for (int i = tid; i < S::WARPS * (RADIX + 1); i += SEG_BLOCK) (&sm.match[0][0])[i] = 0;
-  if (tid == 0) sm.fail = 0;
-  __syncthreads();
-  if (!seg_setup<K, TILE_T>(sm, kin, n, low_bits, key_bits, blockIdx.x, oversize)) return;
+  seg_setup<K>(sm, kin, bound, tile, low_bits, key_bits);
   const uint64_t s = sm.bound[0];
   const uint32_t cnt = (uint32_t)(sm.bound[1] - s);
   if (cnt == 0) return;
@@ -239,47 +279,61 @@ __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_sort(
     const uint32_t j = wofs + i * 32 + lane;
     const bool in = i < ipw && j < cnt;
     key[i] = in ? KeyOps<K>::sub(kin[s + j], base) : KeyOps<K>::zero();
-    val[i] = (HAS_VAL && in) ? vin[s + j] : 0u;
+    val[i] = in ? vin[s + j] : 0u;
   }
   for (int p = 0; p < passes; p++) {
     if (p > 0) {
-      reload_items<K, HAS_VAL, ITEMS>(sm, key, val, ipw, wofs, cnt);
+      reload_items<K, true, ITEMS>(sm, key, val, ipw, wofs, cnt);
       __syncthreads();
     }
     rank_items<K, ITEMS, RANK>(sm, key, rank, ipw, wofs, cnt, p * RADIX_BITS);
     digit_positions(sm);
-    scatter_items<K, HAS_VAL, ITEMS>(sm, key, val, rank, ipw);
+    scatter_items<K, true, ITEMS>(sm, key, val, rank, ipw);
   }
   __syncthreads();
   for (uint32_t j = tid; j < cnt; j += SEG_BLOCK) {
     kout[s + j] = KeyOps<K>::add(sm.keys[j], base);
-    if (HAS_VAL) vout[s + j] = sm.vals[j];
+    vout[s + j] = sm.vals[j];
   }
 }
 
+// Edge keys: distinct keys and multiplicities of tile t at an offset found by
+// decoupled look-back; an oversize tile takes its runs from the gathered,
+// globally sorted and reduced keys (guniq, with run heads gheads at the
+// positions of the gathered buffer, H runs in all, gheads[H] = its length).
 template <class K, int ITEMS, int TILE_T, int RANK>
 __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_rle(
-    const K *__restrict__ kin, K *__restrict__ uniq, uint32_t *__restrict__ mult, uint64_t n, int low_bits,
-    int key_bits, uint64_t *status, uint32_t *ticket, uint32_t epoch, uint32_t spin_limit, uint32_t *err,
-    uint32_t *oversize, uint32_t *total) {
+    const K *__restrict__ kin, const uint64_t *__restrict__ bound, const uint32_t *__restrict__ osize,
+    const uint64_t *__restrict__ ooff, const K *__restrict__ guniq, const uint32_t *__restrict__ gheads, uint32_t H,
+    K *__restrict__ uniq, uint32_t *__restrict__ mult, uint64_t n, int low_bits, int key_bits, uint64_t *status,
+    uint32_t *ticket, uint32_t epoch, uint32_t spin_limit, uint32_t *err, uint32_t *total) {
   using S = SegSortSmem<K, false, ITEMS>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   S &sm = *reinterpret_cast<S *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < S::WARPS * RADIX; i += SEG_BLOCK) (&sm.whist[0][0])[i] = 0;
-  for (int i = tid; i < S::WARPS * (RADIX + 1); i += SEG_BLOCK) (&sm.match[0][0])[i] = 0;
-  if (tid == 0) {
-    sm.tile = atomicAdd(ticket, 1u);
-    sm.fail = 0;
-  }
+  if (tid == 0) sm.tile = atomicAdd(ticket, 1u);
   __syncthreads();
   const uint32_t tile = sm.tile;
   const uint64_t num_tiles = (n + TILE_T - 1) / TILE_T;
-  if (!seg_setup<K, TILE_T>(sm, kin, n, low_bits, key_bits, tile, oversize)) {
-    // successors must still find this tile's word in their look-back
-    if (tid == 0) st_relaxed(status + tile, lb_word(epoch, tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE, 0));
+  if (osize[tile]) {
+    if (tid == 0) {
+      const uint64_t o = ooff[tile];
+      sm.bound[0] = lower_bound_u32(gheads, H, o);
+      sm.bound[1] = lower_bound_u32(gheads, H, o + osize[tile]);
+    }
+    __syncthreads();
+    const uint32_t h0 = (uint32_t)sm.bound[0], count = (uint32_t)(sm.bound[1] - sm.bound[0]);
+    const uint32_t excl = tile_prefix(status, tile, count, epoch, spin_limit, err, &sm.excl);
+    for (uint32_t r = tid; r < count; r += SEG_BLOCK) {
+      uniq[excl + r] = guniq[h0 + r];
+      mult[excl + r] = gheads[h0 + r + 1] - gheads[h0 + r];
+    }
+    if (tile + 1 == num_tiles && tid == 0) *total = excl + count;
     return;
   }
+  for (int i = tid; i < S::WARPS * RADIX; i += SEG_BLOCK) (&sm.whist[0][0])[i] = 0;
+  for (int i = tid; i < S::WARPS * (RADIX + 1); i += SEG_BLOCK) (&sm.match[0][0])[i] = 0;
+  seg_setup<K>(sm, kin, bound, tile, low_bits, key_bits);
   const uint64_t s = sm.bound[0];
   const uint32_t cnt = (uint32_t)(sm.bound[1] - s);
   const K base = sm.base;

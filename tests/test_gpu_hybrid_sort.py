@@ -1,7 +1,7 @@
 """The hybrid sort (global passes over the high digits, then a local sort of
 group-aligned tiles in shared memory, fused with the run-length reduce for the
 edge keys) gives bit-for-bit the graph of the all-global sort and the oracle's,
-including when a group is too long for a tile and the sort falls back."""
+including when a group is too long for a tile and is sorted globally."""
 from __future__ import annotations
 
 import numpy as np
@@ -51,7 +51,7 @@ def test_hybrid_equals_global_sort(dbg, k, n_reads, L):
 
 def test_group_longer_than_window_falls_back(dbg):
     """10,000 copies of one (k+1)-mer form a group longer than a tile can
-    hold (6,144 keys): the edge sort falls back to the global passes."""
+    hold (6,144 keys): that tile is gathered and sorted over every digit."""
     k = 21
     rng = np.random.default_rng(7)
     rep = "".join("ACGT"[c] for c in rng.integers(0, 4, size=k + 1))
@@ -67,7 +67,8 @@ def test_group_longer_than_window_falls_back(dbg):
 def test_node_records_fall_back(dbg):
     """8,000 reads of exactly k bases that share their first seven: 8,000
     node records with equal high bits, a group longer than a tile of the
-    node-record sort can hold, which falls back; plus ordinary reads."""
+    node-record sort can hold, which is gathered and sorted globally; plus
+    ordinary reads."""
     k = 15
     rng = np.random.default_rng(8)
     tails = rng.integers(0, 4, size=(8_000, k - 7))
@@ -78,3 +79,20 @@ def test_node_records_fall_back(dbg):
     ctx = dbg.Context()
     check_parity(dbg, ctx, data, lengths, k)
     assert dbg.dbg_sort_fallbacks(ctx) >= 1
+
+
+def test_long_runs_in_first_and_last_tiles(dbg):
+    """Runs of 10,000 equal keys at the very start (AAA...A, the smallest
+    key) and near the end of the key order (GCC...C), with ordinary reads in
+    between: oversize tiles at both ends and normal tiles in the middle."""
+    k = 31
+    first = "A" * (k + 1)
+    last = "G" + "C" * k
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(100_000, 3_000, 100, 0.01, k, 91))
+    extra = (first * 10_000 + last * 10_000).encode()
+    reads = np.concatenate([reads, np.frombuffer(extra, dtype=np.uint8)])
+    lengths = np.concatenate([lengths, np.full(20_000, k + 1, dtype=np.uint32)])
+    ctx = dbg.Context()
+    got = check_parity(dbg, ctx, reads, lengths, k)
+    assert dbg.dbg_sort_fallbacks(ctx) >= 1
+    assert got["e_mult"][0] >= 10_000 and got["e_mult"].max() >= 10_000
