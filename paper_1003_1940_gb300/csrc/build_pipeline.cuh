@@ -903,9 +903,16 @@ dbg_status build_bucketed_impl(dbg_ctx *ctx, const BucketInput &in, uint64_t bud
     DBG_CUDA_TRY(cudaGetLastError());
     K *kp = ka.as<K>(), *alt = kb.as<K>();
     uint32_t *vn = nullptr, *van = nullptr;
-    DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, cnt, kbits, d_hist, d_digit_base)));
     uint64_t eb64 = 0;
-    DBG_TRY(run_length_reduce<K>(ctx, kp, cnt, alt, headpos.as<uint32_t>(), &eb64));
+    const int p0 = ctx->hybrid_sort ? hybrid_first_pass<K>(cnt, kbits) : 0;
+    if (p0 > 0) {
+      // multiplicities go where the run heads would (headpos is cnt + 1 long)
+      DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, cnt, kbits, d_hist, d_digit_base, p0)));
+      DBG_TRY(seg_rle<K>(ctx, kp, alt, headpos.as<uint32_t>(), cnt, RADIX_BITS * p0, kbits, &eb64));
+    } else {
+      DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, cnt, kbits, d_hist, d_digit_base)));
+      DBG_TRY(run_length_reduce<K>(ctx, kp, cnt, alt, headpos.as<uint32_t>(), &eb64));
+    }
     DBG_TRY(check_device_error(ctx));
     const uint32_t eb = (uint32_t)eb64;
     DevBuf k1, m1, o1;
@@ -914,7 +921,8 @@ dbg_status build_bucketed_impl(dbg_ctx *ctx, const BucketInput &in, uint64_t bud
     DBG_TRY(alloc_buf(ctx, o1, std::max<uint64_t>(1, eb)));
     if (eb)
       DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)eb * (2 * w + 9),
-                 k_edge_finish<K><<<grid_for(eb, 256), 256, 0, s>>>(alt, headpos.as<uint32_t>(), eb, k, k1.as<K>(),
+                 k_edge_finish<K><<<grid_for(eb, 256), 256, 0, s>>>(alt, p0 > 0 ? nullptr : headpos.as<uint32_t>(),
+                                                                   headpos.as<uint32_t>(), eb, k, k1.as<K>(),
                                                                    m1.as<uint32_t>(), o1.as<uint8_t>()));
     ck.push_back(std::move(k1));
     cm.push_back(std::move(m1));
@@ -1003,7 +1011,8 @@ dbg_status build_bucketed_impl(dbg_ctx *ctx, const BucketInput &in, uint64_t bud
     if (R == 0) continue;
     K *rk = ra.as<K>(), *rk_alt = rb.as<K>();
     uint32_t *rv = va.as<uint32_t>(), *rv_alt = vb.as<uint32_t>();
-    DBG_TRY((radix_sort<K, true>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, d_hist, d_digit_base)));
+    const int q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(R, nbits) : 0;
+    DBG_TRY((sort_records<K>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, q0, d_hist, d_digit_base)));
     DBG_TRY(alloc_buf(ctx, row_tmp, (R + 1) * 8));
     uint64_t tot[2] = {0, 0};
     DBG_TRY(assign_node_ids<K>(ctx, rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g, (uint32_t)base_v, base_slot,

@@ -1003,9 +1003,11 @@ __device__ __forceinline__ void edge_ends(const K &z, int k, K &s, K &d, uint32_
   }
 }
 
-// Edges of one bucket: key, multiplicity and orientation at offset e_base.
+// Edges of one bucket: key, multiplicity (from the run heads, or directly
+// from mult_in) and orientation.
 template <class K>
-__global__ void k_edge_finish(const K *__restrict__ uniq, const uint32_t *__restrict__ headpos, uint64_t E, uint32_t k,
+__global__ void k_edge_finish(const K *__restrict__ uniq, const uint32_t *__restrict__ headpos,
+                              const uint32_t *__restrict__ mult_in, uint64_t E, uint32_t k,
                               K *__restrict__ edge_keys, uint32_t *__restrict__ mult, uint8_t *__restrict__ orient) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x) {
     const K z = uniq[e];
@@ -1014,7 +1016,7 @@ __global__ void k_edge_finish(const K *__restrict__ uniq, const uint32_t *__rest
     edge_ends(z, (int)k, s, d, o);
     edge_keys[e] = z;
     orient[e] = (uint8_t)o;
-    mult[e] = headpos[e + 1] - headpos[e];
+    mult[e] = headpos ? headpos[e + 1] - headpos[e] : mult_in[e];
   }
 }
 
