@@ -421,11 +421,13 @@ dbg_status sort_records(dbg_ctx *ctx, K **rk, K **rk_alt, uint32_t **rv, uint32_
 }
 
 // K6 by reduce-then-scan over R sorted node records; returns the node count
-// and the number of edge ends.
+// and the number of edge ends.  E_all > 0: the records hold both ends of
+// all E_all edges, and src / dst are written through the partition of the
+// edge ends by edge range (k_scatter_ends) instead of at random.
 template <class K>
 dbg_status assign_node_ids(dbg_ctx *ctx, const K *rk, const uint32_t *rv, uint64_t R, K *node_keys,
                            uint64_t *row_ptr, dbg_graph *g, uint32_t base_v, uint64_t base_slot, uint64_t *V,
-                           uint64_t *ends) {
+                           uint64_t *ends, uint64_t E_all = 0) {
   cudaStream_t s = ctx->stream;
   const uint64_t tiles = (R + RS_TILE - 1) / RS_TILE;
   DevBuf hc, ec, ho, eo;
@@ -438,10 +440,29 @@ dbg_status assign_node_ids(dbg_ctx *ctx, const K *rk, const uint32_t *rv, uint64
   uint32_t nv = 0, ne = 0;
   DBG_TRY(scan_u32(ctx, hc.as<uint32_t>(), tiles, ho.as<uint64_t>(), &nv, ST_NODE_IDS));
   DBG_TRY(scan_u32(ctx, ec.as<uint32_t>(), tiles, eo.as<uint64_t>(), &ne, ST_NODE_IDS));
-  DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (sizeof(K) + 4) + (double)nv * (sizeof(K) + 8) + (double)ne * 9,
-             k_write_nodes<K><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
-                 rk, rv, R, ho.as<uint64_t>(), eo.as<uint64_t>(), node_keys, row_ptr, g->src.as<uint32_t>(),
-                 g->dst.as<uint32_t>(), g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), base_v, base_slot));
+  if (E_all > 0) {
+    int bshift = 10;
+    while ((E_all + (1ull << bshift) - 1) >> bshift > 256) bshift++;
+    DevBuf part, fill;
+    DBG_TRY(alloc_buf(ctx, part, 2 * E_all * 8));
+    DBG_TRY(alloc_buf(ctx, fill, 256 * 4));
+    DBG_CUDA_TRY(cudaMemsetAsync(fill.p, 0, 256 * 4, s));
+    DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (sizeof(K) + 4) + (double)nv * (sizeof(K) + 8) + (double)ne * 13,
+               k_write_nodes<K, true><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
+                   rk, rv, R, ho.as<uint64_t>(), eo.as<uint64_t>(), node_keys, row_ptr, g->src.as<uint32_t>(),
+                   g->dst.as<uint32_t>(), g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), base_v, base_slot,
+                   part.as<uint64_t>(), fill.as<uint32_t>(), bshift));
+    DBG_LAUNCH(ctx, ST_NODE_IDS, 2.0 * E_all * (8 + 4),
+               k_scatter_ends<<<grid_for(2 * E_all, 256 * 16), 256, 0, s>>>(part.as<uint64_t>(), 2 * E_all,
+                                                                          g->src.as<uint32_t>(),
+                                                                          g->dst.as<uint32_t>()));
+  } else {
+    DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (sizeof(K) + 4) + (double)nv * (sizeof(K) + 8) + (double)ne * 9,
+               k_write_nodes<K, false><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
+                   rk, rv, R, ho.as<uint64_t>(), eo.as<uint64_t>(), node_keys, row_ptr, g->src.as<uint32_t>(),
+                   g->dst.as<uint32_t>(), g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), base_v, base_slot,
+                   nullptr, nullptr, 0));
+  }
   DBG_CUDA_TRY(cudaGetLastError());
   *V = nv;
   *ends = ne;
@@ -600,7 +621,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   if (R > 0) {
     // node keys go to the free record buffer first (|V| is known only after)
     uint64_t ends = 0;
-    DBG_TRY(assign_node_ids<K>(ctx, rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g, 0u, 0ull, &V, &ends));
+    DBG_TRY(assign_node_ids<K>(ctx, rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g, 0u, 0ull, &V, &ends, E));
     DBG_TRY(check_device_error(ctx));
     if (ends != 2 * E) {
       set_error("adjacency holds %llu edge ends, expected %llu", (unsigned long long)ends,

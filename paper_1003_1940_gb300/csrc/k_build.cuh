@@ -1227,14 +1227,23 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_write_heads(const K *__restrict_
 
 // K6 writing pass: node IDs and adjacency slots from the scanned tile
 // offsets of run heads (hoff) and edge-end records (eoff).
-template <class K>
-__global__ __launch_bounds__(SCAN_BLOCK) void k_write_nodes(
+//
+// PART = true: instead of writing src[e] / dst[e] at random, the edge ends
+// (e << 1 | role, node ID) are partitioned by e >> bshift into ends[] (bucket
+// b at b << (bshift + 1): every edge has exactly two ends, so the buckets
+// are full and dense), for k_scatter_ends to write with each bucket's part
+// of src / dst resident in L2.
+template <class K, bool PART>
+__global__ __launch_bounds__(SCAN_BLOCK, 2) void k_write_nodes(
     const K *__restrict__ rkeys, const uint32_t *__restrict__ rvals, uint64_t R, const uint64_t *__restrict__ hoff,
     const uint64_t *__restrict__ eoff, K *__restrict__ node_keys, uint64_t *__restrict__ row_ptr,
     uint32_t *__restrict__ src, uint32_t *__restrict__ dst, uint32_t *__restrict__ adj_edge,
-    uint8_t *__restrict__ adj_role, uint32_t base_v, uint64_t base_slot) {
+    uint8_t *__restrict__ adj_role, uint32_t base_v, uint64_t base_slot, uint64_t *__restrict__ ends,
+    uint32_t *__restrict__ bucket_fill, int bshift) {
   constexpr int WARPS = SCAN_BLOCK / 32;
   __shared__ uint32_t s_cnt_h[RS_ITEMS * WARPS + 1], s_cnt_e[RS_ITEMS * WARPS + 1];
+  __shared__ uint32_t s_bcnt[PART ? 256 : 1], s_bbase[PART ? 256 : 1];
+  if (PART) s_bcnt[threadIdx.x] = 0;  // SCAN_BLOCK == 256 buckets at most
   const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
   K key[RS_ITEMS];
   uint32_t val[RS_ITEMS];
@@ -1267,10 +1276,38 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_write_nodes(
       const uint32_t e = val[i] >> 1, role = val[i] & 1u;
       adj_edge[base_slot + slot] = e;
       adj_role[base_slot + slot] = (uint8_t)role;
-      (role ? dst : src)[e] = base_v + (uint32_t)id;
+      if (PART) {
+        rh[i] = (uint32_t)id;                           // keep the node ID
+        re[i] = atomicAdd(&s_bcnt[e >> bshift], 1u);  // rank within the block's part of the bucket
+      } else {
+        (role ? dst : src)[e] = base_v + (uint32_t)id;
+      }
     }
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) row_ptr[hoff[gridDim.x]] = base_slot + eoff[gridDim.x];
+  if (PART) {
+    __syncthreads();
+    if (s_bcnt[threadIdx.x]) s_bbase[threadIdx.x] = atomicAdd(bucket_fill + threadIdx.x, s_bcnt[threadIdx.x]);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) {
+      const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
+      if (idx >= R || !end[i]) continue;
+      const uint32_t b = (val[i] >> 1) >> bshift;
+      ends[((uint64_t)b << (bshift + 1)) + s_bbase[b] + re[i]] = ((uint64_t)val[i] << 32) | (base_v + rh[i]);
+    }
+  }
+}
+
+// src[e] / dst[e] from the partitioned edge ends, swept in order so that the
+// part of src / dst being written stays in L2.
+static __global__ void k_scatter_ends(const uint64_t *__restrict__ ends, uint64_t n, uint32_t *__restrict__ src,
+                                      uint32_t *__restrict__ dst) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t w = ends[i];
+    const uint32_t v = (uint32_t)(w >> 32);
+    ((v & 1u) ? dst : src)[v >> 1] = (uint32_t)w;
+  }
 }
 
 }  // namespace dbg
