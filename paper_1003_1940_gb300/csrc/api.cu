@@ -339,47 +339,28 @@ dbg_status dbg_build(dbg_ctx *ctx, const char *reads, const uint32_t *lengths, u
   auto rebind = [&](DevBuf &b) { b.al = &g->al; };
 
   dbg_status st = DBG_OK;
-  DevBuf d_reads, d_len;
-  const uint8_t *reads_dev = reinterpret_cast<const uint8_t *>(reads);
+  DevBuf d_len;
   const uint32_t *len_dev = lengths;
+  bool reads_on_dev = true;
   if (n > 0) {
-    const bool reads_on_dev = is_device_ptr(reads), len_on_dev = is_device_ptr(lengths);
-    uint64_t total = 0;
-    if (!len_on_dev) {
-      for (uint64_t r = 0; r < n; r++) total += lengths[r];
+    reads_on_dev = is_device_ptr(reads);
+    if (!is_device_ptr(lengths)) {
       st = alloc_buf(ctx, d_len, n * sizeof(uint32_t));
       if (st == DBG_OK && cudaMemcpyAsync(d_len.p, lengths, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s) != cudaSuccess) {
         set_error("copy of the read lengths to the device failed");
         st = DBG_ECUDA;
       }
       len_dev = d_len.as<uint32_t>();
-    } else if (!reads_on_dev) {
-      // total bases are needed to copy the reads: read the lengths back
-      uint32_t *h = (uint32_t *)std::malloc(n * sizeof(uint32_t));
-      if (!h) st = DBG_ENOMEM;
-      if (st == DBG_OK && cudaMemcpy(h, lengths, n * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
-        st = DBG_ECUDA;
-      for (uint64_t r = 0; st == DBG_OK && r < n; r++) total += h[r];
-      std::free(h);
-    }
-    if (st == DBG_OK && !reads_on_dev) {
-      st = alloc_buf(ctx, d_reads, total);
-      if (st == DBG_OK && total &&
-          cudaMemcpyAsync(d_reads.p, reads, total, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        set_error("copy of the reads to the device failed");
-        st = DBG_ECUDA;
-      }
-      reads_dev = d_reads.as<uint8_t>();
     }
   }
   if (st == DBG_OK) {
-    BuildInput in{reads_dev, len_dev, n, 0, k};
+    // host reads are streamed in by the build once it knows their length
+    BuildInput in{reinterpret_cast<const uint8_t *>(reads), len_dev, n, !reads_on_dev, k};
     st = k <= 31 ? build_graph_u64(ctx, in, g) : build_graph_u128(ctx, in, g);
   }
   for (DevBuf *b : {&g->node_keys, &g->edge_keys, &g->src, &g->dst, &g->orient, &g->mult, &g->row_ptr,
                     &g->adj_nbr, &g->adj_edge, &g->adj_role})
     rebind(*b);
-  d_reads.release();
   d_len.release();
   cudaStreamSynchronize(s);
   prof_resolve(ctx);

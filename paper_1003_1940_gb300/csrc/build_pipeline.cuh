@@ -517,10 +517,22 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   const uint64_t nwords = (total_bases + 31) / 32;
   DBG_TRY(alloc_buf(ctx, packed, (nwords + 3) * sizeof(uint64_t)));
   DBG_CUDA_TRY(cudaMemsetAsync(packed.as<uint64_t>() + nwords, 0, 3 * sizeof(uint64_t), s));
-  if (nwords > 0) {
+  if (nwords > 0 && !in.h_reads) {
     DBG_LAUNCH(ctx, ST_PACK, (double)total_bases + 8.0 * nwords,
-               k_pack<<<grid_for(nwords, 256), 256, 0, s>>>(in.d_reads, total_bases, packed.as<uint64_t>(), nwords,
+               k_pack<<<grid_for(nwords, 256), 256, 0, s>>>(in.reads, total_bases, packed.as<uint64_t>(), nwords,
                                                  ctx->d_err));
+  } else if (nwords > 0) {
+    // host reads: copy them in chunks through a staging buffer, packing each
+    const uint64_t chunk = 256ull << 20;  // bases per copy (a multiple of 32)
+    DevBuf stage;
+    DBG_TRY(alloc_buf(ctx, stage, std::min(chunk, total_bases)));
+    for (uint64_t off = 0; off < total_bases; off += chunk) {
+      const uint64_t len = std::min(chunk, total_bases - off);
+      DBG_CUDA_TRY(cudaMemcpyAsync(stage.p, in.reads + off, len, cudaMemcpyHostToDevice, s));
+      DBG_LAUNCH(ctx, ST_PACK, (double)len * 1.25,
+                 k_pack_at<<<grid_for((len + 31) / 32, 256), 256, 0, s>>>(stage.as<uint8_t>(), len,
+                                                                        packed.as<uint64_t>(), off / 32, ctx->d_err));
+    }
   }
 
   // ---- K2 emit + digit histograms, K3 sort, K4 run-length reduce ----

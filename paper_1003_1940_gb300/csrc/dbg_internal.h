@@ -167,10 +167,10 @@ void prof_resolve(dbg_ctx *ctx);
 
 // The build pipeline for one key width (k <= 31: uint64_t, else 128-bit).
 struct BuildInput {
-  const uint8_t *d_reads;     // device ASCII
+  const uint8_t *reads;       // ASCII, on the device or (h_reads) in host memory
   const uint32_t *d_lengths;  // device
   uint64_t n;
-  uint64_t total_bases;
+  bool h_reads;               // reads are in host memory: streamed in by chunks
   uint32_t k;
 };
 
