@@ -100,8 +100,10 @@ const char *dbg_last_error(void);
  *           read (its canonical edge), STEP-2: radix sort + run-length
  *           reduce (edges with multiplicities), STEP-3: sort of the edge
  *           ends (nodes), STEP-4: adjacency lists.
- *   reads    all reads back to back, ASCII 'A','C','G','T' (no separators)
- *   lengths  n read lengths (bases)
+ *   reads    all reads back to back, ASCII 'A','C','G','T' (no separators);
+ *            device or host memory (host reads are streamed to the device
+ *            in 256 MB pieces; pinned host memory copies fastest)
+ *   lengths  n read lengths (bases), device or host memory
  *   n        number of reads; n = 0 gives an empty graph
  *   k        odd, 1 <= k <= 63 (Section 2: k odd, so no k-mer is its own
  *            reverse complement)
