@@ -41,12 +41,17 @@ __device__ __forceinline__ uint32_t end_side(uint8_t orient, uint32_t role) {
 
 // Per node and side: the edge end alone on that side, if exactly one is.
 // link_node[2v + side] = (w << 1) | side_at_w of the edge's other end, and
-// link_edge[2v + side] = the edge; NONE when the side has 0 or >= 2 ends.
-// The neighbour comes from the adjacency row, so only orient is gathered.
+// link_edge[2v + side] = the edge | (entry base << 32), the edge being NONE
+// when the side has 0 or >= 2 ends.  The entry base is the last base of v's
+// k-mer read as a walk that enters v by that side reads it (forward when
+// entering by the left side, reversed by the right), i.e. the base a walk
+// appends on arriving at v that way.  The neighbour comes from the
+// adjacency row, so only orient is gathered.
+template <class K>
 __global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ adj_nbr,
                              const uint32_t *__restrict__ adj_edge, const uint8_t *__restrict__ adj_role,
-                             const uint8_t *__restrict__ orient, uint64_t V, uint32_t *__restrict__ link_node,
-                             uint32_t *__restrict__ link_edge) {
+                             const uint8_t *__restrict__ orient, const uint64_t *__restrict__ node_keys, uint64_t V,
+                             int k, uint32_t *__restrict__ link_node, uint64_t *__restrict__ link_edge) {
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t cnt[2] = {0, 0}, e_at[2] = {NONE32, NONE32}, far[2] = {NONE32, NONE32};
     const uint64_t p0 = row_ptr[v], p1 = row_ptr[v + 1];
@@ -58,10 +63,12 @@ __global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_
       e_at[sd] = e;
       far[sd] = (adj_nbr[p] << 1) | end_side(o, 1u - role);
     }
+    const K kv = load_node_key<K>(node_keys, v);
+    const uint64_t entry[2] = {KeyOps<K>::low2(kv), 3u - KeyOps<K>::digit(kv, 2 * (k - 1), 2)};
 #pragma unroll
     for (int sd = 0; sd < 2; sd++) {
       link_node[2 * v + sd] = cnt[sd] == 1 ? far[sd] : NONE32;
-      link_edge[2 * v + sd] = cnt[sd] == 1 ? e_at[sd] : NONE32;
+      link_edge[2 * v + sd] = (entry[sd] << 32) | (cnt[sd] == 1 ? e_at[sd] : NONE32);
     }
   }
 }
@@ -70,19 +77,23 @@ __global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_
 // side (s = 0) or its left side (s = 1); the arc exists when the edge there
 // joins two distinct nodes and is alone on the far node's side too.  It
 // enters w on side sw: strand 0 when that is w's left side, 1 otherwise.
-__global__ void k_successors(const uint32_t *__restrict__ link_node, const uint32_t *__restrict__ link_edge,
-                             uint64_t V, uint32_t *__restrict__ succ) {
+// succ_base[x] = succ[x] | (the base appended on that arc) << 32, or all
+// ones, for the walks that write the unitigs' strings.
+__global__ void k_successors(const uint32_t *__restrict__ link_node, const uint64_t *__restrict__ link_edge,
+                             uint64_t V, uint32_t *__restrict__ succ, uint64_t *__restrict__ succ_base) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * V; x += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t v = x >> 1;
     const uint32_t leave = (x & 1) ? 0u : 1u;
     const uint32_t ln = link_node[2 * v + leave];
     uint32_t out = NONE32;
+    uint64_t far = 0;
     if (ln != NONE32) {
       const uint32_t w = ln >> 1, sw = ln & 1u;
-      if (w != (uint32_t)v && link_edge[2 * (uint64_t)w + sw] == link_edge[2 * v + leave])
-        out = 2 * w + (sw == 0 ? 0u : 1u);
+      far = link_edge[2 * (uint64_t)w + sw];
+      if (w != (uint32_t)v && (uint32_t)far == (uint32_t)link_edge[2 * v + leave]) out = 2 * w + (sw == 0 ? 0u : 1u);
     }
     succ[x] = out;
+    succ_base[x] = out == NONE32 ? ~0ull : ((far >> 32) << 32) | out;
   }
 }
 
@@ -366,7 +377,7 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_fast_measure(const uint32_t *__r
 
 template <class K>
 __global__ __launch_bounds__(WALK_BLOCK) void k_fast_write(
-    const uint32_t *__restrict__ succ, const uint32_t *__restrict__ is_head, const uint8_t *__restrict__ hstrand,
+    const uint64_t *__restrict__ succ_base, const uint32_t *__restrict__ is_head, const uint8_t *__restrict__ hstrand,
     const uint64_t *__restrict__ uidx, const uint64_t *__restrict__ off_by_v, const uint64_t *__restrict__ node_keys,
     uint64_t V, uint64_t U, int k, uint64_t *__restrict__ nodes_out, char *__restrict__ seq,
     uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off, uint8_t *__restrict__ circular) {
@@ -384,7 +395,7 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_fast_write(
     if (lane == 0) s_next[w] = 0;
     __syncwarp();
     bool busy = false;
-    uint32_t y = 0;
+    uint32_t y = 0, base = 0;
     uint64_t i = 0, off = 0, so = 0;
     for (;;) {
       if (!busy) {
@@ -402,17 +413,18 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_fast_write(
         busy = true;
       }
       nodes_out[off + i] = y;  // (node ID << 1) | strand
-      const K km = strand_kmer<K>(node_keys, y, k);
       if (i == 0) {
+        const K km = strand_kmer<K>(node_keys, y, k);
         for (int j = 0; j < k; j++) seq[so + j] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - j), 2)];
       } else {
-        seq[so + k - 1 + i] = acgt[KeyOps<K>::low2(km)];
+        seq[so + k - 1 + i] = acgt[base];
       }
-      const uint32_t ny = succ[y];
-      if (ny == NONE32) {
+      const uint64_t nb = succ_base[y];
+      if (nb == ~0ull) {
         busy = false;
       } else {
-        y = ny;
+        y = (uint32_t)nb;
+        base = (uint32_t)(nb >> 32);
         i++;
       }
     }
@@ -489,17 +501,18 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
   bool have_cycles = false;
   if (V > 0) {
     DBG_TRY(alloc_buf(ctx, link_node, n1 * 4));
-    DBG_TRY(alloc_buf(ctx, link_edge, n1 * 4));
+    DBG_TRY(alloc_buf(ctx, link_edge, n1 * 8));
     DBG_TRY(alloc_buf(ctx, succ, n1 * 4));
     DBG_TRY(alloc_buf(ctx, word, n1 * 8));
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + (double)E2 * 10 + 16.0 * V,
-               k_side_links<<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
-                                                       g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
-                                                       g->orient.as<uint8_t>(), V, link_node.as<uint32_t>(),
-                                                       link_edge.as<uint32_t>()));
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 8.0 * n + 8.0 * n,
-               k_successors<<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint32_t>(), V,
-                                                       succ.as<uint32_t>()));
+    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + (double)E2 * 10 + 8.0 * V * g->key_words + 12.0 * n,
+               k_side_links<K><<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
+                                                          g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
+                                                          g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
+                                                          link_node.as<uint32_t>(), link_edge.as<uint64_t>()));
+    // succ_base goes to the ranking words' buffer (free until the general path)
+    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n + 8.0 * n + 12.0 * n,
+               k_successors<<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(), V,
+                                                       succ.as<uint32_t>(), word.as<uint64_t>()));
     link_node.release();
     link_edge.release();
     // ---- fast path: short acyclic lists only ----
@@ -540,7 +553,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
         DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
         DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)V * (4 + 1 + 16 + 8 + 8 * g->key_words + 1) + (double)Uf * (k + 17),
                    k_fast_write<K><<<walk_grid(ctx, V), WALK_BLOCK, 0, s>>>(
-                       succ.as<uint32_t>(), f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_uidx.as<uint64_t>(),
+                       word.as<uint64_t>(), f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_uidx.as<uint64_t>(),
                        f_off.as<uint64_t>(), g->node_keys.as<uint64_t>(), V, Uf, k, u->nodes.as<uint64_t>(),
                        u->seq.as<char>(), u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(),
                        u->circular.as<uint8_t>()));
