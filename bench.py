@@ -220,6 +220,56 @@ def oracle_sample_rate(reads, lengths, k, target_s):
     return edges / dt, dt, m, edges
 
 
+def _partition_worker(job):
+    """One process of the multi-core CPU baseline: every read, one key partition."""
+    reads_path, lengths_path, k, part, parts = job
+    import oracle
+    reads, lengths = np.load(reads_path), np.load(lengths_path)
+    t = time.perf_counter()
+    distinct, inst = oracle.edges_in_partition(reads, lengths, k, part, parts)
+    return time.perf_counter() - t, distinct, inst
+
+
+def oracle_parallel_rate(reads, lengths, k, m):
+    """Edge counting of the first m reads by one process per host core, each
+    scanning every read and keeping one hash partition of the canonical
+    (k+1)-mers.  Returns (edges/s, seconds, processes)."""
+    import multiprocessing as mp
+    import tempfile
+    import oracle
+    oracle.build()
+    parts = os.cpu_count() or 1
+    nb = int(lengths[:m].astype(np.int64).sum())
+    with tempfile.TemporaryDirectory() as d:
+        rp, lp = os.path.join(d, "reads.npy"), os.path.join(d, "lengths.npy")
+        np.save(rp, reads[:nb])
+        np.save(lp, lengths[:m])
+        with mp.get_context("spawn").Pool(parts) as pool:
+            res = pool.map(_partition_worker, [(rp, lp, k, p, parts) for p in range(parts)])
+    dt = max(r[0] for r in res)
+    inst = sum(r[2] for r in res)
+    return inst / dt, dt, parts
+
+
+def cpu_model():
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return f"{line.split(':', 1)[1].strip()} ({platform.machine()})"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup(args)
     if rank != 0:
@@ -252,7 +302,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": {"workload": wl, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -371,9 +422,22 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt, m, edges = oracle_sample_rate(reads, lengths, k, args.cpu_seconds)
+        # the parallel run scans more reads, about as long as the 1-core run
+        m_par = int(min(len(lengths), m * max(1, (os.cpu_count() or 1) // 2)))
+        prate, pdt, parts = oracle_parallel_rate(reads, lengths, k, m_par)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {m} reads ({edges} edge instances) of the same workload, build+compact, "
-                         f"{dt:.1f} s"}
+                         f"{dt:.1f} s",
+               "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+               "parallel": {"value": prate, "unit": UNIT, "cores": parts, "kind": "oracle",
+                            "sample": f"the first {m_par} reads, edge counting only: {parts} processes, each "
+                                      f"scanning every read and keeping one hash partition of the edges, "
+                                      f"{pdt:.1f} s (slowest process)"}}
+
+    # end to end through HBM: the bytes the library's kernels account per step
+    step_bytes = sum(v["bytes"] for v in prof.values()) / args.steps
+    build_ms = sum(v["ms"] for kname, v in prof.items() if not kname.startswith("compact")) / args.steps
+    compact_ms = sum(v["ms"] for kname, v in prof.items() if kname.startswith("compact")) / args.steps
 
     if rank == 0:
         print(json.dumps({
@@ -393,6 +457,12 @@ def run_ours(args):
                          "traffic": traffic, "algorithmic_bytes_per_launch": pass_bytes,
                          "launch_ms": pass_ms},
             "stages": stages,
+            "unique_edges_per_s": (info.get("edges") or 0) * args.steps * ws / (ms_max / 1000.0),
+            "build_ms_per_step": build_ms, "compact_ms_per_step": compact_ms,
+            "hbm_end_to_end": {"bytes_per_step": step_bytes,
+                               "GBps": step_bytes / (ms_max / args.steps / 1000.0) / 1e9,
+                               "frac": step_bytes / (ms_max / args.steps / 1000.0) / 1e9 / peak if peak else None,
+                               "bytes": "algorithmic bytes of every kernel of the step, as the library accounts them"},
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": e2e,

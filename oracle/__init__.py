@@ -87,6 +87,10 @@ def _load():
             lib.orc_count_kplus1.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                              ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                              ctypes.c_void_p]
+            lib.orc_edges_in_partition.restype = ctypes.c_int
+            lib.orc_edges_in_partition.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                                   ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                                   ctypes.c_void_p, ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -218,3 +222,18 @@ def count_kplus1(reads, lengths, k: int, queries: list[str]) -> np.ndarray:
     if rc != ORC_OK:
         raise OracleError(rc, "orc_count_kplus1")
     return counts[:len(queries)]
+
+
+def edges_in_partition(reads, lengths, k: int, part: int, parts: int) -> tuple[int, int]:
+    """(distinct edges, edge instances) of partition `part` of `parts` of the
+    edges (partitioned by a hash of the canonical (k+1)-mer), counted over all
+    reads: the unit of work of the multi-core CPU baseline."""
+    lib = _load()
+    reads, lengths = _as_reads(reads, lengths)
+    d = ctypes.c_uint64(0)
+    i = ctypes.c_uint64(0)
+    rc = lib.orc_edges_in_partition(reads.ctypes.data, lengths.ctypes.data, len(lengths), k, part, parts,
+                                    ctypes.byref(d), ctypes.byref(i))
+    if rc != ORC_OK:
+        raise OracleError(rc, "orc_edges_in_partition")
+    return int(d.value), int(i.value)

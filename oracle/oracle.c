@@ -401,6 +401,56 @@ int orc_count_kplus1(const char *reads, const uint32_t *lengths, uint64_t n, uin
 }
 
 /* ------------------------------------------------------------------ */
+/* one partition of the edges, for the multi-core CPU baseline          */
+/* ------------------------------------------------------------------ */
+
+/* The edges of orc_build (Section 2 definition) whose canonical (k+1)-mer
+ * falls in partition `part` of `parts` (partitioned by a hash of that key),
+ * counted over all reads: *distinct edges and their *instances.  Each of
+ * `parts` processes scans every read and keeps only its own edges, so the
+ * parts together do the edge counting of orc_build once. */
+int orc_edges_in_partition(const char *reads, const uint32_t *lengths, uint64_t n, uint32_t k, uint32_t part,
+                           uint32_t parts, uint64_t *distinct, uint64_t *instances) {
+  if (k < 1 || k > 63 || (k % 2) == 0 || parts == 0 || part >= parts || !distinct || !instances) return ORC_EINVAL;
+  int K = (int)k, M = K + 1;
+  table_t t;
+  if (table_init(&t, 1024) != ORC_OK) return ORC_ENOMEM;
+  u128 mask = (M == 64) ? ~(u128)0 : ((((u128)1) << (2 * M)) - 1);
+  uint64_t inst = 0;
+  const char *read = reads;
+  for (uint64_t r = 0; r < n; r++) {
+    int64_t L = lengths[r];
+    u128 fwd = 0, rev = 0;
+    for (int64_t j = 0; j < L; j++) {
+      int c = base_code(read[j]);
+      if (c < 0) { free(t.slots); return ORC_EINVAL; }
+      fwd = ((fwd << 2) | (u128)c) & mask;
+      rev = (rev >> 2) | ((u128)(3 - c) << (2 * (M - 1)));
+      if (j + 1 < M) continue;
+      u128 z = rev < fwd ? rev : fwd;
+      if (mix64((uint64_t)z ^ mix64((uint64_t)(z >> 64))) % parts != part) continue;
+      /* the edge of the k-mer pair ending at j, named as in orc_build */
+      const int64_t j0 = j + 1 - M;
+      u128 x = mer_value(read + j0, K), y = mer_value(read + j0 + 1, K);
+      u128 xh = mer_canonical(x, K), yh = mer_canonical(y, K);
+      int o1 = (x != xh), o2 = (y != yh);
+      u128 s = xh, d = yh;
+      int a = o1, b = o2;
+      if (tuple_less(yh, xh, !o2, !o1, xh, yh, o1, o2)) { s = yh; d = xh; a = !o2; b = !o1; }
+      slot_t *e = table_find(&t, s, d, (uint8_t)((a << 1) | b), 1);
+      if (!e) { free(t.slots); return ORC_ENOMEM; }
+      e->count++;
+      inst++;
+    }
+    read += L;
+  }
+  *distinct = t.size;
+  *instances = inst;
+  free(t.slots);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* chain compaction by walking the chains (Section 6)                   */
 /* ------------------------------------------------------------------ */
 

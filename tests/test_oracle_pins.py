@@ -305,3 +305,17 @@ def test_sampled_counts_match_full_build():
     # a (k+1)-mer given as its reverse complement counts the same edge
     got_rc = oracle.count_kplus1(reads, lengths, 15, [sm.rc(keys[i]) for i in pick])
     assert list(got_rc) == list(got)
+
+
+def test_edge_partitions_add_up_to_the_graph():
+    """The multi-core baseline's unit of work: the hash partitions of the
+    edges, counted separately, add up to the oracle graph's distinct edges
+    and to sum(L - k) instances, for several partition counts."""
+    from paper_1003_1940_gb300 import readgen
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(20_000, 800, 50, 0.01, 15, 5))
+    g = oracle.build_graph(reads, lengths, 15)
+    inst = int(np.maximum(lengths.astype(np.int64) - 15, 0).sum())
+    for parts in (1, 3, 8):
+        res = [oracle.edges_in_partition(reads, lengths, 15, p, parts) for p in range(parts)]
+        assert sum(d for d, _ in res) == g.n_edges
+        assert sum(i for _, i in res) == inst
