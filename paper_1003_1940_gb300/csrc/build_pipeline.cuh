@@ -362,11 +362,11 @@ dbg_status seg_sort_records(dbg_ctx *ctx, const K *kin, const uint32_t *vin, K *
   return DBG_OK;
 }
 
-// The local pass of STEP-2 over edge keys sorted by their bits from
-// low_bits up: k_seg_rle writes the distinct keys to uniq and their
-// multiplicities to mult; *E = the number of distinct keys.
+// The local pass of STEP-2 over n edge keys sorted by their bits from
+// low_bits up.  Leaves the E distinct keys in kin[0, E) and their
+// multiplicities in mult_out (allocated here); kstage (n keys) is scratch.
 template <class K>
-dbg_status seg_rle(dbg_ctx *ctx, const K *kin, K *uniq, uint32_t *mult, uint64_t n, int low_bits, int key_bits,
+dbg_status seg_rle(dbg_ctx *ctx, K *kin, K *kstage, uint64_t n, int low_bits, int key_bits, DevBuf &mult_out,
                    uint64_t *E) {
   using Sh = SegShape<K>;
   cudaStream_t s = ctx->stream;
@@ -380,27 +380,32 @@ dbg_status seg_rle(dbg_ctx *ctx, const K *kin, K *uniq, uint32_t *mult, uint64_t
     DBG_TRY(alloc_buf(ctx, gheads, ((uint64_t)G + 1) * 4));
     DBG_TRY(run_length_reduce<K>(ctx, gk.as<K>(), G, guniq.as<K>(), gheads.as<uint32_t>(), &H));
   }
-  const int rank = local_rank_method(ctx, sizeof(K) == 16);
-  auto kern = rank == RANK_MATCH    ? k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_MATCH>
-              : rank == RANK_ATOMIC ? k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_ATOMIC>
-                                    : k_seg_rle<K, Sh::ITEMS, Sh::TILE, RANK_BALLOT>;
-  constexpr size_t smem = sizeof(SegSortSmem<K, false, Sh::ITEMS>);
-  set_smem_attrs(kern, smem);
   const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
-  DBG_TRY(ensure_status(ctx, tiles));
-  uint32_t epoch;
-  DBG_TRY(next_epoch(ctx, &epoch));
-  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), s));
-  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 12, 0, sizeof(uint32_t), s));
+  DevBuf mstage, tcount, toff;
+  DBG_TRY(alloc_buf(ctx, mstage, n * 4));
+  DBG_TRY(alloc_buf(ctx, tcount, tiles * 4));
+  DBG_TRY(alloc_buf(ctx, toff, (tiles + 1) * 8));
+  const int rank = local_rank_method(ctx, sizeof(K) == 16);
+  auto radix = rank == RANK_MATCH    ? k_seg_rle<K, Sh::ITEMS, RANK_MATCH>
+               : rank == RANK_ATOMIC ? k_seg_rle<K, Sh::ITEMS, RANK_ATOMIC>
+                                     : k_seg_rle<K, Sh::ITEMS, RANK_BALLOT>;
+  constexpr size_t rsmem = sizeof(SegSortSmem<K, false, Sh::ITEMS>);
+  set_smem_attrs(radix, rsmem);
   DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, (double)n * sizeof(K),
-             kern<<<(unsigned)tiles, SEG_BLOCK, smem, s>>>(
+             radix<<<(unsigned)tiles, SEG_BLOCK, rsmem, s>>>(
                  kin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), guniq.as<K>(),
-                 gheads.as<uint32_t>(), (uint32_t)H, uniq, mult, n, low_bits, key_bits, ctx->d_status,
-                 ctx->d_counters, epoch, ctx->spin_limit, ctx->d_err, ctx->d_counters + 12));
+                 gheads.as<uint32_t>(), (uint32_t)H, kstage, mstage.as<uint32_t>(), tcount.as<uint32_t>(),
+                 low_bits, key_bits));
   DBG_CUDA_TRY(cudaGetLastError());
   uint32_t total = 0;
-  DBG_TRY(read_small(ctx, ctx->d_counters + 12, sizeof(uint32_t), &total));
+  DBG_TRY(scan_u32(ctx, tcount.as<uint32_t>(), tiles, toff.as<uint64_t>(), &total, ST_LOCAL_SORT_EDGES));
   *E = total;
+  DBG_TRY(alloc_buf(ctx, mult_out, std::max<uint64_t>(1, total) * 4));
+  DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, 2.0 * total * (sizeof(K) + 4),
+             k_seg_compact<K><<<(unsigned)std::min<uint64_t>(tiles, 152ull * 16), 256, 0, s>>>(
+                 bound.as<uint64_t>(), tcount.as<uint32_t>(), toff.as<uint64_t>(), tiles, kstage,
+                 mstage.as<uint32_t>(), kin, mult_out.as<uint32_t>()));
+  DBG_CUDA_TRY(cudaGetLastError());
   return DBG_OK;
 }
 
@@ -560,8 +565,8 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
       // high digits globally, then the local sort with the run-length
       // reduce: distinct keys into alt, multiplicities into mult_tmp
       DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, N, kbits, d_hist, d_digit_base, p0)));
-      DBG_TRY(alloc_buf(ctx, mult_tmp, N * sizeof(uint32_t)));
-      DBG_TRY(seg_rle<K>(ctx, kp, alt, mult_tmp.as<uint32_t>(), N, RADIX_BITS * p0, kbits, &E));
+      DBG_TRY(seg_rle<K>(ctx, kp, alt, N, RADIX_BITS * p0, kbits, mult_tmp, &E));
+      std::swap(kp, alt);  // the distinct keys are in the sort's buffer
     } else {
       // every digit globally, then the run-length reduce
       DBG_TRY(alloc_buf(ctx, headpos, (N + 1) * sizeof(uint32_t)));
@@ -941,7 +946,10 @@ dbg_status build_bucketed_impl(dbg_ctx *ctx, const BucketInput &in, uint64_t bud
     if (p0 > 0) {
       // multiplicities go where the run heads would (headpos is cnt + 1 long)
       DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, cnt, kbits, d_hist, d_digit_base, p0)));
-      DBG_TRY(seg_rle<K>(ctx, kp, alt, headpos.as<uint32_t>(), cnt, RADIX_BITS * p0, kbits, &eb64));
+      DevBuf mdense;
+      DBG_TRY(seg_rle<K>(ctx, kp, alt, cnt, RADIX_BITS * p0, kbits, mdense, &eb64));
+      if (eb64) DBG_CUDA_TRY(cudaMemcpyAsync(headpos.p, mdense.p, eb64 * 4, cudaMemcpyDeviceToDevice, s));
+      std::swap(kp, alt);  // the distinct keys are in the sort's buffer
     } else {
       DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, cnt, kbits, d_hist, d_digit_base)));
       DBG_TRY(run_length_reduce<K>(ctx, kp, cnt, alt, headpos.as<uint32_t>(), &eb64));

@@ -17,10 +17,9 @@
 //
 // k_seg_sort sorts (key, payload) records (STEP-3's node records).
 // k_seg_rle finishes STEP-2 on the edge keys: it sorts them and writes each
-// distinct key once with the length of its run (its multiplicity), at an
-// offset found by decoupled look-back over the tiles' distinct-key counts.
-// Equal keys share their high bits, so no run of equal keys crosses a tile
-// boundary.
+// distinct key once with the length of its run (its multiplicity) into the
+// tile's own range; k_seg_compact then packs the tiles' outputs.  Equal keys share their high bits, so no run of
+// equal keys crosses a tile boundary.
 #pragma once
 
 #include "k_build.cuh"
@@ -297,92 +296,115 @@ __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_sort(
   }
 }
 
-// Edge keys: distinct keys and multiplicities of tile t at an offset found by
-// decoupled look-back; an oversize tile takes its runs from the gathered,
-// globally sorted and reduced keys (guniq, with run heads gheads at the
-// positions of the gathered buffer, H runs in all, gheads[H] = its length).
-template <class K, int ITEMS, int TILE_T, int RANK>
+// Edge keys (STEP-2's local pass).  Tile t writes its distinct keys and
+// their multiplicities at the start of its own range, ustage / mstage[bound[t]
+// ...], and their number to tcount[t]; a scan of tcount and k_seg_compact
+// then make the dense edge list.  No tile waits for another.
+
+// The distinct keys of an oversize tile, from the gathered, globally sorted
+// and reduced keys (guniq, run heads gheads at the positions of the gathered
+// buffer, H runs in all, gheads[H] = its length).
+template <class K>
+__device__ __forceinline__ void seg_rle_gathered(uint32_t tile, const uint64_t *__restrict__ bound,
+                                                 const uint32_t *__restrict__ osize, const uint64_t *__restrict__ ooff,
+                                                 const K *__restrict__ guniq, const uint32_t *__restrict__ gheads,
+                                                 uint32_t H, K *__restrict__ ustage, uint32_t *__restrict__ mstage,
+                                                 uint32_t *__restrict__ tcount) {
+  const uint64_t o = ooff[tile], s = bound[tile];
+  const uint32_t h0 = lower_bound_u32(gheads, H, o), h1 = lower_bound_u32(gheads, H, o + osize[tile]);
+  for (uint32_t r = threadIdx.x; r < h1 - h0; r += blockDim.x) {
+    ustage[s + r] = guniq[h0 + r];
+    mstage[s + r] = gheads[h0 + r + 1] - gheads[h0 + r];
+  }
+  if (threadIdx.x == 0) tcount[tile] = h1 - h0;
+}
+
+// Block radix local sort + RLE, one CTA per tile.
+template <class K, int ITEMS, int RANK>
 __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_rle(
     const K *__restrict__ kin, const uint64_t *__restrict__ bound, const uint32_t *__restrict__ osize,
     const uint64_t *__restrict__ ooff, const K *__restrict__ guniq, const uint32_t *__restrict__ gheads, uint32_t H,
-    K *__restrict__ uniq, uint32_t *__restrict__ mult, uint64_t n, int low_bits, int key_bits, uint64_t *status,
-    uint32_t *ticket, uint32_t epoch, uint32_t spin_limit, uint32_t *err, uint32_t *total) {
+    K *__restrict__ ustage, uint32_t *__restrict__ mstage, uint32_t *__restrict__ tcount, int low_bits,
+    int key_bits) {
   using S = SegSortSmem<K, false, ITEMS>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   S &sm = *reinterpret_cast<S *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) sm.tile = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const uint32_t tile = sm.tile;
-  const uint64_t num_tiles = (n + TILE_T - 1) / TILE_T;
-  if (osize[tile]) {
-    if (tid == 0) {
-      const uint64_t o = ooff[tile];
-      sm.bound[0] = lower_bound_u32(gheads, H, o);
-      sm.bound[1] = lower_bound_u32(gheads, H, o + osize[tile]);
+  const uint32_t tile = blockIdx.x;
+  {
+    if (osize[tile]) {
+      seg_rle_gathered<K>(tile, bound, osize, ooff, guniq, gheads, H, ustage, mstage, tcount);
+      return;
+    }
+    for (int i = tid; i < S::WARPS * RADIX; i += SEG_BLOCK) (&sm.whist[0][0])[i] = 0;
+    for (int i = tid; i < S::WARPS * (RADIX + 1); i += SEG_BLOCK) (&sm.match[0][0])[i] = 0;
+    seg_setup<K>(sm, kin, bound, tile, low_bits, key_bits);
+    const uint64_t s = sm.bound[0];
+    const uint32_t cnt = (uint32_t)(sm.bound[1] - s);
+    const K base = sm.base;
+    uint32_t rank[ITEMS];
+    if (cnt > 0) {
+      const int passes = (int)sm.passes;
+      const int ipw = (int)((cnt + SEG_BLOCK - 1) / SEG_BLOCK);
+      const uint32_t wofs = (uint32_t)warp * 32u * ipw;
+      K key[ITEMS];
+      uint32_t none[ITEMS];
+#pragma unroll
+      for (int i = 0; i < ITEMS; i++) {
+        const uint32_t j = wofs + i * 32 + lane;
+        key[i] = (i < ipw && j < cnt) ? KeyOps<K>::sub(kin[s + j], base) : KeyOps<K>::zero();
+      }
+      for (int p = 0; p < passes; p++) {
+        if (p > 0) {
+          reload_items<K, false, ITEMS>(sm, key, none, ipw, wofs, cnt);
+          __syncthreads();
+        }
+        rank_items<K, ITEMS, RANK>(sm, key, rank, ipw, wofs, cnt, p * RADIX_BITS);
+        digit_positions(sm);
+        scatter_items<K, false, ITEMS>(sm, key, none, rank, ipw);
+      }
     }
     __syncthreads();
-    const uint32_t h0 = (uint32_t)sm.bound[0], count = (uint32_t)(sm.bound[1] - sm.bound[0]);
-    const uint32_t excl = tile_prefix(status, tile, count, epoch, spin_limit, err, &sm.excl);
-    for (uint32_t r = tid; r < count; r += SEG_BLOCK) {
-      uniq[excl + r] = guniq[h0 + r];
-      mult[excl + r] = gheads[h0 + r + 1] - gheads[h0 + r];
-    }
-    if (tile + 1 == num_tiles && tid == 0) *total = excl + count;
-    return;
-  }
-  for (int i = tid; i < S::WARPS * RADIX; i += SEG_BLOCK) (&sm.whist[0][0])[i] = 0;
-  for (int i = tid; i < S::WARPS * (RADIX + 1); i += SEG_BLOCK) (&sm.match[0][0])[i] = 0;
-  seg_setup<K>(sm, kin, bound, tile, low_bits, key_bits);
-  const uint64_t s = sm.bound[0];
-  const uint32_t cnt = (uint32_t)(sm.bound[1] - s);
-  const K base = sm.base;
-  uint32_t rank[ITEMS];
-  if (cnt > 0) {
-    const int passes = (int)sm.passes;
-    const int ipw = (int)((cnt + SEG_BLOCK - 1) / SEG_BLOCK);
-    const uint32_t wofs = (uint32_t)warp * 32u * ipw;
-    K key[ITEMS];
-    uint32_t none[ITEMS];
+    // distinct keys: the first key of each run; a run's length is the
+    // distance to the next run's first key
+    bool head[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-      const uint32_t j = wofs + i * 32 + lane;
-      key[i] = (i < ipw && j < cnt) ? KeyOps<K>::sub(kin[s + j], base) : KeyOps<K>::zero();
-    }
-    for (int p = 0; p < passes; p++) {
-      if (p > 0) {
-        reload_items<K, false, ITEMS>(sm, key, none, ipw, wofs, cnt);
-        __syncthreads();
-      }
-      rank_items<K, ITEMS, RANK>(sm, key, rank, ipw, wofs, cnt, p * RADIX_BITS);
-      digit_positions(sm);
-      scatter_items<K, false, ITEMS>(sm, key, none, rank, ipw);
-    }
-  }
-  __syncthreads();
-  // distinct keys: the first key of each run; a run's length is the
-  // distance to the next run's first key
-  bool head[ITEMS];
-#pragma unroll
-  for (int i = 0; i < ITEMS; i++) {
-    const uint32_t j = (uint32_t)i * SEG_BLOCK + tid;
-    head[i] = j < cnt && (j == 0 || !KeyOps<K>::eq(sm.keys[j], sm.keys[j - 1]));
-  }
-  const uint32_t count = tile_flag_ranks<SEG_BLOCK, ITEMS>(head, rank, sm.cnt);
-#pragma unroll
-  for (int i = 0; i < ITEMS; i++)
-    if (head[i]) sm.hpos[rank[i]] = (uint32_t)i * SEG_BLOCK + tid;
-  if (tid == 0) sm.hpos[count] = cnt;
-  const uint32_t excl = tile_prefix(status, tile, count, epoch, spin_limit, err, &sm.excl);
-#pragma unroll
-  for (int i = 0; i < ITEMS; i++) {
-    if (head[i]) {
       const uint32_t j = (uint32_t)i * SEG_BLOCK + tid;
-      uniq[excl + rank[i]] = KeyOps<K>::add(sm.keys[j], base);
-      mult[excl + rank[i]] = sm.hpos[rank[i] + 1] - j;
+      head[i] = j < cnt && (j == 0 || !KeyOps<K>::eq(sm.keys[j], sm.keys[j - 1]));
+    }
+    const uint32_t count = tile_flag_ranks<SEG_BLOCK, ITEMS>(head, rank, sm.cnt);
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++)
+      if (head[i]) sm.hpos[rank[i]] = (uint32_t)i * SEG_BLOCK + tid;
+    if (tid == 0) sm.hpos[count] = cnt;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      if (head[i]) {
+        const uint32_t j = (uint32_t)i * SEG_BLOCK + tid;
+        ustage[s + rank[i]] = KeyOps<K>::add(sm.keys[j], base);
+        mstage[s + rank[i]] = sm.hpos[rank[i] + 1] - j;
+      }
+    }
+    if (tid == 0) tcount[tile] = count;
+  }
+}
+
+// Moves every tile's distinct keys from its staging range to the dense
+// edge list (toff = exclusive scan of tcount).
+template <class K>
+__global__ void k_seg_compact(const uint64_t *__restrict__ bound, const uint32_t *__restrict__ tcount,
+                              const uint64_t *__restrict__ toff, uint64_t tiles, const K *__restrict__ ustage,
+                              const uint32_t *__restrict__ mstage, K *__restrict__ uniq, uint32_t *__restrict__ mult) {
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t s = bound[t], o = toff[t];
+    const uint32_t c = tcount[t];
+    for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
+      uniq[o + r] = ustage[s + r];
+      mult[o + r] = mstage[s + r];
     }
   }
-  if (tile + 1 == num_tiles && tid == 0) *total = excl + count;
 }
 
 }  // namespace dbg
