@@ -375,58 +375,71 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_fast_measure(const uint32_t *__r
   }
 }
 
+// The first node of every kept unitig: its tables, node entry and first
+// k-mer, and where its walk continues (walk[u] = succ_base of the first
+// strand-node: the second one and the base it appends, or all ones).
 template <class K>
-__global__ __launch_bounds__(WALK_BLOCK) void k_fast_write(
-    const uint64_t *__restrict__ succ_base, const uint32_t *__restrict__ is_head, const uint8_t *__restrict__ hstrand,
-    const uint64_t *__restrict__ uidx, const uint64_t *__restrict__ off_by_v, const uint64_t *__restrict__ node_keys,
-    uint64_t V, uint64_t U, int k, uint64_t *__restrict__ nodes_out, char *__restrict__ seq,
-    uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off, uint8_t *__restrict__ circular) {
-  __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
+__global__ void k_fast_heads(const uint64_t *__restrict__ succ_base, const uint32_t *__restrict__ is_head,
+                             const uint8_t *__restrict__ hstrand, const uint64_t *__restrict__ uidx,
+                             const uint64_t *__restrict__ off_by_v, const uint64_t *__restrict__ node_keys,
+                             uint64_t V, uint64_t U, int k, uint64_t *__restrict__ nodes_out, char *__restrict__ seq,
+                             uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
+                             uint8_t *__restrict__ circular, uint64_t *__restrict__ walk) {
+  const char *acgt = "ACGT";
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= V; v += (uint64_t)gridDim.x * blockDim.x) {
+    if (v == V) {
+      node_off[U] = V;
+      seq_off[U] = V + U * (uint64_t)(k - 1);
+      continue;
+    }
+    if (!is_head[v]) continue;
+    const uint64_t u = uidx[v], off = off_by_v[v], so = off + u * (uint64_t)(k - 1);
+    const uint32_t y = 2 * (uint32_t)v + hstrand[v];
+    node_off[u] = off;
+    seq_off[u] = so;
+    circular[u] = 0;
+    nodes_out[off] = y;  // (node ID << 1) | strand
+    const K km = strand_kmer<K>(node_keys, y, k);
+    for (int j = 0; j < k; j++) seq[so + j] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - j), 2)];
+    walk[u] = succ_base[y];
+  }
+}
+
+// The rest of every kept unitig: lanes take unitigs in turn (per-warp
+// chunks, a shared-memory counter) and walk them, writing each node's entry
+// and the base its arc appends; only the successor words are loaded at random.
+__global__ __launch_bounds__(WALK_BLOCK) void k_fast_walk(const uint64_t *__restrict__ succ_base,
+                                                          const uint64_t *__restrict__ walk,
+                                                          const uint64_t *__restrict__ node_off,
+                                                          const uint64_t *__restrict__ seq_off, uint64_t U, int k,
+                                                          uint64_t *__restrict__ nodes_out, char *__restrict__ seq) {
   __shared__ uint32_t s_next[WALK_WARPS];
   const char *acgt = "ACGT";
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    node_off[U] = V;
-    seq_off[U] = V + U * (uint64_t)(k - 1);
-  }
-  const uint64_t chunks = (V + WALK_CHUNK - 1) / WALK_CHUNK;
+  const uint64_t chunks = (U + WALK_CHUNK - 1) / WALK_CHUNK;
   for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
-    const uint32_t cnt = queue_heads(c * WALK_CHUNK, V, s_q[w], [&](uint64_t v) { return is_head[v] != 0; });
+    const uint64_t u0 = c * WALK_CHUNK;
+    const uint32_t cnt = (uint32_t)min((uint64_t)WALK_CHUNK, U - u0);
     if (lane == 0) s_next[w] = 0;
     __syncwarp();
     bool busy = false;
-    uint32_t y = 0, base = 0;
-    uint64_t i = 0, off = 0, so = 0;
+    uint64_t nb = 0, pos = 0, spos = 0;
     for (;;) {
       if (!busy) {
         const uint32_t qi = atomicAdd(&s_next[w], 1u);
         if (qi >= cnt) break;
-        const uint32_t v = s_q[w][qi];
-        const uint64_t u = uidx[v];
-        off = off_by_v[v];
-        so = off + u * (uint64_t)(k - 1);
-        node_off[u] = off;
-        seq_off[u] = so;
-        circular[u] = 0;
-        y = 2 * v + hstrand[v];
-        i = 0;
+        const uint64_t u = u0 + qi;
+        nb = walk[u];
+        if (nb == ~0ull) continue;  // a single node
+        pos = node_off[u] + 1;
+        spos = seq_off[u] + k;
         busy = true;
       }
-      nodes_out[off + i] = y;  // (node ID << 1) | strand
-      if (i == 0) {
-        const K km = strand_kmer<K>(node_keys, y, k);
-        for (int j = 0; j < k; j++) seq[so + j] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - j), 2)];
-      } else {
-        seq[so + k - 1 + i] = acgt[base];
-      }
-      const uint64_t nb = succ_base[y];
-      if (nb == ~0ull) {
-        busy = false;
-      } else {
-        y = (uint32_t)nb;
-        base = (uint32_t)(nb >> 32);
-        i++;
-      }
+      const uint32_t y = (uint32_t)nb;
+      nodes_out[pos++] = y;
+      seq[spos++] = acgt[nb >> 32];
+      nb = succ_base[y];
+      busy = nb != ~0ull;
     }
     __syncwarp();
   }
@@ -551,12 +564,19 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
         DBG_TRY(alloc_buf(ctx, u->nodes, V1 * 8));
         u->total_bases = V + Uf * (uint64_t)(k - 1);
         DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
-        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)V * (4 + 1 + 16 + 8 + 8 * g->key_words + 1) + (double)Uf * (k + 17),
-                   k_fast_write<K><<<walk_grid(ctx, V), WALK_BLOCK, 0, s>>>(
+        DevBuf walk;
+        DBG_TRY(alloc_buf(ctx, walk, std::max<uint64_t>(1, Uf) * 8));
+        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)V * (4 + 1) + (double)Uf * (16 + 8 + 8 * g->key_words + 8 + 25 + k),
+                   k_fast_heads<K><<<grid_of(V + 1), 256, 0, s>>>(
                        word.as<uint64_t>(), f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_uidx.as<uint64_t>(),
                        f_off.as<uint64_t>(), g->node_keys.as<uint64_t>(), V, Uf, k, u->nodes.as<uint64_t>(),
                        u->seq.as<char>(), u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(),
-                       u->circular.as<uint8_t>()));
+                       u->circular.as<uint8_t>(), walk.as<uint64_t>()));
+        if (Uf > 0)
+          DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)(V - Uf) * (8 + 8 + 1) + (double)Uf * 24,
+                     k_fast_walk<<<walk_grid(ctx, Uf), WALK_BLOCK, 0, s>>>(
+                         word.as<uint64_t>(), walk.as<uint64_t>(), u->node_off.as<uint64_t>(),
+                         u->seq_off.as<uint64_t>(), Uf, k, u->nodes.as<uint64_t>(), u->seq.as<char>()));
         DBG_CUDA_TRY(cudaGetLastError());
         DBG_CUDA_TRY(cudaStreamSynchronize(s));
         return check_device_error(ctx);
