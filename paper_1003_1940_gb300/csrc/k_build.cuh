@@ -821,75 +821,6 @@ __global__ void k_isolated(const uint64_t *__restrict__ packed, const uint64_t *
   }
 }
 
-// ---------------------------------------------------------------------------
-// K6 node IDs (STEP-3) + adjacency rows (STEP-4).  (base_v, base_slot) are
-// added to the IDs and adjacency slots written to src/dst and the adjacency
-// arrays, for a node-key range built after others.  Over the node records
-// sorted by key (stable, so edge ends precede isolated records within a
-// node and are in (e, role) order): node ID = number of run heads up to the
-// record minus one; adjacency slot = number of edge-end records before it.
-// Two look-back scans in one pass.  The last tile writes row_ptr[V] and the
-// totals {V, ends}.
-// ---------------------------------------------------------------------------
-template <class K, int ITEMS>
-__global__ __launch_bounds__(SCAN_BLOCK) void k_node_ids(
-    const K *__restrict__ rkeys, const uint32_t *__restrict__ rvals, uint64_t R, K *__restrict__ node_keys,
-    uint64_t *__restrict__ row_ptr, uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
-    uint32_t *__restrict__ adj_edge, uint8_t *__restrict__ adj_role, uint64_t *status_h, uint64_t *status_e,
-    uint32_t *ticket, uint32_t epoch_h, uint32_t epoch_e, uint32_t spin_limit, uint32_t *err,
-    uint32_t *totals, uint32_t base_v, uint64_t base_slot) {
-  constexpr int WARPS = SCAN_BLOCK / 32;
-  constexpr int TILE = SCAN_BLOCK * ITEMS;
-  __shared__ uint32_t s_cnt_h[ITEMS * WARPS + 1], s_cnt_e[ITEMS * WARPS + 1];
-  __shared__ uint32_t s_tile, s_excl_h, s_excl_e;
-  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * TILE;
-  K key[ITEMS];
-  uint32_t val[ITEMS];
-  bool head[ITEMS], end[ITEMS];
-  uint32_t rh[ITEMS], re[ITEMS];
-#pragma unroll
-  for (int i = 0; i < ITEMS; i++) {
-    const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
-    head[i] = end[i] = false;
-    val[i] = REC_NONE;
-    if (idx < R) {
-      key[i] = rkeys[idx];
-      val[i] = rvals[idx];
-      head[i] = idx == 0 || !KeyOps<K>::eq(key[i], rkeys[idx - 1]);
-      end[i] = val[i] != REC_NONE;
-    }
-  }
-  const uint32_t ch = tile_flag_ranks<SCAN_BLOCK, ITEMS>(head, rh, s_cnt_h);
-  const uint32_t ce = tile_flag_ranks<SCAN_BLOCK, ITEMS>(end, re, s_cnt_e);
-  // both look-backs: warp 0 for heads, then for edge ends
-  const uint32_t xh = tile_prefix(status_h, tile, ch, epoch_h, spin_limit, err, &s_excl_h);
-  const uint32_t xe = tile_prefix(status_e, tile, ce, epoch_e, spin_limit, err, &s_excl_e);
-#pragma unroll
-  for (int i = 0; i < ITEMS; i++) {
-    const uint64_t idx = base + (uint64_t)i * SCAN_BLOCK + threadIdx.x;
-    if (idx >= R) continue;
-    const uint32_t id = xh + rh[i] + (head[i] ? 1u : 0u) - 1u;
-    const uint32_t slot = xe + re[i];
-    if (head[i]) {
-      node_keys[id] = key[i];
-      row_ptr[id] = base_slot + slot;
-    }
-    if (end[i]) {
-      const uint32_t e = val[i] >> 1, role = val[i] & 1u;
-      adj_edge[base_slot + slot] = e;
-      adj_role[base_slot + slot] = (uint8_t)role;
-      (role ? dst : src)[e] = base_v + id;
-    }
-  }
-  if (base + TILE >= R && threadIdx.x == 0) {
-    row_ptr[xh + ch] = base_slot + xe + ce;
-    totals[0] = xh + ch;
-    totals[1] = xe + ce;
-  }
-}
 
 // K7 neighbour of every adjacency slot: the edge's other end.
 static __global__ void k_adj_nbr(const uint32_t *__restrict__ adj_edge, const uint8_t *__restrict__ adj_role,
@@ -1225,8 +1156,13 @@ __global__ __launch_bounds__(SCAN_BLOCK) void k_write_heads(const K *__restrict_
   if (base + RS_TILE >= n && threadIdx.x == 0) headpos[off + count] = (uint32_t)n;
 }
 
-// K6 writing pass: node IDs and adjacency slots from the scanned tile
-// offsets of run heads (hoff) and edge-end records (eoff).
+// K6 node IDs (STEP-3) + adjacency rows (STEP-4), the writing pass.  Over
+// the node records sorted by key (stable, so edge ends precede isolated
+// records within a node and are in (e, role) order): node ID = number of run
+// heads up to the record minus one; adjacency slot = number of edge-end
+// records before it -- from the scanned per-tile counts of run heads (hoff)
+// and edge ends (eoff).  (base_v, base_slot) are added to the IDs and slots,
+// for a node-key range built after others.  The last tile writes row_ptr[V].
 //
 // PART = true: instead of writing src[e] / dst[e] at random, the edge ends
 // (e << 1 | role, node ID) are partitioned by e >> bshift into ends[] (bucket
