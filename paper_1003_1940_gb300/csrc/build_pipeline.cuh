@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "k_build.cuh"
 #include "k_segsort.cuh"
@@ -391,11 +392,46 @@ dbg_status seg_rle(dbg_ctx *ctx, K *kin, K *kstage, uint64_t n, int low_bits, in
                                      : k_seg_rle<K, Sh::ITEMS, RANK_BALLOT>;
   constexpr size_t rsmem = sizeof(SegSortSmem<K, false, Sh::ITEMS>);
   set_smem_attrs(radix, rsmem);
-  DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, (double)n * sizeof(K),
-             radix<<<(unsigned)tiles, SEG_BLOCK, rsmem, s>>>(
-                 kin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), guniq.as<K>(),
-                 gheads.as<uint32_t>(), (uint32_t)H, kstage, mstage.as<uint32_t>(), tcount.as<uint32_t>(),
-                 low_bits, key_bits));
+  bool counted = false;
+  if constexpr (std::is_same<K, uint64_t>::value) {
+    if (ctx->count_first) {
+      // count-first; the tiles that overflow their table are listed (after
+      // a counter word) and sorted copy by copy
+      auto count = rank == RANK_MATCH    ? k_seg_count<K, RANK_MATCH>
+                   : rank == RANK_ATOMIC ? k_seg_count<K, RANK_ATOMIC>
+                                         : k_seg_count<K, RANK_BALLOT>;
+      const size_t csmem = rank == RANK_MATCH    ? sizeof(SegCountSmem<K, RANK_MATCH>)
+                           : rank == RANK_ATOMIC ? sizeof(SegCountSmem<K, RANK_ATOMIC>)
+                                                 : sizeof(SegCountSmem<K, RANK_BALLOT>);
+      set_smem_attrs(count, csmem);
+      DevBuf over;
+      DBG_TRY(alloc_buf(ctx, over, (tiles + 1) * 4));
+      uint32_t *over_count = over.as<uint32_t>(), *over_list = over_count + 1;
+      DBG_CUDA_TRY(cudaMemsetAsync(over_count, 0, 4, s));
+      DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, (double)n * sizeof(K),
+                 count<<<(unsigned)tiles, SEG_BLOCK, csmem, s>>>(
+                     kin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), guniq.as<K>(),
+                     gheads.as<uint32_t>(), (uint32_t)H, kstage, mstage.as<uint32_t>(), tcount.as<uint32_t>(),
+                     over_list, over_count, low_bits, key_bits));
+      DBG_CUDA_TRY(cudaGetLastError());
+      uint32_t nover = 0;
+      DBG_TRY(read_small(ctx, over_count, sizeof(uint32_t), &nover));
+      ctx->count_overflow_tiles += nover;
+      if (nover > 0)
+        DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, 0.0,
+                   radix<<<nover, SEG_BLOCK, rsmem, s>>>(
+                       kin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), guniq.as<K>(),
+                       gheads.as<uint32_t>(), (uint32_t)H, kstage, mstage.as<uint32_t>(), tcount.as<uint32_t>(),
+                       low_bits, key_bits, over_list));
+      counted = true;
+    }
+  }
+  if (!counted)
+    DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, (double)n * sizeof(K),
+               radix<<<(unsigned)tiles, SEG_BLOCK, rsmem, s>>>(
+                   kin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), guniq.as<K>(),
+                   gheads.as<uint32_t>(), (uint32_t)H, kstage, mstage.as<uint32_t>(), tcount.as<uint32_t>(),
+                   low_bits, key_bits, nullptr));
   DBG_CUDA_TRY(cudaGetLastError());
   uint32_t total = 0;
   DBG_TRY(scan_u32(ctx, tcount.as<uint32_t>(), tiles, toff.as<uint64_t>(), &total, ST_LOCAL_SORT_EDGES));

@@ -77,6 +77,8 @@ struct dbg_ctx {
   // 3: u128+payload keys; the local sort's ranking for 4: u64, 5: u128 keys
   int sort_variant[6] = {0, 0, 0, 0, 0, 0};
   int hybrid_sort = 1;                 // high digits globally + local sort of group-aligned tiles
+  int count_first = 1;                 // local pass of the edge keys counts copies before sorting
+  uint64_t count_overflow_tiles = 0;  // count-first tiles whose keys did not fit the hash table
   uint64_t local_sort_fallbacks = 0;   // local sorts that met a group longer than their window
   int num_sms = 0;
   // persistent scratch: the look-back status words of every scan and sort

@@ -19,7 +19,9 @@
 // k_seg_rle finishes STEP-2 on the edge keys: it sorts them and writes each
 // distinct key once with the length of its run (its multiplicity) into the
 // tile's own range; k_seg_compact then packs the tiles' outputs.  Equal keys share their high bits, so no run of
-// equal keys crosses a tile boundary.
+// equal keys crosses a tile boundary.  k_seg_count does the same work by
+// counting each tile's copies in a hash table first and sorting only the
+// distinct keys.
 #pragma once
 
 #include "k_build.cuh"
@@ -319,18 +321,19 @@ __device__ __forceinline__ void seg_rle_gathered(uint32_t tile, const uint64_t *
   if (threadIdx.x == 0) tcount[tile] = h1 - h0;
 }
 
-// Block radix local sort + RLE, one CTA per tile.
+// Block radix local sort + RLE, one CTA per tile (every tile, or the tiles
+// of tile_list when it is not null).
 template <class K, int ITEMS, int RANK>
 __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_rle(
     const K *__restrict__ kin, const uint64_t *__restrict__ bound, const uint32_t *__restrict__ osize,
     const uint64_t *__restrict__ ooff, const K *__restrict__ guniq, const uint32_t *__restrict__ gheads, uint32_t H,
     K *__restrict__ ustage, uint32_t *__restrict__ mstage, uint32_t *__restrict__ tcount, int low_bits,
-    int key_bits) {
+    int key_bits, const uint32_t *__restrict__ tile_list) {
   using S = SegSortSmem<K, false, ITEMS>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   S &sm = *reinterpret_cast<S *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t tile = blockIdx.x;
+  const uint32_t tile = tile_list ? tile_list[blockIdx.x] : blockIdx.x;
   {
     if (osize[tile]) {
       seg_rle_gathered<K>(tile, bound, osize, ooff, guniq, gheads, H, ustage, mstage, tcount);
@@ -389,6 +392,174 @@ __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_rle(
     }
     if (tid == 0) tcount[tile] = count;
   }
+}
+
+// Edge keys, counted before they are sorted.  A tile of the local pass
+// holds every copy of each of its keys, and at read coverage c a tile of n
+// keys holds about n / c distinct ones, so k_seg_count counts the copies
+// first, in a shared-memory hash table of TBL slots (linear probing; a slot
+// is claimed by compare-and-swap and counted by atomic add), packs the
+// occupied slots to the front of the table in slot order, and radix-sorts
+// only the distinct keys with their counts as payload.  The output is that
+// of k_seg_rle: each distinct key once, in order, with its multiplicity
+// (STEP-2), staged in the tile's own range.  The table is small so that
+// several CTAs share an SM; a tile whose keys do not fit (a probe longer
+// than PROBES slots) is listed in over_list and sorted by k_seg_rle instead.
+
+// Hash-table slots of the counting pass.  The empty mark is the all-ones
+// key, which no key offset reaches: an offset is key - base <= key, and the
+// all-ones key (T repeated) is never canonical, its reverse complement (A
+// repeated) being smaller.
+template <class K>
+struct SlotOps;
+
+template <>
+struct SlotOps<uint64_t> {
+  __device__ static uint64_t empty() { return ~0ull; }
+  // Fibonacci hashing: the high 32 bits of d times 2^64 / golden ratio
+  __device__ static uint32_t hash(uint64_t d) { return (uint32_t)((d * 0x9e3779b97f4a7c15ull) >> 32); }
+  __device__ static uint64_t load(const uint64_t *p) { return *reinterpret_cast<const volatile uint64_t *>(p); }
+  __device__ static uint64_t cas(uint64_t *p, uint64_t cmp, uint64_t v) {
+    return atomicCAS(reinterpret_cast<unsigned long long *>(p), cmp, v);
+  }
+};
+
+template <class K, int RANK>
+struct SegCountSmem {
+  static constexpr int WARPS = SEG_BLOCK / 32;
+  static constexpr int TBL = 2048;                // hash slots
+  static constexpr int TBITS = 11;                // log2(TBL)
+  static constexpr int ITEMS = TBL / SEG_BLOCK;   // distinct keys per thread in the sort
+  static constexpr int LOAD = 8;                  // keys per thread per load batch
+  static constexpr uint32_t PROBES = 64;          // longest probe before the tile overflows
+  static_assert((1 << TBITS) == TBL, "table size");
+  K keys[TBL];         // hash slots; then the distinct keys, packed and sorted
+  uint32_t vals[TBL];  // copies per slot; then per distinct key
+  uint32_t whist[WARPS][RADIX];
+  uint32_t match[RANK == RANK_ATOMIC ? WARPS : 1][RADIX + 1];
+  uint32_t cnt[ITEMS * WARPS + 1];
+  uint32_t tmp[8];
+  uint64_t bound[2];
+  K base;
+  uint32_t tile, passes, excl, total, overflow;
+};
+
+template <class K, int RANK>
+__global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
+    const K *__restrict__ kin, const uint64_t *__restrict__ bound, const uint32_t *__restrict__ osize,
+    const uint64_t *__restrict__ ooff, const K *__restrict__ guniq, const uint32_t *__restrict__ gheads, uint32_t H,
+    K *__restrict__ ustage, uint32_t *__restrict__ mstage, uint32_t *__restrict__ tcount,
+    uint32_t *__restrict__ over_list, uint32_t *__restrict__ over_count, int low_bits, int key_bits) {
+  using S = SegCountSmem<K, RANK>;
+  using O = SlotOps<K>;
+  constexpr int ITEMS = S::ITEMS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  S &sm = *reinterpret_cast<S *>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t tile = blockIdx.x;
+  if (osize[tile]) {
+    seg_rle_gathered<K>(tile, bound, osize, ooff, guniq, gheads, H, ustage, mstage, tcount);
+    return;
+  }
+  for (int i = tid; i < S::WARPS * RADIX; i += SEG_BLOCK) (&sm.whist[0][0])[i] = 0;
+  if (RANK == RANK_ATOMIC)
+    for (int i = tid; i < S::WARPS * (RADIX + 1); i += SEG_BLOCK) (&sm.match[0][0])[i] = 0;
+  for (int j = tid; j < S::TBL; j += SEG_BLOCK) {
+    sm.keys[j] = O::empty();
+    sm.vals[j] = 0;
+  }
+  if (tid == 0) sm.overflow = 0;
+  seg_setup<K>(sm, kin, bound, tile, low_bits, key_bits);  // synchronises
+  const uint64_t s = sm.bound[0];
+  const uint32_t cnt = (uint32_t)(sm.bound[1] - s);
+  const K base = sm.base;
+  // count: each key into its slot, LOAD keys per thread at a time
+  for (uint32_t j0 = 0; j0 < cnt; j0 += S::LOAD * SEG_BLOCK) {
+    K d[S::LOAD];
+#pragma unroll
+    for (int i = 0; i < S::LOAD; i++) {
+      const uint32_t j = j0 + (uint32_t)i * SEG_BLOCK + tid;
+      d[i] = j < cnt ? KeyOps<K>::sub(kin[s + j], base) : O::empty();
+    }
+    if (*reinterpret_cast<volatile uint32_t *>(&sm.overflow)) break;
+#pragma unroll
+    for (int i = 0; i < S::LOAD; i++) {
+      if (KeyOps<K>::eq(d[i], O::empty())) continue;
+      uint32_t h = O::hash(d[i]) >> (32 - S::TBITS);
+      bool done = false;
+      for (uint32_t probe = 0; probe < S::PROBES; probe++) {
+        K cur = O::load(&sm.keys[h]);
+        if (KeyOps<K>::eq(cur, O::empty())) cur = O::cas(&sm.keys[h], O::empty(), d[i]);
+        if (KeyOps<K>::eq(cur, O::empty()) || KeyOps<K>::eq(cur, d[i])) {
+          atomicAdd(&sm.vals[h], 1u);
+          done = true;
+          break;
+        }
+        h = (h + 1) & (S::TBL - 1);
+      }
+      if (!done) sm.overflow = 1;
+    }
+  }
+  __syncthreads();
+  if (sm.overflow) {
+    if (tid == 0) over_list[atomicAdd(over_count, 1u)] = tile;
+    return;
+  }
+  // pack the occupied slots to the front in slot order: a slot moves to its
+  // rank among the occupied slots (at most its own index) once every slot
+  // has been read
+  uint32_t D;
+  {
+    K pk[ITEMS];
+    uint32_t pc[ITEMS], pr[ITEMS];
+    bool occ[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const uint32_t j = (uint32_t)i * SEG_BLOCK + tid;
+      pk[i] = sm.keys[j];
+      pc[i] = sm.vals[j];
+      occ[i] = !KeyOps<K>::eq(pk[i], O::empty());
+    }
+    D = tile_flag_ranks<SEG_BLOCK, ITEMS>(occ, pr, sm.cnt);
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      if (occ[i]) {
+        sm.keys[pr[i]] = pk[i];
+        sm.vals[pr[i]] = pc[i];
+      }
+    }
+  }
+  __syncthreads();
+  // sort the D distinct keys (with their counts) by their offset bits
+  if (D > 0) {
+    const int passes = (int)sm.passes;
+    const int ipw = (int)((D + SEG_BLOCK - 1) / SEG_BLOCK);
+    const uint32_t wofs = (uint32_t)warp * 32u * ipw;
+    K key[ITEMS];
+    uint32_t val[ITEMS], rank[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const uint32_t j = wofs + i * 32 + lane;
+      const bool in = i < ipw && j < D;
+      key[i] = in ? sm.keys[j] : KeyOps<K>::zero();
+      val[i] = in ? sm.vals[j] : 0u;
+    }
+    for (int p = 0; p < passes; p++) {
+      if (p > 0) {
+        reload_items<K, true, ITEMS>(sm, key, val, ipw, wofs, D);
+        __syncthreads();
+      }
+      rank_items<K, ITEMS, RANK>(sm, key, rank, ipw, wofs, D, p * RADIX_BITS);
+      digit_positions(sm);
+      scatter_items<K, true, ITEMS>(sm, key, val, rank, ipw);
+    }
+    __syncthreads();
+    for (uint32_t r = tid; r < D; r += SEG_BLOCK) {
+      ustage[s + r] = KeyOps<K>::add(sm.keys[r], base);
+      mstage[s + r] = sm.vals[r];
+    }
+  }
+  if (tid == 0) tcount[tile] = D;
 }
 
 // Moves every tile's distinct keys from its staging range to the dense

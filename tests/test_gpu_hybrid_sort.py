@@ -96,3 +96,38 @@ def test_long_runs_in_first_and_last_tiles(dbg):
     got = check_parity(dbg, ctx, reads, lengths, k)
     assert dbg.dbg_sort_fallbacks(ctx) >= 1
     assert got["e_mult"][0] >= 10_000 and got["e_mult"].max() >= 10_000
+
+
+@pytest.mark.parametrize("k,genome,n_reads,L", [(31, 40_000_000, 6_000, 100), (27, 300_000, 40_000, 90),
+                                                (15, 20_000, 20_000, 40)])
+def test_count_first_equals_sorted_runs(dbg, k, genome, n_reads, L):
+    """Counting each tile's copies in a hash table and sorting the distinct
+    keys gives the edge list of sorting every copy: at coverage ~0.015 (almost
+    every key distinct: every tile overflows its table and is sorted copy by
+    copy), ~12 (some tiles near the table's limit) and ~40 (none)."""
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(genome, n_reads, L, 0.01, k, 600 + k))
+    ctx = dbg.Context()
+    _, counted = gpu_graph(dbg, ctx, reads, lengths, k)
+    over = dbg.dbg_sort_count_overflows(ctx)
+    if n_reads * L * 10 < genome:  # coverage below 0.1
+        assert over > 0
+    if k == 15:
+        assert over == 0
+    dbg.dbg_sort_count_first_set(ctx, False)
+    _, runs = gpu_graph(dbg, ctx, reads, lengths, k)
+    same(counted, runs)
+    assert_graph_equal(counted, oracle.build_graph(reads, lengths, k))
+
+
+def test_count_first_one_key_many_copies(dbg):
+    """3,000 copies of one (k+1)-mer (fewer than a tile holds) among
+    ordinary reads: one hash slot takes every copy."""
+    k = 31
+    rng = np.random.default_rng(9)
+    rep = "".join("ACGT"[c] for c in rng.integers(0, 4, size=k + 1))
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(100_000, 4_000, 100, 0.01, k, 92))
+    reads = np.concatenate([reads, np.frombuffer((rep * 3_000).encode(), dtype=np.uint8)])
+    lengths = np.concatenate([lengths, np.full(3_000, k + 1, dtype=np.uint32)])
+    ctx = dbg.Context()
+    got = check_parity(dbg, ctx, reads, lengths, k)
+    assert got["e_mult"].max() >= 3_000
