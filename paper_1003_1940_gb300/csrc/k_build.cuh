@@ -264,23 +264,49 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict_
                                                      const uint64_t *__restrict__ edge_off, uint64_t n_reads,
                                                      uint32_t k, K *__restrict__ keys, int first, int passes,
                                                      unsigned long long *__restrict__ hist) {
-  // one warp per read: lanes take consecutive positions, so every warp-wide
-  // store writes 32 consecutive keys; the digit histograms of passes
-  // [first, passes) are accumulated on the way
+  // Every warp takes a contiguous, 32-aligned range of the N edge instances
+  // (all reads' keys in order), so lanes stay busy across read ends and
+  // every warp-wide store writes 32 consecutive keys.  A lane follows the
+  // read that holds its key: one binary search per warp, then a step to the
+  // next read when the key passes the current one's end.  The digit
+  // histograms of passes [first, passes) are accumulated on the way.
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK) s_hist[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (EMIT_BLOCK / 32);
+  const uint64_t wid = (uint64_t)blockIdx.x * (EMIT_BLOCK / 32) + (threadIdx.x >> 5);
   const int m = (int)k + 1;
-  for (uint64_t r = (uint64_t)blockIdx.x * (EMIT_BLOCK / 32) + (threadIdx.x >> 5); r < n_reads; r += warps) {
-    const uint64_t e0 = __ldg(edge_off + r), cnt = __ldg(edge_off + r + 1) - e0, p0 = __ldg(base_off + r);
-    for (uint64_t j = lane; j < cnt; j += 32) {
-      const K z = load_window<K>(packed, p0 + j, m);
+  const int G = passes - first;  // histogrammed passes
+  uint32_t *hbase = s_hist + first * RADIX;
+  const uint64_t N = __ldg(edge_off + n_reads);
+  const uint64_t per = ((N + warps - 1) / warps + 31) & ~31ull;
+  const uint64_t a = wid * per, b = min(a + per, N);
+  if (a < b) {
+    // the read holding key a + lane: the last read starting at or before a,
+    // then forward (reads without keys are stepped over)
+    uint64_t r = last_le(edge_off, 0, n_reads, a);
+    uint64_t e_hi = __ldg(edge_off + r + 1), pos = __ldg(base_off + r) - __ldg(edge_off + r);
+    for (uint64_t i = a + lane; i < b; i += 32) {
+      while (i >= e_hi) {
+        r++;
+        const uint64_t e_lo = e_hi;
+        e_hi = __ldg(edge_off + r + 1);
+        pos = __ldg(base_off + r) - e_lo;
+      }
+      const K z = load_window<K>(packed, pos + i, m);
       const K key = kmin(z, revcomp(z, m));
-      keys[e0 + j] = key;
-      for (int ps = first; ps < passes; ps++)
-        atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(key, ps * RADIX_BITS, RADIX_BITS)], 1u);
+      keys[i] = key;
+      if (G <= 4) {
+        // the histogrammed digits are the low bytes of one shifted word
+        const uint32_t w = (uint32_t)KeyOps<K>::words_lo(KeyOps<K>::shr(key, first * RADIX_BITS));
+#pragma unroll
+        for (int g = 0; g < 4; g++)
+          if (g < G) atomicAdd(hbase + g * RADIX + ((w >> (8 * g)) & 0xffu), 1u);
+      } else {
+        for (int ps = first; ps < passes; ps++)
+          atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(key, ps * RADIX_BITS, RADIX_BITS)], 1u);
+      }
     }
   }
   __syncthreads();

@@ -106,6 +106,22 @@ def test_empty_and_short(dbg, ctx):
     assert got["V"] == 1 and got["E"] == 0
 
 
+def test_reads_with_few_keys_mixed(dbg, ctx):
+    """Runs of reads with no (k+1)-mer (empty, shorter than k + 1) between
+    reads with 1, 2, 32, 33 and 170 of them, in blocks longer than a warp:
+    the emit kernel's lanes step over many reads and their ends."""
+    k = 21
+    rng = np.random.default_rng(31)
+    choices = np.array([0, 5, k, k + 1, k + 2, k + 32, k + 33, 191])
+    lengths = []
+    for _ in range(400):
+        run = int(rng.integers(1, 80))
+        lengths += [int(choices[rng.integers(0, len(choices))])] * run
+    lengths = np.array(lengths, dtype=np.uint32)
+    reads = np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, size=int(lengths.sum()))]
+    check_parity(dbg, ctx, reads, lengths, k)
+
+
 def test_device_resident_input(dbg, ctx):
     import torch
     reads, lengths = readgen.generate(readgen.tiny_spec())
