@@ -336,6 +336,17 @@ dbg_status dbg_sort_count_first_set(dbg_ctx *ctx, int on);
 uint64_t dbg_sort_count_overflows(const dbg_ctx *ctx);
 
 /* ----------------------------------------------------------------------
+ * Partition-first switch.  With it on (the default) the first global
+ * radix pass over the edge keys (which carry no payload) is an unordered
+ * partition by that digit: keys of one digit keep no particular order,
+ * which no later step depends on (the later passes are stable and equal
+ * keys are identical), and no tile waits for another.  Off, it is a
+ * stable onesweep pass like the others.  The graph is the same either
+ * way.  Node records, whose payload order matters, always sort stably.
+ * -------------------------------------------------------------------- */
+dbg_status dbg_sort_partition_first_set(dbg_ctx *ctx, int on);
+
+/* ----------------------------------------------------------------------
  * Failure detection.  Every device-side wait of the library (decoupled
  * look-back, TMA completion) spins at most spin_limit times, then records
  * DBG_ETIMEOUT in the context's device error word and returns; the call

@@ -599,6 +599,15 @@ uint64_t dbg_sort_fallbacks(const dbg_ctx *ctx) { return ctx ? ctx->local_sort_f
 
 uint64_t dbg_sort_count_overflows(const dbg_ctx *ctx) { return ctx ? ctx->count_overflow_tiles : 0; }
 
+dbg_status dbg_sort_partition_first_set(dbg_ctx *ctx, int on) {
+  if (!ctx) {
+    set_error("null context");
+    return DBG_EINVAL;
+  }
+  ctx->partition_first = on ? 1 : 0;
+  return DBG_OK;
+}
+
 // cache line format: "<gpu name>|<SMs>" v0 v1 v2 v3
 static std::string tune_cache_key(int device) {
   cudaDeviceProp prop;

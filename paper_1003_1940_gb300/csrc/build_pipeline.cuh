@@ -167,12 +167,20 @@ const SortVariant &chosen_variant(dbg_ctx *ctx) {
   return t[v];
 }
 
+template <class F>
+inline void set_smem_attrs(F kern, size_t smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
 // Ascending LSD radix sort of n keys (with optional u32 payloads) whose
 // significant bits are the low `bits`.  `hist` holds the per-pass digit
 // histograms (passes x 256), already accumulated by the producer kernel.
 // Passes below first_pass are skipped: the keys are then sorted by their
-// bits from 8 * first_pass up (stably).  On return the data is in *keys /
-// *vals (the buffers may have been swapped with *alt_keys / *alt_vals).
+// bits from 8 * first_pass up (stably; for keys without payload, with the
+// partition-first switch on, keys equal in those bits end in no particular
+// order).  On return the data is in *keys / *vals (the buffers may have
+// been swapped with *alt_keys / *alt_vals).
 template <class K, bool HAS_VAL>
 dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uint32_t **alt_vals, uint64_t n,
                       int bits, const unsigned long long *d_hist, uint64_t *d_digit_base, int first_pass = 0) {
@@ -185,7 +193,22 @@ dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uin
   cudaStream_t s = ctx->stream;
   DBG_LAUNCH(ctx, HAS_VAL ? ST_SORT_NODES : ST_SORT_EDGES, 0.0,
              k_digit_base<<<passes, RADIX, 0, s>>>(d_hist, d_digit_base));
-  for (int p = first_pass; p < passes; p++) {
+  int p = first_pass;
+  if (!HAS_VAL && ctx->partition_first && p < passes) {
+    // the first pass of keys without payload as a partition (no look-back)
+    constexpr int tile = PART_BLOCK * PartShape<K>::ITEMS;
+    constexpr size_t smem = sizeof(PartSmem<K>);
+    set_smem_attrs(k_partition<K>, smem);
+    const uint64_t tiles = (n + tile - 1) / tile;
+    const unsigned grid = (unsigned)std::min<uint64_t>(tiles, 3ull * (uint64_t)ctx->num_sms);
+    DBG_LAUNCH(ctx, ST_SORT_EDGES, 2.0 * (double)n * (double)sizeof(K),
+               k_partition<K><<<grid, PART_BLOCK, smem, s>>>(
+                   *keys, *alt_keys, n, p * RADIX_BITS,
+                   reinterpret_cast<unsigned long long *>(d_digit_base + p * RADIX), ctx->spin_limit, ctx->d_err));
+    std::swap(*keys, *alt_keys);
+    p++;
+  }
+  for (; p < passes; p++) {
     uint32_t epoch;
     DBG_TRY(next_epoch(ctx, &epoch));
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), s));
@@ -236,12 +259,6 @@ inline int local_rank_method(dbg_ctx *ctx, bool wide) {
   static const int methods[] = {RANK_MATCH, RANK_ATOMIC, RANK_BALLOT};
   const int v = ctx->sort_variant[wide ? 5 : 4];
   return methods[(v >= 0 && v < 3) ? v : 0];
-}
-
-template <class F>
-inline void set_smem_attrs(F kern, size_t smem) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
 inline unsigned grid_for(uint64_t n, int per_block) {

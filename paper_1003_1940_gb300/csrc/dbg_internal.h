@@ -78,6 +78,7 @@ struct dbg_ctx {
   int sort_variant[6] = {0, 0, 0, 0, 0, 0};
   int hybrid_sort = 1;                 // high digits globally + local sort of group-aligned tiles
   int count_first = 1;                 // local pass of the edge keys counts copies before sorting
+  int partition_first = 1;             // first global pass of keys without payload: unordered partition
   uint64_t count_overflow_tiles = 0;  // count-first tiles whose keys did not fit the hash table
   uint64_t local_sort_fallbacks = 0;   // local sorts that met a group longer than their window
   int num_sms = 0;

@@ -396,6 +396,126 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
 }
 
 // ---------------------------------------------------------------------------
+// First radix pass of keys without payload, as a partition: an LSD sort's
+// first pass need not keep the input order of equal digits (any input order
+// is as good as another), so each key takes its rank among the tile's keys
+// of its digit from a shared-memory atomic add, the tile reserves its part of
+// every digit's bucket with one global atomic add per digit (cursor[d]
+// starts at the bucket's first index), and the keys are staged in shared
+// memory by digit so that each run is written contiguously.  No tile waits
+// for another.  The order within a bucket varies from run to run; the later
+// passes are stable, so the sorted result does not.
+//
+// Persistent CTAs (a few per SM) take tiles t, t + grid, ...; while one
+// tile is ranked and written, the next one arrives in the other buffer by
+// one bulk copy (full tiles from a 16-byte aligned source; the last, partial
+// tile by plain loads).  A tile is staged in its own buffer: its keys are in
+// registers by then.
+// ---------------------------------------------------------------------------
+constexpr int PART_BLOCK = 256;
+template <class K> struct PartShape { static constexpr int ITEMS = 32768 / (PART_BLOCK * (int)sizeof(K)); };
+
+template <class K>
+struct PartSmem {
+  static constexpr int ITEMS = PartShape<K>::ITEMS, TILE = PART_BLOCK * ITEMS;
+  K buf[2][TILE];
+  unsigned long long gbase[RADIX];
+  uint64_t bar[2];
+  uint32_t cnt[RADIX], off[RADIX], tmp[8];
+};
+
+template <class K>
+__global__ __launch_bounds__(PART_BLOCK, 3) void k_partition(const K *__restrict__ in, K *__restrict__ out,
+                                                             uint64_t n, int shift,
+                                                             unsigned long long *__restrict__ cursor,
+                                                             uint32_t spin_limit, uint32_t *__restrict__ err) {
+  using S = PartSmem<K>;
+  constexpr int ITEMS = S::ITEMS, TILE = S::TILE;
+  constexpr uint32_t BYTES = TILE * sizeof(K);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  S &sm = *reinterpret_cast<S *>(smem_raw);
+  const int tid = threadIdx.x;
+  const uint64_t tiles = (n + TILE - 1) / TILE;
+  const bool aligned = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+  auto bulk_ok = [&](uint64_t t) { return aligned && (t + 1) * (uint64_t)TILE <= n; };
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint64_t t = blockIdx.x;
+  if (tid == 0 && t < tiles && bulk_ok(t)) {
+    mbar_expect_tx(&sm.bar[0], BYTES);
+    tma_load_bulk(sm.buf[0], in + t * TILE, BYTES, &sm.bar[0]);
+  }
+  uint32_t phase = 0;  // bit b: parity of buffer b's next completion
+  for (int it = 0; t < tiles; t += gridDim.x, it++) {
+    const int b = it & 1;
+    const uint64_t tn = t + gridDim.x;
+    const bool next_bulk = tn < tiles && bulk_ok(tn);
+    if (tid == 0 && next_bulk) {
+      mbar_expect_tx(&sm.bar[b ^ 1], BYTES);
+      tma_load_bulk(sm.buf[b ^ 1], in + tn * TILE, BYTES, &sm.bar[b ^ 1]);
+    }
+    sm.cnt[tid] = 0;  // PART_BLOCK == RADIX
+    const uint64_t base = t * TILE;
+    const uint32_t tcount = n - base < (uint64_t)TILE ? (uint32_t)(n - base) : (uint32_t)TILE;
+    const bool bulk = bulk_ok(t);
+    if (bulk) {
+      const bool ok = __syncthreads_and(mbar_wait(&sm.bar[b], (phase >> b) & 1u, spin_limit));
+      phase ^= 1u << b;
+      if (!ok) {
+        // give up on this launch; first let the copies in flight land
+        if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+        mbar_wait(&sm.bar[b], (phase >> b) & 1u ^ 1u, spin_limit);
+        if (next_bulk) mbar_wait(&sm.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, spin_limit);
+        return;
+      }
+    } else {
+      __syncthreads();
+    }
+    K key[ITEMS];
+    uint32_t rd[ITEMS];  // rank << 8 | digit
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const uint32_t j = (uint32_t)i * PART_BLOCK + tid;
+      if (j < tcount) {
+        key[i] = bulk ? sm.buf[b][j] : in[base + j];
+        const uint32_t d = KeyOps<K>::digit(key[i], shift, RADIX_BITS);
+        rd[i] = (atomicAdd(&sm.cnt[d], 1u) << 8) | d;
+      }
+    }
+    __syncthreads();
+    const uint32_t c = sm.cnt[tid];
+    sm.off[tid] = block_excl_scan_256(c, sm.tmp);
+    const unsigned long long g = c ? atomicAdd(cursor + tid, (unsigned long long)c) : 0ull;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const uint32_t j = (uint32_t)i * PART_BLOCK + tid;
+      if (j < tcount) sm.buf[b][sm.off[rd[i] & 0xffu] + (rd[i] >> 8)] = key[i];
+    }
+    sm.gbase[tid] = g;
+    __syncthreads();
+    for (uint32_t q = tid; q < tcount; q += PART_BLOCK) {
+      const K k = sm.buf[b][q];
+      const uint32_t d = KeyOps<K>::digit(k, shift, RADIX_BITS);
+      const uint64_t dst = sm.gbase[d] + (q - sm.off[d]);
+      if (dst >= n) {  // only reachable if the digit counts were inconsistent
+        atomicOr(err, ERR_INTERNAL);
+        continue;
+      }
+      out[dst] = k;
+    }
+    // this buffer's next use is a bulk copy (async proxy) after these
+    // generic-proxy accesses
+    fence_proxy_async_smem();
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K3 onesweep radix pass (Adinets & Merrill): one launch per 8-bit digit,
 // one CTA per tile.  Tiles are taken in launch order from an atomic ticket,
 // so every tile a tile waits for belongs to a CTA that is already running.

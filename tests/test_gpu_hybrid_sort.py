@@ -131,3 +131,18 @@ def test_count_first_one_key_many_copies(dbg):
     ctx = dbg.Context()
     got = check_parity(dbg, ctx, reads, lengths, k)
     assert got["e_mult"].max() >= 3_000
+
+
+@pytest.mark.parametrize("k,hybrid", [(21, True), (31, True), (31, False), (55, True), (63, False)])
+def test_partition_first_equals_stable_first_pass(dbg, k, hybrid):
+    """The first global pass of the edge keys as an unordered partition gives
+    the graph of a stable first pass, with the hybrid sort and with every
+    digit sorted globally, for 64- and 128-bit keys."""
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(150_000, 12_000, 120, 0.01, k, 700 + k))
+    ctx = dbg.Context()
+    dbg.dbg_sort_hybrid_set(ctx, hybrid)
+    _, part = gpu_graph(dbg, ctx, reads, lengths, k)
+    dbg.dbg_sort_partition_first_set(ctx, False)
+    _, stable = gpu_graph(dbg, ctx, reads, lengths, k)
+    same(part, stable)
+    assert_graph_equal(part, oracle.build_graph(reads, lengths, k))
