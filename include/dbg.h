@@ -363,7 +363,9 @@ dbg_status dbg_selftest_wait(dbg_ctx *ctx, uint32_t spin_limit);
  * read and write by its definition, not measured traffic).  Stage names:
  * offsets, pack, emit, sort_edges, rle, endpoints, sort_nodes, node_ids,
  * adjacency, copies, compact_links, compact_rank, compact_cycles,
- * compact_output.
+ * compact_output, local_sort_edges, local_sort_nodes, partition_edges
+ * (the edge keys' first global pass when it is a partition; sort_edges
+ * then holds their stable onesweep passes).
  * -------------------------------------------------------------------- */
 typedef struct dbg_stage_stat {
   char name[24];

@@ -102,7 +102,7 @@ dbg_status check_device_error(dbg_ctx *ctx) {
 const char *const kStageNames[ST_COUNT] = {
     "offsets", "pack", "emit", "sort_edges", "rle", "endpoints", "sort_nodes", "node_ids",
     "adjacency", "copies", "compact_links", "compact_rank", "compact_cycles", "compact_output",
-    "local_sort_edges", "local_sort_nodes"};
+    "local_sort_edges", "local_sort_nodes", "partition_edges"};
 
 static cudaEvent_t pool_event(dbg_ctx *ctx) {
   if (!ctx->ev_pool.empty()) {

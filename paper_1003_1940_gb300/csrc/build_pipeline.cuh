@@ -201,7 +201,7 @@ dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uin
     set_smem_attrs(k_partition<K>, smem);
     const uint64_t tiles = (n + tile - 1) / tile;
     const unsigned grid = (unsigned)std::min<uint64_t>(tiles, 3ull * (uint64_t)ctx->num_sms);
-    DBG_LAUNCH(ctx, ST_SORT_EDGES, 2.0 * (double)n * (double)sizeof(K),
+    DBG_LAUNCH(ctx, ST_PARTITION_EDGES, 2.0 * (double)n * (double)sizeof(K),
                k_partition<K><<<grid, PART_BLOCK, smem, s>>>(
                    *keys, *alt_keys, n, p * RADIX_BITS,
                    reinterpret_cast<unsigned long long *>(d_digit_base + p * RADIX), ctx->spin_limit, ctx->d_err));
@@ -505,11 +505,24 @@ dbg_status assign_node_ids(dbg_ctx *ctx, const K *rk, const uint32_t *rv, uint64
     DBG_TRY(alloc_buf(ctx, part, 2 * E_all * 8));
     DBG_TRY(alloc_buf(ctx, fill, 256 * 4));
     DBG_CUDA_TRY(cudaMemsetAsync(fill.p, 0, 256 * 4, s));
-    DBG_LAUNCH(ctx, ST_NODE_IDS, (double)R * (sizeof(K) + 4) + (double)nv * (sizeof(K) + 8) + (double)ne * 13,
-               k_write_nodes<K, true><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
-                   rk, rv, R, ho.as<uint64_t>(), eo.as<uint64_t>(), node_keys, row_ptr, g->src.as<uint32_t>(),
-                   g->dst.as<uint32_t>(), g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), base_v, base_slot,
-                   part.as<uint64_t>(), fill.as<uint32_t>(), bshift));
+    const double wbytes = (double)R * (sizeof(K) + 4) + (double)nv * (sizeof(K) + 8) + (double)ne * 13;
+    if constexpr (sizeof(K) == 8) {
+      // persistent CTAs, two per SM, with the next tile's records in flight
+      constexpr size_t smem = sizeof(WriteNodesSmem<K>);
+      set_smem_attrs(k_write_nodes_p<K, true>, smem);
+      const unsigned grid = (unsigned)std::min<uint64_t>(tiles, 2ull * (uint64_t)ctx->num_sms);
+      DBG_LAUNCH(ctx, ST_NODE_IDS, wbytes,
+                 k_write_nodes_p<K, true><<<grid, SCAN_BLOCK, smem, s>>>(
+                     rk, rv, R, ho.as<uint64_t>(), eo.as<uint64_t>(), node_keys, row_ptr, g->src.as<uint32_t>(),
+                     g->dst.as<uint32_t>(), g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), base_v,
+                     base_slot, part.as<uint64_t>(), fill.as<uint32_t>(), bshift, ctx->spin_limit, ctx->d_err));
+    } else {
+      DBG_LAUNCH(ctx, ST_NODE_IDS, wbytes,
+                 k_write_nodes<K, true><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
+                     rk, rv, R, ho.as<uint64_t>(), eo.as<uint64_t>(), node_keys, row_ptr, g->src.as<uint32_t>(),
+                     g->dst.as<uint32_t>(), g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), base_v,
+                     base_slot, part.as<uint64_t>(), fill.as<uint32_t>(), bshift));
+    }
     DBG_LAUNCH(ctx, ST_NODE_IDS, 2.0 * E_all * (8 + 4),
                k_scatter_ends<<<grid_for(2 * E_all, 256 * 16), 256, 0, s>>>(part.as<uint64_t>(), 2 * E_all,
                                                                           g->src.as<uint32_t>(),

@@ -53,7 +53,7 @@ struct DevBuf {
 enum Stage {
   ST_OFFSETS, ST_PACK, ST_EMIT, ST_SORT_EDGES, ST_RLE, ST_ENDPOINTS, ST_SORT_NODES, ST_NODE_IDS,
   ST_ADJACENCY, ST_COPIES, ST_COMPACT_LINKS, ST_COMPACT_RANK, ST_COMPACT_CYCLES, ST_COMPACT_OUTPUT,
-  ST_LOCAL_SORT_EDGES, ST_LOCAL_SORT_NODES, ST_COUNT
+  ST_LOCAL_SORT_EDGES, ST_LOCAL_SORT_NODES, ST_PARTITION_EDGES, ST_COUNT
 };
 extern const char *const kStageNames[ST_COUNT];
 

@@ -1381,6 +1381,136 @@ __global__ __launch_bounds__(SCAN_BLOCK, 2) void k_write_nodes(
   }
 }
 
+// The same writing pass with persistent CTAs (two per SM) over the tiles t,
+// t + grid, ...: while one tile is flagged, ranked and written, the next
+// tile's records arrive by bulk copy in the other buffer (full tiles of
+// 16-byte aligned arrays; the last tile by plain loads into the buffer).
+template <class K>
+struct WriteNodesSmem {
+  static constexpr int WARPS = SCAN_BLOCK / 32;
+  K keys[2][RS_TILE];
+  uint32_t vals[2][RS_TILE];
+  uint32_t cnt_h[RS_ITEMS * WARPS + 1], cnt_e[RS_ITEMS * WARPS + 1];
+  uint32_t bcnt[256], bbase[256];
+  uint64_t bar[2];
+};
+
+template <class K, bool PART>
+__global__ __launch_bounds__(SCAN_BLOCK, 2) void k_write_nodes_p(
+    const K *__restrict__ rkeys, const uint32_t *__restrict__ rvals, uint64_t R, const uint64_t *__restrict__ hoff,
+    const uint64_t *__restrict__ eoff, K *__restrict__ node_keys, uint64_t *__restrict__ row_ptr,
+    uint32_t *__restrict__ src, uint32_t *__restrict__ dst, uint32_t *__restrict__ adj_edge,
+    uint8_t *__restrict__ adj_role, uint32_t base_v, uint64_t base_slot, uint64_t *__restrict__ ends,
+    uint32_t *__restrict__ bucket_fill, int bshift, uint32_t spin_limit, uint32_t *__restrict__ err) {
+  using S = WriteNodesSmem<K>;
+  constexpr uint32_t KB = RS_TILE * sizeof(K), VB = RS_TILE * sizeof(uint32_t);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  S &sm = *reinterpret_cast<S *>(smem_raw);
+  const int tid = threadIdx.x;
+  const uint64_t tiles = (R + RS_TILE - 1) / RS_TILE;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(rkeys) | reinterpret_cast<uintptr_t>(rvals)) & 15) == 0;
+  auto bulk_ok = [&](uint64_t t) { return aligned && (t + 1) * (uint64_t)RS_TILE <= R; };
+  auto issue = [&](uint64_t t, int b) {
+    mbar_expect_tx(&sm.bar[b], KB + VB);
+    tma_load_bulk(sm.keys[b], rkeys + t * RS_TILE, KB, &sm.bar[b]);
+    tma_load_bulk(sm.vals[b], rvals + t * RS_TILE, VB, &sm.bar[b]);
+  };
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint64_t t = blockIdx.x;
+  if (tid == 0 && t < tiles && bulk_ok(t)) issue(t, 0);
+  uint32_t phase = 0;  // bit b: parity of buffer b's next completion
+  for (int it = 0; t < tiles; t += gridDim.x, it++) {
+    const int b = it & 1;
+    const uint64_t tn = t + gridDim.x;
+    const bool next_bulk = tn < tiles && bulk_ok(tn);
+    if (tid == 0 && next_bulk) issue(tn, b ^ 1);
+    if (PART) sm.bcnt[tid] = 0;  // SCAN_BLOCK == 256 buckets at most
+    const uint64_t base = t * RS_TILE;
+    const uint32_t tcount = R - base < (uint64_t)RS_TILE ? (uint32_t)(R - base) : (uint32_t)RS_TILE;
+    if (bulk_ok(t)) {
+      const bool ok = __syncthreads_and(mbar_wait(&sm.bar[b], (phase >> b) & 1u, spin_limit));
+      phase ^= 1u << b;
+      if (!ok) {
+        // give up on this launch; first let the copies in flight land
+        if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+        mbar_wait(&sm.bar[b], ((phase >> b) & 1u) ^ 1u, spin_limit);
+        if (next_bulk) mbar_wait(&sm.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, spin_limit);
+        return;
+      }
+    } else {
+      for (uint32_t j = tid; j < tcount; j += SCAN_BLOCK) {
+        sm.keys[b][j] = rkeys[base + j];
+        sm.vals[b][j] = rvals[base + j];
+      }
+      __syncthreads();
+    }
+    uint32_t val[RS_ITEMS];
+    bool head[RS_ITEMS], end[RS_ITEMS];
+    uint32_t rh[RS_ITEMS], re[RS_ITEMS];
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) {
+      const uint32_t j = (uint32_t)i * SCAN_BLOCK + tid;
+      const bool in = j < tcount;
+      val[i] = in ? sm.vals[b][j] : REC_NONE;
+      bool h = false;
+      if (in) {
+        const K k = sm.keys[b][j];
+        if (j > 0) h = !KeyOps<K>::eq(k, sm.keys[b][j - 1]);
+        else h = base == 0 || !KeyOps<K>::eq(k, rkeys[base - 1]);
+      }
+      head[i] = h;
+      end[i] = val[i] != REC_NONE;
+    }
+    tile_flag_ranks<SCAN_BLOCK, RS_ITEMS>(head, rh, sm.cnt_h);
+    tile_flag_ranks<SCAN_BLOCK, RS_ITEMS>(end, re, sm.cnt_e);
+    const uint64_t xh = hoff[t], xe = eoff[t];
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) {
+      const uint32_t j = (uint32_t)i * SCAN_BLOCK + tid;
+      if (j >= tcount) continue;
+      const uint64_t id = xh + rh[i] + (head[i] ? 1u : 0u) - 1u;
+      const uint64_t slot = xe + re[i];
+      if (head[i]) {
+        node_keys[id] = sm.keys[b][j];
+        row_ptr[id] = base_slot + slot;
+      }
+      if (end[i]) {
+        const uint32_t e = val[i] >> 1, role = val[i] & 1u;
+        adj_edge[base_slot + slot] = e;
+        adj_role[base_slot + slot] = (uint8_t)role;
+        if (PART) {
+          rh[i] = (uint32_t)id;                             // keep the node ID
+          re[i] = atomicAdd(&sm.bcnt[e >> bshift], 1u);  // rank within the tile's part of the bucket
+        } else {
+          (role ? dst : src)[e] = base_v + (uint32_t)id;
+        }
+      }
+    }
+    if (t == tiles - 1 && tid == 0) row_ptr[hoff[tiles]] = base_slot + eoff[tiles];
+    if (PART) {
+      __syncthreads();
+      if (sm.bcnt[tid]) sm.bbase[tid] = atomicAdd(bucket_fill + tid, sm.bcnt[tid]);
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < RS_ITEMS; i++) {
+        const uint32_t j = (uint32_t)i * SCAN_BLOCK + tid;
+        if (j >= tcount || !end[i]) continue;
+        const uint32_t bk = (val[i] >> 1) >> bshift;
+        ends[((uint64_t)bk << (bshift + 1)) + sm.bbase[bk] + re[i]] = ((uint64_t)val[i] << 32) | (base_v + rh[i]);
+      }
+    }
+    // this buffer's next use is a bulk copy (async proxy) after these
+    // generic-proxy accesses
+    fence_proxy_async_smem();
+    __syncthreads();
+  }
+}
+
 // src[e] / dst[e] from the partitioned edge ends, swept in order so that the
 // part of src / dst being written stays in L2.
 static __global__ void k_scatter_ends(const uint64_t *__restrict__ ends, uint64_t n, uint32_t *__restrict__ src,
