@@ -969,12 +969,30 @@ __global__ void k_isolated(const uint64_t *__restrict__ packed, const uint64_t *
 
 
 // K7 neighbour of every adjacency slot: the edge's other end.
+// (Eight slots per thread at a time: their edge words, then their
+// gathers, then their stores.)
 static __global__ void k_adj_nbr(const uint32_t *__restrict__ adj_edge, const uint8_t *__restrict__ adj_role,
                           const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst, uint64_t n,
                           uint32_t *__restrict__ nbr) {
-  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t e = adj_edge[p];
-    nbr[p] = adj_role[p] ? __ldg(src + e) : __ldg(dst + e);
+  constexpr int U = 8;
+  const uint64_t step = (uint64_t)blockDim.x * U;
+  for (uint64_t p0 = (uint64_t)blockIdx.x * step + threadIdx.x; p0 < n; p0 += (uint64_t)gridDim.x * step) {
+    uint32_t e[U], v[U];
+    uint8_t r[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const uint64_t p = p0 + (uint64_t)u * blockDim.x;
+      e[u] = p < n ? adj_edge[p] : 0u;
+      r[u] = p < n ? adj_role[p] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      v[u] = p0 + (uint64_t)u * blockDim.x < n ? (r[u] ? __ldg(src + e[u]) : __ldg(dst + e[u])) : 0u;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const uint64_t p = p0 + (uint64_t)u * blockDim.x;
+      if (p < n) nbr[p] = v[u];
+    }
   }
 }
 
@@ -1513,12 +1531,26 @@ __global__ __launch_bounds__(SCAN_BLOCK, 2) void k_write_nodes_p(
 
 // src[e] / dst[e] from the partitioned edge ends, swept in order so that the
 // part of src / dst being written stays in L2.
+// Each thread loads STREAM_U entries before it stores any, so that many
+// loads are in flight.
+constexpr int STREAM_U = 8;
+
 static __global__ void k_scatter_ends(const uint64_t *__restrict__ ends, uint64_t n, uint32_t *__restrict__ src,
                                       uint32_t *__restrict__ dst) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t w = ends[i];
-    const uint32_t v = (uint32_t)(w >> 32);
-    ((v & 1u) ? dst : src)[v >> 1] = (uint32_t)w;
+  const uint64_t step = (uint64_t)blockDim.x * STREAM_U;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * step + threadIdx.x; i0 < n; i0 += (uint64_t)gridDim.x * step) {
+    uint64_t w[STREAM_U];
+#pragma unroll
+    for (int u = 0; u < STREAM_U; u++) {
+      const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+      w[u] = i < n ? ends[i] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < STREAM_U; u++) {
+      if (i0 + (uint64_t)u * blockDim.x >= n) break;
+      const uint32_t v = (uint32_t)(w[u] >> 32);
+      ((v & 1u) ? dst : src)[v >> 1] = (uint32_t)w[u];
+    }
   }
 }
 
