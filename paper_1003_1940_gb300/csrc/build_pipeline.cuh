@@ -47,6 +47,22 @@ void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *
                                                       epoch, ctx->spin_limit, ctx->d_err);
 }
 
+template <class K, bool V, int BLOCK, int ITEMS, int RANK, int MINB, int LB>
+void launch_onesweep_p(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *vin, uint32_t *vout, uint64_t n,
+                       int shift, const uint64_t *digit_base, uint32_t epoch) {
+  auto kern = k_onesweep_p<K, V, BLOCK, ITEMS, RANK, MINB, LB>;
+  constexpr size_t smem = sizeof(OnesweepPSmem<K, V, BLOCK, ITEMS>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  const uint64_t tiles = (n + BLOCK * ITEMS - 1) / (BLOCK * ITEMS);
+  const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)MINB * (uint64_t)ctx->num_sms);
+  kern<<<grid, BLOCK, smem, ctx->stream>>>(static_cast<const K *>(kin), static_cast<K *>(kout), vin, vout, n, shift,
+                                           digit_base, ctx->d_status, ctx->d_counters, epoch, ctx->spin_limit,
+                                           ctx->d_err);
+}
+
+#define DBG_SVP(K, V, B, I, R, M, L, NAME) \
+  SortVariant { NAME, (B) * (I), &launch_onesweep_p<K, V, B, I, R, M, L> }
 #define DBG_SV(K, V, B, I, R, T, M, NAME) \
   SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, false> }
 #define DBG_SVE(K, V, B, I, R, T, M, NAME) \
@@ -91,6 +107,10 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SVL(uint64_t, false, 256, 16, RANK_ATOMIC, true, 2, false, 4, "256x16 atomic tma occ2 lb4"),
         DBG_SVL(uint64_t, false, 256, 8, RANK_ATOMIC, true, 4, false, 4, "256x8 atomic tma occ4 lb4"),
         DBG_SVL(uint64_t, false, 256, 10, RANK_ATOMIC, true, 3, false, 8, "256x10 atomic tma occ3 lb8"),
+        DBG_SVP(uint64_t, false, 256, 12, RANK_ATOMIC, 3, 4, "256x12 atomic persistent occ3 lb4"),
+        DBG_SVP(uint64_t, false, 256, 12, RANK_ATOMIC, 3, 8, "256x12 atomic persistent occ3 lb8"),
+        DBG_SVP(uint64_t, false, 256, 8, RANK_ATOMIC, 4, 4, "256x8 atomic persistent occ4 lb4"),
+        DBG_SVP(uint64_t, false, 256, 12, RANK_MATCH, 3, 4, "256x12 match persistent occ3 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -114,6 +134,9 @@ template <> struct SortKind<uint64_t, true> {
         DBG_SVL(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, false, 4, "256x10 atomic tma occ3 lb4"),
         DBG_SVL(uint64_t, true, 256, 10, RANK_ATOMIC, true, 3, false, 8, "256x10 atomic tma occ3 lb8"),
         DBG_SVL(uint64_t, true, 256, 8, RANK_ATOMIC, true, 3, false, 8, "256x8 atomic tma occ3 lb8"),
+        DBG_SVP(uint64_t, true, 256, 8, RANK_ATOMIC, 3, 4, "256x8 atomic persistent occ3 lb4"),
+        DBG_SVP(uint64_t, true, 256, 10, RANK_ATOMIC, 2, 4, "256x10 atomic persistent occ2 lb4"),
+        DBG_SVP(uint64_t, true, 256, 6, RANK_ATOMIC, 4, 4, "256x6 atomic persistent occ4 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;

@@ -743,6 +743,186 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
 }
 
 // ---------------------------------------------------------------------------
+// K3 onesweep pass, persistent form: MIN_BLOCKS CTAs per SM each loop over
+// tiles taken from the atomic ticket.  Once a tile's inclusive prefix is
+// published, the CTA takes its next ticket and starts that tile's bulk copy
+// into its other buffer, so the copy lands while the current tile is staged
+// (in its own buffer: its keys are in registers by then) and written.  A
+// ticket is taken only by a CTA that holds no unpublished tile, so every
+// look-back ends.  Ranking and look-back are those of k_onesweep.
+// ---------------------------------------------------------------------------
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS>
+struct OnesweepPSmem {
+  static constexpr int WARPS = BLOCK / 32;
+  static constexpr int TILE = BLOCK * ITEMS;
+  K keys[2][TILE];
+  uint32_t vals[2][HAS_VAL ? TILE : 1];
+  uint32_t whist[WARPS][RADIX];
+  uint32_t match[WARPS][RADIX + 1];
+  uint64_t gbase[RADIX];
+  uint64_t bar[2];
+  uint32_t tmp[8];
+  uint32_t tnext;
+};
+
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, int MIN_BLOCKS, int LB>
+__global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
+    const K *__restrict__ kin, K *__restrict__ kout, const uint32_t *__restrict__ vin, uint32_t *__restrict__ vout,
+    uint64_t n, int shift, const uint64_t *__restrict__ digit_base, uint64_t *__restrict__ status,
+    uint32_t *ticket, uint32_t epoch, uint32_t spin_limit, uint32_t *err) {
+  using S = OnesweepPSmem<K, HAS_VAL, BLOCK, ITEMS>;
+  constexpr int WARPS = S::WARPS;
+  constexpr int TILE = S::TILE;
+  constexpr uint32_t KB = TILE * sizeof(K), VB = HAS_VAL ? TILE * sizeof(uint32_t) : 0;
+  static_assert(BLOCK >= RADIX, "one thread per digit");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  S &sm = *reinterpret_cast<S *>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t tiles = (n + TILE - 1) / TILE;
+  const bool aligned =
+      ((reinterpret_cast<uintptr_t>(kin) | (HAS_VAL ? reinterpret_cast<uintptr_t>(vin) : 0)) & 15) == 0;
+  auto bulk_ok = [&](uint64_t t) { return aligned && (t + 1) * (uint64_t)TILE <= n; };
+  auto issue = [&](uint64_t t, int b) {
+    mbar_expect_tx(&sm.bar[b], KB + VB);
+    tma_load_bulk(sm.keys[b], kin + t * TILE, KB, &sm.bar[b]);
+    if (HAS_VAL) tma_load_bulk(sm.vals[b], vin + t * TILE, VB, &sm.bar[b]);
+  };
+  if (RANK == RANK_ATOMIC)
+    for (int i = tid; i < WARPS * (RADIX + 1); i += BLOCK) (&sm.match[0][0])[i] = 0;
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_init_fence();
+    const uint32_t t0 = atomicAdd(ticket, 1u);
+    sm.tnext = t0;
+    if (t0 < tiles && bulk_ok(t0)) issue(t0, 0);
+  }
+  __syncthreads();
+  uint32_t tile = sm.tnext;
+  uint32_t phase = 0;  // bit b: parity of buffer b's next completion
+  for (int it = 0; tile < tiles; it++) {
+    const int b = it & 1;
+    for (int i = tid; i < WARPS * RADIX; i += BLOCK) (&sm.whist[0][0])[i] = 0;
+    const uint64_t base = (uint64_t)tile * TILE;
+    const uint32_t tile_n = n - base < (uint64_t)TILE ? (uint32_t)(n - base) : (uint32_t)TILE;
+    const bool bulk = bulk_ok(tile);
+    if (bulk) {
+      const bool ok = __syncthreads_and(mbar_wait(&sm.bar[b], (phase >> b) & 1u, spin_limit));
+      phase ^= 1u << b;
+      if (!ok) {
+        // give up on this launch; first let the copies in flight land
+        if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+        mbar_wait(&sm.bar[b], ((phase >> b) & 1u) ^ 1u, spin_limit);
+        return;
+      }
+    } else {
+      __syncthreads();
+    }
+    const int wofs = warp * 32 * ITEMS;
+    K key[ITEMS];
+    uint32_t val[ITEMS];
+    uint32_t rank[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const uint32_t li = wofs + i * 32 + lane;
+      if (bulk) {
+        key[i] = sm.keys[b][li];
+        if (HAS_VAL) val[i] = sm.vals[b][li];
+      } else if (li < tile_n) {
+        key[i] = kin[base + li];
+        if (HAS_VAL) val[i] = vin[base + li];
+      } else {
+        key[i] = KeyOps<K>::zero();
+        val[i] = 0;
+      }
+    }
+    const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const bool valid = (uint32_t)(wofs + i * 32 + lane) < tile_n;
+      const uint32_t d = valid ? KeyOps<K>::digit(key[i], shift, RADIX_BITS) : (uint32_t)RADIX;
+      unsigned peers;
+      if (RANK == RANK_MATCH) {
+        peers = __match_any_sync(0xffffffffu, d);
+      } else {
+        atomicOr(&sm.match[warp][d], 1u << lane);
+        __syncwarp();
+        peers = sm.match[warp][d];
+        __syncwarp();
+        if (lane == __ffs(peers) - 1) sm.match[warp][d] = 0;
+      }
+      const int leader = __ffs(peers) - 1;
+      uint32_t before = 0;
+      if (lane == leader && valid) {
+        before = sm.whist[warp][d];
+        sm.whist[warp][d] = before + __popc(peers);
+      }
+      before = __shfl_sync(0xffffffffu, before, leader);
+      rank[i] = ((before + __popc(peers & lt_mask)) << 9) | d;
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t cnt = 0;
+    if (tid < RADIX) {
+#pragma unroll
+      for (int w = 0; w < WARPS; w++) cnt += sm.whist[w][tid];
+      st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE, cnt));
+    }
+    const uint32_t tstart = block_excl_scan_256(cnt, sm.tmp);
+    if (tid < RADIX) {
+      uint32_t run = tstart;
+#pragma unroll
+      for (int w = 0; w < WARPS; w++) {
+        const uint32_t c = sm.whist[w][tid];
+        sm.whist[w][tid] = run;
+        run += c;
+      }
+      uint32_t excl = 0;
+      if (tile > 0) {
+        excl = LB > 1 ? lookback_exclusive_batched<LB>(status + tid, RADIX, tile, epoch, spin_limit, err)
+                      : lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
+        st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, LB_INCLUSIVE, excl + cnt));
+      }
+      sm.gbase[tid] = digit_base[tid] + excl - tstart;
+    }
+    __syncthreads();
+    // this tile's prefix is published: take the next ticket and start its
+    // copy, which lands while this tile is staged and written
+    if (tid == 0) {
+      const uint32_t tn = atomicAdd(ticket, 1u);
+      sm.tnext = tn;
+      if (tn < tiles && bulk_ok(tn)) issue(tn, b ^ 1);
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const uint32_t d = rank[i] & 0x1ffu;
+      if (d < RADIX) {
+        const uint32_t q = sm.whist[warp][d] + (rank[i] >> 9);
+        sm.keys[b][q] = key[i];
+        if (HAS_VAL) sm.vals[b][q] = val[i];
+      }
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j < tile_n; j += BLOCK) {
+      const K kk = sm.keys[b][j];
+      const uint32_t d = KeyOps<K>::digit(kk, shift, RADIX_BITS);
+      const uint64_t dst = sm.gbase[d] + j;
+      if (dst >= n) {  // only reachable if the digit counts were inconsistent
+        atomicOr(err, ERR_INTERNAL);
+        continue;
+      }
+      kout[dst] = kk;
+      if (HAS_VAL) vout[dst] = sm.vals[b][j];
+    }
+    // this buffer's next use is a bulk copy (async proxy) after these
+    // generic-proxy accesses
+    fence_proxy_async_smem();
+    __syncthreads();
+    tile = sm.tnext;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K4 run-length reduce (STEP-2): unique keys of the sorted array and the
 // index of the first element of each run, by a single pass with look-back.
 // The last tile writes headpos[E] = n and E itself to *total.
