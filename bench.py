@@ -151,10 +151,47 @@ def measured_traffic(workload_name, scale, variant):
     text = open(src).read()
     section = text[text.index("// K3 onesweep radix pass"):text.index("// K4 run-length reduce")]
     digest = hashlib.sha256(section.encode()).hexdigest()[:16]
-    if (fields.get("source_sha256_16") != digest or fields.get("workload") != workload_name
-            or fields.get("variant") != variant):
+    if fields.get("source_sha256_16") != digest or fields.get("workload") != workload_name:
         return None
-    return float(fields["bytes_per_launch"])
+    # one captured figure per variant: "bytes_per_launch <variant name>: <bytes>"
+    got = fields.get(f"bytes_per_launch {variant}")
+    return float(got) if got else None
+
+
+def parse_cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        lo, _, hi = part.partition("-")
+        cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
+def bind_near_gpu(device):
+    """Runs this process on the host cores local to the GPU (those of them it
+    may use), so that the pinned host buffers of the end-to-end step are
+    allocated on the GPU's NUMA node; reports what it found and did."""
+    import torch
+    info = {"bound": False}
+    try:
+        p = torch.cuda.get_device_properties(device)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        base = f"/sys/bus/pci/devices/{bus}"
+        info["gpu_pci"] = bus
+        info["gpu_numa_node"] = int(open(f"{base}/numa_node").read())
+        local = parse_cpulist(open(f"{base}/local_cpulist").read())
+        allowed = set(os.sched_getaffinity(0))
+        both = local & allowed
+        info["allowed_cpus"] = len(allowed)
+        info["gpu_local_allowed_cpus"] = len(both)
+        if both and both != allowed:
+            os.sched_setaffinity(0, both)
+            info["bound"] = True
+            info["_restore"] = sorted(allowed)
+    except (OSError, ValueError, AttributeError) as e:
+        info["error"] = type(e).__name__
+    return info
 
 
 def dist_setup(args):
@@ -242,7 +279,7 @@ def oracle_parallel_rate(reads, lengths, k, m):
     import tempfile
     import oracle
     oracle.build()
-    parts = os.cpu_count() or 1
+    parts = len(os.sched_getaffinity(0)) or 1
     nb = int(lengths[:m].astype(np.int64).sum())
     with tempfile.TemporaryDirectory() as d:
         rp, lp = os.path.join(d, "reads.npy"), os.path.join(d, "lengths.npy")
@@ -319,6 +356,7 @@ def run_ours(args):
     import torch
     ws, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
+    host = bind_near_gpu(local)
     from paper_1003_1940_gb300 import build_lib, dbg
     build_lib.build()
     dbg.load()
@@ -387,7 +425,8 @@ def run_ours(args):
     pass_ms = srt["ms"] / max(1, srt["launches"] - args.steps) if n_pass > 0 else 0.0
     pass_bytes = srt["bytes"] / max(1, n_pass)
     achieved = pass_bytes / (pass_ms / 1000.0) / 1e9 if pass_ms > 0 else 0.0
-    traffic = measured_traffic(args.workload, args.scale, variants.get(0))
+    ekind = 0 if k <= 31 else 2  # sort kind of the edge keys: 64- or 128-bit
+    traffic = measured_traffic(args.workload, args.scale, variants.get(ekind))
 
     stages = {name: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
@@ -405,10 +444,11 @@ def run_ours(args):
 
         def step_host():
             g = dbg.dbg_build(ctx, h_reads, h_len, k)
-            u = dbg.dbg_compact(ctx, g)
             e = dbg.dbg_graph_num_edges(g)
-            dbg._check(dbg._lib.dbg_graph_edges(g.handle, None, None, None, None,
-                                                h_mult.data_ptr() if e else None), "dbg_graph_edges")
+            # the multiplicities come back while the graph is compacted
+            dbg.dbg_graph_edges_async(g, mult=h_mult.data_ptr() if e else None)
+            u = dbg.dbg_compact(ctx, g)
+            dbg.dbg_graph_wait(g)
             out_bytes["d2h"] = 4 * e
             u.free()
             g.free()
@@ -426,10 +466,13 @@ def run_ours(args):
                "d2h_bytes_per_step": int(out_bytes.get("d2h", 0))}
 
     cpu = None
+    if host.get("bound"):  # the host baselines use every core the process may use
+        os.sched_setaffinity(0, host.pop("_restore"))
+    host.pop("_restore", None)
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt, m, edges = oracle_sample_rate(reads, lengths, k, args.cpu_seconds)
         # the parallel run scans more reads, about as long as the 1-core run
-        m_par = int(min(len(lengths), m * max(1, (os.cpu_count() or 1) // 2)))
+        m_par = int(min(len(lengths), m * max(1, len(os.sched_getaffinity(0)) // 2)))
         prate, pdt, parts = oracle_parallel_rate(reads, lengths, k, m_par)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {m} reads ({edges} edge instances) of the same workload, build+compact, "
@@ -458,7 +501,10 @@ def run_ours(args):
                        "sort_variants": variants, "count_first": bool(args.count_first),
                        "partition_first": bool(args.partition_first),
                        "autotune_pass_ms": {kd: [round(x, 4) for x in v] for kd, v in tune_ms.items()}},
-            "roofline": {"bound": "hbm", "kernel": "k_onesweep (edge keys, one 8-bit digit pass)",
+            "roofline": {"bound": "hbm",
+                         "kernel": f"{'k_onesweep_p' if 'persistent' in (variants.get(ekind) or '') else 'k_onesweep'}"
+                                   f" ({variants.get(ekind)}; {'64' if ekind == 0 else '128'}-bit edge keys,"
+                                   f" one stable 8-bit digit pass)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": pass_bytes,
@@ -473,6 +519,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": e2e,
+            "host": host,
             "cpu_baseline": cpu,
         }))
     if ws > 1:

@@ -134,6 +134,18 @@ dbg_status dbg_graph_nodes(const dbg_graph *g, uint64_t *keys);
 dbg_status dbg_graph_edges(const dbg_graph *g, uint64_t *keys, uint32_t *src, uint32_t *dst,
                            uint8_t *orient, uint32_t *mult);
 
+/* The same copies, started on a stream of the graph's own and returned from
+ * at once, so that they overlap later work on the GPU (e.g. dbg_compact of
+ * the same graph, which only reads it).  Host buffers should be pinned for
+ * the copies to run asynchronously; they must stay valid, and be left
+ * unread, until dbg_graph_wait returns.  dbg_graph_wait blocks until every
+ * copy started on the graph is done (DBG_OK at once if none was);
+ * dbg_graph_free waits for them too.  Errors of the copies are reported by
+ * the call that starts them or by dbg_graph_wait. */
+dbg_status dbg_graph_edges_async(dbg_graph *g, uint64_t *keys, uint32_t *src, uint32_t *dst,
+                                 uint8_t *orient, uint32_t *mult);
+dbg_status dbg_graph_wait(dbg_graph *g);
+
 /* Adjacency (STEP-4) in CSR form: row_ptr has num_nodes + 1 entries; entry
  * p of a row holds the neighbour node ID, the edge ID and the role (0: the
  * row's node is the edge's src end, 1: its dst end).  A self-loop appears

@@ -499,6 +499,34 @@ dbg_status dbg_graph_edges(const dbg_graph *g, uint64_t *keys, uint32_t *src, ui
   return DBG_OK;
 }
 
+dbg_status dbg_graph_edges_async(dbg_graph *g, uint64_t *keys, uint32_t *src, uint32_t *dst, uint8_t *orient,
+                                 uint32_t *mult) {
+  if (!g) return DBG_EINVAL;
+  DeviceScope scope(g->device);
+  if (!g->copy_stream) DBG_CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+  const uint64_t E = g->num_edges;
+  const struct {
+    void *dst;
+    const void *src;
+    size_t bytes;
+  } parts[] = {{keys, g->edge_keys.p, E * g->key_words * sizeof(uint64_t)},
+               {src, g->src.p, E * sizeof(uint32_t)},
+               {dst, g->dst.p, E * sizeof(uint32_t)},
+               {orient, g->orient.p, E},
+               {mult, g->mult.p, E * sizeof(uint32_t)}};
+  for (const auto &c : parts)
+    if (c.dst && c.bytes) DBG_CUDA_TRY(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, g->copy_stream));
+  return DBG_OK;
+}
+
+dbg_status dbg_graph_wait(dbg_graph *g) {
+  if (!g) return DBG_EINVAL;
+  if (!g->copy_stream) return DBG_OK;
+  DeviceScope scope(g->device);
+  DBG_CUDA_TRY(cudaStreamSynchronize(g->copy_stream));
+  return DBG_OK;
+}
+
 dbg_status dbg_graph_csr(const dbg_graph *g, uint64_t *row_ptr, uint32_t *nbr, uint32_t *edge, uint8_t *role) {
   if (!g) return DBG_EINVAL;
   const uint64_t A = 2 * g->num_edges;
@@ -532,6 +560,10 @@ dbg_status dbg_graph_device_view(const dbg_graph *g, dbg_graph_view *v) {
 void dbg_graph_free(dbg_graph *g) {
   if (!g) return;
   DeviceScope scope(g->device);
+  if (g->copy_stream) {  // read-backs in flight finish before the arrays go
+    cudaStreamSynchronize(g->copy_stream);
+    cudaStreamDestroy(g->copy_stream);
+  }
   delete g;  // DevBuf destructors release in stream order
 }
 

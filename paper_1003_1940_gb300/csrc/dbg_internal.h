@@ -106,6 +106,7 @@ struct dbg_graph {
   int device = 0;
   uint32_t edge_buckets = 1, node_buckets = 1;  // key ranges used (bucket path)
   dbg::DevBuf node_keys, edge_keys, src, dst, orient, mult, row_ptr, adj_nbr, adj_edge, adj_role;
+  cudaStream_t copy_stream = nullptr;  // read-backs started by dbg_graph_edges_async
 };
 
 struct dbg_unitigs {

@@ -70,6 +70,8 @@ _SIGNATURES = [
     ("dbg_graph_num_instances", ctypes.c_uint64, [_P]),
     ("dbg_graph_nodes", ctypes.c_int, [_P, _P]),
     ("dbg_graph_edges", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("dbg_graph_edges_async", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("dbg_graph_wait", ctypes.c_int, [_P]),
     ("dbg_graph_csr", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("dbg_graph_device_view", ctypes.c_int, [_P, _P]),
     ("dbg_graph_free", None, [_P]),
@@ -295,6 +297,19 @@ def dbg_graph_edges(g: Graph) -> dict:
     _check(_lib.dbg_graph_edges(g.handle, *(ctypes.c_void_p(a.ctypes.data) for a in (keys, src, dst, orient, mult))),
            "dbg_graph_edges")
     return {"keys": keys.reshape(-1, W), "src": src, "dst": dst, "orient": orient, "mult": mult}
+
+
+def dbg_graph_edges_async(g: Graph, keys: int | None = None, src: int | None = None, dst: int | None = None,
+                          orient: int | None = None, mult: int | None = None) -> None:
+    """Starts the edge-array copies into caller-owned buffers (raw addresses,
+    e.g. pinned tensors' data_ptr(); None skips an array); dbg_graph_wait
+    finishes them."""
+    ptrs = (ctypes.c_void_p(a) if a else None for a in (keys, src, dst, orient, mult))
+    _check(_lib.dbg_graph_edges_async(g.handle, *ptrs), "dbg_graph_edges_async")
+
+
+def dbg_graph_wait(g: Graph) -> None:
+    _check(_lib.dbg_graph_wait(g.handle), "dbg_graph_wait")
 
 
 def dbg_graph_csr(g: Graph) -> dict:

@@ -217,6 +217,37 @@ def test_persistent_sort_variants_many_tiles(dbg):
     assert tried >= 2
 
 
+def test_async_edge_readback_during_compaction(dbg, ctx):
+    """dbg_graph_edges_async into pinned host buffers, overlapped with the
+    compaction of the same graph, gives what dbg_graph_edges gives; waiting
+    with nothing started returns at once; freeing a graph with copies in
+    flight waits for them."""
+    import torch
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(300_000, 40_000, 100, 0.01, 31, 44))
+    g = dbg.dbg_build(ctx, reads, lengths, 31)
+    dbg.dbg_graph_wait(g)
+    E, W = dbg.dbg_graph_num_edges(g), dbg.dbg_graph_key_words(g)
+    keys = torch.empty(E * W, dtype=torch.int64).pin_memory()
+    src, dst, mult = (torch.empty(E, dtype=torch.int32).pin_memory() for _ in range(3))
+    orient = torch.empty(E, dtype=torch.uint8).pin_memory()
+    dbg.dbg_graph_edges_async(g, keys.data_ptr(), src.data_ptr(), dst.data_ptr(), orient.data_ptr(),
+                              mult.data_ptr())
+    u = dbg.dbg_compact(ctx, g)
+    dbg.dbg_graph_wait(g)
+    want = dbg.dbg_graph_edges(g)
+    np.testing.assert_array_equal(keys.numpy().view(np.uint64).reshape(-1, W), want["keys"])
+    np.testing.assert_array_equal(src.numpy().view(np.uint32), want["src"])
+    np.testing.assert_array_equal(dst.numpy().view(np.uint32), want["dst"])
+    np.testing.assert_array_equal(orient.numpy(), want["orient"])
+    np.testing.assert_array_equal(mult.numpy().view(np.uint32), want["mult"])
+    assert dbg.dbg_unitigs_count(u) > 0
+    u.free()
+    mult2 = torch.zeros(E, dtype=torch.int32).pin_memory()
+    dbg.dbg_graph_edges_async(g, mult=mult2.data_ptr())
+    g.free()  # waits for the copy
+    np.testing.assert_array_equal(mult2.numpy().view(np.uint32), want["mult"])
+
+
 def test_autotune_and_cache(dbg, tmp_path):
     c = dbg.Context()
     cache = str(tmp_path / "tune.txt")
