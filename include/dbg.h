@@ -335,14 +335,14 @@ dbg_status dbg_sort_hybrid_set(dbg_ctx *ctx, int on);
 uint64_t dbg_sort_fallbacks(const dbg_ctx *ctx);
 
 /* ----------------------------------------------------------------------
- * Count-first switch (k <= 31).  With it on (the default) the local pass
+ * Count-first switch.  With it on (the default) the local pass
  * of the hybrid edge-key sort counts each tile's copies of every key in a
  * shared-memory hash table of 2048 slots and sorts only the distinct keys,
  * which at read coverage c are about 1/c of them; a tile whose distinct
  * keys do not fit (about 1500 and up) is sorted copy by copy instead, and
  * dbg_sort_count_overflows counts such tiles over the context's builds.
  * Off, every tile is sorted copy by copy.  The edge list is the same
- * either way.  Wider keys always take the second form.
+ * either way.
  * -------------------------------------------------------------------- */
 dbg_status dbg_sort_count_first_set(dbg_ctx *ctx, int on);
 uint64_t dbg_sort_count_overflows(const dbg_ctx *ctx);

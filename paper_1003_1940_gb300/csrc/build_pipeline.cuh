@@ -433,7 +433,7 @@ dbg_status seg_rle(dbg_ctx *ctx, K *kin, K *kstage, uint64_t n, int low_bits, in
   constexpr size_t rsmem = sizeof(SegSortSmem<K, false, Sh::ITEMS>);
   set_smem_attrs(radix, rsmem);
   bool counted = false;
-  if constexpr (std::is_same<K, uint64_t>::value) {
+  {
     if (ctx->count_first) {
       // count-first; the tiles that overflow their table are listed (after
       // a counter word) and sorted copy by copy

@@ -413,14 +413,40 @@ __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_rle(
 template <class K>
 struct SlotOps;
 
+// claim(p, d) returns the slot's key, having stored d there if it was empty
+// (then it returns empty): the caller has found d's slot when it gets empty
+// or d, and probes on otherwise.
 template <>
 struct SlotOps<uint64_t> {
   __device__ static uint64_t empty() { return ~0ull; }
   // Fibonacci hashing: the high 32 bits of d times 2^64 / golden ratio
   __device__ static uint32_t hash(uint64_t d) { return (uint32_t)((d * 0x9e3779b97f4a7c15ull) >> 32); }
-  __device__ static uint64_t load(const uint64_t *p) { return *reinterpret_cast<const volatile uint64_t *>(p); }
-  __device__ static uint64_t cas(uint64_t *p, uint64_t cmp, uint64_t v) {
-    return atomicCAS(reinterpret_cast<unsigned long long *>(p), cmp, v);
+  __device__ static uint64_t claim(uint64_t *p, uint64_t d) {
+    // a 64-bit load is single-copy atomic, so it settles most probes
+    // without an atomic operation
+    const uint64_t cur = *reinterpret_cast<const volatile uint64_t *>(p);
+    if (cur != ~0ull) return cur;
+    return atomicCAS(reinterpret_cast<unsigned long long *>(p), ~0ull, d);
+  }
+};
+
+template <>
+struct SlotOps<Key128> {
+  __device__ static Key128 empty() { return Key128{~0ull, ~0ull}; }
+  __device__ static uint32_t hash(Key128 d) {
+    return (uint32_t)(((d.lo ^ (d.hi * 0x9e3779b97f4a7c15ull)) * 0xc2b2ae3d27d4eb4full) >> 32);
+  }
+  // every probe is a 128-bit compare-and-swap, which also reads the slot
+  // whole (two 64-bit loads could see a slot half written)
+  __device__ static Key128 claim(Key128 *p, Key128 d) {
+    Key128 old;
+    asm volatile(
+        "{\n .reg .b128 c, n, o;\n mov.b128 c, {%2, %3};\n mov.b128 n, {%4, %5};\n"
+        " atom.shared.cas.b128 o, [%6], c, n;\n mov.b128 {%0, %1}, o;\n}"
+        : "=l"(old.hi), "=l"(old.lo)
+        : "l"(~0ull), "l"(~0ull), "l"(d.hi), "l"(d.lo), "r"(smem_u32(p))
+        : "memory");
+    return old;
   }
 };
 
@@ -488,8 +514,7 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
       uint32_t h = O::hash(d[i]) >> (32 - S::TBITS);
       bool done = false;
       for (uint32_t probe = 0; probe < S::PROBES; probe++) {
-        K cur = O::load(&sm.keys[h]);
-        if (KeyOps<K>::eq(cur, O::empty())) cur = O::cas(&sm.keys[h], O::empty(), d[i]);
+        const K cur = O::claim(&sm.keys[h], d[i]);
         if (KeyOps<K>::eq(cur, O::empty()) || KeyOps<K>::eq(cur, d[i])) {
           atomicAdd(&sm.vals[h], 1u);
           done = true;

@@ -99,7 +99,8 @@ def test_long_runs_in_first_and_last_tiles(dbg):
 
 
 @pytest.mark.parametrize("k,genome,n_reads,L", [(31, 40_000_000, 6_000, 100), (27, 300_000, 40_000, 90),
-                                                (15, 20_000, 20_000, 40)])
+                                                (15, 20_000, 20_000, 40), (55, 40_000_000, 4_000, 150),
+                                                (47, 300_000, 20_000, 120), (63, 100_000, 6_000, 150)])
 def test_count_first_equals_sorted_runs(dbg, k, genome, n_reads, L):
     """Counting each tile's copies in a hash table and sorting the distinct
     keys gives the edge list of sorting every copy: at coverage ~0.015 (almost
