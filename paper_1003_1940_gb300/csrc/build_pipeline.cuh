@@ -155,6 +155,8 @@ template <> struct SortKind<Key128, false> {
         DBG_SVL(Key128, false, 256, 8, RANK_ATOMIC, true, 2, true, 4, "256x8 atomic tma occ2 early lb4"),
         DBG_SVL(Key128, false, 256, 8, RANK_ATOMIC, true, 2, false, 8, "256x8 atomic tma occ2 lb8"),
         DBG_SVL(Key128, false, 256, 6, RANK_ATOMIC, true, 3, false, 8, "256x6 atomic tma occ3 lb8"),
+        DBG_SVP(Key128, false, 256, 6, RANK_ATOMIC, 3, 4, "256x6 atomic persistent occ3 lb4"),
+        DBG_SVP(Key128, false, 256, 8, RANK_ATOMIC, 2, 4, "256x8 atomic persistent occ2 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -171,12 +173,14 @@ template <> struct SortKind<Key128, true> {
         DBG_SVD(Key128, true, 256, 6, RANK_ATOMIC, true, 3, true, "256x6 atomic tma occ3 early direct"),
         DBG_SVL(Key128, true, 256, 6, RANK_ATOMIC, true, 3, true, 4, "256x6 atomic tma occ3 early lb4"),
         DBG_SVL(Key128, true, 256, 6, RANK_ATOMIC, true, 3, false, 8, "256x6 atomic tma occ3 lb8"),
+        DBG_SVP(Key128, true, 256, 6, RANK_ATOMIC, 2, 4, "256x6 atomic persistent occ2 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
   }
 };
 #undef DBG_SV
+#undef DBG_SVP
 #undef DBG_SVE
 #undef DBG_SVD
 #undef DBG_SVL

@@ -189,24 +189,26 @@ def test_every_sort_variant_sorts_identically(dbg, ctx):
             dbg.dbg_sort_variant_set(ctx, kd, 0)
 
 
-def test_persistent_sort_variants_many_tiles(dbg):
+@pytest.mark.parametrize("k,kinds", [(31, (0, 1)), (55, (2, 3))])
+def test_persistent_sort_variants_many_tiles(dbg, k, kinds):
     """The persistent onesweep variants (each CTA loops over tiles, the next
     tile's bulk copy in flight) on enough keys for several tiles per CTA:
-    every digit sorted globally, 7.1 M edge keys and about 4 M node records,
-    graphs identical to variant 0's, which matches the oracle's."""
-    reads, lengths = readgen.generate(readgen.ReadSetSpec(2_000_000, 60_000, 150, 0.01, 31, 43))
+    every digit sorted globally, 5.7-7.1 M edge keys and 4-5 M node records,
+    64- and 128-bit keys, graphs identical to variant 0's, which matches the
+    oracle's."""
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(2_000_000, 60_000, 150, 0.01, k, 43))
     ctx = dbg.Context()
     dbg.dbg_sort_hybrid_set(ctx, False)
-    _, ref = gpu_graph(dbg, ctx, reads, lengths, 31)
+    _, ref = gpu_graph(dbg, ctx, reads, lengths, k)
     from parity import assert_graph_equal
-    assert_graph_equal(ref, oracle.build_graph(reads, lengths, 31))
+    assert_graph_equal(ref, oracle.build_graph(reads, lengths, k))
     tried = 0
-    for kd in (0, 1):
+    for kd in kinds:
         for v in range(dbg.dbg_sort_variant_count(kd)):
             if "persistent" not in dbg.dbg_sort_variant_name(kd, v):
                 continue
             dbg.dbg_sort_variant_set(ctx, kd, v)
-            _, got = gpu_graph(dbg, ctx, reads, lengths, 31)
+            _, got = gpu_graph(dbg, ctx, reads, lengths, k)
             for key in ref:
                 if isinstance(ref[key], np.ndarray):
                     np.testing.assert_array_equal(got[key], ref[key], err_msg=f"{kd}/{v} {key}")
