@@ -243,8 +243,8 @@ __device__ __forceinline__ Key128 load_window<Key128>(const uint64_t *packed, ui
 // ---------------------------------------------------------------------------
 // K2 emit (STEP-1): key edge_off[r] + j of read r is the canonical (k+1)-mer
 // min(z, revcomp z) of z = r[j .. j+k].  The block also accumulates the
-// digit histograms of every radix pass of the sort that follows (one
-// upfront histogram for all passes, as in onesweep).
+// digit histograms of the sort's global radix passes (one upfront histogram
+// for all of them, as in onesweep).
 // ---------------------------------------------------------------------------
 constexpr int EMIT_BLOCK = 256, EMIT_ITEMS = 8, EMIT_TILE = EMIT_BLOCK * EMIT_ITEMS;
 
