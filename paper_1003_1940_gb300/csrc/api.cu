@@ -66,6 +66,11 @@ dbg_status ensure_status(dbg_ctx *ctx, size_t words) {
   return DBG_OK;
 }
 
+dbg_status ensure_copy_stream(dbg_ctx *ctx) {
+  if (!ctx->copy_stream) DBG_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  return DBG_OK;
+}
+
 dbg_status next_epoch(dbg_ctx *ctx, uint32_t *epoch) {
   if (ctx->epoch >= 0x3fffffffu) {
     // the 30-bit epoch wrapped: old words could look current again
@@ -302,6 +307,10 @@ void dbg_destroy(dbg_ctx *ctx) {
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   if (ctx->ev) cudaEventDestroy(ctx->ev);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

@@ -610,47 +610,81 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     return DBG_EOVERFLOW;
   }
 
-  // ---- K1 pack ----
-  DevBuf packed;
-  const uint64_t nwords = (total_bases + 31) / 32;
-  DBG_TRY(alloc_buf(ctx, packed, (nwords + 3) * sizeof(uint64_t)));
-  DBG_CUDA_TRY(cudaMemsetAsync(packed.as<uint64_t>() + nwords, 0, 3 * sizeof(uint64_t), s));
-  if (nwords > 0 && !in.h_reads) {
-    DBG_LAUNCH(ctx, ST_PACK, (double)total_bases + 8.0 * nwords,
-               k_pack<<<grid_for(nwords, 256), 256, 0, s>>>(in.reads, total_bases, packed.as<uint64_t>(), nwords,
-                                                 ctx->d_err));
-  } else if (nwords > 0) {
-    // host reads: copy them in chunks through a staging buffer, packing each
-    const uint64_t chunk = 256ull << 20;  // bases per copy (a multiple of 32)
-    DevBuf stage;
-    DBG_TRY(alloc_buf(ctx, stage, std::min(chunk, total_bases)));
-    for (uint64_t off = 0; off < total_bases; off += chunk) {
-      const uint64_t len = std::min(chunk, total_bases - off);
-      DBG_CUDA_TRY(cudaMemcpyAsync(stage.p, in.reads + off, len, cudaMemcpyHostToDevice, s));
-      DBG_LAUNCH(ctx, ST_PACK, (double)len * 1.25,
-                 k_pack_at<<<grid_for((len + 31) / 32, 256), 256, 0, s>>>(stage.as<uint8_t>(), len,
-                                                                        packed.as<uint64_t>(), off / 32, ctx->d_err));
-    }
-  }
-
-  // ---- K2 emit + digit histograms, K3 sort, K4 run-length reduce ----
+  // ---- K2 set-up: key buffers and histograms come first, so that host
+  // reads can be emitted chunk by chunk as they are packed ----
   const int kbits = 2 * ((int)k + 1);
   const int kpasses = passes_for_bits(kbits);
   DevBuf keys_a, keys_b, headpos, mult_tmp, uniq;
   uint64_t E = 0;
   K *sorted = nullptr;
+  // the hybrid sort needs the histograms of its global passes only
+  const int p0 = ctx->hybrid_sort ? hybrid_first_pass<K>(N, kbits) : 0;
   if (N > 0) {
     DBG_TRY(alloc_buf(ctx, keys_a, N * sizeof(K)));
     DBG_TRY(alloc_buf(ctx, keys_b, N * sizeof(K)));
     DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
-    // the hybrid sort needs the histograms of its global passes only
-    const int p0 = ctx->hybrid_sort ? hybrid_first_pass<K>(N, kbits) : 0;
-    {
-      DBG_LAUNCH(ctx, ST_EMIT, 8.0 * nwords + 16.0 * n + (double)N * sizeof(K),
-                 k_emit<K><<<(unsigned)std::min<uint64_t>(grid_for(n, EMIT_BLOCK / 32), 152ull * 64), EMIT_BLOCK, 0, s>>>(
-                     packed.as<uint64_t>(), base_off.as<uint64_t>(), edge_off.as<uint64_t>(), n, k, keys_a.as<K>(),
-                     p0, kpasses, d_hist));
+  }
+  DevBuf packed;
+  const uint64_t nwords = (total_bases + 31) / 32;
+  // K2 emit over the keys [krange[0], krange[1]) (all of them: nullptr)
+  auto emit = [&](const uint64_t *krange, double bytes) -> dbg_status {
+    DBG_LAUNCH(ctx, ST_EMIT, bytes,
+               k_emit<K><<<(unsigned)std::min<uint64_t>(grid_for(n, EMIT_BLOCK / 32), 152ull * 64), EMIT_BLOCK, 0,
+                           s>>>(packed.as<uint64_t>(), base_off.as<uint64_t>(), edge_off.as<uint64_t>(), n, k,
+                                keys_a.as<K>(), p0, kpasses, d_hist, krange));
+    DBG_CUDA_TRY(cudaGetLastError());
+    return DBG_OK;
+  };
+
+  // ---- K1 pack (+ K2 emit) ----
+  DBG_TRY(alloc_buf(ctx, packed, (nwords + 3) * sizeof(uint64_t)));
+  DBG_CUDA_TRY(cudaMemsetAsync(packed.as<uint64_t>() + nwords, 0, 3 * sizeof(uint64_t), s));
+  bool emitted = false;
+  if (nwords > 0 && !in.h_reads) {
+    DBG_LAUNCH(ctx, ST_PACK, (double)total_bases + 8.0 * nwords,
+               k_pack<<<grid_for(nwords, 256), 256, 0, s>>>(in.reads, total_bases, packed.as<uint64_t>(), nwords,
+                                                 ctx->d_err));
+  } else if (nwords > 0) {
+    // host reads: chunks are copied on a stream of their own into two
+    // staging buffers in turn while the build's stream packs the previous
+    // chunk and emits the reads that end in the chunks packed so far
+    const uint64_t chunk = 256ull << 20;  // bases per copy (a multiple of 32)
+    const uint32_t chunks = (uint32_t)((total_bases + chunk - 1) / chunk);
+    DBG_TRY(ensure_copy_stream(ctx));
+    cudaStream_t cs = ctx->copy_stream;
+    DevBuf stage[2], kbound;
+    const uint64_t slen = std::min(chunk, total_bases);
+    DBG_TRY(alloc_buf(ctx, stage[0], slen));
+    if (chunks > 1) DBG_TRY(alloc_buf(ctx, stage[1], slen));
+    DBG_TRY(alloc_buf(ctx, kbound, (chunks + 1) * sizeof(uint64_t)));
+    if (N > 0)
+      DBG_LAUNCH(ctx, ST_EMIT, 0.0,
+                 k_chunk_key_bounds<<<grid_for(chunks + 1, 64), 64, 0, s>>>(
+                     base_off.as<uint64_t>(), edge_off.as<uint64_t>(), n, chunk, chunks, kbound.as<uint64_t>()));
+    EventSet ev;
+    DBG_TRY(ev.create(2 * chunks + 1));
+    cudaEvent_t ready = ev.e[2 * chunks];  // the stage buffers exist on the build's stream
+    DBG_CUDA_TRY(cudaEventRecord(ready, s));
+    DBG_CUDA_TRY(cudaStreamWaitEvent(cs, ready, 0));
+    for (uint32_t c = 0; c < chunks; c++) {
+      const uint64_t off = (uint64_t)c * chunk, len = std::min(chunk, total_bases - off);
+      DevBuf &st = stage[c & 1];
+      if (c >= 2) DBG_CUDA_TRY(cudaStreamWaitEvent(cs, ev.e[2 * (c - 2) + 1], 0));  // packed c - 2
+      DBG_CUDA_TRY(cudaMemcpyAsync(st.p, in.reads + off, len, cudaMemcpyHostToDevice, cs));
+      DBG_CUDA_TRY(cudaEventRecord(ev.e[2 * c], cs));
+      DBG_CUDA_TRY(cudaStreamWaitEvent(s, ev.e[2 * c], 0));
+      DBG_LAUNCH(ctx, ST_PACK, (double)len * 1.25,
+                 k_pack_at<<<grid_for((len + 31) / 32, 256), 256, 0, s>>>(st.as<uint8_t>(), len,
+                                                                        packed.as<uint64_t>(), off / 32, ctx->d_err));
+      DBG_CUDA_TRY(cudaEventRecord(ev.e[2 * c + 1], s));
+      if (N > 0) DBG_TRY(emit(kbound.as<uint64_t>() + c, (double)len / 4.0 + (double)N * sizeof(K) / chunks));
     }
+    emitted = true;
+  }
+
+  // ---- K2 emit + digit histograms, K3 sort, K4 run-length reduce ----
+  if (N > 0) {
+    if (!emitted) DBG_TRY(emit(nullptr, 8.0 * nwords + 16.0 * n + (double)N * sizeof(K)));
     DBG_CUDA_TRY(cudaGetLastError());
     K *kp = keys_a.as<K>(), *alt = keys_b.as<K>();
     uint32_t *vn = nullptr, *van = nullptr;

@@ -91,6 +91,7 @@ struct dbg_ctx {
   uint32_t *d_counters = nullptr;  // small per-call counters (tile tickets, totals)
   uint32_t *h_pinned = nullptr;    // pinned host mirror for small read-backs
   cudaEvent_t ev = nullptr;
+  cudaStream_t copy_stream = nullptr;  // host-to-device copies that overlap the build's stream
   // profiling
   bool prof = false;
   uint64_t launches = 0;
@@ -137,6 +138,27 @@ namespace dbg {
 dbg_status alloc_buf(dbg_ctx *ctx, DevBuf &b, size_t bytes);
 // grows the persistent look-back status array to at least `words` words
 dbg_status ensure_status(dbg_ctx *ctx, size_t words);
+// creates the context's copy stream on first use
+dbg_status ensure_copy_stream(dbg_ctx *ctx);
+
+// events owned for one call, destroyed when it returns
+struct EventSet {
+  std::vector<cudaEvent_t> e;
+  dbg_status create(size_t count) {
+    e.assign(count, nullptr);
+    for (cudaEvent_t &x : e)
+      if (cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) {
+        x = nullptr;
+        set_error("cudaEventCreate failed");
+        return DBG_ECUDA;
+      }
+    return DBG_OK;
+  }
+  ~EventSet() {
+    for (cudaEvent_t x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
 // next epoch for a look-back scan; clears the status array when it wraps
 dbg_status next_epoch(dbg_ctx *ctx, uint32_t *epoch);
 // reads the device error word and maps it to a status (and clears it)

@@ -263,10 +263,12 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict_
                                                      const uint64_t *__restrict__ base_off,
                                                      const uint64_t *__restrict__ edge_off, uint64_t n_reads,
                                                      uint32_t k, K *__restrict__ keys, int first, int passes,
-                                                     unsigned long long *__restrict__ hist) {
-  // Every warp takes a contiguous, 32-aligned range of the N edge instances
-  // (all reads' keys in order), so lanes stay busy across read ends and
-  // every warp-wide store writes 32 consecutive keys.  A lane follows the
+                                                     unsigned long long *__restrict__ hist,
+                                                     const uint64_t *__restrict__ krange) {
+  // Every warp takes a contiguous, 32-aligned range of the keys to emit
+  // (all of the N edge instances, or [krange[0], krange[1]) of them when
+  // krange is given), so lanes stay busy across read ends and every
+  // warp-wide store writes 32 consecutive keys.  A lane follows the
   // read that holds its key: one binary search per warp, then a step to the
   // next read when the key passes the current one's end.  The digit
   // histograms of passes [first, passes) are accumulated on the way.
@@ -279,9 +281,9 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict_
   const int m = (int)k + 1;
   const int G = passes - first;  // histogrammed passes
   uint32_t *hbase = s_hist + first * RADIX;
-  const uint64_t N = __ldg(edge_off + n_reads);
-  const uint64_t per = ((N + warps - 1) / warps + 31) & ~31ull;
-  const uint64_t a = wid * per, b = min(a + per, N);
+  const uint64_t lo = krange ? krange[0] : 0, hi = krange ? krange[1] : __ldg(edge_off + n_reads);
+  const uint64_t per = ((hi - lo + warps - 1) / warps + 31) & ~31ull;
+  const uint64_t a = lo + wid * per, b = min(a + per, hi);
   if (a < b) {
     // the read holding key a + lane: the last read starting at or before a,
     // then forward (reads without keys are stepped over)
@@ -312,6 +314,29 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict_
   __syncthreads();
   for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK)
     if (s_hist[i]) atomicAdd(hist + i, (unsigned long long)s_hist[i]);
+}
+
+// Host reads arrive in chunks of `chunk` bases; once chunks 0..c are packed,
+// the reads that end in them can be emitted.  bound[c + 1] = the first key
+// of the first read that does not (edge_off of the number of reads whose
+// bases all lie below (c + 1) * chunk), bound[0] = 0.
+static __global__ void k_chunk_key_bounds(const uint64_t *__restrict__ base_off,
+                                          const uint64_t *__restrict__ edge_off, uint64_t n, uint64_t chunk,
+                                          uint32_t chunks, uint64_t *__restrict__ bound) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c <= chunks; c += gridDim.x * blockDim.x) {
+    if (c == 0) {
+      bound[0] = 0;
+      continue;
+    }
+    const uint64_t end = (uint64_t)c * chunk;
+    uint64_t lo = 0, hi = n;  // largest r in [0, n] with base_off[r] <= end
+    while (lo < hi) {
+      const uint64_t mid = hi - (hi - lo) / 2;
+      if (base_off[mid] <= end) lo = mid;
+      else hi = mid - 1;
+    }
+    bound[c] = edge_off[lo];
+  }
 }
 
 // Digit histograms of passes [first, last) of n keys (any order): what the

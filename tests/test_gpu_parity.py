@@ -219,6 +219,27 @@ def test_persistent_sort_variants_many_tiles(dbg, k, kinds):
     assert tried >= 2
 
 
+@pytest.mark.parametrize("n_reads,L", [(2_400_000, 150), (2_200_000, 128)])
+def test_host_reads_over_several_chunks(dbg, ctx, n_reads, L):
+    """Host reads of more than one 256 M-base chunk: each chunk is copied
+    while the previous one is packed and its complete reads emitted.  Reads
+    straddle the chunk boundary (L = 150) or end exactly on it (L = 128:
+    2^21 reads per chunk).  The graph equals the one built from device
+    reads, from pageable and from pinned host memory."""
+    import torch
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(3_000_000, n_reads, L, 0.01, 31, 45))
+    assert int(lengths.sum()) > 256 << 20
+    _, dev = gpu_graph(dbg, ctx, torch.from_numpy(reads).cuda(),
+                       torch.from_numpy(lengths.view(np.int32)).cuda(), 31)
+    for host in (reads, torch.from_numpy(reads).pin_memory()):
+        _, got = gpu_graph(dbg, ctx, host, lengths, 31)
+        for key in dev:
+            if isinstance(dev[key], np.ndarray):
+                np.testing.assert_array_equal(got[key], dev[key], err_msg=key)
+            else:
+                assert got[key] == dev[key], key
+
+
 def test_async_edge_readback_during_compaction(dbg, ctx):
     """dbg_graph_edges_async into pinned host buffers, overlapped with the
     compaction of the same graph, gives what dbg_graph_edges gives; waiting
