@@ -36,3 +36,18 @@ def test_replica_aggregation_two_ranks():
             rate, ms, mx = out[r]
             assert ms == 200.0 and mx == 1.0
             assert abs(rate - 3000.0 / 0.2) < 1e-6
+
+
+def test_host_binding_helpers():
+    """The bench's host placement: CPU lists as Linux writes them, and a
+    machine without a usable GPU leaves the process where it is."""
+    import bench
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("") == set()
+    before = os.sched_getaffinity(0)
+    info = bench.bind_near_gpu(0)
+    if info["bound"]:  # a GPU box whose process may use cores away from the GPU
+        assert os.sched_getaffinity(0) < before
+        os.sched_setaffinity(0, info["_restore"])
+    else:
+        assert os.sched_getaffinity(0) == before and "_restore" not in info
