@@ -311,9 +311,11 @@ dbg_status dbg_rle_u64_noalloc(const uint64_t *keys, uint64_t n, uint64_t *uniq,
  * (0 = 2^25; 128-bit kinds use n / 2) and keeps the fastest of kinds 0-3 in
  * the context.  cache_path (may be NULL) names a text file of choices keyed
  * by GPU name and SM count: a matching line is used instead of timing, and
- * a new result is appended.  ms_out (may be NULL) receives 4 x 32 pass
- * times in ms (kind-major; at most 32 variants per kind).
+ * a new result is appended.  ms_out (may be NULL) receives 4 x
+ * DBG_MAX_SORT_VARIANTS pass times in ms (kind-major; variant v of kind k at
+ * k * DBG_MAX_SORT_VARIANTS + v).
  * -------------------------------------------------------------------- */
+#define DBG_MAX_SORT_VARIANTS 64 /* per kind */
 uint32_t dbg_sort_variant_count(uint32_t kind);
 const char *dbg_sort_variant_name(uint32_t kind, uint32_t variant);
 dbg_status dbg_sort_variant_set(dbg_ctx *ctx, uint32_t kind, uint32_t variant);

@@ -701,8 +701,14 @@ dbg_status dbg_autotune(dbg_ctx *ctx, uint64_t n, const char *cache_path, double
   }
   if (n == 0) n = 1ull << 25;
   double *m = ms_out;
-  dbg_status st = autotune_u64(ctx, n, m ? m : nullptr, m ? m + 32 : nullptr);
-  if (st == DBG_OK) st = autotune_u128(ctx, n / 2, m ? m + 64 : nullptr, m ? m + 96 : nullptr);
+  constexpr int W = DBG_MAX_SORT_VARIANTS;
+  for (uint32_t kd = 0; kd < 4; kd++)
+    if (dbg_sort_variant_count(kd) > (uint32_t)W) {
+      set_error("sort kind %u has more than %d variants", kd, W);
+      return DBG_EINVAL;
+    }
+  dbg_status st = autotune_u64(ctx, n, m ? m : nullptr, m ? m + W : nullptr);
+  if (st == DBG_OK) st = autotune_u128(ctx, n / 2, m ? m + 2 * W : nullptr, m ? m + 3 * W : nullptr);
   cudaStreamSynchronize(ctx->stream);
   prof_resolve(ctx);
   if (st != DBG_OK) return st;

@@ -111,6 +111,8 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SVP(uint64_t, false, 256, 12, RANK_ATOMIC, 3, 8, "256x12 atomic persistent occ3 lb8"),
         DBG_SVP(uint64_t, false, 256, 8, RANK_ATOMIC, 4, 4, "256x8 atomic persistent occ4 lb4"),
         DBG_SVP(uint64_t, false, 256, 12, RANK_MATCH, 3, 4, "256x12 match persistent occ3 lb4"),
+        DBG_SVP(uint64_t, false, 256, 16, RANK_ATOMIC, 2, 4, "256x16 atomic persistent occ2 lb4"),
+        DBG_SVP(uint64_t, false, 512, 8, RANK_ATOMIC, 2, 4, "512x8 atomic persistent occ2 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;

@@ -433,11 +433,14 @@ def dbg_sort_fallbacks(ctx: Context) -> int:
     return int(_lib.dbg_sort_fallbacks(ctx.handle))
 
 
+MAX_SORT_VARIANTS = 64  # DBG_MAX_SORT_VARIANTS of dbg.h: stride of the autotune report
+
+
 def dbg_autotune(ctx: Context, n: int = 0, cache_path: str | None = None) -> dict:
     """Times every radix-sort variant; returns {kind: [ms per variant]}."""
-    ms = (ctypes.c_double * 128)()
+    ms = (ctypes.c_double * (4 * MAX_SORT_VARIANTS))()
     _check(_lib.dbg_autotune(ctx.handle, n, cache_path.encode() if cache_path else None, ms), "dbg_autotune")
-    return {kd: [ms[kd * 32 + v] for v in range(dbg_sort_variant_count(kd))] for kd in range(4)}
+    return {kd: [ms[kd * MAX_SORT_VARIANTS + v] for v in range(dbg_sort_variant_count(kd))] for kd in range(4)}
 
 
 # ---------------------------------------------------------------------------

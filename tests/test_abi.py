@@ -36,3 +36,16 @@ def test_options_init_without_gpu():
     lib.dbg_options_init(ctypes.byref(opt))
     assert opt.struct_size == ctypes.sizeof(dbg.dbg_options)
     assert opt.device == -1
+
+
+def test_sort_variant_tables_fit_the_autotune_report():
+    """Every sort kind's variant table fits the per-kind stride of the
+    autotune report (DBG_MAX_SORT_VARIANTS), and each variant has a name."""
+    dbg.load(build=True)
+    stride = int(re.search(r"#define DBG_MAX_SORT_VARIANTS (\d+)", open(HEADER).read()).group(1))
+    assert stride == dbg.MAX_SORT_VARIANTS
+    for kd in range(4):
+        count = dbg.dbg_sort_variant_count(kd)
+        assert 1 <= count <= stride
+        names = [dbg.dbg_sort_variant_name(kd, v) for v in range(count)]
+        assert all(names) and len(set(names)) == count
