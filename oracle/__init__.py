@@ -2,7 +2,8 @@
 
 The oracle restates the definitions of the bi-directed de Bruijn graph
 (Section 2 of Kundeti et al., arXiv 1003.1940), the adjacency of STEP-4
-(Section 3) and chain compaction (Section 6) on the CPU.  Only the tests,
+(Section 3), chain compaction (Section 6) and node multiplicities (the
+k-mer occurrence counts of Section 7's roadmap discussion) on the CPU.  Only the tests,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use it;
 the GPU library never imports it and shares no code with it.
 """
@@ -87,6 +88,13 @@ def _load():
             lib.orc_count_kplus1.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                              ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                              ctypes.c_void_p]
+            lib.orc_node_mult.restype = ctypes.c_int
+            lib.orc_node_mult.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                          ctypes.POINTER(ctypes.c_uint64),
+                                          ctypes.POINTER(ctypes.POINTER(ctypes.c_uint64)),
+                                          ctypes.POINTER(ctypes.POINTER(ctypes.c_uint64))]
+            lib.orc_free.restype = None
+            lib.orc_free.argtypes = [ctypes.c_void_p]
             lib.orc_edges_in_partition.restype = ctypes.c_int
             lib.orc_edges_in_partition.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                                    ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -237,3 +245,24 @@ def edges_in_partition(reads, lengths, k: int, part: int, parts: int) -> tuple[i
     if rc != ORC_OK:
         raise OracleError(rc, "orc_edges_in_partition")
     return int(d.value), int(i.value)
+
+
+def node_multiplicities(reads, lengths, k: int) -> tuple[np.ndarray, np.ndarray]:
+    """Canonical k-mers of the forward reads (the nodes of Section 2) in
+    ascending order as (n, 2) high/low u64 words, and how many positions of
+    the forward reads hold each of them or its reverse complement."""
+    lib = _load()
+    reads, lengths = _as_reads(reads, lengths)
+    m = ctypes.c_uint64(0)
+    kp, cp = ctypes.POINTER(ctypes.c_uint64)(), ctypes.POINTER(ctypes.c_uint64)()
+    rc = lib.orc_node_mult(reads.ctypes.data, lengths.ctypes.data, len(lengths), k, ctypes.byref(m),
+                           ctypes.byref(kp), ctypes.byref(cp))
+    if rc != ORC_OK:
+        raise OracleError(rc, "orc_node_mult")
+    try:
+        keys = _copy(kp, 2 * m.value, np.uint64).reshape(-1, 2)
+        counts = _copy(cp, m.value, np.uint64)
+    finally:
+        lib.orc_free(ctypes.cast(kp, ctypes.c_void_p))
+        lib.orc_free(ctypes.cast(cp, ctypes.c_void_p))
+    return keys, counts

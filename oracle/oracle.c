@@ -401,6 +401,68 @@ int orc_count_kplus1(const char *reads, const uint32_t *lengths, uint64_t n, uin
 }
 
 /* ------------------------------------------------------------------ */
+/* node multiplicities                                                   */
+/* ------------------------------------------------------------------ */
+
+static int cmp_slot_key(const void *pa, const void *pb) {
+  return cmp_u128(((const slot_t *)pa)->a, ((const slot_t *)pb)->a);
+}
+
+/* For every node of orc_build -- the canonical k-mers of the forward reads
+ * of length >= k (Section 2) -- the number of positions of the forward
+ * reads whose k-mer is it or its reverse complement: STEP-2's counting
+ * (Section 3) applied to k-mers, the table of k-mer occurrences that
+ * VELVET's roadmap is drawn from (Section 7).  *keys receives 2 words
+ * (high, low) per node in ascending order, *counts one count per node;
+ * both are allocated here (free them with orc_free). */
+int orc_node_mult(const char *reads, const uint32_t *lengths, uint64_t n, uint32_t k, uint64_t *n_nodes,
+                  uint64_t **keys, uint64_t **counts) {
+  if (k < 1 || k > 63 || (k % 2) == 0 || !n_nodes || !keys || !counts) return ORC_EINVAL;
+  const int K = (int)k;
+  table_t t;
+  if (table_init(&t, 1024) != ORC_OK) return ORC_ENOMEM;
+  /* slide a k-base window along each read */
+  u128 mask = (K == 64) ? ~(u128)0 : ((((u128)1) << (2 * K)) - 1);
+  const char *read = reads;
+  for (uint64_t r = 0; r < n; r++) {
+    int64_t L = lengths[r];
+    u128 fwd = 0, rev = 0;
+    for (int64_t j = 0; j < L; j++) {
+      int c = base_code(read[j]);
+      if (c < 0) { free(t.slots); return ORC_EINVAL; }
+      fwd = ((fwd << 2) | (u128)c) & mask;
+      rev = (rev >> 2) | ((u128)(3 - c) << (2 * (K - 1)));
+      if (j + 1 < K) continue;
+      slot_t *sl = table_find(&t, rev < fwd ? rev : fwd, 0, 0, 1);
+      if (!sl) { free(t.slots); return ORC_ENOMEM; }
+      sl->count++;
+    }
+    read += L;
+  }
+  /* the occupied slots, in key order */
+  uint64_t m = 0;
+  for (uint64_t i = 0; i < t.cap; i++)
+    if (t.slots[i].used) t.slots[m++] = t.slots[i];
+  qsort(t.slots, m, sizeof(slot_t), cmp_slot_key);
+  *keys = (uint64_t *)malloc((m ? m : 1) * 2 * sizeof(uint64_t));
+  *counts = (uint64_t *)malloc((m ? m : 1) * sizeof(uint64_t));
+  if (!*keys || !*counts) {
+    free(*keys); free(*counts); free(t.slots);
+    return ORC_ENOMEM;
+  }
+  for (uint64_t i = 0; i < m; i++) {
+    (*keys)[2 * i] = (uint64_t)(t.slots[i].a >> 64);
+    (*keys)[2 * i + 1] = (uint64_t)t.slots[i].a;
+    (*counts)[i] = t.slots[i].count;
+  }
+  *n_nodes = m;
+  free(t.slots);
+  return ORC_OK;
+}
+
+void orc_free(void *p) { free(p); }
+
+/* ------------------------------------------------------------------ */
 /* one partition of the edges, for the multi-core CPU baseline          */
 /* ------------------------------------------------------------------ */
 

@@ -319,3 +319,54 @@ def test_edge_partitions_add_up_to_the_graph():
         res = [oracle.edges_in_partition(reads, lengths, 15, p, parts) for p in range(parts)]
         assert sum(d for d, _ in res) == g.n_edges
         assert sum(i for _, i in res) == inst
+
+
+# ---------------------------------------------------------------------------
+# node multiplicities (the k-mer counting of STEP-2 applied to nodes; the
+# k-mer occurrence table behind VELVET's roadmap, Section 7)
+# ---------------------------------------------------------------------------
+
+def node_counts_by_strings(reads: list[str], k: int) -> dict[str, int]:
+    """Occurrences of each canonical k-mer over the forward reads, by strings."""
+    c: dict[str, int] = {}
+    for r in reads:
+        for j in range(len(r) - k + 1):
+            s = sm.canonical(r[j:j + k])
+            c[s] = c.get(s, 0) + 1
+    return c
+
+
+def oracle_node_counts(reads: list[str], k: int) -> dict[str, int]:
+    lengths = np.array([len(r) for r in reads], dtype=np.uint32)
+    keys, counts = oracle.node_multiplicities("".join(reads).encode(), lengths, k)
+    vals = [(int(h) << 64) | int(l) for h, l in keys]
+    assert vals == sorted(vals) and len(set(vals)) == len(vals)
+    return {kmer_str(v, k): int(c) for v, c in zip(vals, counts)}
+
+
+def test_node_multiplicities_worked_example():
+    """By hand: ACGT at k = 3 reads ACG and CGT = rc(ACG), so ACG twice;
+    AAGTA reads AAG, AGT (canonical ACT, its reverse complement) and GTA."""
+    assert oracle_node_counts(["ACGT", "AAGTA"], 3) == {"ACG": 2, "AAG": 1, "ACT": 1, "GTA": 1}
+
+
+@pytest.mark.parametrize("k,L", [(1, 6), (3, 6), (5, 6)])
+def test_node_multiplicities_exhaustive_single_reads(k, L):
+    for t in itertools.product("ACGT", repeat=L):
+        r = "".join(t)
+        assert oracle_node_counts([r], k) == node_counts_by_strings([r], k), r
+
+
+@pytest.mark.parametrize("k", [3, 5, 7, 11])
+def test_node_multiplicities_random_read_sets(k):
+    """Random read sets with reads shorter than k, of exactly k and longer;
+    also the closed form (each read of length L >= k holds L - k + 1 k-mers)
+    and the node set of the graph."""
+    rng = np.random.default_rng(k)
+    for _ in range(30):
+        reads = ["".join("ACGT"[c] for c in rng.integers(0, 4, size=int(rng.integers(0, 25))))
+                 for _ in range(int(rng.integers(1, 12)))]
+        got = oracle_node_counts(reads, k)
+        assert got == node_counts_by_strings(reads, k)
+        assert sum(got.values()) == sum(max(0, len(r) - k + 1) for r in reads)
+        assert sorted(got) == graph_strings(build(reads, k))[0]
