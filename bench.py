@@ -58,6 +58,8 @@ def parse():
                     help="1: the edge keys' local pass counts copies in a hash table before sorting")
     ap.add_argument("--partition-first", type=int, default=1, choices=(0, 1),
                     help="1: the edge keys' first global pass is an unordered partition")
+    ap.add_argument("--node-mult", action="store_true",
+                    help="the build also counts node multiplicities (an extra k-mer sort)")
     ap.add_argument("--sort-variant", default="", help="a,b,c,d: fixed radix variants per key kind instead "
                                                         "of the autotuner (profiling captures)")
     return ap.parse_args()
@@ -393,6 +395,7 @@ def run_ours(args):
             dbg.dbg_sort_variant_set(ctx, kd, args.local_variant)
     dbg.dbg_sort_count_first_set(ctx, bool(args.count_first))
     dbg.dbg_sort_partition_first_set(ctx, bool(args.partition_first))
+    dbg.dbg_node_mult_set(ctx, bool(args.node_mult))
     variants = {kd: dbg.dbg_sort_variant_name(kd, dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(6)}
     for _ in range(args.warmup):
         step()
@@ -499,7 +502,7 @@ def run_ours(args):
                        "l2": "inputs and sort buffers far larger than L2 (1.5 GB reads, 8.3 GB keys)",
                        "parallelism": f"replicas x{ws}",
                        "sort_variants": variants, "count_first": bool(args.count_first),
-                       "partition_first": bool(args.partition_first),
+                       "partition_first": bool(args.partition_first), "node_mult": bool(args.node_mult),
                        "autotune_pass_ms": {kd: [round(x, 4) for x in v] for kd, v in tune_ms.items()}},
             "roofline": {"bound": "hbm",
                          "kernel": f"{'k_onesweep_p' if 'persistent' in (variants.get(ekind) or '') else 'k_onesweep'}"

@@ -134,6 +134,17 @@ dbg_status dbg_graph_nodes(const dbg_graph *g, uint64_t *keys);
 dbg_status dbg_graph_edges(const dbg_graph *g, uint64_t *keys, uint32_t *src, uint32_t *dst,
                            uint8_t *orient, uint32_t *mult);
 
+/* Node multiplicities: for every node (ascending key order, as
+ * dbg_graph_nodes), the number of positions of the forward reads whose
+ * k-mer is the node's k-mer or its reverse complement -- STEP-2's counting
+ * applied to k-mers, the k-mer occurrence table from which VELVET's roadmap
+ * is drawn (Section 7).  They are counted by dbg_build when the context's
+ * switch is on (dbg_node_mult_set; off by default: an extra k-mer sort),
+ * not by dbg_build_bucketed.  mult: num_nodes uint32_t.  DBG_EINVAL if the
+ * graph was built without them. */
+dbg_status dbg_node_mult_set(dbg_ctx *ctx, int on);
+dbg_status dbg_graph_node_mult(const dbg_graph *g, uint32_t *mult);
+
 /* The same copies, started on a stream of the graph's own and returned from
  * at once, so that they overlap later work on the GPU (e.g. dbg_compact of
  * the same graph, which only reads it).  Host buffers should be pinned for
@@ -379,7 +390,9 @@ dbg_status dbg_selftest_wait(dbg_ctx *ctx, uint32_t spin_limit);
  * adjacency, copies, compact_links, compact_rank, compact_cycles,
  * compact_output, local_sort_edges, local_sort_nodes, partition_edges
  * (the edge keys' first global pass when it is a partition; sort_edges
- * then holds their stable onesweep passes).
+ * then holds their stable onesweep passes), node_mult (the k-mer counting
+ * for node multiplicities, whose sort passes count under the edge-key
+ * sort stages).
  * -------------------------------------------------------------------- */
 typedef struct dbg_stage_stat {
   char name[24];

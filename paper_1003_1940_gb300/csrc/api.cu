@@ -107,7 +107,7 @@ dbg_status check_device_error(dbg_ctx *ctx) {
 const char *const kStageNames[ST_COUNT] = {
     "offsets", "pack", "emit", "sort_edges", "rle", "endpoints", "sort_nodes", "node_ids",
     "adjacency", "copies", "compact_links", "compact_rank", "compact_cycles", "compact_output",
-    "local_sort_edges", "local_sort_nodes", "partition_edges"};
+    "local_sort_edges", "local_sort_nodes", "partition_edges", "node_mult"};
 
 static cudaEvent_t pool_event(dbg_ctx *ctx) {
   if (!ctx->ev_pool.empty()) {
@@ -368,7 +368,7 @@ dbg_status dbg_build(dbg_ctx *ctx, const char *reads, const uint32_t *lengths, u
     st = k <= 31 ? build_graph_u64(ctx, in, g) : build_graph_u128(ctx, in, g);
   }
   for (DevBuf *b : {&g->node_keys, &g->edge_keys, &g->src, &g->dst, &g->orient, &g->mult, &g->row_ptr,
-                    &g->adj_nbr, &g->adj_edge, &g->adj_role})
+                    &g->adj_nbr, &g->adj_edge, &g->adj_role, &g->node_mult})
     rebind(*b);
   d_len.release();
   cudaStreamSynchronize(s);
@@ -508,6 +508,16 @@ dbg_status dbg_graph_edges(const dbg_graph *g, uint64_t *keys, uint32_t *src, ui
   return DBG_OK;
 }
 
+dbg_status dbg_graph_node_mult(const dbg_graph *g, uint32_t *mult) {
+  if (!g) return DBG_EINVAL;
+  if (!g->node_mult.p) {
+    set_error("node multiplicities were not counted for this graph (dbg_node_mult_set before dbg_build)");
+    return DBG_EINVAL;
+  }
+  if (g->num_nodes && !mult) return DBG_EINVAL;
+  return copy_plain(g->device, mult, g->node_mult.p, g->num_nodes * sizeof(uint32_t));
+}
+
 dbg_status dbg_graph_edges_async(dbg_graph *g, uint64_t *keys, uint32_t *src, uint32_t *dst, uint8_t *orient,
                                  uint32_t *mult) {
   if (!g) return DBG_EINVAL;
@@ -639,6 +649,15 @@ dbg_status dbg_sort_count_first_set(dbg_ctx *ctx, int on) {
 uint64_t dbg_sort_fallbacks(const dbg_ctx *ctx) { return ctx ? ctx->local_sort_fallbacks : 0; }
 
 uint64_t dbg_sort_count_overflows(const dbg_ctx *ctx) { return ctx ? ctx->count_overflow_tiles : 0; }
+
+dbg_status dbg_node_mult_set(dbg_ctx *ctx, int on) {
+  if (!ctx) {
+    set_error("null context");
+    return DBG_EINVAL;
+  }
+  ctx->node_mult = on ? 1 : 0;
+  return DBG_OK;
+}
 
 dbg_status dbg_sort_partition_first_set(dbg_ctx *ctx, int on) {
   if (!ctx) {

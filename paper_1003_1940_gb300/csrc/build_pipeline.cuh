@@ -569,6 +569,69 @@ dbg_status assign_node_ids(dbg_ctx *ctx, const K *rk, const uint32_t *rv, uint64
   return DBG_OK;
 }
 
+// Node multiplicities: the k-mers of the reads (each read of length L >= k
+// holds L - k + 1), emitted, sorted and counted like STEP-2's edge keys.  The
+// distinct canonical k-mers of the reads of length >= k are exactly the
+// nodes, in the same ascending order, so counts[i] belongs to node i; *Vk =
+// their number, which the caller checks against |V|.
+template <class K>
+dbg_status count_node_kmers(dbg_ctx *ctx, const DevBuf &packed, const DevBuf &base_off, const uint32_t *d_lengths,
+                            uint64_t n, uint64_t N, uint32_t k, unsigned long long *d_hist,
+                            uint64_t *d_digit_base, DevBuf &counts, uint64_t *Vk) {
+  cudaStream_t s = ctx->stream;
+  *Vk = 0;
+  if (n == 0) return DBG_OK;
+  // the k-mers number at most N + n (N edge instances, one more k-mer per
+  // read); the offsets' scan keeps 32-bit totals
+  if (N + n > 0xffffffffull) {
+    set_error("%llu edge instances and %llu reads: too many k-mers to count in one build",
+              (unsigned long long)N, (unsigned long long)n);
+    return DBG_EOVERFLOW;
+  }
+  DevBuf per, koff;
+  DBG_TRY(alloc_buf(ctx, per, n * sizeof(uint32_t)));
+  DBG_TRY(alloc_buf(ctx, koff, (n + 1) * sizeof(uint64_t)));
+  DBG_LAUNCH(ctx, ST_NODE_MULT, 8.0 * n,
+             k_kmer_counts<<<grid_for(n, 256), 256, 0, s>>>(d_lengths, n, k, per.as<uint32_t>()));
+  uint32_t low32 = 0;
+  DBG_TRY(scan_u32(ctx, per.as<uint32_t>(), n, koff.as<uint64_t>(), &low32, ST_NODE_MULT));
+  uint64_t M = 0;
+  DBG_TRY(read_small(ctx, koff.as<uint64_t>() + n, sizeof(uint64_t), &M));
+  if (M == 0) return DBG_OK;
+  const int kbits = 2 * (int)k;
+  const int passes = passes_for_bits(kbits);
+  const int p0 = ctx->hybrid_sort ? hybrid_first_pass<K>(M, kbits) : 0;
+  DevBuf ka, kb, headpos;
+  DBG_TRY(alloc_buf(ctx, ka, M * sizeof(K)));
+  DBG_TRY(alloc_buf(ctx, kb, M * sizeof(K)));
+  DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
+  // emitting with k - 1 gives windows of k bases at the k-mer offsets
+  DBG_LAUNCH(ctx, ST_NODE_MULT, 8.0 * n + (double)M * sizeof(K),
+             k_emit<K><<<(unsigned)std::min<uint64_t>(grid_for(n, EMIT_BLOCK / 32), 152ull * 64), EMIT_BLOCK, 0, s>>>(
+                 packed.as<uint64_t>(), base_off.as<uint64_t>(), koff.as<uint64_t>(), n, k - 1, ka.as<K>(), p0,
+                 passes, d_hist, nullptr));
+  DBG_CUDA_TRY(cudaGetLastError());
+  K *kp = ka.as<K>(), *alt = kb.as<K>();
+  uint32_t *vn = nullptr, *van = nullptr;
+  uint64_t D = 0;
+  if (p0 > 0) {
+    DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, M, kbits, d_hist, d_digit_base, p0)));
+    DBG_TRY(seg_rle<K>(ctx, kp, alt, M, RADIX_BITS * p0, kbits, counts, &D));
+  } else {
+    DBG_TRY(alloc_buf(ctx, headpos, (M + 1) * sizeof(uint32_t)));
+    DBG_TRY((radix_sort<K, false>(ctx, &kp, &alt, &vn, &van, M, kbits, d_hist, d_digit_base)));
+    DBG_TRY(run_length_reduce<K>(ctx, kp, M, alt, headpos.as<uint32_t>(), &D));
+    DBG_TRY(alloc_buf(ctx, counts, std::max<uint64_t>(1, D) * sizeof(uint32_t)));
+    DBG_LAUNCH(ctx, ST_NODE_MULT, 8.0 * D,
+               k_counts_from_heads<<<grid_for(D, 256), 256, 0, s>>>(headpos.as<uint32_t>(), D,
+                                                                   counts.as<uint32_t>()));
+  }
+  DBG_CUDA_TRY(cudaGetLastError());
+  DBG_TRY(check_device_error(ctx));
+  *Vk = D;
+  return DBG_OK;
+}
+
 template <class K>
 dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   cudaStream_t s = ctx->stream;
@@ -713,6 +776,13 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   }
   g->num_edges = E;
 
+  // ---- node multiplicities (optional), while the packed reads are here ----
+  DevBuf node_counts;
+  uint64_t Vk = 0;
+  if (ctx->node_mult)
+    DBG_TRY(count_node_kmers<K>(ctx, packed, base_off, in.d_lengths, n, N, k, d_hist, d_digit_base, node_counts,
+                                &Vk));
+
   // ---- K5 edge ends + records of reads of length k ----
   const uint64_t R = 2 * E + I;
   const int nbits = 2 * (int)k;
@@ -776,6 +846,15 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     }
   }
   g->num_nodes = V;
+  if (ctx->node_mult) {
+    if (Vk != V) {
+      set_error("node multiplicities: %llu distinct k-mers for %llu nodes", (unsigned long long)Vk,
+                (unsigned long long)V);
+      return DBG_ECUDA;
+    }
+    if (V == 0) DBG_TRY(alloc_buf(ctx, node_counts, sizeof(uint32_t)));
+    g->node_mult = std::move(node_counts);
+  }
   DBG_TRY(alloc_buf(ctx, g->node_keys, std::max<uint64_t>(1, V) * sizeof(K)));
   DBG_TRY(alloc_buf(ctx, g->row_ptr, (V + 1) * sizeof(uint64_t)));
   if (V > 0) {

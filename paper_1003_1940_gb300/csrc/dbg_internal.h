@@ -53,7 +53,7 @@ struct DevBuf {
 enum Stage {
   ST_OFFSETS, ST_PACK, ST_EMIT, ST_SORT_EDGES, ST_RLE, ST_ENDPOINTS, ST_SORT_NODES, ST_NODE_IDS,
   ST_ADJACENCY, ST_COPIES, ST_COMPACT_LINKS, ST_COMPACT_RANK, ST_COMPACT_CYCLES, ST_COMPACT_OUTPUT,
-  ST_LOCAL_SORT_EDGES, ST_LOCAL_SORT_NODES, ST_PARTITION_EDGES, ST_COUNT
+  ST_LOCAL_SORT_EDGES, ST_LOCAL_SORT_NODES, ST_PARTITION_EDGES, ST_NODE_MULT, ST_COUNT
 };
 extern const char *const kStageNames[ST_COUNT];
 
@@ -79,6 +79,7 @@ struct dbg_ctx {
   int hybrid_sort = 1;                 // high digits globally + local sort of group-aligned tiles
   int count_first = 1;                 // local pass of the edge keys counts copies before sorting
   int partition_first = 1;             // first global pass of keys without payload: unordered partition
+  int node_mult = 0;                   // dbg_build also counts every node's k-mer occurrences
   uint64_t count_overflow_tiles = 0;  // count-first tiles whose keys did not fit the hash table
   uint64_t local_sort_fallbacks = 0;   // local sorts that met a group longer than their window
   int num_sms = 0;
@@ -107,6 +108,7 @@ struct dbg_graph {
   int device = 0;
   uint32_t edge_buckets = 1, node_buckets = 1;  // key ranges used (bucket path)
   dbg::DevBuf node_keys, edge_keys, src, dst, orient, mult, row_ptr, adj_nbr, adj_edge, adj_role;
+  dbg::DevBuf node_mult;  // k-mer occurrences per node, when the build counted them
   cudaStream_t copy_stream = nullptr;  // read-backs started by dbg_graph_edges_async
 };
 

@@ -316,6 +316,21 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict_
     if (s_hist[i]) atomicAdd(hist + i, (unsigned long long)s_hist[i]);
 }
 
+// Node multiplicities: the k-mers of read r (L >= k of them: L - k + 1) and,
+// after their sort and run-length reduce, each distinct k-mer's count from
+// the run heads (headpos[E] = the number of k-mers).
+static __global__ void k_kmer_counts(const uint32_t *__restrict__ len, uint64_t n, uint32_t k,
+                                     uint32_t *__restrict__ out) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x)
+    out[r] = len[r] >= k ? len[r] - k + 1 : 0u;
+}
+
+static __global__ void k_counts_from_heads(const uint32_t *__restrict__ headpos, uint64_t E,
+                                           uint32_t *__restrict__ counts) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += (uint64_t)gridDim.x * blockDim.x)
+    counts[i] = headpos[i + 1] - headpos[i];
+}
+
 // Host reads arrive in chunks of `chunk` bases; once chunks 0..c are packed,
 // the reads that end in them can be emitted.  bound[c + 1] = the first key
 // of the first read that does not (edge_off of the number of reads whose

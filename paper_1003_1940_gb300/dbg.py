@@ -71,6 +71,8 @@ _SIGNATURES = [
     ("dbg_graph_nodes", ctypes.c_int, [_P, _P]),
     ("dbg_graph_edges", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     ("dbg_graph_edges_async", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("dbg_node_mult_set", ctypes.c_int, [_P, ctypes.c_int]),
+    ("dbg_graph_node_mult", ctypes.c_int, [_P, _P]),
     ("dbg_graph_wait", ctypes.c_int, [_P]),
     ("dbg_graph_csr", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("dbg_graph_device_view", ctypes.c_int, [_P, _P]),
@@ -297,6 +299,17 @@ def dbg_graph_edges(g: Graph) -> dict:
     _check(_lib.dbg_graph_edges(g.handle, *(ctypes.c_void_p(a.ctypes.data) for a in (keys, src, dst, orient, mult))),
            "dbg_graph_edges")
     return {"keys": keys.reshape(-1, W), "src": src, "dst": dst, "orient": orient, "mult": mult}
+
+
+def dbg_node_mult_set(ctx: Context, on: bool) -> None:
+    _check(_lib.dbg_node_mult_set(ctx.handle, 1 if on else 0), "dbg_node_mult_set")
+
+
+def dbg_graph_node_mult(g: Graph) -> np.ndarray:
+    """k-mer occurrences per node (the build must have counted them)."""
+    out = _np_out(dbg_graph_num_nodes(g), np.uint32)
+    _check(_lib.dbg_graph_node_mult(g.handle, ctypes.c_void_p(out.ctypes.data)), "dbg_graph_node_mult")
+    return out
 
 
 def dbg_graph_edges_async(g: Graph, keys: int | None = None, src: int | None = None, dst: int | None = None,
