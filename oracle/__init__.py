@@ -69,6 +69,19 @@ class _Unitigs(ctypes.Structure):
     ]
 
 
+class _Range(ctypes.Structure):
+    _fields_ = [
+        ("n_edges", ctypes.c_uint64),
+        ("n_nodes", ctypes.c_uint64),
+        ("edge_keys", ctypes.POINTER(ctypes.c_uint64)),
+        ("src_keys", ctypes.POINTER(ctypes.c_uint64)),
+        ("dst_keys", ctypes.POINTER(ctypes.c_uint64)),
+        ("orient", ctypes.POINTER(ctypes.c_uint8)),
+        ("mult", ctypes.POINTER(ctypes.c_uint64)),
+        ("node_keys", ctypes.POINTER(ctypes.c_uint64)),
+    ]
+
+
 def _load():
     global _lib
     with _lock:
@@ -99,6 +112,12 @@ def _load():
             lib.orc_edges_in_partition.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                                    ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                    ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_graph_range.restype = ctypes.c_int
+            lib.orc_graph_range.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.POINTER(_Range))]
+            lib.orc_range_free.restype = None
+            lib.orc_range_free.argtypes = [ctypes.POINTER(_Range)]
             _lib = lib
     return _lib
 
@@ -266,3 +285,42 @@ def node_multiplicities(reads, lengths, k: int) -> tuple[np.ndarray, np.ndarray]
         lib.orc_free(ctypes.cast(kp, ctypes.c_void_p))
         lib.orc_free(ctypes.cast(cp, ctypes.c_void_p))
     return keys, counts
+
+
+def _bound_words(v: int) -> np.ndarray:
+    if not 0 <= v < (1 << 128):
+        raise ValueError("key bound out of range")
+    return np.array([v >> 64, v & ((1 << 64) - 1)], dtype=np.uint64)
+
+
+def graph_range(reads, lengths, k: int, edge_range: tuple[int, int],
+                node_range: tuple[int, int]) -> dict:
+    """The slice of the oracle graph whose keys lie in the given inclusive
+    ranges: edges with lo <= canonical (k+1)-mer <= hi, ascending, each with
+    the keys of its src and dst nodes, its orientation and multiplicity; and
+    the nodes (canonical k-mers) with lo <= key <= hi, ascending.  Keys are
+    (n, 2) high/low u64 words.  Concatenating the slices of consecutive
+    ranges gives the node and edge lists of ``build_graph``."""
+    lib = _load()
+    reads, lengths = _as_reads(reads, lengths)
+    b = [_bound_words(x) for x in (*edge_range, *node_range)]
+    out = ctypes.POINTER(_Range)()
+    rc = lib.orc_graph_range(reads.ctypes.data, lengths.ctypes.data, len(lengths), k,
+                             b[0].ctypes.data, b[1].ctypes.data, b[2].ctypes.data, b[3].ctypes.data,
+                             ctypes.byref(out))
+    if rc != ORC_OK:
+        raise OracleError(rc, "orc_graph_range")
+    try:
+        r = out.contents
+        ne, nv = int(r.n_edges), int(r.n_nodes)
+        res = {
+            "edge_keys": _copy(r.edge_keys, 2 * ne, np.uint64).reshape(ne, 2),
+            "src_keys": _copy(r.src_keys, 2 * ne, np.uint64).reshape(ne, 2),
+            "dst_keys": _copy(r.dst_keys, 2 * ne, np.uint64).reshape(ne, 2),
+            "orient": _copy(r.orient, ne, np.uint8),
+            "mult": _copy(r.mult, ne, np.uint64),
+            "node_keys": _copy(r.node_keys, 2 * nv, np.uint64).reshape(nv, 2),
+        }
+    finally:
+        lib.orc_range_free(out)
+    return res

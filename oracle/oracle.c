@@ -513,6 +513,150 @@ int orc_edges_in_partition(const char *reads, const uint32_t *lengths, uint64_t 
 }
 
 /* ------------------------------------------------------------------ */
+/* one key range of the graph, for inputs too large to build at once    */
+/* ------------------------------------------------------------------ */
+
+/* The slice of orc_build's graph whose keys lie in given ranges: the edges
+ * (Section 2, named and counted exactly as orc_build does) whose canonical
+ * (k+1)-mer key z satisfies elo <= z <= ehi, and the nodes (canonical k-mers
+ * of the forward reads, Section 2) whose key x satisfies nlo <= x <= nhi.
+ * Bounds are inclusive (high, low) word pairs.  An edge is listed with the
+ * keys of its two end nodes instead of their IDs (a node's ID is its rank
+ * among ALL nodes, which one slice does not see).  Edges come out by
+ * ascending key, nodes ascending, so cutting the key spaces into ranges and
+ * concatenating the slices in range order gives orc_build's node and edge
+ * lists.  Every read is scanned; only keys in range are kept. */
+typedef struct {
+  uint64_t n_edges, n_nodes;
+  uint64_t *edge_keys;  /* 2 words per edge: canonical (k+1)-mer */
+  uint64_t *src_keys;   /* 2 words per edge: node key at the src end */
+  uint64_t *dst_keys;   /* 2 words per edge: node key at the dst end */
+  uint8_t *orient;      /* (o1 << 1) | o2 */
+  uint64_t *mult;       /* occurrences over the forward reads */
+  uint64_t *node_keys;  /* 2 words per node */
+} orc_range;
+
+void orc_range_free(orc_range *r) {
+  if (!r) return;
+  free(r->edge_keys); free(r->src_keys); free(r->dst_keys);
+  free(r->orient); free(r->mult); free(r->node_keys);
+  free(r);
+}
+
+static u128 words_u128(const uint64_t *w) { return ((u128)w[0] << 64) | w[1]; }
+
+int orc_graph_range(const char *reads, const uint32_t *lengths, uint64_t n, uint32_t k, const uint64_t *elo,
+                    const uint64_t *ehi, const uint64_t *nlo, const uint64_t *nhi, orc_range **out) {
+  if (!out || !elo || !ehi || !nlo || !nhi) return ORC_EINVAL;
+  *out = NULL;
+  if (k < 1 || k > 63 || (k % 2) == 0) return ORC_EINVAL;
+  if (n > 0 && (!reads || !lengths)) return ORC_EINVAL;
+  const int K = (int)k, M = K + 1;
+  const u128 e0 = words_u128(elo), e1 = words_u128(ehi), n0 = words_u128(nlo), n1 = words_u128(nhi);
+  table_t nodes_t, edges_t;
+  if (table_init(&nodes_t, 1024) != ORC_OK) return ORC_ENOMEM;
+  if (table_init(&edges_t, 1024) != ORC_OK) { free(nodes_t.slots); return ORC_ENOMEM; }
+  int rc = ORC_OK;
+  /* the k-base and (k+1)-base windows ending at base j, and their reverse
+   * complements, updated one base at a time */
+  const u128 kmask = ((((u128)1) << (2 * K)) - 1);
+  const u128 mmask = (M == 64) ? ~(u128)0 : ((((u128)1) << (2 * M)) - 1);
+  const char *read = reads;
+  for (uint64_t r = 0; r < n && rc == ORC_OK; r++) {
+    int64_t L = lengths[r];
+    u128 kf = 0, kr = 0, mf = 0, mr = 0;
+    for (int64_t j = 0; j < L; j++) {
+      int c = base_code(read[j]);
+      if (c < 0) { rc = ORC_EINVAL; break; }
+      kf = ((kf << 2) | (u128)c) & kmask;
+      kr = (kr >> 2) | ((u128)(3 - c) << (2 * (K - 1)));
+      mf = ((mf << 2) | (u128)c) & mmask;
+      mr = (mr >> 2) | ((u128)(3 - c) << (2 * (M - 1)));
+      if (j + 1 >= K) {
+        /* node: the canonical k-mer read[j-K+1 .. j] */
+        u128 x = kr < kf ? kr : kf;
+        if (x >= n0 && x <= n1 && !table_find(&nodes_t, x, 0, 0, 1)) { rc = ORC_ENOMEM; break; }
+      }
+      if (j + 1 >= M) {
+        /* edge: the k-mer pair read[j-K .. j-1], read[j-K+1 .. j] */
+        u128 z = mr < mf ? mr : mf;
+        if (z < e0 || z > e1) continue;
+        const int64_t j0 = j + 1 - M;
+        u128 x = mer_value(read + j0, K), y = mer_value(read + j0 + 1, K);
+        u128 xh = mer_canonical(x, K), yh = mer_canonical(y, K);
+        int o1 = (x != xh), o2 = (y != yh);
+        u128 s = xh, d = yh;
+        int a = o1, b = o2;
+        if (tuple_less(yh, xh, !o2, !o1, xh, yh, o1, o2)) { s = yh; d = xh; a = !o2; b = !o1; }
+        slot_t *e = table_find(&edges_t, s, d, (uint8_t)((a << 1) | b), 1);
+        if (!e) { rc = ORC_ENOMEM; break; }
+        e->count++;
+      }
+    }
+    read += L;
+  }
+  orc_range *res = NULL;
+  edge_rec *edges = NULL;
+  u128 *nodes = NULL;
+  if (rc == ORC_OK) {
+    res = (orc_range *)calloc(1, sizeof(orc_range));
+    edges = (edge_rec *)malloc((edges_t.size + 1) * sizeof(edge_rec));
+    nodes = (u128 *)malloc((nodes_t.size + 1) * sizeof(u128));
+    if (!res || !edges || !nodes) rc = ORC_ENOMEM;
+  }
+  if (rc == ORC_OK) {
+    uint64_t ne = 0, nv = 0;
+    for (uint64_t i = 0; i < edges_t.cap && rc == ORC_OK; i++) {
+      slot_t *s = &edges_t.slots[i];
+      if (!s->used) continue;
+      edge_rec *e = &edges[ne++];
+      e->src = s->a; e->dst = s->b; e->o1 = s->tag >> 1; e->o2 = s->tag & 1; e->count = s->count;
+      /* the key is the canonical form of the (k+1)-mer the edge spells */
+      u128 x = e->o1 ? mer_revcomp(e->src, K) : e->src;
+      u128 y = e->o2 ? mer_revcomp(e->dst, K) : e->dst;
+      if ((x & ((((u128)1) << (2 * (K - 1))) - 1)) != (y >> 2)) { rc = ORC_EINTERNAL; break; }
+      e->key = mer_canonical((x << 2) | (y & 3), M);
+    }
+    for (uint64_t i = 0; i < nodes_t.cap; i++)
+      if (nodes_t.slots[i].used) nodes[nv++] = nodes_t.slots[i].a;
+    res->n_edges = ne;
+    res->n_nodes = nv;
+  }
+  free(nodes_t.slots);
+  free(edges_t.slots);
+  if (rc == ORC_OK) {
+    uint64_t ne = res->n_edges, nv = res->n_nodes;
+    qsort(edges, ne, sizeof(edge_rec), cmp_edge_by_key);
+    qsort(nodes, nv, sizeof(u128), cmp_node);
+    res->edge_keys = (uint64_t *)malloc((2 * ne + 1) * sizeof(uint64_t));
+    res->src_keys = (uint64_t *)malloc((2 * ne + 1) * sizeof(uint64_t));
+    res->dst_keys = (uint64_t *)malloc((2 * ne + 1) * sizeof(uint64_t));
+    res->orient = (uint8_t *)malloc(ne + 1);
+    res->mult = (uint64_t *)malloc((ne + 1) * sizeof(uint64_t));
+    res->node_keys = (uint64_t *)malloc((2 * nv + 1) * sizeof(uint64_t));
+    if (!res->edge_keys || !res->src_keys || !res->dst_keys || !res->orient || !res->mult || !res->node_keys)
+      rc = ORC_ENOMEM;
+    for (uint64_t i = 0; rc == ORC_OK && i < ne; i++) {
+      const edge_rec *e = &edges[i];
+      res->edge_keys[2 * i] = (uint64_t)(e->key >> 64); res->edge_keys[2 * i + 1] = (uint64_t)e->key;
+      res->src_keys[2 * i] = (uint64_t)(e->src >> 64); res->src_keys[2 * i + 1] = (uint64_t)e->src;
+      res->dst_keys[2 * i] = (uint64_t)(e->dst >> 64); res->dst_keys[2 * i + 1] = (uint64_t)e->dst;
+      res->orient[i] = (uint8_t)((e->o1 << 1) | e->o2);
+      res->mult[i] = e->count;
+    }
+    for (uint64_t v = 0; rc == ORC_OK && v < nv; v++) {
+      res->node_keys[2 * v] = (uint64_t)(nodes[v] >> 64);
+      res->node_keys[2 * v + 1] = (uint64_t)nodes[v];
+    }
+  }
+  free(edges);
+  free(nodes);
+  if (rc != ORC_OK) { orc_range_free(res); return rc; }
+  *out = res;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* chain compaction by walking the chains (Section 6)                   */
 /* ------------------------------------------------------------------ */
 

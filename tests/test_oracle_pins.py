@@ -370,3 +370,83 @@ def test_node_multiplicities_random_read_sets(k):
         assert got == node_counts_by_strings(reads, k)
         assert sum(got.values()) == sum(max(0, len(r) - k + 1) for r in reads)
         assert sorted(got) == graph_strings(build(reads, k))[0]
+
+
+# ---------------------------------------------------------------------------
+# key-range slices of the graph (the unit of work of the full-size parity
+# tests: one process per key range, every read scanned)
+# ---------------------------------------------------------------------------
+
+def range_slices(reads, lengths, k, cuts_e, cuts_n):
+    """Concatenated slices over the ranges [c_i, c_{i+1} - 1] (edge and node
+    ranges cut independently; (1, 0) is an empty range)."""
+    ep = [oracle.graph_range(reads, lengths, k, (a, b - 1), (1, 0)) for a, b in zip(cuts_e[:-1], cuts_e[1:])]
+    np_ = [oracle.graph_range(reads, lengths, k, (1, 0), (a, b - 1)) for a, b in zip(cuts_n[:-1], cuts_n[1:])]
+    out = {f: np.concatenate([p[f] for p in ep]) for f in ep[0] if f != "node_keys"}
+    out["node_keys"] = np.concatenate([p["node_keys"] for p in np_])
+    return out
+
+
+def random_cuts(rng, bits, count):
+    inner = sorted({int(rng.integers(0, 1 << 62)) << max(0, bits - 62) >> max(0, 62 - bits)
+                    for _ in range(count)})
+    return [0] + [c for c in inner if 0 < c < (1 << bits)] + [1 << bits]
+
+
+@pytest.mark.parametrize("k,lo,hi", [(1, 2, 6), (5, 4, 30), (15, 10, 60), (31, 30, 90), (33, 30, 90),
+                                     (55, 50, 160), (63, 60, 160)])
+def test_graph_range_slices_make_up_the_graph(k, lo, hi):
+    """Slices over consecutive key ranges, concatenated in range order, give
+    orc_build's node list and its edge list: keys, the keys of both end
+    nodes (through orc_build's IDs), orientation and multiplicity."""
+    rng = np.random.default_rng(700 + k)
+    reads, lengths = readgen.random_reads(rng, 300, lo, hi, b"ACGT" if k > 3 else b"ACG")
+    g = oracle.build_graph(reads, lengths, k)
+    for count in (1, 5, 17):
+        s = range_slices(reads, lengths, k, random_cuts(rng, 2 * k + 2, count - 1),
+                         random_cuts(rng, 2 * k, count - 1))
+        np.testing.assert_array_equal(s["node_keys"], g.node_keys)
+        np.testing.assert_array_equal(s["edge_keys"], g.edge_keys)
+        np.testing.assert_array_equal(s["src_keys"], g.node_keys[g.src])
+        np.testing.assert_array_equal(s["dst_keys"], g.node_keys[g.dst])
+        np.testing.assert_array_equal(s["orient"], g.orient)
+        np.testing.assert_array_equal(s["mult"], g.mult.astype(np.uint64))
+    assert int(s["mult"].sum()) == int(np.maximum(lengths.astype(np.int64) - k, 0).sum())
+
+
+def test_graph_range_against_strings():
+    """A narrow slice equals the string model's edges and nodes whose
+    canonical strings fall in the range (lexicographic = integer order)."""
+    rng = np.random.default_rng(71)
+    k = 5
+    reads = ["".join(rng.choice(list("ACGT"), size=int(rng.integers(4, 30)))) for _ in range(40)]
+    lengths = np.array([len(r) for r in reads], dtype=np.uint32)
+    raw = "".join(reads).encode()
+    to_int = lambda s: int("".join("0123"["ACGT".index(c)] for c in s), 4)
+    want_edges = sm.edge_multiset(reads, k)
+    for lo_s, hi_s in (("AAAAAA", "CTTTTT"), ("CAGAAA", "GGGGGG"), ("TAAAAA", "TTTTTT")):
+        nlo, nhi = to_int(lo_s[:k]), to_int(hi_s[:k])
+        s = oracle.graph_range(raw, lengths, k, (to_int(lo_s), to_int(hi_s)), (nlo, nhi))
+        got_nodes = [kmer_str(int(h) << 64 | int(l), k) for h, l in s["node_keys"]]
+        assert got_nodes == [v for v in sm.nodes_of(reads, k) if lo_s[:k] <= v <= hi_s[:k]]
+        got = {}
+        for i in range(len(s["mult"])):
+            a = kmer_str(int(s["src_keys"][i, 1]), k)
+            b = kmer_str(int(s["dst_keys"][i, 1]), k)
+            o = int(s["orient"][i])
+            x, y = sm.oriented_kmer(a, o >> 1), sm.oriented_kmer(b, o & 1)
+            assert kmer_str(int(s["edge_keys"][i, 1]), k + 1) == sm.canonical(x + y[-1])
+            got[sm.edge_class(x, y)] = int(s["mult"][i])
+        want = {c: m for c, m in want_edges.items()
+                if lo_s <= sm.canonical(next(iter(c))[0] + next(iter(c))[1][-1]) <= hi_s}
+        assert got == want
+
+
+def test_graph_range_empty_and_bad_arguments():
+    reads, lengths = b"ACGTACGTTG", np.array([10], dtype=np.uint32)
+    s = oracle.graph_range(reads, lengths, 3, (5, 4), (9, 2))  # lo > hi: nothing
+    assert len(s["mult"]) == 0 and len(s["node_keys"]) == 0
+    with pytest.raises(oracle.OracleError):
+        oracle.graph_range(reads, lengths, 4, (0, 255), (0, 63))
+    with pytest.raises(oracle.OracleError):
+        oracle.graph_range(b"ACGTNCGTTG", lengths, 3, (0, 255), (0, 63))
