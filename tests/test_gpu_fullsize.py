@@ -13,6 +13,8 @@ import pytest
 
 import oracle
 import strings_model as sm
+from range_parity import compare_by_ranges
+from unitig_checks import check_unitigs_maximal
 from paper_1003_1940_gb300 import readgen
 
 pytestmark = pytest.mark.gpu
@@ -146,3 +148,28 @@ def test_full_size_compaction_invariants(built):
             km = s[i:i + K]
             assert kmer_int(sm.canonical(km)) == int(nk[int(x) >> 1])
             assert (km == sm.canonical(km)) == ((int(x) & 1) == 0)
+
+
+def test_full_size_against_oracle_by_key_ranges(built):
+    """Every node and every edge against the oracle, element by element: the
+    key spaces are cut into 64 ranges and each range's slice of the oracle
+    graph (one process per host core, every read scanned) is compared with
+    the same keys of the library's graph -- edge keys, both end nodes through
+    src / dst, orientation, multiplicity, node keys -- and the ranges together
+    hold all of the library's edges and nodes."""
+    dbg, ctx, g, reads, lengths = built
+    e = dbg.dbg_graph_edges(g)
+    arrays = {"edge_keys": e["keys"], "node_keys": dbg.dbg_graph_nodes(g), "src": e["src"], "dst": e["dst"],
+              "orient": e["orient"], "mult": e["mult"]}
+    res = compare_by_ranges(arrays, reads, lengths, K, parts=64)
+    assert res["edges"] == dbg.dbg_graph_num_edges(g) and res["nodes"] == dbg.dbg_graph_num_nodes(g)
+
+
+def test_full_size_compaction_is_maximal(built):
+    """Every pair of consecutive unitig nodes is joined by a mergeable edge
+    (distinct nodes, both end sides of degree 1) and every mergeable edge
+    joins such a pair: no unitig is split or could be extended."""
+    dbg, ctx, g, reads, lengths = built
+    u = dbg.dbg_compact(ctx, g)
+    res = check_unitigs_maximal(dbg, g, dbg.dbg_unitigs_get(u))
+    assert res["unitigs"] == dbg.dbg_unitigs_count(u) and res["mergeable"] > 0

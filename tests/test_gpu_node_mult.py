@@ -72,3 +72,17 @@ def test_node_multiplicities_global_sort_and_off(dbg):
     for key in with_counts:
         if isinstance(with_counts[key], np.ndarray):
             np.testing.assert_array_equal(with_counts[key], without[key], err_msg=key)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+@pytest.mark.parametrize("hybrid", [True, False])
+def test_node_multiplicities_smallest_k(dbg, k, hybrid):
+    """The smallest k: the k-mer windows are emitted by the edge-key kernel
+    run with k - 1 (0, 2 or 4 bases of overlap), on short random reads of
+    lengths 0 .. 12, with the hybrid and the all-global sort."""
+    rng = np.random.default_rng(950 + k)
+    reads, lengths = readgen.random_reads(rng, 3_000, 0, 12)
+    ctx = dbg.Context()
+    dbg.dbg_node_mult_set(ctx, True)
+    dbg.dbg_sort_hybrid_set(ctx, hybrid)
+    check(dbg, ctx, reads, lengths, k)
