@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--workload", choices=["large", "long_k", "tiny"], default="large")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and served measurements added to the default line (N = 1 only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle sample time")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (profiling captures only)")
     ap.add_argument("--mode", choices=["build", "batched", "served"], default="build",
@@ -440,23 +442,41 @@ def run_ours(args):
     if not args.no_e2e:
         h_reads = torch.from_numpy(reads).pin_memory()
         h_len = torch.from_numpy(lengths.view(np.int32)).pin_memory()
-        # the step's result read back: the edge multiplicities, into pinned
-        # host memory (sized for every edge instance, the upper bound)
-        h_mult = torch.empty(N, dtype=torch.int32).pin_memory()
+        # the step's whole result comes back into pinned host memory: node
+        # keys, edges, adjacency and unitigs.  Buffers are sized by the first
+        # (untimed) call; the same input gives the same sizes every step.
+        bufs = {}
         out_bytes = {}
 
-        def step_host():
+        def buf(name, n, dtype, alloc):
+            if alloc:
+                bufs[name] = torch.empty(max(1, n), dtype=dtype).pin_memory()
+            t = bufs[name]
+            assert t.numel() >= n, name
+            out_bytes[name] = n * t.element_size()
+            return t.data_ptr() if n else None
+
+        def step_host(alloc=False):
             g = dbg.dbg_build(ctx, h_reads, h_len, k)
-            e = dbg.dbg_graph_num_edges(g)
-            # the multiplicities come back while the graph is compacted
-            dbg.dbg_graph_edges_async(g, mult=h_mult.data_ptr() if e else None)
+            V, E, W = dbg.dbg_graph_num_nodes(g), dbg.dbg_graph_num_edges(g), dbg.dbg_graph_key_words(g)
+            # the graph comes back while it is compacted
+            dbg.dbg_graph_nodes_async(g, buf("nodes", V * W, torch.int64, alloc))
+            dbg.dbg_graph_edges_async(g, buf("keys", E * W, torch.int64, alloc), buf("src", E, torch.int32, alloc),
+                                      buf("dst", E, torch.int32, alloc), buf("orient", E, torch.uint8, alloc),
+                                      buf("mult", E, torch.int32, alloc))
+            dbg.dbg_graph_csr_async(g, buf("row_ptr", V + 1, torch.int64, alloc), buf("nbr", 2 * E, torch.int32, alloc),
+                                    buf("edge", 2 * E, torch.int32, alloc), buf("role", 2 * E, torch.uint8, alloc))
             u = dbg.dbg_compact(ctx, g)
+            U, T = dbg.dbg_unitigs_count(u), dbg.dbg_unitigs_total_bases(u)
+            dbg.dbg_unitigs_get_into(u, buf("u_node_off", U + 1, torch.int64, alloc),
+                                     buf("u_nodes", V, torch.int64, alloc),
+                                     buf("u_seq_off", U + 1, torch.int64, alloc),
+                                     buf("u_seq", T, torch.uint8, alloc), buf("u_circular", U, torch.uint8, alloc))
             dbg.dbg_graph_wait(g)
-            out_bytes["d2h"] = 4 * e
             u.free()
             g.free()
 
-        step_host()
+        step_host(alloc=True)
         barrier(ws)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -466,7 +486,24 @@ def run_ours(args):
         el = max_over_ranks(time.perf_counter() - t, ws)
         e2e = {"value": N * args.steps * ws / el, "unit": UNIT,
                "h2d_bytes_per_step": int(reads.nbytes + lengths.nbytes),
-               "d2h_bytes_per_step": int(out_bytes.get("d2h", 0))}
+               "d2h_bytes_per_step": int(sum(out_bytes.values())),
+               "d2h": "the whole result: node keys, edges (keys, src, dst, orient, mult), adjacency "
+                      "(row_ptr, neighbour, edge, role) and unitigs (offsets, nodes, sequence, circular flags)"}
+        bufs.clear()
+
+    # the batched and served workloads, beside the main line (one GPU only)
+    extras = {}
+    if rank == 0 and ws == 1 and not args.no_extras and args.workload == "large" and args.scale == 1.0 \
+            and not args.node_mult:
+        specs_b, sets_b = batched_inputs(args)
+        ctx_b = dbg.Context(device=local)
+        for kd in range(6):
+            dbg.dbg_sort_variant_set(ctx_b, kd, dbg.dbg_sort_variant_get(ctx, kd))
+        extras["batched"] = measure_batched(args, sets_b, ctx_b)
+        extras["served"] = measure_served(args, sets_b, ctx_b, d_reads, d_len, spec)
+        del sets_b
+        ctx_b.close()
+        torch.cuda.empty_cache()
 
     cpu = None
     if host.get("bound"):  # the host baselines use every core the process may use
@@ -522,6 +559,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": e2e,
+            **extras,
             "host": host,
             "cpu_baseline": cpu,
         }))
@@ -545,15 +583,12 @@ def batched_inputs(args):
     return specs, sets
 
 
-def run_batched(args):
+def measure_batched(args, sets, ctx):
+    """256 one-at-a-time dbg_build calls against one dbg_build_batch call
+    over the same read sets (device-resident inputs)."""
     import torch
-    from paper_1003_1940_gb300 import build_lib, dbg
-    build_lib.build()
-    dbg.load()
-    specs, sets = batched_inputs(args)
+    from paper_1003_1940_gb300 import dbg
     N = sum(s[3] for s in sets)
-    ctx = dbg.Context()
-    dbg.dbg_autotune(ctx)
     trip = [(r, l, k) for r, l, k, _ in sets]
     # warm-up: a few sets both ways
     for g in dbg.dbg_build_batch(ctx, trip[:8], workers=args.workers):
@@ -572,25 +607,37 @@ def run_batched(args):
     bat = time.perf_counter() - t
     for g in graphs:
         g.free()
-    print(json.dumps({
-        "metric": METRIC + " (batched vs one-at-a-time)", "value": N / bat, "unit": UNIT,
-        "one_at_a_time": N / one, "speedup": one / bat, "batched_s": bat, "one_at_a_time_s": one,
-        "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-        "config": {"workload": f"{len(sets)} read sets: genome log-uniform 10 kbp-5 Mbp, coverage U[10,60], "
-                               f"L in {{36,75,100,150}}, errors U[0,1%], k in {{21,31}}",
-                   "edge_instances": N, "workers": args.workers,
-                   "largest_set_instances": max(s[3] for s in sets)}}))
+    return {"value": N / bat, "unit": UNIT, "one_at_a_time": N / one, "speedup": one / bat, "batched_s": bat,
+            "one_at_a_time_s": one, "edge_instances": N, "sets": len(sets), "workers": args.workers,
+            "largest_set_instances": max(s[3] for s in sets),
+            "workload": f"{len(sets)} read sets: genome log-uniform 10 kbp-5 Mbp, coverage U[10,60], "
+                        f"L in {{36,75,100,150}}, errors U[0,1%], k in {{21,31}}"}
 
 
-def run_served(args):
-    import threading as th
-    import torch
+def run_batched(args):
     from paper_1003_1940_gb300 import build_lib, dbg
     build_lib.build()
     dbg.load()
     specs, sets = batched_inputs(args)
     ctx = dbg.Context()
     dbg.dbg_autotune(ctx)
+    res = measure_batched(args, sets, ctx)
+    print(json.dumps({
+        "metric": METRIC + " (batched vs one-at-a-time)", "value": res["value"], "unit": UNIT,
+        "one_at_a_time": res["one_at_a_time"], "speedup": res["speedup"], "batched_s": res["batched_s"],
+        "one_at_a_time_s": res["one_at_a_time_s"], "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": res["workload"], "edge_instances": res["edge_instances"], "workers": args.workers,
+                   "largest_set_instances": res["largest_set_instances"]}}))
+
+
+def measure_served(args, sets, ctx, big_r=None, big_l=None, big_spec=None):
+    """Request-server capacity (closed loop over the read sets), then
+    Poisson arrivals at 0.5, 0.8 and 1.0 of it: latency p50 / p99 and
+    throughput; at 0.8 one larger request (the large workload, on the key-
+    range bucket path) joins the stream."""
+    import threading as th
+    import torch
+    from paper_1003_1940_gb300 import dbg
     variants = [dbg.dbg_sort_variant_get(ctx, kd) for kd in range(4)]
     # capacity: a closed loop over the whole set list
     srv = dbg.Server(workers=args.workers, sort_variant=variants)
@@ -599,10 +646,11 @@ def run_served(args):
     for x in ts:
         dbg.dbg_poll(srv, x)[0].free()
     cap = len(sets) / (time.perf_counter() - t)
-    # one larger request: the 15 M-read workload, through the bucket path
-    big_spec = readgen.large_spec(args.scale)
-    big_r, big_l = readgen.generate(big_spec)
-    big_r, big_l = torch.from_numpy(big_r).cuda(), torch.from_numpy(big_l.view(np.int32)).cuda()
+    if big_spec is None:
+        # one larger request: the 15 M-read workload, through the bucket path
+        big_spec = readgen.large_spec(args.scale)
+        big_r, big_l = readgen.generate(big_spec)
+        big_r, big_l = torch.from_numpy(big_r).cuda(), torch.from_numpy(big_l.view(np.int32)).cuda()
     out = {}
     for load in (0.5, 0.8, 1.0):
         rate = load * cap
@@ -659,9 +707,19 @@ def run_served(args):
                           "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                           "big_request": big}
     srv.close()
-    print(json.dumps({"metric": METRIC + " (served, Poisson arrivals)", "unit": UNIT,
-                      "capacity_sets_per_s": cap, "loads": out, "workers": args.workers,
-                      "data": "synthetic", "n_gpus": 1}))
+    return {"unit": UNIT, "capacity_sets_per_s": cap, "loads": out, "workers": args.workers,
+            "requests_per_load": 2 * len(sets)}
+
+
+def run_served(args):
+    from paper_1003_1940_gb300 import build_lib, dbg
+    build_lib.build()
+    dbg.load()
+    specs, sets = batched_inputs(args)
+    ctx = dbg.Context()
+    dbg.dbg_autotune(ctx)
+    res = measure_served(args, sets, ctx)
+    print(json.dumps({"metric": METRIC + " (served, Poisson arrivals)", "data": "synthetic", "n_gpus": 1, **res}))
 
 
 def main():

@@ -58,7 +58,8 @@ typedef enum dbg_status {
   DBG_ETIMEOUT = 4,    /* a bounded device-side wait reached its limit */
   DBG_ECANCELLED = 5,  /* request cancelled (serving) */
   DBG_EOVERFLOW = 6,   /* more than 2^32 - 1 edge instances, edges or nodes in one build */
-  DBG_EAGAIN = 7       /* dbg_poll without waiting: the request has not finished */
+  DBG_EAGAIN = 7,      /* dbg_poll without waiting: the request has not finished */
+  DBG_EINTERNAL = 8    /* an internal consistency check failed (a library defect); no result */
 } dbg_status;
 
 typedef struct dbg_ctx dbg_ctx;
@@ -155,6 +156,10 @@ dbg_status dbg_graph_node_mult(const dbg_graph *g, uint32_t *mult);
  * the call that starts them or by dbg_graph_wait. */
 dbg_status dbg_graph_edges_async(dbg_graph *g, uint64_t *keys, uint32_t *src, uint32_t *dst,
                                  uint8_t *orient, uint32_t *mult);
+/* The node keys and the adjacency (as dbg_graph_nodes / dbg_graph_csr), the
+ * same way. */
+dbg_status dbg_graph_nodes_async(dbg_graph *g, uint64_t *keys);
+dbg_status dbg_graph_csr_async(dbg_graph *g, uint64_t *row_ptr, uint32_t *nbr, uint32_t *edge, uint8_t *role);
 dbg_status dbg_graph_wait(dbg_graph *g);
 
 /* Adjacency (STEP-4) in CSR form: row_ptr has num_nodes + 1 entries; entry
@@ -224,7 +229,7 @@ typedef struct dbg_server_options {
   int32_t device;           /* -1 = the current device */
   uint32_t workers;         /* concurrent builds (each its own stream), 1..64; default 4 */
   uint32_t spin_limit;      /* as in dbg_options; 0 = default */
-  uint64_t mem_budget;      /* device bytes all running requests may hold; 0 = 80 % of free memory */
+  uint64_t mem_budget;      /* device bytes running requests and unfreed results may hold; 0 = 80 % of free memory */
   uint32_t sort_variant[4]; /* radix sort variant per key kind (see dbg_sort_variant_set) */
   uint32_t reserved[8];
 } dbg_server_options;
@@ -233,22 +238,39 @@ typedef struct dbg_request_stats {
   double queue_s;      /* submission to start */
   double run_s;        /* start to finish */
   double latency_s;    /* submission to finish */
-  uint64_t footprint;  /* estimated device bytes charged to the budget */
+  uint64_t footprint;  /* worst-case device bytes of the in-memory build */
   uint32_t bucketed;   /* 1 if built by the key-range bucket path */
+  uint32_t retries;    /* times the build ran out of device memory and waited to run again */
+  uint64_t charged;    /* bytes charged while it ran (bucket path: its key-range budget) */
 } dbg_request_stats;
 
 void dbg_server_options_init(dbg_server_options *opt);
 
 /* Starts `workers` worker threads, each with its own context and stream.
- * Requests are admitted in submission order as soon as a worker is free and
- * their estimated footprint fits the budget next to the running ones
- * (continuous admission); their kernels overlap on the device.  A request
- * whose footprint exceeds the whole budget runs on the bucket path.
+ * Admission (continuous: a request that arrives while others run starts as
+ * soon as it is admitted; their kernels overlap on the device):
+ *   - a request's footprint is the worst-case peak of its in-memory build
+ *     (every edge instance a distinct edge, every local-sort group oversize),
+ *     computed at submission from the read lengths (device-resident lengths
+ *     are copied to the host for it);
+ *   - the first queued request whose footprint fits the budget next to what
+ *     is charged runs when a worker is free (any request may run when none
+ *     runs); it is charged its footprint while it runs;
+ *   - a finished graph stays charged at its real size until dbg_graph_free
+ *     (polled or not), so results count against the budget too;
+ *   - a request whose footprint exceeds the whole budget runs on the bucket
+ *     path with the part of the budget that is free when it starts (at least
+ *     a quarter of what it asks, or whatever is free when it runs alone);
+ *   - a build that still runs out of device memory (taken outside the
+ *     budget) is queued again until another request finishes; alone, it
+ *     fails with DBG_ENOMEM.
  * Results are the same graphs dbg_build returns for the same read set. */
 dbg_status dbg_server_create(dbg_server **srv, const dbg_server_options *opt);
 /* Waits for running requests; frees results nobody polled. */
 void dbg_server_destroy(dbg_server *srv);
 uint64_t dbg_server_budget(const dbg_server *srv);
+/* Bytes charged to the budget now: running requests and unfreed results. */
+uint64_t dbg_server_charged(const dbg_server *srv);
 dbg_status dbg_submit(dbg_server *srv, const dbg_readset *req, uint64_t *ticket);
 /* wait != 0 blocks until the request has finished; otherwise returns
  * DBG_EAGAIN while it runs.  On success *out is the graph (the caller frees
@@ -280,9 +302,12 @@ dbg_status dbg_build_bucketed(dbg_ctx *ctx, const char *reads, const uint32_t *l
 void dbg_graph_buckets(const dbg_graph *g, uint32_t *edge_ranges, uint32_t *node_ranges);
 
 /* ----------------------------------------------------------------------
- * dbg_rle_u64_noalloc -- the run-length reduce that dbg_build runs on its
- * sorted 64-bit edge keys (distinct keys and where each run starts), as a
- * call that allocates no memory at all.  The paper has no counterpart: this
+ * dbg_rle_u64_noalloc -- STEP-2's run-length reduce over sorted 64-bit keys
+ * (the distinct keys and where each run starts), as a call that allocates no
+ * memory at all.  It runs a single-pass reduce with decoupled look-back that
+ * dbg_build itself does not use (the build counts copies inside its local
+ * sort pass); both give the same distinct keys and multiplicities.  The
+ * paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at call
  * time -- a host program whose memory manager reserved the whole GPU up
  * front, a plugin whose host framework forbids allocation after start-up,
@@ -292,9 +317,10 @@ void dbg_graph_buckets(const dbg_graph *g, uint32_t *edge_ranges, uint32_t *node
  *   keys       device, n keys in ascending order
  *   n          0 <= n <= 2^26 (67,108,864); larger n returns DBG_EINVAL
  *   uniq       device, room for n keys: the distinct keys, ascending
- *   run_start  device, room for n + 1 entries: index in `keys` of each
- *              distinct key's first occurrence, then n; the multiplicity of
- *              uniq[i] is run_start[i + 1] - run_start[i]
+ *   run_start  device, room for n + 1 entries (never NULL, also for n = 0):
+ *              index in `keys` of each distinct key's first occurrence, then
+ *              n; the multiplicity of uniq[i] is run_start[i + 1] -
+ *              run_start[i]
  *   count      host: receives the number of distinct keys
  *   stream     cudaStream_t to run on (NULL = the legacy default stream);
  *              the call returns after the stream has finished its work

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI: contexts, device memory, dbg_build and the graph
 // accessors.  Every compute step runs in the CUDA kernels of this library.
+#include <initializer_list>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
@@ -101,7 +102,7 @@ dbg_status check_device_error(dbg_ctx *ctx) {
     return DBG_EOVERFLOW;
   }
   set_error("device consistency check failed (code %u)", e);
-  return DBG_ECUDA;
+  return DBG_EINTERNAL;
 }
 
 const char *const kStageNames[ST_COUNT] = {
@@ -518,24 +519,45 @@ dbg_status dbg_graph_node_mult(const dbg_graph *g, uint32_t *mult) {
   return copy_plain(g->device, mult, g->node_mult.p, g->num_nodes * sizeof(uint32_t));
 }
 
+namespace {
+struct CopyPart {
+  void *dst;
+  const void *src;
+  size_t bytes;
+};
+// starts the copies of the given parts on the graph's own copy stream
+dbg_status copy_parts_async(dbg_graph *g, std::initializer_list<CopyPart> parts) {
+  DeviceScope scope(g->device);
+  if (!g->copy_stream) DBG_CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+  for (const CopyPart &c : parts)
+    if (c.dst && c.bytes) DBG_CUDA_TRY(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, g->copy_stream));
+  return DBG_OK;
+}
+}  // namespace
+
 dbg_status dbg_graph_edges_async(dbg_graph *g, uint64_t *keys, uint32_t *src, uint32_t *dst, uint8_t *orient,
                                  uint32_t *mult) {
   if (!g) return DBG_EINVAL;
-  DeviceScope scope(g->device);
-  if (!g->copy_stream) DBG_CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
   const uint64_t E = g->num_edges;
-  const struct {
-    void *dst;
-    const void *src;
-    size_t bytes;
-  } parts[] = {{keys, g->edge_keys.p, E * g->key_words * sizeof(uint64_t)},
-               {src, g->src.p, E * sizeof(uint32_t)},
-               {dst, g->dst.p, E * sizeof(uint32_t)},
-               {orient, g->orient.p, E},
-               {mult, g->mult.p, E * sizeof(uint32_t)}};
-  for (const auto &c : parts)
-    if (c.dst && c.bytes) DBG_CUDA_TRY(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, g->copy_stream));
-  return DBG_OK;
+  return copy_parts_async(g, {{keys, g->edge_keys.p, E * g->key_words * sizeof(uint64_t)},
+                              {src, g->src.p, E * sizeof(uint32_t)},
+                              {dst, g->dst.p, E * sizeof(uint32_t)},
+                              {orient, g->orient.p, E},
+                              {mult, g->mult.p, E * sizeof(uint32_t)}});
+}
+
+dbg_status dbg_graph_nodes_async(dbg_graph *g, uint64_t *keys) {
+  if (!g) return DBG_EINVAL;
+  return copy_parts_async(g, {{keys, g->node_keys.p, g->num_nodes * g->key_words * sizeof(uint64_t)}});
+}
+
+dbg_status dbg_graph_csr_async(dbg_graph *g, uint64_t *row_ptr, uint32_t *nbr, uint32_t *edge, uint8_t *role) {
+  if (!g) return DBG_EINVAL;
+  const uint64_t A = 2 * g->num_edges;
+  return copy_parts_async(g, {{row_ptr, g->row_ptr.p, (g->num_nodes + 1) * sizeof(uint64_t)},
+                              {nbr, g->adj_nbr.p, A * sizeof(uint32_t)},
+                              {edge, g->adj_edge.p, A * sizeof(uint32_t)},
+                              {role, g->adj_role.p, A}});
 }
 
 dbg_status dbg_graph_wait(dbg_graph *g) {
@@ -583,7 +605,10 @@ void dbg_graph_free(dbg_graph *g) {
     cudaStreamSynchronize(g->copy_stream);
     cudaStreamDestroy(g->copy_stream);
   }
+  std::shared_ptr<BudgetShare> budget = std::move(g->budget);
+  const uint64_t charged = g->charged;
   delete g;  // DevBuf destructors release in stream order
+  if (budget) budget->release(charged);
 }
 
 static const char *variant_name_of(uint32_t kind, uint32_t v, uint32_t *count) {

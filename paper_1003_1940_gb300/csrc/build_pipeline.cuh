@@ -842,7 +842,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     if (ends != 2 * E) {
       set_error("adjacency holds %llu edge ends, expected %llu", (unsigned long long)ends,
                 (unsigned long long)(2 * E));
-      return DBG_ECUDA;
+      return DBG_EINTERNAL;
     }
   }
   g->num_nodes = V;
@@ -850,7 +850,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     if (Vk != V) {
       set_error("node multiplicities: %llu distinct k-mers for %llu nodes", (unsigned long long)Vk,
                 (unsigned long long)V);
-      return DBG_ECUDA;
+      return DBG_EINTERNAL;
     }
     if (V == 0) DBG_TRY(alloc_buf(ctx, node_counts, sizeof(uint32_t)));
     g->node_mult = std::move(node_counts);
@@ -1284,7 +1284,7 @@ dbg_status build_bucketed_impl(dbg_ctx *ctx, const BucketInput &in, uint64_t bud
   if (base_slot != 2 * E) {
     set_error("adjacency holds %llu edge ends, expected %llu", (unsigned long long)base_slot,
               (unsigned long long)(2 * E));
-    return DBG_ECUDA;
+    return DBG_EINTERNAL;
   }
   const uint64_t V = base_v;
   g->num_nodes = V;

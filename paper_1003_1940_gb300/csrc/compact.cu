@@ -554,7 +554,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
         DBG_TRY(scan_excl(ctx, f_len.as<uint32_t>(), V, f_off.as<uint64_t>(), &total));
         if (total != V) {
           set_error("unitigs hold %u nodes, expected %llu", total, (unsigned long long)V);
-          return DBG_ECUDA;
+          return DBG_EINTERNAL;
         }
         const uint64_t Uf = U32;
         u->count = Uf;
@@ -626,7 +626,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
         DBG_TRY(jump_until_stable(ctx, cycl.as<uint32_t>(), C, word.as<uint64_t>(), &still));
         if (still != 0) {
           set_error("%u strand-nodes stayed on cycles after they were opened", still);
-          return DBG_ECUDA;
+          return DBG_EINTERNAL;
         }
       }
     }
@@ -655,7 +655,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
     DBG_TRY(scan_excl(ctx, len_at_head.as<uint32_t>(), V, off_by_v.as<uint64_t>(), &total));
     if (total != V) {
       set_error("unitigs hold %u nodes, expected %llu", total, (unsigned long long)V);
-      return DBG_ECUDA;
+      return DBG_EINTERNAL;
     }
     U = U32;
   }

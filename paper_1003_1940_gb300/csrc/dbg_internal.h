@@ -3,8 +3,12 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <condition_variable>
 #include <cstdint>
 #include <cstdio>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -101,6 +105,24 @@ struct dbg_ctx {
   dbg_stage_stat stats[dbg::ST_COUNT] = {};
 };
 
+namespace dbg {
+// Device bytes charged to a request server's budget.  A graph a server
+// built keeps its bytes charged, through its own reference to this record,
+// until dbg_graph_free, which may come after the server is gone.
+struct BudgetShare {
+  std::mutex mu;
+  std::condition_variable cv;  // signalled whenever bytes are released
+  uint64_t in_use = 0;
+  void release(uint64_t bytes) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      in_use -= std::min(in_use, bytes);
+    }
+    cv.notify_all();
+  }
+};
+}  // namespace dbg
+
 struct dbg_graph {
   uint32_t k = 0, key_words = 1;
   uint64_t num_nodes = 0, num_edges = 0, num_instances = 0;
@@ -110,6 +132,16 @@ struct dbg_graph {
   dbg::DevBuf node_keys, edge_keys, src, dst, orient, mult, row_ptr, adj_nbr, adj_edge, adj_role;
   dbg::DevBuf node_mult;  // k-mer occurrences per node, when the build counted them
   cudaStream_t copy_stream = nullptr;  // read-backs started by dbg_graph_edges_async
+  std::shared_ptr<dbg::BudgetShare> budget;  // the server budget this graph is charged to, if any
+  uint64_t charged = 0;
+  // device bytes of the graph's arrays
+  uint64_t device_bytes() const {
+    uint64_t b = 0;
+    for (const dbg::DevBuf *x : {&node_keys, &edge_keys, &src, &dst, &orient, &mult, &row_ptr, &adj_nbr,
+                                 &adj_edge, &adj_role, &node_mult})
+      b += x->bytes;
+    return b;
+  }
 };
 
 struct dbg_unitigs {
@@ -214,8 +246,10 @@ dbg_status build_bucketed_u64(dbg_ctx *ctx, const BucketInput &in, uint64_t budg
                               uint32_t *nb);
 dbg_status build_bucketed_u128(dbg_ctx *ctx, const BucketInput &in, uint64_t budget, dbg_graph *g, uint32_t *eb,
                                uint32_t *nb);
-// estimated peak device bytes of one in-memory build
-uint64_t build_footprint(const uint32_t *lengths, uint64_t n, uint32_t k, bool lengths_on_host);
+// Worst-case peak device bytes of one in-memory build of n reads holding
+// `bases` bases and N edge instances (I reads of length exactly k).
+uint64_t build_footprint(uint64_t n, uint64_t bases, uint64_t N, uint64_t I, uint32_t k, bool reads_on_host,
+                         bool lengths_on_host);
 
 dbg_status build_graph_u64(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g);
 dbg_status autotune_u64(dbg_ctx *ctx, uint64_t n, double *ms_keys, double *ms_pairs);

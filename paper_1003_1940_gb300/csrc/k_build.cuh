@@ -630,7 +630,10 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
       if (HAS_VAL) tma_load_bulk(sm.vals, vin + base, vb, &sm.bar);
     }
     if (!__syncthreads_and(mbar_wait(&sm.bar, 0, spin_limit))) {
+      // give up on this launch; first let the copy in flight land (a CTA
+      // must not retire with a bulk copy into its shared memory pending)
       if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+      mbar_wait(&sm.bar, 0, spin_limit);
       return;
     }
   }

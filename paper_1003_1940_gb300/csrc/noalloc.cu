@@ -2,10 +2,15 @@
 // keys with no memory allocation at all, for callers that cannot allocate
 // device memory themselves or let a library do it (see include/dbg.h).
 //
-// The reduce kernel is the one dbg_build runs (k_rle); its scratch -- the
-// per-tile look-back status words, the tile ticket, the unique-key total and
-// the device error word -- lives in one file-scope __device__ array instead
-// of memory from an allocator.
+// The reduce is k_rle, a single pass with decoupled look-back.  dbg_build
+// does not launch it: the build counts each key's copies inside the local
+// pass of its hybrid sort (or, with every digit sorted globally, reduces by
+// a counting pass, a scan and a writing pass), which yields the same
+// distinct keys and multiplicities; the test of this entry point checks it
+// against dbg_build's edges.  k_rle's scratch -- the per-tile look-back
+// status words, the tile ticket, the unique-key total and the device error
+// word -- lives in one file-scope __device__ array instead of memory from an
+// allocator.
 #include <mutex>
 
 #include "k_build.cuh"
@@ -54,7 +59,7 @@ using namespace dbg;
 
 extern "C" dbg_status dbg_rle_u64_noalloc(const uint64_t *keys, uint64_t n, uint64_t *uniq, uint32_t *run_start,
                                           uint64_t *count, void *stream) {
-  if (!count || (n > 0 && (!keys || !uniq || !run_start))) {
+  if (!count || !run_start || (n > 0 && (!keys || !uniq))) {
     set_error("dbg_rle_u64_noalloc: NULL argument");
     return DBG_EINVAL;
   }
@@ -71,7 +76,9 @@ extern "C" dbg_status dbg_rle_u64_noalloc(const uint64_t *keys, uint64_t n, uint
   uint64_t *status = scratch;
   uint32_t *small = reinterpret_cast<uint32_t *>(scratch + kNoAllocTiles);  // ticket, total, err
   if (n == 0) {
+    // run_start holds n + 1 = 1 entry: the end of the (empty) input
     DBG_CUDA_TRY(cudaMemsetAsync(run_start, 0, sizeof(uint32_t), s));
+    DBG_CUDA_TRY(cudaStreamSynchronize(s));
     *count = 0;
     return DBG_OK;
   }

@@ -15,9 +15,10 @@ import numpy as np
 
 from . import build_lib
 
-DBG_OK, DBG_EINVAL, DBG_ENOMEM, DBG_ECUDA, DBG_ETIMEOUT, DBG_ECANCELLED, DBG_EOVERFLOW, DBG_EAGAIN = range(8)
+DBG_OK, DBG_EINVAL, DBG_ENOMEM, DBG_ECUDA, DBG_ETIMEOUT, DBG_ECANCELLED, DBG_EOVERFLOW, DBG_EAGAIN, \
+    DBG_EINTERNAL = range(9)
 _STATUS = {0: "DBG_OK", 1: "DBG_EINVAL", 2: "DBG_ENOMEM", 3: "DBG_ECUDA", 4: "DBG_ETIMEOUT",
-           5: "DBG_ECANCELLED", 6: "DBG_EOVERFLOW", 7: "DBG_EAGAIN"}
+           5: "DBG_ECANCELLED", 6: "DBG_EOVERFLOW", 7: "DBG_EAGAIN", 8: "DBG_EINTERNAL"}
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -71,6 +72,8 @@ _SIGNATURES = [
     ("dbg_graph_nodes", ctypes.c_int, [_P, _P]),
     ("dbg_graph_edges", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     ("dbg_graph_edges_async", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("dbg_graph_nodes_async", ctypes.c_int, [_P, _P]),
+    ("dbg_graph_csr_async", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("dbg_node_mult_set", ctypes.c_int, [_P, ctypes.c_int]),
     ("dbg_graph_node_mult", ctypes.c_int, [_P, _P]),
     ("dbg_graph_wait", ctypes.c_int, [_P]),
@@ -321,6 +324,18 @@ def dbg_graph_edges_async(g: Graph, keys: int | None = None, src: int | None = N
     _check(_lib.dbg_graph_edges_async(g.handle, *ptrs), "dbg_graph_edges_async")
 
 
+def dbg_graph_nodes_async(g: Graph, keys: int | None = None) -> None:
+    """Starts the node-key copy into a caller-owned buffer (raw address)."""
+    _check(_lib.dbg_graph_nodes_async(g.handle, ctypes.c_void_p(keys) if keys else None), "dbg_graph_nodes_async")
+
+
+def dbg_graph_csr_async(g: Graph, row_ptr: int | None = None, nbr: int | None = None, edge: int | None = None,
+                        role: int | None = None) -> None:
+    """Starts the adjacency copies into caller-owned buffers (raw addresses)."""
+    ptrs = (ctypes.c_void_p(a) if a else None for a in (row_ptr, nbr, edge, role))
+    _check(_lib.dbg_graph_csr_async(g.handle, *ptrs), "dbg_graph_csr_async")
+
+
 def dbg_graph_wait(g: Graph) -> None:
     _check(_lib.dbg_graph_wait(g.handle), "dbg_graph_wait")
 
@@ -374,6 +389,14 @@ def dbg_unitigs_get(u: Unitigs) -> dict:
     return {"node_off": node_off, "nodes": nodes, "seq_off": seq_off, "seq": seq.tobytes(), "circular": circ}
 
 
+def dbg_unitigs_get_into(u: Unitigs, node_off: int | None = None, nodes: int | None = None,
+                         seq_off: int | None = None, seq: int | None = None, circular: int | None = None) -> None:
+    """dbg_unitigs_get into caller-owned buffers (raw host or device
+    addresses, e.g. pinned tensors' data_ptr(); None skips an array)."""
+    ptrs = (ctypes.c_void_p(a) if a else None for a in (node_off, nodes, seq_off, seq, circular))
+    _check(_lib.dbg_unitigs_get(u.handle, *ptrs), "dbg_unitigs_get")
+
+
 def dbg_unitigs_free(u: Unitigs):
     u.free()
 
@@ -400,7 +423,23 @@ def dbg_launch_count(ctx: Context) -> int:
 
 def dbg_rle_u64_noalloc(keys, n: int, uniq, run_start, stream=None) -> int:
     """Run-length reduce of n sorted u64 keys with no allocation (device
-    tensors in, device tensors out); returns the number of distinct keys."""
+    tensors in, device tensors out); returns the number of distinct keys.
+    keys and uniq hold at least n 8-byte elements, run_start at least n + 1
+    4-byte elements; all three contiguous, on the current CUDA device."""
+    import torch
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    for name, t, need, size in (("keys", keys, n, 8), ("uniq", uniq, n, 8), ("run_start", run_start, n + 1, 4)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.element_size() != size or t.is_floating_point():
+            raise ValueError(f"{name} must hold {size}-byte integers")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} elements, needs {need}")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on cuda:{t.device.index}, not the current device")
     count = ctypes.c_uint64(0)
     s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(_lib.dbg_rle_u64_noalloc(ctypes.c_void_p(_ptr(keys)[0]), n, ctypes.c_void_p(_ptr(uniq)[0]),
@@ -472,7 +511,8 @@ class dbg_server_options(ctypes.Structure):
 
 class dbg_request_stats(ctypes.Structure):
     _fields_ = [("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("latency_s", ctypes.c_double),
-                ("footprint", ctypes.c_uint64), ("bucketed", ctypes.c_uint32)]
+                ("footprint", ctypes.c_uint64), ("bucketed", ctypes.c_uint32), ("retries", ctypes.c_uint32),
+                ("charged", ctypes.c_uint64)]
 
 
 DBG_REQ_BUCKETED = 1
@@ -481,6 +521,7 @@ _SIGNATURES += [
     ("dbg_server_create", ctypes.c_int, [_P, _P]),
     ("dbg_server_destroy", None, [_P]),
     ("dbg_server_budget", ctypes.c_uint64, [_P]),
+    ("dbg_server_charged", ctypes.c_uint64, [_P]),
     ("dbg_submit", ctypes.c_int, [_P, _P, _P]),
     ("dbg_poll", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P, _P]),
     ("dbg_build_batch", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint32, _P]),
@@ -529,6 +570,10 @@ class Server:
     def budget(self) -> int:
         return int(_lib.dbg_server_budget(self.handle))
 
+    def charged(self) -> int:
+        """Bytes charged to the budget: running requests and unfreed results."""
+        return int(_lib.dbg_server_charged(self.handle))
+
     def close(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
             _lib.dbg_server_destroy(self.handle)
@@ -565,7 +610,8 @@ def dbg_poll(srv: Server, ticket: int, wait: bool = True):
     srv._inputs.pop(ticket, None)
     _check(rc, "dbg_poll")
     stats = {"queue_s": st.queue_s, "run_s": st.run_s, "latency_s": st.latency_s,
-             "footprint": int(st.footprint), "bucketed": bool(st.bucketed)}
+             "footprint": int(st.footprint), "bucketed": bool(st.bucketed), "retries": int(st.retries),
+             "charged": int(st.charged)}
     return Graph(srv, out), stats
 
 

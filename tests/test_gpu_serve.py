@@ -120,3 +120,51 @@ def test_server_over_budget_request_takes_bucket_path(dbg, ctx):
     assert_same(graph_arrays(dbg, g), graph_arrays(dbg, dbg.dbg_build(ctx, reads, lengths, 31)))
     g.free()
     srv.close()
+
+
+def test_server_queues_requests_over_budget(dbg, ctx):
+    """Requests whose combined worst-case footprint exceeds the budget queue
+    instead of failing: at most two run at once under a budget of 2.5
+    footprints, results stay charged until they are freed, and each result
+    equals its one-at-a-time build."""
+    specs = [readgen.ReadSetSpec(100_000, 25_000, 100, 0.01, 31, 300 + i) for i in range(8)]
+    sets = [readgen.generate(sp) for sp in specs]
+    probe = dbg.Server(workers=1, mem_budget=1 << 40)
+    g, st = dbg.dbg_poll(probe, dbg.dbg_submit(probe, *sets[0], 31))
+    footprint = st["footprint"]
+    g.free()
+    assert probe.charged() == 0
+    probe.close()
+    budget = int(2.5 * footprint)
+    srv = dbg.Server(workers=6, mem_budget=budget)
+    tickets = [dbg.dbg_submit(srv, r, l, 31) for r, l in sets]
+    results = [dbg.dbg_poll(srv, t) for t in tickets]
+    assert all(not s["bucketed"] and s["charged"] == s["footprint"] for _, s in results)
+    # submissions came within milliseconds of each other: overlap of the
+    # [start, finish] intervals measured from submission
+    spans = [(s["queue_s"], s["latency_s"]) for _, s in results]
+    most = max(sum(1 for a, b in spans if a <= t < b) for t, _ in spans)
+    assert most <= 2, spans
+    assert srv.charged() > 0  # the results, not yet freed
+    for (r, l), (g, _) in zip(sets, results):
+        assert_same(graph_arrays(dbg, g), graph_arrays(dbg, dbg.dbg_build(ctx, r, l, 31)))
+        g.free()
+    assert srv.charged() == 0
+    srv.close()
+
+
+def test_server_device_lengths_footprint(dbg):
+    """The footprint of a request with device-resident lengths equals that
+    of the same request with host lengths (it is computed from the lengths,
+    copied to the host at submission)."""
+    import torch
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(50_000, 10_000, 75, 0.01, 21, 71))
+    srv = dbg.Server(workers=2, mem_budget=1 << 40)
+    g1, s1 = dbg.dbg_poll(srv, dbg.dbg_submit(srv, torch.from_numpy(reads).cuda(), lengths, 21))
+    g2, s2 = dbg.dbg_poll(srv, dbg.dbg_submit(srv, torch.from_numpy(reads).cuda(),
+                                              torch.from_numpy(lengths.view(np.int32)).cuda(), 21))
+    assert s1["footprint"] == s2["footprint"] > 0
+    assert_same(graph_arrays(dbg, g1), graph_arrays(dbg, g2))
+    g1.free()
+    g2.free()
+    srv.close()

@@ -44,7 +44,22 @@ def test_noalloc_rle_rejects_oversize_and_handles_empty():
     dbg.load()
     d = torch.zeros(1, dtype=torch.int64, device="cuda")
     r = torch.zeros(2, dtype=torch.int32, device="cuda")
-    with pytest.raises(dbg.DbgError) as e:
-        dbg.dbg_rle_u64_noalloc(d, (1 << 26) + 1, d, r)
-    assert e.value.status == dbg.DBG_EINVAL
+    # the library's own check, through the raw C ABI (the Python wrapper
+    # refuses the undersized buffers before calling it)
+    import ctypes
+    cnt = ctypes.c_uint64(0)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    st = dbg._lib.dbg_rle_u64_noalloc(p(d), (1 << 26) + 1, p(d), p(r), ctypes.byref(cnt), None)
+    assert st == dbg.DBG_EINVAL
+    assert dbg._lib.dbg_rle_u64_noalloc(p(d), 0, p(d), None, ctypes.byref(cnt), None) == dbg.DBG_EINVAL
+    r.fill_(7)
     assert dbg.dbg_rle_u64_noalloc(d, 0, d, r) == 0
+    assert int(r[0]) == 0  # run_start[n] = n, written before the call returns
+    # buffers too small, of the wrong element size or on the host are refused
+    # before anything reaches the GPU
+    with pytest.raises(ValueError):
+        dbg.dbg_rle_u64_noalloc(d, 2, d, r)
+    with pytest.raises(ValueError):
+        dbg.dbg_rle_u64_noalloc(d.view(torch.int32), 1, d, r)
+    with pytest.raises(ValueError):
+        dbg.dbg_rle_u64_noalloc(d.cpu(), 1, d, r)
