@@ -106,6 +106,8 @@ def _load():
                                           ctypes.POINTER(ctypes.c_uint64),
                                           ctypes.POINTER(ctypes.POINTER(ctypes.c_uint64)),
                                           ctypes.POINTER(ctypes.POINTER(ctypes.c_uint64))]
+            lib.orc_node_reads.restype = ctypes.c_int
+            lib.orc_node_reads.argtypes = lib.orc_node_mult.argtypes
             lib.orc_free.restype = None
             lib.orc_free.argtypes = [ctypes.c_void_p]
             lib.orc_edges_in_partition.restype = ctypes.c_int
@@ -324,3 +326,24 @@ def graph_range(reads, lengths, k: int, edge_range: tuple[int, int],
     finally:
         lib.orc_range_free(out)
     return res
+
+
+def node_reads(reads, lengths, k: int) -> tuple[np.ndarray, np.ndarray]:
+    """Canonical k-mers of the forward reads (the nodes) in ascending order
+    as (n, 2) high/low u64 words, and how many distinct reads contain each
+    of them on either strand (VELVET's roadmap keeps those in >= 2 reads)."""
+    lib = _load()
+    reads, lengths = _as_reads(reads, lengths)
+    m = ctypes.c_uint64(0)
+    kp, cp = ctypes.POINTER(ctypes.c_uint64)(), ctypes.POINTER(ctypes.c_uint64)()
+    rc = lib.orc_node_reads(reads.ctypes.data, lengths.ctypes.data, len(lengths), k, ctypes.byref(m),
+                            ctypes.byref(kp), ctypes.byref(cp))
+    if rc != ORC_OK:
+        raise OracleError(rc, "orc_node_reads")
+    try:
+        keys = _copy(kp, 2 * m.value, np.uint64).reshape(-1, 2)
+        counts = _copy(cp, m.value, np.uint64)
+    finally:
+        lib.orc_free(ctypes.cast(kp, ctypes.c_void_p))
+        lib.orc_free(ctypes.cast(cp, ctypes.c_void_p))
+    return keys, counts

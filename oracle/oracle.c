@@ -463,6 +463,76 @@ int orc_node_mult(const char *reads, const uint32_t *lengths, uint64_t n, uint32
 void orc_free(void *p) { free(p); }
 
 /* ------------------------------------------------------------------ */
+/* the roadmap counts: distinct reads per node                          */
+/* ------------------------------------------------------------------ */
+
+/* For every node of orc_build (canonical k-mers of the forward reads of
+ * length >= k, Section 2), the number of distinct reads that contain it on
+ * either strand.  VELVET keeps the k-mers present in at least 2 reads, its
+ * "roadmap" (Section 7).  Each read's canonical k-mers are collected,
+ * sorted and deduplicated, and every distinct one counts the read once.
+ * Outputs as orc_node_mult (free them with orc_free). */
+int orc_node_reads(const char *reads, const uint32_t *lengths, uint64_t n, uint32_t k, uint64_t *n_nodes,
+                   uint64_t **keys, uint64_t **counts) {
+  if (k < 1 || k > 63 || (k % 2) == 0 || !n_nodes || !keys || !counts) return ORC_EINVAL;
+  const int K = (int)k;
+  table_t t;
+  if (table_init(&t, 1024) != ORC_OK) return ORC_ENOMEM;
+  uint64_t cap = 0;
+  u128 *mine = NULL;
+  const char *read = reads;
+  int rc = ORC_OK;
+  for (uint64_t r = 0; r < n && rc == ORC_OK; r++) {
+    int64_t L = lengths[r];
+    uint64_t m = 0;
+    if (L >= K) {
+      if ((uint64_t)(L - K + 1) > cap) {
+        cap = (uint64_t)(L - K + 1);
+        free(mine);
+        mine = (u128 *)malloc(cap * sizeof(u128));
+        if (!mine) { rc = ORC_ENOMEM; break; }
+      }
+      for (int64_t j = 0; j + K <= L; j++) {
+        for (int i = 0; i < K; i++)
+          if (base_code(read[j + i]) < 0) { rc = ORC_EINVAL; break; }
+        if (rc != ORC_OK) break;
+        mine[m++] = mer_canonical(mer_value(read + j, K), K);
+      }
+    }
+    if (rc != ORC_OK) break;
+    /* the read's distinct canonical k-mers count it once each */
+    qsort(mine, m, sizeof(u128), cmp_node);
+    for (uint64_t i = 0; i < m; i++) {
+      if (i > 0 && mine[i] == mine[i - 1]) continue;
+      slot_t *sl = table_find(&t, mine[i], 0, 0, 1);
+      if (!sl) { rc = ORC_ENOMEM; break; }
+      sl->count++;
+    }
+    read += L;
+  }
+  free(mine);
+  if (rc != ORC_OK) { free(t.slots); return rc; }
+  uint64_t m = 0;
+  for (uint64_t i = 0; i < t.cap; i++)
+    if (t.slots[i].used) t.slots[m++] = t.slots[i];
+  qsort(t.slots, m, sizeof(slot_t), cmp_slot_key);
+  *keys = (uint64_t *)malloc((m ? m : 1) * 2 * sizeof(uint64_t));
+  *counts = (uint64_t *)malloc((m ? m : 1) * sizeof(uint64_t));
+  if (!*keys || !*counts) {
+    free(*keys); free(*counts); free(t.slots);
+    return ORC_ENOMEM;
+  }
+  for (uint64_t i = 0; i < m; i++) {
+    (*keys)[2 * i] = (uint64_t)(t.slots[i].a >> 64);
+    (*keys)[2 * i + 1] = (uint64_t)t.slots[i].a;
+    (*counts)[i] = t.slots[i].count;
+  }
+  *n_nodes = m;
+  free(t.slots);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* one partition of the edges, for the multi-core CPU baseline          */
 /* ------------------------------------------------------------------ */
 

@@ -373,6 +373,55 @@ def test_node_multiplicities_random_read_sets(k):
 
 
 # ---------------------------------------------------------------------------
+# roadmap counts: distinct reads per node (VELVET keeps the k-mers present in
+# at least 2 reads, Section 7)
+# ---------------------------------------------------------------------------
+
+def node_reads_by_strings(reads: list[str], k: int) -> dict[str, int]:
+    """Distinct reads holding each canonical k-mer (either strand), by strings."""
+    c: dict[str, int] = {}
+    for r in reads:
+        for s in {sm.canonical(r[j:j + k]) for j in range(len(r) - k + 1)}:
+            c[s] = c.get(s, 0) + 1
+    return c
+
+
+def oracle_node_reads(reads: list[str], k: int) -> dict[str, int]:
+    lengths = np.array([len(r) for r in reads], dtype=np.uint32)
+    keys, counts = oracle.node_reads("".join(reads).encode(), lengths, k)
+    vals = [(int(h) << 64) | int(l) for h, l in keys]
+    assert vals == sorted(vals) and len(set(vals)) == len(vals)
+    return {kmer_str(v, k): int(c) for v, c in zip(vals, counts)}
+
+
+def test_node_reads_worked_example():
+    """By hand, k = 3: ACGT holds ACG twice (ACG, and CGT = rc ACG) but is
+    one read; CGTT holds CGT (ACG) and GTT (AAC); AAC also in AACA."""
+    got = oracle_node_reads(["ACGT", "CGTT", "AACA"], 3)
+    assert got == {"ACG": 2, "AAC": 2, "ACA": 1}
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 9])
+def test_node_reads_random_read_sets(k):
+    """Against the string model; never above the occurrence count, equal to
+    it where no read holds a k-mer twice; same node set as the graph."""
+    rng = np.random.default_rng(40 + k)
+    for trial in range(40):
+        alphabet = "ACGT" if trial % 2 else "AC"
+        reads = ["".join(rng.choice(list(alphabet), size=int(rng.integers(0, 3 * k + 8))))
+                 for _ in range(int(rng.integers(1, 10)))]
+        got = oracle_node_reads(reads, k)
+        assert got == node_reads_by_strings(reads, k)
+        occ = oracle_node_counts(reads, k)
+        assert got.keys() == occ.keys() and all(got[x] <= occ[x] for x in got)
+        once = all(len({sm.canonical(r[j:j + k]) for j in range(len(r) - k + 1)}) == max(0, len(r) - k + 1)
+                   for r in reads)
+        if once:
+            assert got == occ
+        assert sorted(got) == graph_strings(build(reads, k))[0]
+
+
+# ---------------------------------------------------------------------------
 # key-range slices of the graph (the unit of work of the full-size parity
 # tests: one process per key range, every read scanned)
 # ---------------------------------------------------------------------------
