@@ -146,6 +146,20 @@ dbg_status dbg_graph_edges(const dbg_graph *g, uint64_t *keys, uint32_t *src, ui
 dbg_status dbg_node_mult_set(dbg_ctx *ctx, int on);
 dbg_status dbg_graph_node_mult(const dbg_graph *g, uint32_t *mult);
 
+/* Roadmap counts (Section 7: VELVET builds its graph from the k-mers present
+ * in at least 2 reads, its "roadmap"): for every node, the number of
+ * distinct reads that hold its k-mer on either strand.  Counted by dbg_build
+ * when the context's switch is on (dbg_node_reads_set; off by default: a
+ * sort of (k-mer, read) records), not by dbg_build_bucketed.  reads:
+ * num_nodes uint32_t.  DBG_EINVAL if the graph was built without them.
+ * dbg_roadmap_nodes writes the IDs of the nodes held by at least min_reads
+ * distinct reads, ascending, to ids (host or device, room for num_nodes
+ * entries; NULL to count only) and their number to *count. */
+dbg_status dbg_node_reads_set(dbg_ctx *ctx, int on);
+dbg_status dbg_graph_node_reads(const dbg_graph *g, uint32_t *reads);
+dbg_status dbg_roadmap_nodes(dbg_ctx *ctx, const dbg_graph *g, uint32_t min_reads, uint32_t *ids,
+                             uint64_t *count);
+
 /* The same copies, started on a stream of the graph's own and returned from
  * at once, so that they overlap later work on the GPU (e.g. dbg_compact of
  * the same graph, which only reads it).  Host buffers should be pinned for
@@ -271,6 +285,16 @@ void dbg_server_destroy(dbg_server *srv);
 uint64_t dbg_server_budget(const dbg_server *srv);
 /* Bytes charged to the budget now: running requests and unfreed results. */
 uint64_t dbg_server_charged(const dbg_server *srv);
+typedef struct dbg_server_counters {
+  uint64_t charged;       /* as dbg_server_charged */
+  uint64_t peak_charged;  /* the most charged right after an admission */
+  uint64_t finished;      /* requests finished (successfully or not) */
+  uint32_t running;       /* requests running now */
+  uint32_t peak_running;  /* the most that ran at once */
+  uint32_t queued;        /* requests waiting for admission */
+  uint32_t reserved;
+} dbg_server_counters;
+dbg_status dbg_server_stats(const dbg_server *srv, dbg_server_counters *out);
 dbg_status dbg_submit(dbg_server *srv, const dbg_readset *req, uint64_t *ticket);
 /* wait != 0 blocks until the request has finished; otherwise returns
  * DBG_EAGAIN while it runs.  On success *out is the graph (the caller frees

@@ -369,7 +369,7 @@ dbg_status dbg_build(dbg_ctx *ctx, const char *reads, const uint32_t *lengths, u
     st = k <= 31 ? build_graph_u64(ctx, in, g) : build_graph_u128(ctx, in, g);
   }
   for (DevBuf *b : {&g->node_keys, &g->edge_keys, &g->src, &g->dst, &g->orient, &g->mult, &g->row_ptr,
-                    &g->adj_nbr, &g->adj_edge, &g->adj_role, &g->node_mult})
+                    &g->adj_nbr, &g->adj_edge, &g->adj_role, &g->node_mult, &g->node_reads})
     rebind(*b);
   d_len.release();
   cudaStreamSynchronize(s);
@@ -682,6 +682,54 @@ dbg_status dbg_node_mult_set(dbg_ctx *ctx, int on) {
   }
   ctx->node_mult = on ? 1 : 0;
   return DBG_OK;
+}
+
+dbg_status dbg_node_reads_set(dbg_ctx *ctx, int on) {
+  if (!ctx) {
+    set_error("null context");
+    return DBG_EINVAL;
+  }
+  ctx->node_reads = on ? 1 : 0;
+  return DBG_OK;
+}
+
+dbg_status dbg_graph_node_reads(const dbg_graph *g, uint32_t *reads) {
+  if (!g) return DBG_EINVAL;
+  if (!g->node_reads.p) {
+    set_error("read counts were not counted for this graph (dbg_node_reads_set before dbg_build)");
+    return DBG_EINVAL;
+  }
+  if (g->num_nodes && !reads) return DBG_EINVAL;
+  return copy_plain(g->device, reads, g->node_reads.p, g->num_nodes * sizeof(uint32_t));
+}
+
+dbg_status dbg_roadmap_nodes(dbg_ctx *ctx, const dbg_graph *g, uint32_t min_reads, uint32_t *ids,
+                             uint64_t *count) {
+  if (!ctx || !g || !count) {
+    set_error("ctx, graph or count is NULL");
+    return DBG_EINVAL;
+  }
+  if (!g->node_reads.p) {
+    set_error("read counts were not counted for this graph (dbg_node_reads_set before dbg_build)");
+    return DBG_EINVAL;
+  }
+  DeviceScope scope(ctx->device);
+  DevBuf tmp;
+  uint32_t *d_ids = nullptr;
+  if (ids) {
+    if (is_device_ptr(ids)) {
+      d_ids = ids;
+    } else {
+      DBG_TRY(alloc_buf(ctx, tmp, std::max<uint64_t>(1, g->num_nodes) * 4));
+      d_ids = tmp.as<uint32_t>();
+    }
+  }
+  dbg_status st = roadmap_nodes(ctx, g, min_reads, d_ids, count);
+  if (st == DBG_OK && ids && d_ids != ids && *count)
+    st = copy_plain(ctx->device, ids, d_ids, *count * sizeof(uint32_t));
+  cudaStreamSynchronize(ctx->stream);
+  prof_resolve(ctx);
+  return st;
 }
 
 dbg_status dbg_sort_partition_first_set(dbg_ctx *ctx, int on) {

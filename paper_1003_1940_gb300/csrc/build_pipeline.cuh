@@ -632,6 +632,72 @@ dbg_status count_node_kmers(dbg_ctx *ctx, const DevBuf &packed, const DevBuf &ba
   return DBG_OK;
 }
 
+// Distinct reads per node (the roadmap counts): every k-mer of the reads
+// with its read index, stably sorted by key (the records of one key keep
+// their read order, which is ascending), then per key the number of records
+// that start its run or follow a record of another read.  As for the
+// multiplicities, the distinct keys are exactly the nodes, in node order.
+template <class K>
+dbg_status count_node_reads(dbg_ctx *ctx, const DevBuf &packed, const DevBuf &base_off, const uint32_t *d_lengths,
+                            uint64_t n, uint64_t N, uint32_t k, unsigned long long *d_hist,
+                            uint64_t *d_digit_base, DevBuf &counts, uint64_t *Vk) {
+  cudaStream_t s = ctx->stream;
+  *Vk = 0;
+  if (n == 0) return DBG_OK;
+  if (N + n > 0xffffffffull) {
+    set_error("%llu edge instances and %llu reads: too many k-mers to count in one build",
+              (unsigned long long)N, (unsigned long long)n);
+    return DBG_EOVERFLOW;
+  }
+  DevBuf per, koff;
+  DBG_TRY(alloc_buf(ctx, per, n * sizeof(uint32_t)));
+  DBG_TRY(alloc_buf(ctx, koff, (n + 1) * sizeof(uint64_t)));
+  DBG_LAUNCH(ctx, ST_NODE_MULT, 8.0 * n,
+             k_kmer_counts<<<grid_for(n, 256), 256, 0, s>>>(d_lengths, n, k, per.as<uint32_t>()));
+  uint32_t low32 = 0;
+  DBG_TRY(scan_u32(ctx, per.as<uint32_t>(), n, koff.as<uint64_t>(), &low32, ST_NODE_MULT));
+  uint64_t M = 0;
+  DBG_TRY(read_small(ctx, koff.as<uint64_t>() + n, sizeof(uint64_t), &M));
+  if (M == 0) return DBG_OK;
+  per.release();
+  const int kbits = 2 * (int)k;
+  const int q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(M, kbits) : 0;
+  DevBuf ka, kb, va, vb;
+  DBG_TRY(alloc_buf(ctx, ka, M * sizeof(K)));
+  DBG_TRY(alloc_buf(ctx, kb, M * sizeof(K)));
+  DBG_TRY(alloc_buf(ctx, va, M * sizeof(uint32_t)));
+  DBG_TRY(alloc_buf(ctx, vb, M * sizeof(uint32_t)));
+  DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
+  // windows of k bases at the k-mer offsets, each with its read index
+  DBG_LAUNCH(ctx, ST_NODE_MULT, 8.0 * n + (double)M * (sizeof(K) + 4),
+             k_emit<K><<<(unsigned)std::min<uint64_t>(grid_for(n, EMIT_BLOCK / 32), 152ull * 64), EMIT_BLOCK, 0, s>>>(
+                 packed.as<uint64_t>(), base_off.as<uint64_t>(), koff.as<uint64_t>(), n, k - 1, ka.as<K>(), q0,
+                 passes_for_bits(kbits), d_hist, nullptr, va.as<uint32_t>()));
+  DBG_CUDA_TRY(cudaGetLastError());
+  koff.release();
+  K *kp = ka.as<K>(), *kalt = kb.as<K>();
+  uint32_t *vp = va.as<uint32_t>(), *valt = vb.as<uint32_t>();
+  DBG_TRY((sort_records<K>(ctx, &kp, &kalt, &vp, &valt, M, kbits, q0, d_hist, d_digit_base)));
+  // flags into the free payload buffer, their scan, the key runs
+  DBG_LAUNCH(ctx, ST_NODE_MULT, (double)M * (2 * sizeof(K) + 12),
+             k_read_change_flags<K><<<grid_for(M, 256 * 8), 256, 0, s>>>(kp, vp, M, valt));
+  DevBuf F, headpos;
+  DBG_TRY(alloc_buf(ctx, F, (M + 1) * sizeof(uint64_t)));
+  uint32_t low = 0;
+  DBG_TRY(scan_u32(ctx, valt, M, F.as<uint64_t>(), &low, ST_NODE_MULT));
+  DBG_TRY(alloc_buf(ctx, headpos, (M + 1) * sizeof(uint32_t)));
+  uint64_t D = 0;
+  DBG_TRY(run_length_reduce<K>(ctx, kp, M, kalt, headpos.as<uint32_t>(), &D));
+  DBG_TRY(alloc_buf(ctx, counts, std::max<uint64_t>(1, D) * sizeof(uint32_t)));
+  DBG_LAUNCH(ctx, ST_NODE_MULT, 12.0 * D,
+             k_counts_between<<<grid_for(D, 256), 256, 0, s>>>(headpos.as<uint32_t>(), F.as<uint64_t>(), D,
+                                                               counts.as<uint32_t>()));
+  DBG_CUDA_TRY(cudaGetLastError());
+  DBG_TRY(check_device_error(ctx));
+  *Vk = D;
+  return DBG_OK;
+}
+
 template <class K>
 dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   cudaStream_t s = ctx->stream;
@@ -777,11 +843,14 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   g->num_edges = E;
 
   // ---- node multiplicities (optional), while the packed reads are here ----
-  DevBuf node_counts;
-  uint64_t Vk = 0;
+  DevBuf node_counts, read_counts;
+  uint64_t Vk = 0, Vr = 0;
   if (ctx->node_mult)
     DBG_TRY(count_node_kmers<K>(ctx, packed, base_off, in.d_lengths, n, N, k, d_hist, d_digit_base, node_counts,
                                 &Vk));
+  if (ctx->node_reads)
+    DBG_TRY(count_node_reads<K>(ctx, packed, base_off, in.d_lengths, n, N, k, d_hist, d_digit_base, read_counts,
+                                &Vr));
 
   // ---- K5 edge ends + records of reads of length k ----
   const uint64_t R = 2 * E + I;
@@ -854,6 +923,15 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     }
     if (V == 0) DBG_TRY(alloc_buf(ctx, node_counts, sizeof(uint32_t)));
     g->node_mult = std::move(node_counts);
+  }
+  if (ctx->node_reads) {
+    if (Vr != V) {
+      set_error("node read counts: %llu distinct k-mers for %llu nodes", (unsigned long long)Vr,
+                (unsigned long long)V);
+      return DBG_EINTERNAL;
+    }
+    if (V == 0) DBG_TRY(alloc_buf(ctx, read_counts, sizeof(uint32_t)));
+    g->node_reads = std::move(read_counts);
   }
   DBG_TRY(alloc_buf(ctx, g->node_keys, std::max<uint64_t>(1, V) * sizeof(K)));
   DBG_TRY(alloc_buf(ctx, g->row_ptr, (V + 1) * sizeof(uint64_t)));

@@ -84,6 +84,7 @@ struct dbg_ctx {
   int count_first = 1;                 // local pass of the edge keys counts copies before sorting
   int partition_first = 1;             // first global pass of keys without payload: unordered partition
   int node_mult = 0;                   // dbg_build also counts every node's k-mer occurrences
+  int node_reads = 0;                  // dbg_build also counts the distinct reads holding every node
   uint64_t count_overflow_tiles = 0;  // count-first tiles whose keys did not fit the hash table
   uint64_t local_sort_fallbacks = 0;   // local sorts that met a group longer than their window
   int num_sms = 0;
@@ -130,7 +131,8 @@ struct dbg_graph {
   int device = 0;
   uint32_t edge_buckets = 1, node_buckets = 1;  // key ranges used (bucket path)
   dbg::DevBuf node_keys, edge_keys, src, dst, orient, mult, row_ptr, adj_nbr, adj_edge, adj_role;
-  dbg::DevBuf node_mult;  // k-mer occurrences per node, when the build counted them
+  dbg::DevBuf node_mult;   // k-mer occurrences per node, when the build counted them
+  dbg::DevBuf node_reads;  // distinct reads per node, when the build counted them
   cudaStream_t copy_stream = nullptr;  // read-backs started by dbg_graph_edges_async
   std::shared_ptr<dbg::BudgetShare> budget;  // the server budget this graph is charged to, if any
   uint64_t charged = 0;
@@ -138,7 +140,7 @@ struct dbg_graph {
   uint64_t device_bytes() const {
     uint64_t b = 0;
     for (const dbg::DevBuf *x : {&node_keys, &edge_keys, &src, &dst, &orient, &mult, &row_ptr, &adj_nbr,
-                                 &adj_edge, &adj_role, &node_mult})
+                                 &adj_edge, &adj_role, &node_mult, &node_reads})
       b += x->bytes;
     return b;
   }
@@ -252,6 +254,9 @@ uint64_t build_footprint(uint64_t n, uint64_t bases, uint64_t N, uint64_t I, uin
                          bool lengths_on_host);
 
 dbg_status build_graph_u64(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g);
+// IDs of the nodes held by at least t distinct reads (device buffer of
+// num_nodes entries, or NULL for the count only)
+dbg_status roadmap_nodes(dbg_ctx *ctx, const dbg_graph *g, uint32_t t, uint32_t *d_ids, uint64_t *count);
 dbg_status autotune_u64(dbg_ctx *ctx, uint64_t n, double *ms_keys, double *ms_pairs);
 dbg_status autotune_u128(dbg_ctx *ctx, uint64_t n, double *ms_keys, double *ms_pairs);
 const char *sort_variant_name_u64(bool pairs, uint32_t v, uint32_t *count);

@@ -264,7 +264,8 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict_
                                                      const uint64_t *__restrict__ edge_off, uint64_t n_reads,
                                                      uint32_t k, K *__restrict__ keys, int first, int passes,
                                                      unsigned long long *__restrict__ hist,
-                                                     const uint64_t *__restrict__ krange) {
+                                                     const uint64_t *__restrict__ krange,
+                                                     uint32_t *__restrict__ read_of = nullptr) {
   // Every warp takes a contiguous, 32-aligned range of the keys to emit
   // (all of the N edge instances, or [krange[0], krange[1]) of them when
   // krange is given), so lanes stay busy across read ends and every
@@ -299,6 +300,7 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_emit(const uint64_t *__restrict_
       const K z = load_window<K>(packed, pos + i, m);
       const K key = kmin(z, revcomp(z, m));
       keys[i] = key;
+      if (read_of) read_of[i] = (uint32_t)r;
       if (G <= 4) {
         // the histogrammed digits are the low bytes of one shifted word
         const uint32_t w = (uint32_t)KeyOps<K>::words_lo(KeyOps<K>::shr(key, first * RADIX_BITS));
@@ -329,6 +331,24 @@ static __global__ void k_counts_from_heads(const uint32_t *__restrict__ headpos,
                                            uint32_t *__restrict__ counts) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += (uint64_t)gridDim.x * blockDim.x)
     counts[i] = headpos[i + 1] - headpos[i];
+}
+
+// Distinct reads per node: over (k-mer key, read) records sorted by key with
+// the reads of one key in ascending order, flag[i] = 1 where record i starts
+// a key's run or holds another read than record i - 1.
+template <class K>
+__global__ void k_read_change_flags(const K *__restrict__ keys, const uint32_t *__restrict__ read_of, uint64_t M,
+                                    uint32_t *__restrict__ flag) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (uint64_t)gridDim.x * blockDim.x)
+    flag[i] = (i == 0 || !KeyOps<K>::eq(keys[i], keys[i - 1]) || read_of[i] != read_of[i - 1]) ? 1u : 0u;
+}
+
+// counts[j] = flags in key run j = F[headpos[j + 1]] - F[headpos[j]] (F the
+// exclusive scan of the flags, headpos the runs' first records, then M)
+static __global__ void k_counts_between(const uint32_t *__restrict__ headpos, const uint64_t *__restrict__ F,
+                                        uint64_t D, uint32_t *__restrict__ counts) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < D; j += (uint64_t)gridDim.x * blockDim.x)
+    counts[j] = (uint32_t)(F[headpos[j + 1]] - F[headpos[j]]);
 }
 
 // Host reads arrive in chunks of `chunk` bases; once chunks 0..c are packed,

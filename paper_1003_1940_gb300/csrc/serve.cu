@@ -62,8 +62,8 @@ struct dbg_server {
   // charged bytes, and the lock and wake-up of the queue; graphs the server
   // built hold a reference until they are freed
   std::shared_ptr<dbg::BudgetShare> bud = std::make_shared<dbg::BudgetShare>();
-  uint32_t running = 0;
-  uint64_t finishes = 0;
+  uint32_t running = 0, peak_running = 0;
+  uint64_t finishes = 0, peak_charged = 0;
   uint64_t next_ticket = 1;
   bool stopping = false;
   std::condition_variable cv_done;
@@ -141,6 +141,8 @@ static void worker_main(dbg_server *srv, int idx) {
           req->charge = charge;
           bud.in_use += charge;
           srv->running++;
+          srv->peak_running = std::max(srv->peak_running, srv->running);
+          srv->peak_charged = std::max(srv->peak_charged, bud.in_use);
           break;
         }
         bud.cv.wait(lk);
@@ -266,6 +268,18 @@ uint64_t dbg_server_charged(const dbg_server *srv) {
   if (!srv) return 0;
   std::lock_guard<std::mutex> lk(srv->bud->mu);
   return srv->bud->in_use;
+}
+
+dbg_status dbg_server_stats(const dbg_server *srv, dbg_server_counters *out) {
+  if (!srv || !out) return DBG_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->bud->mu);
+  out->charged = srv->bud->in_use;
+  out->peak_charged = srv->peak_charged;
+  out->finished = srv->finishes;
+  out->running = srv->running;
+  out->peak_running = srv->peak_running;
+  out->queued = (uint32_t)srv->queue.size();
+  return DBG_OK;
 }
 
 dbg_status dbg_submit(dbg_server *srv, const dbg_readset *req, uint64_t *ticket) {

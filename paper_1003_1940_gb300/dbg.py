@@ -76,6 +76,9 @@ _SIGNATURES = [
     ("dbg_graph_csr_async", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("dbg_node_mult_set", ctypes.c_int, [_P, ctypes.c_int]),
     ("dbg_graph_node_mult", ctypes.c_int, [_P, _P]),
+    ("dbg_node_reads_set", ctypes.c_int, [_P, ctypes.c_int]),
+    ("dbg_graph_node_reads", ctypes.c_int, [_P, _P]),
+    ("dbg_roadmap_nodes", ctypes.c_int, [_P, _P, ctypes.c_uint32, _P, _P]),
     ("dbg_graph_wait", ctypes.c_int, [_P]),
     ("dbg_graph_csr", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("dbg_graph_device_view", ctypes.c_int, [_P, _P]),
@@ -315,6 +318,28 @@ def dbg_graph_node_mult(g: Graph) -> np.ndarray:
     return out
 
 
+def dbg_node_reads_set(ctx: Context, on: bool) -> None:
+    _check(_lib.dbg_node_reads_set(ctx.handle, 1 if on else 0), "dbg_node_reads_set")
+
+
+def dbg_graph_node_reads(g: Graph) -> np.ndarray:
+    """Distinct reads holding each node's k-mer (either strand), node order."""
+    out = _np_out(dbg_graph_num_nodes(g), np.uint32)
+    _check(_lib.dbg_graph_node_reads(g.handle, ctypes.c_void_p(out.ctypes.data)), "dbg_graph_node_reads")
+    return out
+
+
+def dbg_roadmap_nodes(ctx: Context, g: Graph, min_reads: int = 2) -> np.ndarray:
+    """IDs (ascending) of the nodes held by at least min_reads distinct reads."""
+    count = ctypes.c_uint64(0)
+    _check(_lib.dbg_roadmap_nodes(ctx.handle, g.handle, min_reads, None, ctypes.byref(count)), "dbg_roadmap_nodes")
+    ids = _np_out(count.value, np.uint32)
+    if count.value:
+        _check(_lib.dbg_roadmap_nodes(ctx.handle, g.handle, min_reads, ctypes.c_void_p(ids.ctypes.data),
+                                      ctypes.byref(count)), "dbg_roadmap_nodes")
+    return ids
+
+
 def dbg_graph_edges_async(g: Graph, keys: int | None = None, src: int | None = None, dst: int | None = None,
                           orient: int | None = None, mult: int | None = None) -> None:
     """Starts the edge-array copies into caller-owned buffers (raw addresses,
@@ -515,6 +540,12 @@ class dbg_request_stats(ctypes.Structure):
                 ("charged", ctypes.c_uint64)]
 
 
+class dbg_server_counters(ctypes.Structure):
+    _fields_ = [("charged", ctypes.c_uint64), ("peak_charged", ctypes.c_uint64), ("finished", ctypes.c_uint64),
+                ("running", ctypes.c_uint32), ("peak_running", ctypes.c_uint32), ("queued", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
 DBG_REQ_BUCKETED = 1
 _SIGNATURES += [
     ("dbg_server_options_init", None, [_P]),
@@ -522,6 +553,7 @@ _SIGNATURES += [
     ("dbg_server_destroy", None, [_P]),
     ("dbg_server_budget", ctypes.c_uint64, [_P]),
     ("dbg_server_charged", ctypes.c_uint64, [_P]),
+    ("dbg_server_stats", ctypes.c_int, [_P, _P]),
     ("dbg_submit", ctypes.c_int, [_P, _P, _P]),
     ("dbg_poll", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P, _P]),
     ("dbg_build_batch", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint32, _P]),
@@ -573,6 +605,11 @@ class Server:
     def charged(self) -> int:
         """Bytes charged to the budget: running requests and unfreed results."""
         return int(_lib.dbg_server_charged(self.handle))
+
+    def stats(self) -> dict:
+        c = dbg_server_counters()
+        _check(_lib.dbg_server_stats(self.handle, ctypes.byref(c)), "dbg_server_stats")
+        return {f: int(getattr(c, f)) for f, _ in dbg_server_counters._fields_ if f != "reserved"}
 
     def close(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
