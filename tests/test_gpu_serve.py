@@ -152,16 +152,17 @@ def test_server_queues_requests_over_budget(dbg, ctx):
 
 
 def test_server_device_lengths_footprint(dbg):
-    """The footprint of a request with device-resident lengths equals that
-    of the same request with host lengths (it is computed from the lengths,
-    copied to the host at submission)."""
+    """The footprint of a request with device-resident lengths is that of the
+    same request with host lengths (it is computed from the lengths, copied
+    to the host at submission), less the device copy of the lengths that a
+    build from host lengths makes."""
     import torch
     reads, lengths = readgen.generate(readgen.ReadSetSpec(50_000, 10_000, 75, 0.01, 21, 71))
     srv = dbg.Server(workers=2, mem_budget=1 << 40)
     g1, s1 = dbg.dbg_poll(srv, dbg.dbg_submit(srv, torch.from_numpy(reads).cuda(), lengths, 21))
     g2, s2 = dbg.dbg_poll(srv, dbg.dbg_submit(srv, torch.from_numpy(reads).cuda(),
                                               torch.from_numpy(lengths.view(np.int32)).cuda(), 21))
-    assert s1["footprint"] == s2["footprint"] > 0
+    assert s1["footprint"] == s2["footprint"] + 4 * len(lengths) and s2["footprint"] > 0
     assert_same(graph_arrays(dbg, g1), graph_arrays(dbg, g2))
     g1.free()
     g2.free()
