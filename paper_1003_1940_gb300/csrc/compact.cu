@@ -20,10 +20,7 @@
 
 namespace dbg {
 
-// "no strand-node / no edge"; bit 31 stays free in successor words for the
-// fast path's claim bits (so compaction takes fewer than 2^30 nodes)
-constexpr uint32_t NONE32 = 0x7fffffffu;
-constexpr uint32_t CLAIM = 0x80000000u;
+constexpr uint32_t NONE32 = 0xffffffffu;
 
 template <class K>
 __device__ __forceinline__ K load_node_key(const uint64_t *keys, uint64_t v);
@@ -292,29 +289,15 @@ __global__ void k_unitig_write(const uint32_t *__restrict__ head, const uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// Fast path, for graphs whose lists are acyclic and at most about 2 * cap
-// strand-nodes long (the usual case).  Each open unitig appears as two
-// mirrored lists, v_0 -> ... -> v_{L-1} and v_{L-1}^1 -> ... -> v_0^1; one
-// walker starts at each list head and the two walk towards each other,
-// claiming nodes, until they meet, so every node is visited once in all
-// (instead of both lists being walked end to end).  A walker claims node v
-// by setting the claim bit of its own strand's successor word with one
-// atomic OR on the word pair of v (succ[2v], succ[2v + 1]), which also
-// returns its successor and tells whether the other walker got there first.
-// Then the two walkers of each unitig are paired, the copy to keep is
-// decided from their first k-mers, the unitigs are placed by scans over
-// their first nodes, and every walker walks its half once more, writing its
-// nodes and bases straight into place: the kept copy's walker forwards from
-// the unitig's start, the other backwards from its end on the other strands.
+// Fast path, for graphs whose lists are all at most `cap` strand-nodes long
+// and acyclic (the usual case): one walk per list head measures the list
+// and picks the copy to keep; a second walk writes each kept unitig's nodes
+// and bases in order.  No per-strand-node ranking state is written.
 // ---------------------------------------------------------------------------
 template <class K>
 __device__ __forceinline__ K strand_kmer(const uint64_t *node_keys, uint32_t x, int k) {
   K km = load_node_key<K>(node_keys, x >> 1);
   return (x & 1u) ? revcomp(km, k) : km;
-}
-
-__device__ __forceinline__ bool is_list_head(const uint32_t *succ, uint64_t x) {
-  return (succ[x ^ 1] & ~CLAIM) == NONE32;
 }
 
 // Walk scheduling: each warp takes a chunk of WALK_CHUNK indices, queues the
@@ -338,52 +321,49 @@ __device__ __forceinline__ uint32_t queue_heads(uint64_t base, uint64_t n, uint3
   return cnt;
 }
 
-// Phase 1: the claiming walks.  hrec[x] = (nodes claimed by walker x, how it
-// stopped): (y << 1) when its list ended at strand-node y, (v << 1) | 1 when
-// the other walker had claimed node v.  last_of[v] = x when v is the last
-// node walker x claimed.  A walker reaching `cap` nodes counts in too_long.
-__global__ __launch_bounds__(WALK_BLOCK) void k_half_claim(uint32_t *__restrict__ succ, uint64_t n, uint32_t cap,
-                                                           uint2 *__restrict__ hrec, uint32_t *__restrict__ last_of,
-                                                           uint32_t *covered, uint32_t *too_long) {
+template <class K>
+__global__ __launch_bounds__(WALK_BLOCK) void k_fast_measure(const uint32_t *__restrict__ succ, uint64_t n,
+                                                             const uint64_t *__restrict__ node_keys, int k,
+                                                             uint32_t cap, uint32_t *__restrict__ is_head,
+                                                             uint32_t *__restrict__ len_at_head,
+                                                             uint8_t *__restrict__ hstrand, uint32_t *covered,
+                                                             uint32_t *too_long) {
   __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
   __shared__ uint32_t s_next[WALK_WARPS];
-  unsigned long long *pairs = reinterpret_cast<unsigned long long *>(succ);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
   uint32_t cov = 0, lng = 0;
   for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
-    const uint32_t cnt = queue_heads(c * WALK_CHUNK, n, s_q[w], [&](uint64_t x) { return is_list_head(succ, x); });
+    const uint32_t cnt = queue_heads(c * WALK_CHUNK, n, s_q[w], [&](uint64_t x) { return succ[x ^ 1] == NONE32; });
     if (lane == 0) s_next[w] = 0;
     __syncwarp();
+    uint32_t head = NONE32, y = 0, L = 0;
     for (;;) {
-      const uint32_t qi = atomicAdd(&s_next[w], 1u);
-      if (qi >= cnt) break;
-      const uint32_t x = s_q[w][qi];
-      uint32_t y = x, d = 0, last = NONE32, stop;
-      for (;;) {
-        const uint32_t v = y >> 1, sh = 32u * (y & 1u);
-        const unsigned long long old = atomicOr(pairs + v, (unsigned long long)CLAIM << sh);
-        if ((uint32_t)(old >> (32u - sh)) & CLAIM) {  // the other strand's walker owns v
-          stop = (v << 1) | 1u;
-          break;
-        }
-        d++;
-        last = v;
-        const uint32_t nx = (uint32_t)(old >> sh) & ~CLAIM;
-        if (nx == NONE32) {
-          stop = y << 1;
-          break;
-        }
-        if (d >= cap) {
-          lng++;
-          stop = y << 1;
-          break;
-        }
-        y = nx;
+      if (head == NONE32) {
+        const uint32_t qi = atomicAdd(&s_next[w], 1u);
+        if (qi >= cnt) break;
+        head = s_q[w][qi];
+        y = head;
+        L = 1;
       }
-      hrec[x] = make_uint2(d, stop);
-      if (d > 0) last_of[last] = x;
-      cov += d;
+      const uint32_t ny = succ[y];
+      if (ny != NONE32 && L < cap) {
+        y = ny;
+        L++;
+        continue;
+      }
+      if (ny != NONE32) {
+        lng++;
+      } else if (KeyOps<K>::less(strand_kmer<K>(node_keys, head, k), strand_kmer<K>(node_keys, y ^ 1u, k))) {
+        // the mirror copy starts at the tail on the other strand; the copy
+        // whose first k-mer is smaller spells the smaller string
+        const uint32_t v = head >> 1;
+        is_head[v] = 1;
+        len_at_head[v] = L;
+        hstrand[v] = (uint8_t)(head & 1u);
+        cov += 2 * L;
+      }
+      head = NONE32;
     }
     __syncwarp();
   }
@@ -395,52 +375,17 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_half_claim(uint32_t *__restrict_
   }
 }
 
-// The other walker of walker x's unitig.
-__device__ __forceinline__ uint32_t half_partner(uint2 r, const uint32_t *last_of) {
-  return (r.y & 1u) ? last_of[r.y >> 1] : ((r.y >> 1) ^ 1u);
-}
-
-// Phase 2: per pair of walkers (handled by the smaller): the unitig's length,
-// the copy kept (the one whose first k-mer is smaller spells the smaller
-// string), and its first node h: is_head[h], len_at_head[h], hstrand[h];
-// uhead[x] = h for both walkers.
+// The first node of every kept unitig: its tables, node entry and first
+// k-mer, and where its walk continues (walk[u] = succ_base of the first
+// strand-node: the second one and the base it appends, or all ones).
 template <class K>
-__global__ void k_half_pair(const uint32_t *__restrict__ succ, uint64_t n, const uint2 *__restrict__ hrec,
-                            const uint32_t *__restrict__ last_of, const uint64_t *__restrict__ node_keys, int k,
-                            uint32_t *__restrict__ uhead, uint32_t *__restrict__ is_head,
-                            uint32_t *__restrict__ len_at_head, uint8_t *__restrict__ hstrand, uint32_t *err) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    if (!is_list_head(succ, i)) continue;
-    const uint32_t x = (uint32_t)i;
-    const uint2 r = hrec[x];
-    const uint32_t p = half_partner(r, last_of);
-    if (p >= n || p == x) {
-      atomicOr(err, ERR_INTERNAL);
-      continue;
-    }
-    if (x > p) continue;
-    const uint2 rp = hrec[p];
-    if (half_partner(rp, last_of) != x) {
-      atomicOr(err, ERR_INTERNAL);
-      continue;
-    }
-    const uint32_t kept = KeyOps<K>::less(strand_kmer<K>(node_keys, p, k), strand_kmer<K>(node_keys, x, k)) ? p : x;
-    const uint32_t h = kept >> 1;
-    is_head[h] = 1;
-    len_at_head[h] = r.x + rp.x;
-    hstrand[h] = (uint8_t)(kept & 1u);
-    uhead[x] = h;
-    uhead[p] = h;
-  }
-}
-
-// Per unitig (at its first node h): offsets and flags; hinfo[h] = (first
-// slot, unitig index, length, strand of h).
-__global__ void k_half_heads(const uint32_t *__restrict__ is_head, const uint64_t *__restrict__ uidx,
-                             const uint64_t *__restrict__ off_by_v, const uint32_t *__restrict__ len_at_head,
-                             const uint8_t *__restrict__ hstrand, uint64_t V, uint64_t U, int k,
+__global__ void k_fast_heads(const uint64_t *__restrict__ succ_base, const uint32_t *__restrict__ is_head,
+                             const uint8_t *__restrict__ hstrand, const uint64_t *__restrict__ uidx,
+                             const uint64_t *__restrict__ off_by_v, const uint64_t *__restrict__ node_keys,
+                             uint64_t V, uint64_t U, int k, uint64_t *__restrict__ nodes_out, char *__restrict__ seq,
                              uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
-                             uint8_t *__restrict__ circular, uint4 *__restrict__ hinfo) {
+                             uint8_t *__restrict__ circular, uint64_t *__restrict__ walk) {
+  const char *acgt = "ACGT";
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= V; v += (uint64_t)gridDim.x * blockDim.x) {
     if (v == V) {
       node_off[U] = V;
@@ -448,79 +393,56 @@ __global__ void k_half_heads(const uint32_t *__restrict__ is_head, const uint64_
       continue;
     }
     if (!is_head[v]) continue;
-    const uint64_t u = uidx[v], off = off_by_v[v];
+    const uint64_t u = uidx[v], off = off_by_v[v], so = off + u * (uint64_t)(k - 1);
+    const uint32_t y = 2 * (uint32_t)v + hstrand[v];
     node_off[u] = off;
-    seq_off[u] = off + u * (uint64_t)(k - 1);
+    seq_off[u] = so;
     circular[u] = 0;
-    hinfo[v] = make_uint4((uint32_t)off, (uint32_t)u, len_at_head[v], hstrand[v]);
+    nodes_out[off] = y;  // (node ID << 1) | strand
+    const K km = strand_kmer<K>(node_keys, y, k);
+    for (int j = 0; j < k; j++) seq[so + j] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - j), 2)];
+    walk[u] = succ_base[y];
   }
 }
 
-// Phase 3: every walker walks its half again (hrec[x].x nodes), loading
-// only successor words (successor | appended base << 32), and writes its
-// part of the unitig.  The kept copy's walker writes nodes j = 0, 1, ... at
-// the unitig's start, its first k-mer and then the base each arc appends;
-// the other walker writes node j at position L - 1 - j on the other strand,
-// the k-mer of its first node (the unitig's last k bases) and, for each arc,
-// the complement of the base it appends, which is the base k - 1 positions
-// before the end of the kept string's part it covers.  The two parts
-// overlap in k - 1 bases, written the same by both.
-template <class K>
-__global__ __launch_bounds__(WALK_BLOCK) void k_half_write(const uint32_t *__restrict__ succ,
-                                                           const uint64_t *__restrict__ succ_base, uint64_t n,
-                                                           const uint2 *__restrict__ hrec,
-                                                           const uint32_t *__restrict__ uhead,
-                                                           const uint4 *__restrict__ hinfo,
-                                                           const uint64_t *__restrict__ node_keys, int k,
-                                                           uint64_t *__restrict__ nodes_out, char *__restrict__ seq) {
-  __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
+// The rest of every kept unitig: lanes take unitigs in turn (per-warp
+// chunks, a shared-memory counter) and walk them, writing each node's entry
+// and the base its arc appends; only the successor words are loaded at random.
+__global__ __launch_bounds__(WALK_BLOCK) void k_fast_walk(const uint64_t *__restrict__ succ_base,
+                                                          const uint64_t *__restrict__ walk,
+                                                          const uint64_t *__restrict__ node_off,
+                                                          const uint64_t *__restrict__ seq_off, uint64_t U, int k,
+                                                          uint64_t *__restrict__ nodes_out, char *__restrict__ seq) {
   __shared__ uint32_t s_next[WALK_WARPS];
   const char *acgt = "ACGT";
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint64_t chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
+  const uint64_t chunks = (U + WALK_CHUNK - 1) / WALK_CHUNK;
   for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
-    const uint32_t cnt = queue_heads(c * WALK_CHUNK, n, s_q[w],
-                                     [&](uint64_t x) { return is_list_head(succ, x) && hrec[x].x > 0; });
+    const uint64_t u0 = c * WALK_CHUNK;
+    const uint32_t cnt = (uint32_t)min((uint64_t)WALK_CHUNK, U - u0);
     if (lane == 0) s_next[w] = 0;
     __syncwarp();
+    bool busy = false;
+    uint64_t nb = 0, pos = 0, spos = 0;
     for (;;) {
-      const uint32_t qi = atomicAdd(&s_next[w], 1u);
-      if (qi >= cnt) break;
-      const uint32_t x = s_q[w][qi];
-      const uint32_t d = hrec[x].x;
-      const uint32_t h = uhead[x];
-      const uint4 hi = hinfo[h];  // (first slot, unitig index, length, strand of h)
-      const bool kept = x == 2 * h + hi.w;
-      const uint64_t off = hi.x, L = hi.z, so = off + (uint64_t)hi.y * (uint64_t)(k - 1);
-      // the k-mer of the walker's first node, on the kept strand
-      const uint32_t y0 = kept ? x : (x ^ 1u);
-      const K km = strand_kmer<K>(node_keys, y0, k);
-      const uint64_t at = kept ? so : so + L - 1;
-      for (int j = 0; j < k; j++) seq[at + j] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - j), 2)];
-      uint32_t y = x;
-      for (uint32_t j = 0;; j++) {
-        if (kept)
-          nodes_out[off + j] = y;
-        else
-          nodes_out[off + L - 1 - j] = y ^ 1u;
-        if (j + 1 == d) break;
-        const uint64_t nb = succ_base[y];
-        y = (uint32_t)nb;
-        const uint32_t b = (uint32_t)(nb >> 32) & 3u;
-        if (kept)
-          seq[so + k + j] = acgt[b];
-        else
-          seq[so + L - 2 - j] = acgt[3u - b];
+      if (!busy) {
+        const uint32_t qi = atomicAdd(&s_next[w], 1u);
+        if (qi >= cnt) break;
+        const uint64_t u = u0 + qi;
+        nb = walk[u];
+        if (nb == ~0ull) continue;  // a single node
+        pos = node_off[u] + 1;
+        spos = seq_off[u] + k;
+        busy = true;
       }
+      const uint32_t y = (uint32_t)nb;
+      nodes_out[pos++] = y;
+      seq[spos++] = acgt[nb >> 32];
+      nb = succ_base[y];
+      busy = nb != ~0ull;
     }
     __syncwarp();
   }
-}
-
-// Clears the claim bits (before the general path reads the successors).
-__global__ void k_clear_claims(uint32_t *__restrict__ succ, uint64_t n) {
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
-    succ[x] &= ~CLAIM;
 }
 
 // enough warps to fill the device, at most one per chunk
@@ -608,37 +530,28 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
     link_edge.release();
     // ---- fast path: short acyclic lists only ----
     {
-      DevBuf hrec, last_of, uhead, f_is_head, f_len, f_strand, f_uidx, f_off;
-      DBG_TRY(alloc_buf(ctx, hrec, n1 * 8));
-      DBG_TRY(alloc_buf(ctx, last_of, V1 * 4));
+      DevBuf f_is_head, f_len, f_strand, f_uidx, f_off;
+      DBG_TRY(alloc_buf(ctx, f_is_head, V1 * 4));
+      DBG_TRY(alloc_buf(ctx, f_len, V1 * 4));
+      DBG_TRY(alloc_buf(ctx, f_strand, V1));
+      DBG_CUDA_TRY(cudaMemsetAsync(f_is_head.p, 0, V1 * 4, s));
+      DBG_CUDA_TRY(cudaMemsetAsync(f_len.p, 0, V1 * 4, s));
       DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 10, 0, 2 * sizeof(uint32_t), s));
-      DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 16.0 * V,
-                 k_half_claim<<<walk_grid(ctx, n), WALK_BLOCK, 0, s>>>(succ.as<uint32_t>(), n, kWalkCap,
-                                                                       hrec.as<uint2>(), last_of.as<uint32_t>(),
-                                                                       ctx->d_counters + 10, ctx->d_counters + 11));
+      DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 32.0 * n + 16.0 * V,
+                 k_fast_measure<K><<<walk_grid(ctx, n), WALK_BLOCK, 0, s>>>(succ.as<uint32_t>(), n,
+                                                                            g->node_keys.as<uint64_t>(), k,
+                                                              kWalkCap, f_is_head.as<uint32_t>(),
+                                                              f_len.as<uint32_t>(), f_strand.as<uint8_t>(),
+                                                              ctx->d_counters + 10, ctx->d_counters + 11));
       DBG_CUDA_TRY(cudaGetLastError());
       uint32_t cnt[2] = {0, 0};
       DBG_TRY(read_small(ctx, ctx->d_counters + 10, sizeof(cnt), cnt));
-      if (cnt[1] == 0 && cnt[0] == V) {
-        DBG_TRY(alloc_buf(ctx, uhead, n1 * 4));
-        DBG_TRY(alloc_buf(ctx, f_is_head, V1 * 4));
-        DBG_TRY(alloc_buf(ctx, f_len, V1 * 4));
-        DBG_TRY(alloc_buf(ctx, f_strand, V1));
-        DBG_CUDA_TRY(cudaMemsetAsync(f_is_head.p, 0, V1 * 4, s));
-        DBG_CUDA_TRY(cudaMemsetAsync(f_len.p, 0, V1 * 4, s));
-        DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 16.0 * V,
-                   k_half_pair<K><<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n, hrec.as<uint2>(),
-                                                             last_of.as<uint32_t>(), g->node_keys.as<uint64_t>(), k,
-                                                             uhead.as<uint32_t>(), f_is_head.as<uint32_t>(),
-                                                             f_len.as<uint32_t>(), f_strand.as<uint8_t>(),
-                                                             ctx->d_err));
-        DBG_CUDA_TRY(cudaGetLastError());
+      if (cnt[1] == 0 && cnt[0] == n) {
         DBG_TRY(alloc_buf(ctx, f_uidx, (V + 1) * 8));
         DBG_TRY(alloc_buf(ctx, f_off, (V + 1) * 8));
         uint32_t U32 = 0, total = 0;
         DBG_TRY(scan_excl(ctx, f_is_head.as<uint32_t>(), V, f_uidx.as<uint64_t>(), &U32));
         DBG_TRY(scan_excl(ctx, f_len.as<uint32_t>(), V, f_off.as<uint64_t>(), &total));
-        DBG_TRY(check_device_error(ctx));
         if (total != V) {
           set_error("unitigs hold %u nodes, expected %llu", total, (unsigned long long)V);
           return DBG_EINTERNAL;
@@ -651,26 +564,23 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
         DBG_TRY(alloc_buf(ctx, u->nodes, V1 * 8));
         u->total_bases = V + Uf * (uint64_t)(k - 1);
         DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
-        DevBuf hinfo;
-        DBG_TRY(alloc_buf(ctx, hinfo, V1 * sizeof(uint4)));
-        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)V * 4 + (double)Uf * (16 + 8 + 4 + 1 + 8 + 8 + 1 + 16),
-                   k_half_heads<<<grid_of(V + 1), 256, 0, s>>>(
-                       f_is_head.as<uint32_t>(), f_uidx.as<uint64_t>(), f_off.as<uint64_t>(), f_len.as<uint32_t>(),
-                       f_strand.as<uint8_t>(), V, Uf, k, u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(),
-                       u->circular.as<uint8_t>(), hinfo.as<uint4>()));
-        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT,
-                   4.0 * n + (double)V * (8 + 8 + 1) + 2.0 * Uf * (8 + 4 + 16 + 8 * g->key_words + k),
-                   k_half_write<K><<<walk_grid(ctx, n), WALK_BLOCK, 0, s>>>(
-                       succ.as<uint32_t>(), word.as<uint64_t>(), n, hrec.as<uint2>(), uhead.as<uint32_t>(),
-                       hinfo.as<uint4>(), g->node_keys.as<uint64_t>(), k, u->nodes.as<uint64_t>(),
-                       u->seq.as<char>()));
+        DevBuf walk;
+        DBG_TRY(alloc_buf(ctx, walk, std::max<uint64_t>(1, Uf) * 8));
+        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)V * (4 + 1) + (double)Uf * (16 + 8 + 8 * g->key_words + 8 + 25 + k),
+                   k_fast_heads<K><<<grid_of(V + 1), 256, 0, s>>>(
+                       word.as<uint64_t>(), f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_uidx.as<uint64_t>(),
+                       f_off.as<uint64_t>(), g->node_keys.as<uint64_t>(), V, Uf, k, u->nodes.as<uint64_t>(),
+                       u->seq.as<char>(), u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(),
+                       u->circular.as<uint8_t>(), walk.as<uint64_t>()));
+        if (Uf > 0)
+          DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)(V - Uf) * (8 + 8 + 1) + (double)Uf * 24,
+                     k_fast_walk<<<walk_grid(ctx, Uf), WALK_BLOCK, 0, s>>>(
+                         word.as<uint64_t>(), walk.as<uint64_t>(), u->node_off.as<uint64_t>(),
+                         u->seq_off.as<uint64_t>(), Uf, k, u->nodes.as<uint64_t>(), u->seq.as<char>()));
         DBG_CUDA_TRY(cudaGetLastError());
         DBG_CUDA_TRY(cudaStreamSynchronize(s));
         return check_device_error(ctx);
       }
-      // long lists or cycles: the general path reads plain successors
-      DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n,
-                 k_clear_claims<<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n));
     }
     // ---- general path: long lists or cycles present ----
     DBG_CUDA_TRY(cudaMemsetAsync(word.p, 0xff, n * 8, s));
@@ -794,8 +704,8 @@ dbg_status dbg_compact(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs **out) {
     set_error("ctx or graph is NULL");
     return DBG_EINVAL;
   }
-  if (g->num_nodes >= (1ull << 30)) {
-    set_error("compaction handles fewer than 2^30 nodes");
+  if (g->num_nodes >= 0x7fffffffull) {
+    set_error("compaction handles fewer than 2^31 nodes");
     return DBG_EOVERFLOW;
   }
   int prev = -1;
