@@ -82,6 +82,24 @@ class _Range(ctypes.Structure):
     ]
 
 
+class _Simple(ctypes.Structure):
+    _fields_ = [
+        ("n_units", ctypes.c_uint64),
+        ("n_edges", ctypes.c_uint64),
+        ("removed", ctypes.c_uint64),
+        ("node_off", ctypes.POINTER(ctypes.c_uint64)),
+        ("nodes", ctypes.POINTER(ctypes.c_uint64)),
+        ("seq_off", ctypes.POINTER(ctypes.c_uint64)),
+        ("seq", ctypes.POINTER(ctypes.c_char)),
+        ("circular", ctypes.POINTER(ctypes.c_uint8)),
+        ("unit_a", ctypes.POINTER(ctypes.c_uint32)),
+        ("unit_b", ctypes.POINTER(ctypes.c_uint32)),
+        ("side_a", ctypes.POINTER(ctypes.c_uint8)),
+        ("side_b", ctypes.POINTER(ctypes.c_uint8)),
+        ("edge", ctypes.POINTER(ctypes.c_uint32)),
+    ]
+
+
 def _load():
     global _lib
     with _lock:
@@ -118,6 +136,11 @@ def _load():
             lib.orc_graph_range.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.POINTER(_Range))]
+            lib.orc_simplify.restype = ctypes.c_int
+            lib.orc_simplify.argtypes = [ctypes.POINTER(_Graph), ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.POINTER(_Simple))]
+            lib.orc_simple_free.restype = None
+            lib.orc_simple_free.argtypes = [ctypes.POINTER(_Simple)]
             lib.orc_range_free.restype = None
             lib.orc_range_free.argtypes = [ctypes.POINTER(_Range)]
             _lib = lib
@@ -347,3 +370,39 @@ def node_reads(reads, lengths, k: int) -> tuple[np.ndarray, np.ndarray]:
         lib.orc_free(ctypes.cast(kp, ctypes.c_void_p))
         lib.orc_free(ctypes.cast(cp, ctypes.c_void_p))
     return keys, counts
+
+
+class OracleSimple:
+    """The simplified graph (Section 6 / 6.1): units (reported chains and
+    single nodes) as node lists and strings, and the edges between units."""
+
+    def __init__(self, ptr, k):
+        r = ptr.contents
+        self.k = k
+        self.n_units, self.n_edges, self.removed = int(r.n_units), int(r.n_edges), int(r.removed)
+        U, M = self.n_units, self.n_edges
+        self.node_off = _copy(r.node_off, U + 1, np.uint64)
+        self.nodes = _copy(r.nodes, int(self.node_off[-1]) if U else 0, np.uint64)
+        self.seq_off = _copy(r.seq_off, U + 1, np.uint64)
+        n_seq = int(self.seq_off[-1]) if U else 0
+        self.seq = ctypes.string_at(r.seq, n_seq) if n_seq else b""
+        self.circular = _copy(r.circular, U, np.uint8)
+        self.unit_a = _copy(r.unit_a, M, np.uint32)
+        self.unit_b = _copy(r.unit_b, M, np.uint32)
+        self.side_a = _copy(r.side_a, M, np.uint8)
+        self.side_b = _copy(r.side_b, M, np.uint8)
+        self.edge = _copy(r.edge, M, np.uint32)
+        _lib.orc_simple_free(ptr)
+
+    def strings(self) -> list[str]:
+        return [self.seq[self.seq_off[i]:self.seq_off[i + 1]].decode() for i in range(self.n_units)]
+
+
+def simplify(graph: OracleGraph, min_nodes: int = 3) -> OracleSimple:
+    """The simplified graph with chains of at least min_nodes nodes merged."""
+    lib = _load()
+    out = ctypes.POINTER(_Simple)()
+    rc = lib.orc_simplify(graph._ptr, min_nodes, ctypes.byref(out))
+    if rc != ORC_OK:
+        raise OracleError(rc, "orc_simplify")
+    return OracleSimple(out, graph.k)

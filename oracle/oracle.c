@@ -789,7 +789,17 @@ static int spell_chain(const orc_graph *g, const uint64_t *list, uint64_t m, cha
   return 1;
 }
 
-int orc_compact(const orc_graph *g, orc_unitigs **out) {
+/* The chains of the graph under one of two merging rules:
+ *   literal = 0: an edge is merged when its ends are on distinct nodes and
+ *                each end's side carries no other edge end (the unitigs);
+ *   literal = 1: Section 6.1's candidate edges, "adjacent on nodes with
+ *                exactly one in and out degree": an edge is merged when its
+ *                ends are on distinct nodes that both have exactly one edge
+ *                end on each side (a walk enters a node by one side and
+ *                leaves by the other, so a node's in- and out-degree are its
+ *                two side degrees).
+ * Every node lies in exactly one chain (singletons included). */
+static int compact_rule(const orc_graph *g, int literal, orc_unitigs **out) {
   if (!g || !out) return ORC_EINVAL;
   *out = NULL;
   uint64_t nv = g->n_nodes, ne = g->n_edges;
@@ -820,6 +830,9 @@ int orc_compact(const orc_graph *g, orc_unitigs **out) {
     int o1 = g->orient[i] >> 1, o2 = g->orient[i] & 1;
     int sa_ = o1 ? SIDE_L : SIDE_R, sb_ = o2 ? SIDE_R : SIDE_L;
     if (a == b || deg[2 * a + sa_] != 1 || deg[2 * b + sb_] != 1) continue;
+    if (literal && !(deg[2 * a + SIDE_L] == 1 && deg[2 * a + SIDE_R] == 1 && deg[2 * b + SIDE_L] == 1 &&
+                     deg[2 * b + SIDE_R] == 1))
+      continue;
     link[2 * a + sa_].node = (int64_t)b; link[2 * a + sa_].side = sb_;
     link[2 * b + sb_].node = (int64_t)a; link[2 * b + sb_].side = sa_;
   }
@@ -893,5 +906,168 @@ int orc_compact(const orc_graph *g, orc_unitigs **out) {
   free(sa); free(sb);
   if (rc != ORC_OK) { orc_unitigs_free(u); return rc; }
   *out = u;
+  return ORC_OK;
+}
+
+int orc_compact(const orc_graph *g, orc_unitigs **out) { return compact_rule(g, 0, out); }
+
+/* ------------------------------------------------------------------ */
+/* the simplified graph: the literal compaction of Section 6.1          */
+/* ------------------------------------------------------------------ */
+
+/* Section 6.1 merges the chains of candidate edges (compact_rule, literal
+ * = 1) and reports "only the chains which are resultant of compaction of at
+ * least three bi-directed nodes"; Section 6 describes the compacted graph:
+ * a merged chain is one node labelled with its spelled string, and an edge
+ * that touches a chain anywhere but at its two free ends no longer fits the
+ * label and is removed as inconsistent.  Here:
+ *   - units: every chain of at least min_nodes nodes (its nodes, string and
+ *     circular flag as a unitig), and every node of a shorter chain on its
+ *     own (positive strand, its k-mer), ordered by their first node's ID;
+ *   - edges: every edge not inside a reported chain, in edge-ID order, each
+ *     end relabelled to (unit, side): the end at a unit's first node on that
+ *     node's entry side is the unit's left side (0), the end at its last
+ *     node on the exit side its right side (1) -- a node on strand 0 is
+ *     entered by its left side and left by its right, on strand 1 the other
+ *     way round; any other end is inconsistent, and its edge is removed and
+ *     counted in `removed`. */
+typedef struct {
+  uint64_t n_units, n_edges, removed;
+  uint64_t *node_off;  /* n_units + 1 */
+  uint64_t *nodes;     /* (node ID << 1) | strand */
+  uint64_t *seq_off;   /* n_units + 1 */
+  char *seq;
+  uint8_t *circular;
+  uint32_t *unit_a, *unit_b;  /* per edge: the units of its src and dst ends */
+  uint8_t *side_a, *side_b;   /* 0 left, 1 right */
+  uint32_t *edge;             /* the edge's ID in the graph */
+} orc_simple;
+
+void orc_simple_free(orc_simple *s) {
+  if (!s) return;
+  free(s->node_off); free(s->nodes); free(s->seq_off); free(s->seq); free(s->circular);
+  free(s->unit_a); free(s->unit_b); free(s->side_a); free(s->side_b); free(s->edge);
+  free(s);
+}
+
+typedef struct { uint64_t first_node, chain, node; int whole; } unit_ref;
+
+static int cmp_unit_ref(const void *pa, const void *pb) {
+  uint64_t a = ((const unit_ref *)pa)->first_node, b = ((const unit_ref *)pb)->first_node;
+  return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+int orc_simplify(const orc_graph *g, uint32_t min_nodes, orc_simple **out) {
+  if (!g || !out) return ORC_EINVAL;
+  *out = NULL;
+  orc_unitigs *ch = NULL;
+  int rc = compact_rule(g, 1, &ch);
+  if (rc != ORC_OK) return rc;
+  const uint64_t nv = g->n_nodes, ne = g->n_edges;
+  const int K = (int)g->k;
+  orc_simple *s = (orc_simple *)calloc(1, sizeof(orc_simple));
+  unit_ref *refs = (unit_ref *)malloc((nv + 1) * sizeof(unit_ref));
+  uint64_t *unit_of = (uint64_t *)malloc((nv + 1) * sizeof(uint64_t));
+  uint64_t *pos_of = (uint64_t *)malloc((nv + 1) * sizeof(uint64_t));
+  uint8_t *strand_of = (uint8_t *)malloc(nv + 1);
+  uint64_t *deg = (uint64_t *)calloc(2 * nv + 1, sizeof(uint64_t));
+  uint64_t *ulen = (uint64_t *)malloc((nv + 1) * sizeof(uint64_t));
+  if (!s || !refs || !unit_of || !pos_of || !strand_of || !deg || !ulen) rc = ORC_ENOMEM;
+
+  /* units: reported chains whole, the nodes of the others one by one */
+  uint64_t nu = 0;
+  for (uint64_t c = 0; rc == ORC_OK && c < ch->count; c++) {
+    const uint64_t m = ch->node_off[c + 1] - ch->node_off[c];
+    if (m >= min_nodes) {
+      refs[nu].first_node = ch->nodes[ch->node_off[c]] >> 1;
+      refs[nu].chain = c; refs[nu].whole = 1; nu++;
+    } else {
+      for (uint64_t i = 0; i < m; i++) {
+        refs[nu].first_node = ch->nodes[ch->node_off[c] + i] >> 1;
+        refs[nu].node = refs[nu].first_node; refs[nu].whole = 0; nu++;
+      }
+    }
+  }
+  if (rc == ORC_OK) {
+    qsort(refs, nu, sizeof(unit_ref), cmp_unit_ref);
+    s->n_units = nu;
+    s->node_off = (uint64_t *)malloc((nu + 1) * sizeof(uint64_t));
+    s->seq_off = (uint64_t *)malloc((nu + 1) * sizeof(uint64_t));
+    s->nodes = (uint64_t *)malloc((nv + 1) * sizeof(uint64_t));
+    s->circular = (uint8_t *)malloc(nu + 1);
+    s->seq = (char *)malloc(nv + nu * (uint64_t)(K - 1) + 1);
+    if (!s->node_off || !s->seq_off || !s->nodes || !s->circular || !s->seq) rc = ORC_ENOMEM;
+  }
+  uint64_t no = 0, so = 0;
+  for (uint64_t u = 0; rc == ORC_OK && u < nu; u++) {
+    s->node_off[u] = no;
+    s->seq_off[u] = so;
+    if (refs[u].whole) {
+      const uint64_t c = refs[u].chain, m = ch->node_off[c + 1] - ch->node_off[c];
+      memcpy(s->nodes + no, ch->nodes + ch->node_off[c], m * sizeof(uint64_t));
+      memcpy(s->seq + so, ch->seq + ch->seq_off[c], m + (uint64_t)K - 1);
+      s->circular[u] = ch->circular[c];
+      ulen[u] = m;
+    } else {
+      s->nodes[no] = refs[u].node << 1;
+      mer_spell(graph_node(g, refs[u].node), K, s->seq + so);
+      s->circular[u] = 0;
+      ulen[u] = 1;
+    }
+    for (uint64_t i = 0; i < ulen[u]; i++) {
+      const uint64_t x = s->nodes[no + i];
+      unit_of[x >> 1] = u; pos_of[x >> 1] = i; strand_of[x >> 1] = (uint8_t)(x & 1);
+    }
+    no += ulen[u];
+    so += ulen[u] + (uint64_t)K - 1;
+  }
+  if (rc == ORC_OK) {
+    s->node_off[nu] = no;
+    s->seq_off[nu] = so;
+    if (no != nv) rc = ORC_EINTERNAL;
+  }
+
+  /* edges: drop those inside reported chains, relabel the others' ends */
+  for (uint64_t i = 0; rc == ORC_OK && i < ne; i++) {
+    deg[2 * (uint64_t)g->src[i] + ((g->orient[i] >> 1) ? SIDE_L : SIDE_R)]++;
+    deg[2 * (uint64_t)g->dst[i] + ((g->orient[i] & 1) ? SIDE_R : SIDE_L)]++;
+  }
+  if (rc == ORC_OK) {
+    s->unit_a = (uint32_t *)malloc((ne + 1) * sizeof(uint32_t));
+    s->unit_b = (uint32_t *)malloc((ne + 1) * sizeof(uint32_t));
+    s->side_a = (uint8_t *)malloc(ne + 1);
+    s->side_b = (uint8_t *)malloc(ne + 1);
+    s->edge = (uint32_t *)malloc((ne + 1) * sizeof(uint32_t));
+    if (!s->unit_a || !s->unit_b || !s->side_a || !s->side_b || !s->edge) rc = ORC_ENOMEM;
+  }
+  uint64_t kept = 0;
+  for (uint64_t i = 0; rc == ORC_OK && i < ne; i++) {
+    const uint64_t a = g->src[i], b = g->dst[i];
+    const int sa = (g->orient[i] >> 1) ? SIDE_L : SIDE_R, sb = (g->orient[i] & 1) ? SIDE_R : SIDE_L;
+    const int simple_a = deg[2 * a + SIDE_L] == 1 && deg[2 * a + SIDE_R] == 1;
+    const int simple_b = deg[2 * b + SIDE_L] == 1 && deg[2 * b + SIDE_R] == 1;
+    /* a candidate edge lies inside its chain; reported chains swallow it */
+    if (a != b && simple_a && simple_b && ulen[unit_of[a]] > 1) continue;
+    const uint64_t ends[2] = {a, b};
+    const int sides[2] = {sa, sb};
+    int unit_side[2] = {-1, -1};
+    for (int j = 0; j < 2; j++) {
+      const uint64_t x = ends[j], u = unit_of[x];
+      const int st = strand_of[x];
+      const int entry = st ? SIDE_R : SIDE_L, exit_ = st ? SIDE_L : SIDE_R;
+      if (!s->circular[u] && pos_of[x] == 0 && sides[j] == entry) unit_side[j] = 0;
+      else if (!s->circular[u] && pos_of[x] == ulen[u] - 1 && sides[j] == exit_) unit_side[j] = 1;
+    }
+    if (unit_side[0] < 0 || unit_side[1] < 0) { s->removed++; continue; }
+    s->unit_a[kept] = (uint32_t)unit_of[a]; s->side_a[kept] = (uint8_t)unit_side[0];
+    s->unit_b[kept] = (uint32_t)unit_of[b]; s->side_b[kept] = (uint8_t)unit_side[1];
+    s->edge[kept] = (uint32_t)i;
+    kept++;
+  }
+  if (rc == ORC_OK) s->n_edges = kept;
+  free(refs); free(unit_of); free(pos_of); free(strand_of); free(deg); free(ulen);
+  orc_unitigs_free(ch);
+  if (rc != ORC_OK) { orc_simple_free(s); return rc; }
+  *out = s;
   return ORC_OK;
 }

@@ -499,3 +499,133 @@ def test_graph_range_empty_and_bad_arguments():
         oracle.graph_range(reads, lengths, 4, (0, 255), (0, 63))
     with pytest.raises(oracle.OracleError):
         oracle.graph_range(b"ACGTNCGTTG", lengths, 3, (0, 255), (0, 63))
+
+
+# ---------------------------------------------------------------------------
+# the simplified graph: Section 6.1's literal compaction (candidate edges on
+# nodes with one edge end on each side, chains of at least min_nodes nodes
+# reported) and the relabelled edges between units (Section 6)
+# ---------------------------------------------------------------------------
+
+def side_degrees(g):
+    deg = np.zeros((g.n_nodes, 2), dtype=np.int64)  # [:, 0] left, [:, 1] right
+    for i in range(g.n_edges):
+        o1, o2 = int(g.orient[i]) >> 1, int(g.orient[i]) & 1
+        deg[g.src[i], 0 if o1 else 1] += 1
+        deg[g.dst[i], 1 if o2 else 0] += 1
+    return deg
+
+
+def literal_components(g):
+    """Node sets of the chains by definition: union-find over the candidate
+    edges (distinct end nodes, both with exactly one edge end per side)."""
+    deg = side_degrees(g)
+    simple = (deg[:, 0] == 1) & (deg[:, 1] == 1)
+    parent = list(range(g.n_nodes))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    cand = 0
+    for i in range(g.n_edges):
+        a, b = int(g.src[i]), int(g.dst[i])
+        if a != b and simple[a] and simple[b]:
+            parent[find(a)] = find(b)
+            cand += 1
+    comps = {}
+    for v in range(g.n_nodes):
+        comps.setdefault(find(v), set()).add(v)
+    return sorted(sorted(c) for c in comps.values()), cand
+
+
+def check_simple(g, s, min_nodes):
+    k = g.k
+    nodes = [kmer_str(v, k) for v in g.node_ints()]
+    # units hold every node once and spell their nodes, like unitigs
+    ids = [int(x) >> 1 for x in s.nodes]
+    assert sorted(ids) == list(range(g.n_nodes))
+    firsts = [int(s.nodes[s.node_off[u]]) >> 1 for u in range(s.n_units)]
+    assert firsts == sorted(firsts)
+    strs = s.strings()
+    for u in range(s.n_units):
+        lst = s.nodes[s.node_off[u]:s.node_off[u + 1]]
+        assert len(strs[u]) == len(lst) + k - 1
+        for i, x in enumerate(lst):
+            km = strs[u][i:i + k]
+            assert sm.canonical(km) == nodes[int(x) >> 1] and (km == nodes[int(x) >> 1]) == ((int(x) & 1) == 0)
+    # the reported chains are exactly the definition's components of size >= min_nodes
+    comps, cand = literal_components(g)
+    multi = [sorted(int(x) >> 1 for x in s.nodes[s.node_off[u]:s.node_off[u + 1]])
+             for u in range(s.n_units) if s.node_off[u + 1] - s.node_off[u] > 1]
+    assert sorted(multi) == [c for c in comps if len(c) >= max(2, min_nodes)]
+    # every edge is inside a reported chain or relabelled, none is removed
+    inside = sum(len(c) - 1 for c in comps if len(c) >= max(2, min_nodes))
+    inside += sum(1 for u in range(s.n_units) if s.circular[u])
+    assert s.removed == 0 and s.n_edges + inside == g.n_edges
+    assert list(s.edge) == sorted(s.edge)
+    # a relabelled edge joins the unit strings consistently: read unit a so
+    # that the edge leaves by side_a and unit b so that it enters by side_b;
+    # they overlap in k - 1 bases and spell the edge's (k+1)-mer
+    keys = [kmer_str(z, k + 1) for z in g.edge_ints()]
+    for j in range(s.n_edges):
+        x = strs[s.unit_a[j]] if s.side_a[j] == 1 else sm.rc(strs[s.unit_a[j]])
+        y = strs[s.unit_b[j]] if s.side_b[j] == 0 else sm.rc(strs[s.unit_b[j]])
+        assert x[len(x) - k + 1:] == y[:k - 1]
+        assert sm.canonical(x[len(x) - k:] + y[k - 1]) == keys[s.edge[j]]
+
+
+def test_simplify_single_read_closed_form():
+    """One read whose k-mers are distinct is a path of m nodes: its two end
+    nodes have a side with no edge, so the candidates join the m - 2 inner
+    nodes; with m - 2 >= 3 the units are first node, inner chain, last node
+    joined by two edges, otherwise m single nodes and m - 1 edges."""
+    rng = np.random.default_rng(31)
+    for k, L in ((5, 12), (7, 13), (7, 16), (9, 30), (5, 9)):
+        r = distinct_kmer_read(rng, L, k)
+        g = build([r], k)
+        s = oracle.simplify(g, 3)
+        m = L - k + 1
+        check_simple(g, s, 3)
+        if m - 2 >= 3:
+            assert s.n_units == 3 and s.n_edges == 2
+            assert sorted(len(x) for x in s.strings()) == [k, k, m - 2 + k - 1]
+        else:
+            assert s.n_units == m and s.n_edges == m - 1
+
+
+@pytest.mark.parametrize("k,min_nodes", [(3, 1), (3, 3), (5, 2), (5, 3), (7, 3), (9, 4)])
+def test_simplify_random_read_sets(k, min_nodes):
+    rng = np.random.default_rng(500 + 10 * k + min_nodes)
+    for trial in range(25):
+        genome = "".join(rng.choice(list("ACGT"), size=int(rng.integers(20, 120))))
+        reads = []
+        for _ in range(int(rng.integers(3, 30))):
+            a = int(rng.integers(0, len(genome) - k))
+            r = genome[a:a + int(rng.integers(k, 3 * k + 10))]
+            reads.append(sm.rc(r) if rng.random() < 0.5 else r)
+        g = build(reads, k)
+        s = oracle.simplify(g, min_nodes)
+        check_simple(g, s, min_nodes)
+
+
+def test_simplify_circular_and_min_nodes_one():
+    """A circular genome tiled by reads whose nodes all have one edge end per
+    side is one circular unit; with min_nodes = 1 the units are exactly the
+    components of the candidate edges (the literal chains)."""
+    rng = np.random.default_rng(33)
+    k = 7
+    genome = distinct_kmer_read(rng, 60, k)
+    circ = genome + genome[:k]
+    reads = [circ[i:i + 20] for i in range(0, len(genome), 5)] + [circ[len(genome) - 10:] + circ[k:k + 15]]
+    g = build(reads, k)
+    s = oracle.simplify(g, 3)
+    check_simple(g, s, 3)
+    assert s.n_units == 1 and s.circular[0] == 1 and s.n_edges == 0
+    g2 = build([genome[:40], genome[30:]], k)
+    s1 = oracle.simplify(g2, 1)
+    check_simple(g2, s1, 1)
+    comps, _ = literal_components(g2)
+    assert s1.n_units == len(comps)
