@@ -221,6 +221,38 @@ dbg_status dbg_unitigs_get(const dbg_unitigs *u, uint64_t *node_off, uint64_t *n
 void dbg_unitigs_free(dbg_unitigs *u);
 
 /* ----------------------------------------------------------------------
+ * dbg_simplify -- the simplified bi-directed graph (Section 6) with the
+ * literal chain compaction of Section 6.1.
+ * Candidate edges are those "adjacent on nodes with exactly one in and out
+ * degree": an edge whose ends lie on two distinct nodes that each carry
+ * exactly one edge end on each side (a walk enters a node by one side and
+ * leaves by the other).  Their chains (paths or cycles, found by the list
+ * ranking of dbg_compact) of at least min_nodes nodes are merged into one
+ * unit each (Section 6.1 reports chains of at least 3); every other node is
+ * a unit of its own, on its positive strand.  Units are listed like
+ * unitigs (dbg_simple_units: node lists, spelled strings, circular flags),
+ * ascending by first node ID.  Every edge not inside a merged chain is kept
+ * in graph edge order with its ends relabelled to (unit, side): side 0 is
+ * the unit's left side (its first node's entry side), 1 its right side (its
+ * last node's exit side).  An edge with an end anywhere else on a unit no
+ * longer fits the unit's label (Section 6); it is removed and counted in
+ * dbg_simple_removed_edges (none exist under this candidate rule).
+ *   unit_a, side_a: the src end; unit_b, side_b: the dst end; edge: its ID
+ *   in g.  Any pointer may be NULL.  Host or device buffers.
+ * -------------------------------------------------------------------- */
+typedef struct dbg_simple dbg_simple;
+dbg_status dbg_simplify(dbg_ctx *ctx, const dbg_graph *g, uint32_t min_nodes, dbg_simple **out);
+uint64_t dbg_simple_num_units(const dbg_simple *s);
+uint64_t dbg_simple_num_edges(const dbg_simple *s);
+uint64_t dbg_simple_removed_edges(const dbg_simple *s);
+uint64_t dbg_simple_total_bases(const dbg_simple *s);
+dbg_status dbg_simple_units(const dbg_simple *s, uint64_t *node_off, uint64_t *nodes, uint64_t *seq_off, char *seq,
+                            uint8_t *circular);
+dbg_status dbg_simple_edges(const dbg_simple *s, uint32_t *unit_a, uint8_t *side_a, uint32_t *unit_b,
+                            uint8_t *side_b, uint32_t *edge);
+void dbg_simple_free(dbg_simple *s);
+
+/* ----------------------------------------------------------------------
  * Many constructions at once (batched builds and a request server).
  *
  * A read set as dbg_build takes it.  The buffers are borrowed until the

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libdbg.so")
 
-SOURCES = ["api.cu", "build_u64.cu", "build_u128.cu", "compact.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["api.cu", "build_u64.cu", "build_u128.cu", "compact.cu", "noalloc.cu", "serve.cu", "simplify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
               f"-I{INCLUDE}"]

@@ -39,7 +39,8 @@ __device__ __forceinline__ uint32_t end_side(uint8_t orient, uint32_t role) {
   return role == 0 ? (o1 ? 0u : 1u) : (o2 ? 1u : 0u);
 }
 
-// Per node and side: the edge end alone on that side, if exactly one is.
+// Per node and side: the edge end alone on that side, if exactly one is
+// (with `literal`, only at nodes whose two sides each carry one end).
 // link_node[2v + side] = (w << 1) | side_at_w of the edge's other end, and
 // link_edge[2v + side] = the edge | (entry base << 32), the edge being NONE
 // when the side has 0 or >= 2 ends.  The entry base is the last base of v's
@@ -51,7 +52,8 @@ template <class K>
 __global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ adj_nbr,
                              const uint32_t *__restrict__ adj_edge, const uint8_t *__restrict__ adj_role,
                              const uint8_t *__restrict__ orient, const uint64_t *__restrict__ node_keys, uint64_t V,
-                             int k, uint32_t *__restrict__ link_node, uint64_t *__restrict__ link_edge) {
+                             int k, bool literal, uint32_t *__restrict__ link_node,
+                             uint64_t *__restrict__ link_edge) {
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t cnt[2] = {0, 0}, e_at[2] = {NONE32, NONE32}, far[2] = {NONE32, NONE32};
     const uint64_t p0 = row_ptr[v], p1 = row_ptr[v + 1];
@@ -65,10 +67,13 @@ __global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_
     }
     const K kv = load_node_key<K>(node_keys, v);
     const uint64_t entry[2] = {KeyOps<K>::low2(kv), 3u - KeyOps<K>::digit(kv, 2 * (k - 1), 2)};
+    // the literal rule (Section 6.1) links only nodes with one end per side
+    const bool ok = !literal || (cnt[0] == 1 && cnt[1] == 1);
 #pragma unroll
     for (int sd = 0; sd < 2; sd++) {
-      link_node[2 * v + sd] = cnt[sd] == 1 ? far[sd] : NONE32;
-      link_edge[2 * v + sd] = (entry[sd] << 32) | (cnt[sd] == 1 ? e_at[sd] : NONE32);
+      const bool one = ok && cnt[sd] == 1;
+      link_node[2 * v + sd] = one ? far[sd] : NONE32;
+      link_edge[2 * v + sd] = (entry[sd] << 32) | (one ? e_at[sd] : NONE32);
     }
   }
 }
@@ -502,7 +507,7 @@ static dbg_status jump_until_stable(dbg_ctx *ctx, const uint32_t *list, uint32_t
 constexpr uint32_t kWalkCap = 2048;
 
 template <class K>
-static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u) {
+static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u, bool literal = false) {
   cudaStream_t s = ctx->stream;
   const uint64_t V = g->num_nodes, n = 2 * V, E2 = 2 * g->num_edges;
   const int k = (int)g->k;
@@ -521,7 +526,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
                k_side_links<K><<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
                                                           g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
                                                           g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
-                                                          link_node.as<uint32_t>(), link_edge.as<uint64_t>()));
+                                                          literal, link_node.as<uint32_t>(), link_edge.as<uint64_t>()));
     // succ_base goes to the ranking words' buffer (free until the general path)
     DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n + 8.0 * n + 12.0 * n,
                k_successors<<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(), V,
@@ -691,6 +696,10 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u)
   return check_device_error(ctx);
 }
 
+dbg_status compact_chains(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u, bool literal) {
+  return g->key_words == 1 ? compact_impl<uint64_t>(ctx, g, u, literal) : compact_impl<Key128>(ctx, g, u, literal);
+}
+
 }  // namespace dbg
 
 using namespace dbg;
@@ -715,7 +724,7 @@ dbg_status dbg_compact(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs **out) {
   if (!u) return DBG_ENOMEM;
   u->al = ctx->al;
   u->device = ctx->device;
-  dbg_status st = g->key_words == 1 ? compact_impl<uint64_t>(ctx, g, u) : compact_impl<Key128>(ctx, g, u);
+  dbg_status st = compact_chains(ctx, g, u, false);
   for (DevBuf *b : {&u->node_off, &u->nodes, &u->seq_off, &u->seq, &u->circular}) b->al = &u->al;
   cudaStreamSynchronize(ctx->stream);
   prof_resolve(ctx);

@@ -153,6 +153,13 @@ struct dbg_unitigs {
   dbg::DevBuf node_off, nodes, seq_off, seq, circular;
 };
 
+// The simplified graph: units (as unitigs) and the relabelled edges.
+struct dbg_simple {
+  dbg_unitigs units;
+  uint64_t num_edges = 0, removed = 0;
+  dbg::DevBuf unit_a, unit_b, side_a, side_b, edge;
+};
+
 namespace dbg {
 
 #define DBG_CUDA_TRY(expr)                                                              \
@@ -254,6 +261,9 @@ uint64_t build_footprint(uint64_t n, uint64_t bases, uint64_t N, uint64_t I, uin
                          bool lengths_on_host);
 
 dbg_status build_graph_u64(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g);
+// The chains of g into u: the unitigs (literal = false) or the chains of
+// Section 6.1's candidate edges (literal = true).
+dbg_status compact_chains(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u, bool literal);
 // IDs of the nodes held by at least t distinct reads (device buffer of
 // num_nodes entries, or NULL for the count only)
 dbg_status roadmap_nodes(dbg_ctx *ctx, const dbg_graph *g, uint32_t t, uint32_t *d_ids, uint64_t *count);

@@ -88,6 +88,14 @@ _SIGNATURES = [
     ("dbg_unitigs_total_bases", ctypes.c_uint64, [_P]),
     ("dbg_unitigs_get", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     ("dbg_unitigs_free", None, [_P]),
+    ("dbg_simplify", ctypes.c_int, [_P, _P, ctypes.c_uint32, _P]),
+    ("dbg_simple_num_units", ctypes.c_uint64, [_P]),
+    ("dbg_simple_num_edges", ctypes.c_uint64, [_P]),
+    ("dbg_simple_removed_edges", ctypes.c_uint64, [_P]),
+    ("dbg_simple_total_bases", ctypes.c_uint64, [_P]),
+    ("dbg_simple_units", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("dbg_simple_edges", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("dbg_simple_free", None, [_P]),
     ("dbg_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
     ("dbg_profile_read", ctypes.c_uint32, [_P, _P, ctypes.c_uint32]),
     ("dbg_launch_count", ctypes.c_uint64, [_P]),
@@ -420,6 +428,49 @@ def dbg_unitigs_get_into(u: Unitigs, node_off: int | None = None, nodes: int | N
     addresses, e.g. pinned tensors' data_ptr(); None skips an array)."""
     ptrs = (ctypes.c_void_p(a) if a else None for a in (node_off, nodes, seq_off, seq, circular))
     _check(_lib.dbg_unitigs_get(u.handle, *ptrs), "dbg_unitigs_get")
+
+
+class Simple:
+    """dbg_simple: the simplified graph (units and relabelled edges)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx, self.handle = ctx, handle
+
+    def free(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.dbg_simple_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.free()
+
+
+def dbg_simplify(ctx: Context, g: Graph, min_nodes: int = 3) -> Simple:
+    out = ctypes.c_void_p()
+    _check(_lib.dbg_simplify(ctx.handle, g.handle, min_nodes, ctypes.byref(out)), "dbg_simplify")
+    return Simple(ctx, out)
+
+
+def dbg_simple_get(s: Simple) -> dict:
+    """Units (node_off, nodes, seq_off, seq, circular) and edges (unit_a,
+    side_a, unit_b, side_b, edge) as host arrays, plus removed."""
+    U, M = int(_lib.dbg_simple_num_units(s.handle)), int(_lib.dbg_simple_num_edges(s.handle))
+    node_off, seq_off = _np_out(U + 1, np.uint64), _np_out(U + 1, np.uint64)
+    _check(_lib.dbg_simple_units(s.handle, ctypes.c_void_p(node_off.ctypes.data), None, None, None, None),
+           "dbg_simple_units")
+    nodes = _np_out(int(node_off[-1]) if U else 0, np.uint64)
+    seq = _np_out(int(_lib.dbg_simple_total_bases(s.handle)), np.uint8)
+    circ = _np_out(U, np.uint8)
+    _check(_lib.dbg_simple_units(s.handle, None, ctypes.c_void_p(nodes.ctypes.data),
+                                 ctypes.c_void_p(seq_off.ctypes.data), ctypes.c_void_p(seq.ctypes.data),
+                                 ctypes.c_void_p(circ.ctypes.data)), "dbg_simple_units")
+    ua, ub, ed = _np_out(M, np.uint32), _np_out(M, np.uint32), _np_out(M, np.uint32)
+    sa, sb = _np_out(M, np.uint8), _np_out(M, np.uint8)
+    _check(_lib.dbg_simple_edges(s.handle, *(ctypes.c_void_p(a.ctypes.data) for a in (ua, sa, ub, sb, ed))),
+           "dbg_simple_edges")
+    return {"node_off": node_off, "nodes": nodes, "seq_off": seq_off, "seq": seq.tobytes(), "circular": circ,
+            "unit_a": ua, "side_a": sa, "unit_b": ub, "side_b": sb, "edge": ed,
+            "removed": int(_lib.dbg_simple_removed_edges(s.handle))}
 
 
 def dbg_unitigs_free(u: Unitigs):
