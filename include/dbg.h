@@ -210,6 +210,22 @@ void dbg_graph_free(dbg_graph *g);
  * -------------------------------------------------------------------- */
 dbg_status dbg_compact(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs **out);
 
+/* ----------------------------------------------------------------------
+ * dbg_compact_bucketed -- dbg_compact with the out-of-core list ranking of
+ * Section 6.2: the ranking words of the 2|V| strand-nodes (list head,
+ * distance) live in host memory, and each round of pointer jumping is a
+ * join of every unresolved strand-node's word with its ancestor's word,
+ * sorted by the ancestor's key range and processed range by range on the
+ * device in pieces that fit mem_budget bytes (0 = half the free device
+ * memory).  Cycles are found when the rounds stop shrinking, labelled by
+ * their smallest strand-node with the same joins, opened there and ranked
+ * again.  The graph itself, the successors and the final selection and
+ * output stay on the device.  The unitigs are identical to dbg_compact's.
+ * join_launches (may be NULL) receives the number of join launches.
+ * -------------------------------------------------------------------- */
+dbg_status dbg_compact_bucketed(dbg_ctx *ctx, const dbg_graph *g, uint64_t mem_budget, dbg_unitigs **out,
+                                uint32_t *join_launches);
+
 uint64_t dbg_unitigs_count(const dbg_unitigs *u);
 uint64_t dbg_unitigs_total_bases(const dbg_unitigs *u);
 /* node_off, seq_off: count + 1 entries; nodes: num_nodes entries, each

@@ -14,6 +14,7 @@
 // fly and break them").  Of each mirrored pair the copy with the smaller
 // spelled string is kept (Section 6.1: canonicalize and remove duplicates).
 #include <algorithm>
+#include <vector>
 #include <cstring>
 
 #include "k_build.cuh"
@@ -113,9 +114,9 @@ __device__ __forceinline__ uint32_t pred_of(const uint32_t *__restrict__ succ, u
 // distance.  A list head is (itself, 0).  Words are read and written whole,
 // so a thread that reads a neighbour mid-update sees either its old or its
 // new (ancestor, distance) pair, both valid.
-__device__ __forceinline__ uint64_t pk(uint32_t a, uint32_t d) { return ((uint64_t)a << 32) | d; }
-__device__ __forceinline__ uint32_t pk_a(uint64_t w) { return (uint32_t)(w >> 32); }
-__device__ __forceinline__ uint32_t pk_d(uint64_t w) { return (uint32_t)w; }
+__host__ __device__ __forceinline__ uint64_t pk(uint32_t a, uint32_t d) { return ((uint64_t)a << 32) | d; }
+__host__ __device__ __forceinline__ uint32_t pk_a(uint64_t w) { return (uint32_t)(w >> 32); }
+__host__ __device__ __forceinline__ uint32_t pk_d(uint64_t w) { return (uint32_t)w; }
 __device__ __forceinline__ bool pk_root(uint64_t w, uint32_t x) { return pk_a(w) == x && pk_d(w) == 0; }
 constexpr uint64_t UNSET64 = ~0ull;
 
@@ -503,6 +504,80 @@ static dbg_status jump_until_stable(dbg_ctx *ctx, const uint32_t *list, uint32_t
   return DBG_ETIMEOUT;
 }
 
+// The general path's ending, from the ranking words (word[x] = (list head,
+// rank) of every strand-node), the successors and the cycle marks: the kept
+// copy of every unitig, its tables, node list and string.  Also the empty
+// graph's (V = 0) tables.
+template <class K>
+static dbg_status finish_from_words(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u, DevBuf &word, DevBuf &succ,
+                                    DevBuf &cyc, bool have_cycles) {
+  cudaStream_t s = ctx->stream;
+  const uint64_t V = g->num_nodes, n = 2 * V;
+  const int k = (int)g->k;
+  u->num_nodes = V;
+  const uint64_t V1 = std::max<uint64_t>(1, V);
+  DevBuf strand, head, rank, is_head, len_at_head, uidx, off_by_v;
+  uint64_t U = 0;
+  if (V > 0) {
+    DBG_TRY(alloc_buf(ctx, strand, V1));
+    DBG_TRY(alloc_buf(ctx, head, V1 * 4));
+    DBG_TRY(alloc_buf(ctx, rank, V1 * 4));
+    DBG_TRY(alloc_buf(ctx, is_head, V1 * 4));
+    DBG_TRY(alloc_buf(ctx, len_at_head, V1 * 4));
+    DBG_CUDA_TRY(cudaMemsetAsync(len_at_head.p, 0, V1 * 4, s));
+    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 16.0 * n + 8.0 * V + 17.0 * V,
+               k_select<K><<<grid_of(V), 256, 0, s>>>(word.as<uint64_t>(), succ.as<uint32_t>(),
+                                                      have_cycles ? cyc.as<uint8_t>() : nullptr,
+                                                      g->node_keys.as<uint64_t>(), V, k, strand.as<uint8_t>(),
+                                                      head.as<uint32_t>(), rank.as<uint32_t>(),
+                                                      is_head.as<uint32_t>(), len_at_head.as<uint32_t>()));
+    DBG_CUDA_TRY(cudaGetLastError());
+    word.release();
+    succ.release();
+    DBG_TRY(alloc_buf(ctx, uidx, (V + 1) * 8));
+    DBG_TRY(alloc_buf(ctx, off_by_v, (V + 1) * 8));
+    uint32_t U32 = 0, total = 0;
+    DBG_TRY(scan_excl(ctx, is_head.as<uint32_t>(), V, uidx.as<uint64_t>(), &U32));
+    DBG_TRY(scan_excl(ctx, len_at_head.as<uint32_t>(), V, off_by_v.as<uint64_t>(), &total));
+    if (total != V) {
+      set_error("unitigs hold %u nodes, expected %llu", total, (unsigned long long)V);
+      return DBG_EINTERNAL;
+    }
+    U = U32;
+  }
+  u->count = U;
+  const uint64_t U1 = std::max<uint64_t>(1, U);
+  DBG_TRY(alloc_buf(ctx, u->node_off, (U + 1) * 8));
+  DBG_TRY(alloc_buf(ctx, u->seq_off, (U + 1) * 8));
+  DBG_TRY(alloc_buf(ctx, u->circular, U1));
+  DBG_TRY(alloc_buf(ctx, u->nodes, V1 * 8));
+  u->total_bases = V + U * (uint64_t)(k - 1);
+  DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
+  if (V > 0) {
+    DevBuf hinfo;
+    DBG_TRY(alloc_buf(ctx, hinfo, V1 * sizeof(uint4)));
+    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 4.0 * V + 16.0 * U * 5,
+               k_unitig_offsets<<<grid_of(V + 1), 256, 0, s>>>(
+                   is_head.as<uint32_t>(), uidx.as<uint64_t>(), off_by_v.as<uint64_t>(), len_at_head.as<uint32_t>(),
+                   have_cycles ? cyc.as<uint8_t>() : nullptr, strand.as<uint8_t>(), V, U, k,
+                   u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(), u->circular.as<uint8_t>(),
+                   hinfo.as<uint4>()));
+    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT,
+               (double)V * (4 + 4 + 1 + 16 + 8 * g->key_words + 8 + 1) + (double)U * k,
+               k_unitig_write<K><<<grid_of(V), 256, 0, s>>>(head.as<uint32_t>(), rank.as<uint32_t>(),
+                                                            strand.as<uint8_t>(), hinfo.as<uint4>(),
+                                                            g->node_keys.as<uint64_t>(), V, k,
+                                                            u->nodes.as<uint64_t>(), u->seq.as<char>(), ctx->d_err));
+    DBG_CUDA_TRY(cudaGetLastError());
+  } else {
+    DBG_CUDA_TRY(cudaMemsetAsync(u->node_off.p, 0, 8, s));
+    DBG_CUDA_TRY(cudaMemsetAsync(u->seq_off.p, 0, 8, s));
+  }
+  DBG_CUDA_TRY(cudaStreamSynchronize(s));
+  return check_device_error(ctx);
+}
+
+
 // Lists of up to this many strand-nodes are ranked by one walking thread.
 constexpr uint32_t kWalkCap = 2048;
 
@@ -514,8 +589,6 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
   u->num_nodes = V;
   const uint64_t V1 = std::max<uint64_t>(1, V), n1 = std::max<uint64_t>(1, n);
   DevBuf link_node, link_edge, succ, word, active, cycl, lab, cyc;
-  DevBuf strand, head, rank, is_head, len_at_head, uidx, off_by_v;
-  uint64_t U = 0;
   bool have_cycles = false;
   if (V > 0) {
     DBG_TRY(alloc_buf(ctx, link_node, n1 * 4));
@@ -638,62 +711,263 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
     active.release();
     cycl.release();
     lab.release();
-    DBG_TRY(alloc_buf(ctx, strand, V1));
-    DBG_TRY(alloc_buf(ctx, head, V1 * 4));
-    DBG_TRY(alloc_buf(ctx, rank, V1 * 4));
-    DBG_TRY(alloc_buf(ctx, is_head, V1 * 4));
-    DBG_TRY(alloc_buf(ctx, len_at_head, V1 * 4));
-    DBG_CUDA_TRY(cudaMemsetAsync(len_at_head.p, 0, V1 * 4, s));
-    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 16.0 * n + 8.0 * V + 17.0 * V,
-               k_select<K><<<grid_of(V), 256, 0, s>>>(word.as<uint64_t>(), succ.as<uint32_t>(),
-                                                      have_cycles ? cyc.as<uint8_t>() : nullptr,
-                                                      g->node_keys.as<uint64_t>(), V, k, strand.as<uint8_t>(),
-                                                      head.as<uint32_t>(), rank.as<uint32_t>(),
-                                                      is_head.as<uint32_t>(), len_at_head.as<uint32_t>()));
+  }
+  return finish_from_words<K>(ctx, g, u, word, succ, cyc, have_cycles);
+}
+
+// ---------------------------------------------------------------------------
+// Out-of-core ranking (Section 6.2): list ranking as rounds of sort-join over
+// key ranges.  The ranking word of every strand-node, W[x] = (ancestor,
+// distance), lives in host memory.  A round takes every unresolved x, sorts
+// its request -- the word W[x], whose ancestor is the join key -- by the
+// ancestor's key range, and for each range brings the words of that range
+// (the other side of the join, sorted by their own index) to the device
+// with the range's requests, in batches that fit the memory budget; the
+// device combines each request with its ancestor's word, and the results
+// replace the words once the round is over (pointer jumping, synchronous).
+// A strand-node whose ancestor is a list head does not jump and leaves the
+// unresolved set.  When a round jumps as many strand-nodes as the one
+// before, only cycles remain; they are labelled by their smallest
+// strand-node with the same rounds (min-label doubling), opened there and
+// ranked again.  The paper's join of the successor tuples (x, y) with the
+// tuples (y, y') becomes the join of W[x] with W[ancestor of x].
+// ---------------------------------------------------------------------------
+
+// One synchronous round, for requests whose ancestor lies in the slice
+// [lo, lo + m) of the words: mode 0 jumps (unless the ancestor is a list
+// head), mode 1 takes the smaller label.  jumped counts the jumps.
+__global__ void k_join_round(const uint64_t *__restrict__ req, uint64_t R, const uint64_t *__restrict__ slice,
+                             uint32_t lo, int mode, uint64_t *__restrict__ out, uint8_t *__restrict__ moved,
+                             uint32_t *jumped) {
+  uint32_t local = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t w = req[i];
+    const uint32_t t = pk_a(w);
+    const uint64_t wt = slice[t - lo];
+    if (mode == 0) {
+      const bool stay = pk_root(wt, t);
+      out[i] = stay ? w : pk(pk_a(wt), (uint32_t)min((uint64_t)pk_d(w) + pk_d(wt), (uint64_t)0x7fffffffu));
+      moved[i] = stay ? 0 : 1;
+      local += stay ? 0u : 1u;
+    } else {
+      out[i] = pk(pk_a(wt), min(pk_d(w), pk_d(wt)));
+      moved[i] = 1;
+    }
+  }
+  local = __reduce_add_sync(0xffffffffu, local);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(jumped, local);
+}
+
+namespace {
+struct PinnedBuf {
+  void *p = nullptr;
+  PinnedBuf() = default;
+  PinnedBuf(const PinnedBuf &) = delete;
+  PinnedBuf &operator=(const PinnedBuf &) = delete;
+  ~PinnedBuf() {
+    if (p) cudaFreeHost(p);
+  }
+  dbg_status alloc(size_t bytes) {
+    if (cudaMallocHost(&p, std::max<size_t>(bytes, 8)) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      set_error("cudaMallocHost of %zu bytes failed", bytes);
+      return DBG_ENOMEM;
+    }
+    return DBG_OK;
+  }
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// device buffers of one batch of a round
+struct JoinBufs {
+  DevBuf req, out, moved, slice;
+  uint64_t batch = 0, slice_len = 0;
+};
+}  // namespace
+
+// One round over the strand-nodes in act (words in W, n of them): the
+// requests grouped by their ancestor's slice, each slice's requests joined
+// on the device in batches; then the words replaced.  act keeps the nodes
+// that moved (mode 0: jumped; mode 1: all).  Returns the jumps.
+static dbg_status join_round(dbg_ctx *ctx, std::vector<uint32_t> &act, uint64_t *W, uint64_t n, int mode,
+                             JoinBufs &jb, PinnedBuf &h_req, PinnedBuf &h_out, PinnedBuf &h_moved,
+                             uint64_t *jumped) {
+  cudaStream_t s = ctx->stream;
+  const uint64_t A = act.size(), S = jb.slice_len;
+  const uint64_t nb = (n + S - 1) / S;
+  std::vector<uint64_t> start(nb + 1, 0);
+  for (uint32_t x : act) start[pk_a(W[x]) / S + 1]++;
+  for (uint64_t b = 0; b < nb; b++) start[b + 1] += start[b];
+  std::vector<uint32_t> order(A);
+  {
+    std::vector<uint64_t> fill(start.begin(), start.end() - 1);
+    uint64_t *req = h_req.as<uint64_t>();
+    for (uint32_t x : act) {
+      const uint64_t w = W[x];
+      const uint64_t q = fill[pk_a(w) / S]++;
+      order[q] = x;
+      req[q] = w;
+    }
+  }
+  DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 12, 0, sizeof(uint32_t), s));
+  for (uint64_t b = 0; b < nb; b++) {
+    const uint64_t r0 = start[b], r1 = start[b + 1];
+    if (r0 == r1) continue;
+    const uint64_t lo = b * S, m = std::min(S, n - lo);
+    DBG_CUDA_TRY(cudaMemcpyAsync(jb.slice.p, W + lo, m * 8, cudaMemcpyHostToDevice, s));
+    for (uint64_t r = r0; r < r1; r += jb.batch) {
+      const uint64_t R = std::min(jb.batch, r1 - r);
+      DBG_CUDA_TRY(cudaMemcpyAsync(jb.req.p, h_req.as<uint64_t>() + r, R * 8, cudaMemcpyHostToDevice, s));
+      DBG_LAUNCH(ctx, ST_COMPACT_RANK, 25.0 * R,
+                 k_join_round<<<grid_of(R), 256, 0, s>>>(jb.req.as<uint64_t>(), R, jb.slice.as<uint64_t>(),
+                                                         (uint32_t)lo, mode, jb.out.as<uint64_t>(),
+                                                         jb.moved.as<uint8_t>(), ctx->d_counters + 12));
+      DBG_CUDA_TRY(cudaMemcpyAsync(h_out.as<uint64_t>() + r, jb.out.p, R * 8, cudaMemcpyDeviceToHost, s));
+      DBG_CUDA_TRY(cudaMemcpyAsync(h_moved.as<uint8_t>() + r, jb.moved.p, R, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  DBG_CUDA_TRY(cudaGetLastError());
+  uint32_t j = 0;
+  DBG_TRY(read_small(ctx, ctx->d_counters + 12, sizeof(uint32_t), &j));  // synchronizes the stream
+  *jumped = j;
+  // every slice has been read: the new words replace the old ones
+  const uint64_t *out = h_out.as<uint64_t>();
+  const uint8_t *moved = h_moved.as<uint8_t>();
+  act.clear();
+  for (uint64_t q = 0; q < A; q++) {
+    W[order[q]] = out[q];
+    if (moved[q]) act.push_back(order[q]);
+  }
+  std::sort(act.begin(), act.end());
+  return DBG_OK;
+}
+
+// Rounds of jumping over act until no strand-node jumps or the jumps stop
+// shrinking (only cycles left); returns those left.
+static dbg_status jump_rounds(dbg_ctx *ctx, std::vector<uint32_t> &act, uint64_t *W, uint64_t n, JoinBufs &jb,
+                              PinnedBuf &h_req, PinnedBuf &h_out, PinnedBuf &h_moved, uint64_t *left) {
+  uint64_t prev = ~0ull, jumped = 0;
+  for (int r = 0; r < 96 && !act.empty(); r++) {
+    DBG_TRY(join_round(ctx, act, W, n, 0, jb, h_req, h_out, h_moved, &jumped));
+    if (jumped == 0 || jumped == prev) {
+      *left = jumped;
+      return DBG_OK;
+    }
+    prev = jumped;
+  }
+  *left = act.empty() ? 0 : jumped;
+  if (!act.empty() && jumped != prev) {
+    set_error("list ranking did not converge");
+    return DBG_ETIMEOUT;
+  }
+  return DBG_OK;
+}
+
+template <class K>
+static dbg_status compact_bucketed_impl(dbg_ctx *ctx, const dbg_graph *g, uint64_t budget, dbg_unitigs *u,
+                                        uint32_t *rounds) {
+  cudaStream_t s = ctx->stream;
+  const uint64_t V = g->num_nodes, n = 2 * V;
+  const int k = (int)g->k;
+  DevBuf succ, word, cyc;
+  if (V == 0) return finish_from_words<K>(ctx, g, u, word, succ, cyc, false);
+  // successors on the device (the graph is there), then to host memory
+  {
+    DevBuf link_node, link_edge;
+    DBG_TRY(alloc_buf(ctx, link_node, n * 4));
+    DBG_TRY(alloc_buf(ctx, link_edge, n * 8));
+    DBG_TRY(alloc_buf(ctx, succ, n * 4));
+    DBG_TRY(alloc_buf(ctx, word, n * 8));
+    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + 20.0 * g->num_edges + 8.0 * V * g->key_words + 12.0 * n,
+               k_side_links<K><<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
+                                                          g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
+                                                          g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
+                                                          false, link_node.as<uint32_t>(), link_edge.as<uint64_t>()));
+    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 32.0 * n,
+               k_successors<<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(), V,
+                                                       succ.as<uint32_t>(), word.as<uint64_t>()));
     DBG_CUDA_TRY(cudaGetLastError());
-    word.release();
-    succ.release();
-    DBG_TRY(alloc_buf(ctx, uidx, (V + 1) * 8));
-    DBG_TRY(alloc_buf(ctx, off_by_v, (V + 1) * 8));
-    uint32_t U32 = 0, total = 0;
-    DBG_TRY(scan_excl(ctx, is_head.as<uint32_t>(), V, uidx.as<uint64_t>(), &U32));
-    DBG_TRY(scan_excl(ctx, len_at_head.as<uint32_t>(), V, off_by_v.as<uint64_t>(), &total));
-    if (total != V) {
-      set_error("unitigs hold %u nodes, expected %llu", total, (unsigned long long)V);
+  }
+  word.release();
+  PinnedBuf h_succ, h_W, h_lab, h_req, h_out, h_moved;
+  DBG_TRY(h_succ.alloc(n * 4));
+  DBG_TRY(h_W.alloc(n * 8));
+  DBG_TRY(h_req.alloc(n * 8));
+  DBG_TRY(h_out.alloc(n * 8));
+  DBG_TRY(h_moved.alloc(n));
+  DBG_CUDA_TRY(cudaMemcpyAsync(h_succ.p, succ.p, n * 4, cudaMemcpyDeviceToHost, s));
+  DBG_CUDA_TRY(cudaStreamSynchronize(s));
+  const uint32_t *sc = h_succ.as<uint32_t>();
+  uint64_t *W = h_W.as<uint64_t>();
+  auto pred = [&](uint64_t x) -> uint32_t {
+    const uint32_t m = sc[x ^ 1];
+    return m == NONE32 ? NONE32 : (m ^ 1u);
+  };
+  // the device side of a round within the budget: a slice of words and a
+  // batch of requests, results and flags (8 + 8 + 8 + 1 bytes per entry)
+  JoinBufs jb;
+  const uint64_t per = std::max<uint64_t>(1u << 12, budget / 25);
+  jb.slice_len = std::min<uint64_t>(n, per);
+  jb.batch = std::min<uint64_t>(n, per);
+  DBG_TRY(alloc_buf(ctx, jb.slice, jb.slice_len * 8));
+  DBG_TRY(alloc_buf(ctx, jb.req, jb.batch * 8));
+  DBG_TRY(alloc_buf(ctx, jb.out, jb.batch * 8));
+  DBG_TRY(alloc_buf(ctx, jb.moved, jb.batch));
+  // initial words: a list head is its own root; every other strand-node
+  // points at its predecessor at distance 1
+  std::vector<uint32_t> act;
+  for (uint64_t x = 0; x < n; x++) {
+    const uint32_t p = pred(x);
+    W[x] = p == NONE32 ? pk((uint32_t)x, 0) : pk(p, 1);
+    if (p != NONE32) act.push_back((uint32_t)x);
+  }
+  uint64_t left = 0;
+  const uint64_t r0 = ctx->launches;
+  DBG_TRY(jump_rounds(ctx, act, W, n, jb, h_req, h_out, h_moved, &left));
+  bool have_cycles = false;
+  std::vector<uint8_t> h_cyc;
+  if (left > 0) {
+    // cycles: min-label doubling over their strand-nodes, then opened at the
+    // smallest and ranked again
+    have_cycles = true;
+    std::vector<uint32_t> cyc_nodes = act;
+    DBG_TRY(h_lab.alloc(n * 8));
+    uint64_t *lab = h_lab.as<uint64_t>();
+    for (uint32_t x : cyc_nodes) lab[x] = pk(pred(x), x);
+    int R = 2;
+    while ((1ull << (R - 2)) < cyc_nodes.size()) R++;
+    for (int r = 0; r < R; r++) {
+      std::vector<uint32_t> all = cyc_nodes;
+      uint64_t dummy = 0;
+      DBG_TRY(join_round(ctx, all, lab, n, 1, jb, h_req, h_out, h_moved, &dummy));
+    }
+    h_cyc.assign(n, 0);
+    act.clear();
+    for (uint32_t x : cyc_nodes) {
+      const uint32_t m = pk_d(lab[x]);
+      h_cyc[x] = (m & 1u) ? 2 : 1;
+      W[x] = m == x ? pk(x, 0) : pk(pred(x), 1);
+      if (m != x) act.push_back(x);
+    }
+    uint64_t still = 0;
+    DBG_TRY(jump_rounds(ctx, act, W, n, jb, h_req, h_out, h_moved, &still));
+    if (still != 0) {
+      set_error("%llu strand-nodes stayed on cycles after they were opened", (unsigned long long)still);
       return DBG_EINTERNAL;
     }
-    U = U32;
   }
-  u->count = U;
-  const uint64_t U1 = std::max<uint64_t>(1, U);
-  DBG_TRY(alloc_buf(ctx, u->node_off, (U + 1) * 8));
-  DBG_TRY(alloc_buf(ctx, u->seq_off, (U + 1) * 8));
-  DBG_TRY(alloc_buf(ctx, u->circular, U1));
-  DBG_TRY(alloc_buf(ctx, u->nodes, V1 * 8));
-  u->total_bases = V + U * (uint64_t)(k - 1);
-  DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
-  if (V > 0) {
-    DevBuf hinfo;
-    DBG_TRY(alloc_buf(ctx, hinfo, V1 * sizeof(uint4)));
-    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 4.0 * V + 16.0 * U * 5,
-               k_unitig_offsets<<<grid_of(V + 1), 256, 0, s>>>(
-                   is_head.as<uint32_t>(), uidx.as<uint64_t>(), off_by_v.as<uint64_t>(), len_at_head.as<uint32_t>(),
-                   have_cycles ? cyc.as<uint8_t>() : nullptr, strand.as<uint8_t>(), V, U, k,
-                   u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(), u->circular.as<uint8_t>(),
-                   hinfo.as<uint4>()));
-    DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT,
-               (double)V * (4 + 4 + 1 + 16 + 8 * g->key_words + 8 + 1) + (double)U * k,
-               k_unitig_write<K><<<grid_of(V), 256, 0, s>>>(head.as<uint32_t>(), rank.as<uint32_t>(),
-                                                            strand.as<uint8_t>(), hinfo.as<uint4>(),
-                                                            g->node_keys.as<uint64_t>(), V, k,
-                                                            u->nodes.as<uint64_t>(), u->seq.as<char>(), ctx->d_err));
-    DBG_CUDA_TRY(cudaGetLastError());
-  } else {
-    DBG_CUDA_TRY(cudaMemsetAsync(u->node_off.p, 0, 8, s));
-    DBG_CUDA_TRY(cudaMemsetAsync(u->seq_off.p, 0, 8, s));
+  *rounds = (uint32_t)(ctx->launches - r0);
+  jb = JoinBufs();
+  // the ranking words back on the device for the rest of the general path
+  DBG_TRY(alloc_buf(ctx, word, n * 8));
+  DBG_CUDA_TRY(cudaMemcpyAsync(word.p, W, n * 8, cudaMemcpyHostToDevice, s));
+  if (have_cycles) {
+    DBG_TRY(alloc_buf(ctx, cyc, n));
+    DBG_CUDA_TRY(cudaMemcpyAsync(cyc.p, h_cyc.data(), n, cudaMemcpyHostToDevice, s));
   }
-  DBG_CUDA_TRY(cudaStreamSynchronize(s));
-  return check_device_error(ctx);
+  DBG_CUDA_TRY(cudaStreamSynchronize(s));  // the host words may go
+  return finish_from_words<K>(ctx, g, u, word, succ, cyc, have_cycles);
 }
 
 dbg_status compact_chains(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u, bool literal) {
@@ -728,6 +1002,48 @@ dbg_status dbg_compact(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs **out) {
   for (DevBuf *b : {&u->node_off, &u->nodes, &u->seq_off, &u->seq, &u->circular}) b->al = &u->al;
   cudaStreamSynchronize(ctx->stream);
   prof_resolve(ctx);
+  if (st != DBG_OK) {
+    cudaGetLastError();
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream);
+    delete u;
+  } else {
+    *out = u;
+  }
+  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  return st;
+}
+
+dbg_status dbg_compact_bucketed(dbg_ctx *ctx, const dbg_graph *g, uint64_t mem_budget, dbg_unitigs **out,
+                                uint32_t *join_launches) {
+  if (!out) return DBG_EINVAL;
+  *out = nullptr;
+  if (!ctx || !g) {
+    set_error("ctx or graph is NULL");
+    return DBG_EINVAL;
+  }
+  if (g->num_nodes >= 0x7fffffffull) {
+    set_error("compaction handles fewer than 2^31 nodes");
+    return DBG_EOVERFLOW;
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != ctx->device) cudaSetDevice(ctx->device);
+  if (mem_budget == 0) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    mem_budget = free_b / 2;
+  }
+  dbg_unitigs *u = new (std::nothrow) dbg_unitigs();
+  if (!u) return DBG_ENOMEM;
+  u->al = ctx->al;
+  u->device = ctx->device;
+  uint32_t launches = 0;
+  dbg_status st = g->key_words == 1 ? compact_bucketed_impl<uint64_t>(ctx, g, mem_budget, u, &launches)
+                                    : compact_bucketed_impl<Key128>(ctx, g, mem_budget, u, &launches);
+  for (DevBuf *b : {&u->node_off, &u->nodes, &u->seq_off, &u->seq, &u->circular}) b->al = &u->al;
+  cudaStreamSynchronize(ctx->stream);
+  prof_resolve(ctx);
+  if (join_launches) *join_launches = launches;
   if (st != DBG_OK) {
     cudaGetLastError();
     cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream);

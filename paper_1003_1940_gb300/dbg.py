@@ -84,6 +84,7 @@ _SIGNATURES = [
     ("dbg_graph_device_view", ctypes.c_int, [_P, _P]),
     ("dbg_graph_free", None, [_P]),
     ("dbg_compact", ctypes.c_int, [_P, _P, _P]),
+    ("dbg_compact_bucketed", ctypes.c_int, [_P, _P, ctypes.c_uint64, _P, _P]),
     ("dbg_unitigs_count", ctypes.c_uint64, [_P]),
     ("dbg_unitigs_total_bases", ctypes.c_uint64, [_P]),
     ("dbg_unitigs_get", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -396,6 +397,16 @@ def dbg_compact(ctx: Context, g: Graph) -> Unitigs:
     out = ctypes.c_void_p()
     _check(_lib.dbg_compact(ctx.handle, g.handle, ctypes.byref(out)), "dbg_compact")
     return Unitigs(ctx, out)
+
+
+def dbg_compact_bucketed(ctx: Context, g: Graph, mem_budget: int = 0) -> tuple:
+    """Unitigs by the out-of-core list ranking (sort-join rounds over key
+    ranges of host-resident ranking words); returns (Unitigs, join launches)."""
+    out = ctypes.c_void_p()
+    launches = ctypes.c_uint32(0)
+    _check(_lib.dbg_compact_bucketed(ctx.handle, g.handle, mem_budget, ctypes.byref(out), ctypes.byref(launches)),
+           "dbg_compact_bucketed")
+    return Unitigs(ctx, out), int(launches.value)
 
 
 def dbg_unitigs_count(u: Unitigs) -> int:
