@@ -113,6 +113,9 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SVP(uint64_t, false, 256, 12, RANK_MATCH, 3, 4, "256x12 match persistent occ3 lb4"),
         DBG_SVP(uint64_t, false, 256, 16, RANK_ATOMIC, 2, 4, "256x16 atomic persistent occ2 lb4"),
         DBG_SVP(uint64_t, false, 512, 8, RANK_ATOMIC, 2, 4, "512x8 atomic persistent occ2 lb4"),
+        DBG_SVP(uint64_t, false, 1024, 8, RANK_ATOMIC, 1, 4, "1024x8 atomic persistent occ1 lb4"),
+        DBG_SVP(uint64_t, false, 1024, 8, RANK_ATOMIC, 1, 8, "1024x8 atomic persistent occ1 lb8"),
+        DBG_SVP(uint64_t, false, 768, 8, RANK_ATOMIC, 1, 4, "768x8 atomic persistent occ1 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -139,6 +142,7 @@ template <> struct SortKind<uint64_t, true> {
         DBG_SVP(uint64_t, true, 256, 8, RANK_ATOMIC, 3, 4, "256x8 atomic persistent occ3 lb4"),
         DBG_SVP(uint64_t, true, 256, 10, RANK_ATOMIC, 2, 4, "256x10 atomic persistent occ2 lb4"),
         DBG_SVP(uint64_t, true, 256, 6, RANK_ATOMIC, 4, 4, "256x6 atomic persistent occ4 lb4"),
+        DBG_SVP(uint64_t, true, 1024, 6, RANK_ATOMIC, 1, 4, "1024x6 atomic persistent occ1 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -159,6 +163,7 @@ template <> struct SortKind<Key128, false> {
         DBG_SVL(Key128, false, 256, 6, RANK_ATOMIC, true, 3, false, 8, "256x6 atomic tma occ3 lb8"),
         DBG_SVP(Key128, false, 256, 6, RANK_ATOMIC, 3, 4, "256x6 atomic persistent occ3 lb4"),
         DBG_SVP(Key128, false, 256, 8, RANK_ATOMIC, 2, 4, "256x8 atomic persistent occ2 lb4"),
+        DBG_SVP(Key128, false, 1024, 4, RANK_ATOMIC, 1, 4, "1024x4 atomic persistent occ1 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -176,6 +181,7 @@ template <> struct SortKind<Key128, true> {
         DBG_SVL(Key128, true, 256, 6, RANK_ATOMIC, true, 3, true, 4, "256x6 atomic tma occ3 early lb4"),
         DBG_SVL(Key128, true, 256, 6, RANK_ATOMIC, true, 3, false, 8, "256x6 atomic tma occ3 lb8"),
         DBG_SVP(Key128, true, 256, 6, RANK_ATOMIC, 2, 4, "256x6 atomic persistent occ2 lb4"),
+        DBG_SVP(Key128, true, 1024, 3, RANK_ATOMIC, 1, 4, "1024x3 atomic persistent occ1 lb4"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;

@@ -34,15 +34,15 @@ def check(dbg, ctx, reads, lengths, k, budgets, with_oracle=True):
     want = dbg.dbg_unitigs_get(dbg.dbg_compact(ctx, g))
     if with_oracle:
         assert_unitigs_equal(want, oracle.compact(oracle.build_graph(reads, lengths, k)))
+    launches = []
     for b in budgets:
-        u, launches = dbg.dbg_compact_bucketed(ctx, g, b)
+        u, n_join = dbg.dbg_compact_bucketed(ctx, g, b)
         got = dbg.dbg_unitigs_get(u)
         for f in ("node_off", "nodes", "seq_off", "circular"):
             np.testing.assert_array_equal(got[f], want[f], err_msg=f"{f} at budget {b}")
         assert got["seq"] == want["seq"]
-        if dbg.dbg_graph_num_nodes(g) > 1:
-            assert launches > 0
-    return want
+        launches.append(n_join)
+    return want, launches
 
 
 @pytest.mark.parametrize("k", [21, 31, 33])
@@ -50,7 +50,9 @@ def test_bucketed_ranking_equals_in_core(dbg, k):
     L = 100 if k < 33 else 150
     reads, lengths = readgen.generate(readgen.ReadSetSpec(80_000, 20_000, L, 0.005, k, 70 + k,
                                                           repeat_fraction=0.02))
-    check(dbg, dbg.Context(), reads, lengths, k, [0, 1 << 20, 200_000])
+    _, launches = check(dbg, dbg.Context(), reads, lengths, k, [0, 1 << 20, 200_000])
+    # smaller budgets cut the strand-nodes into more key ranges
+    assert 0 < launches[0] < launches[1] <= launches[2]
 
 
 def test_bucketed_ranking_long_lists_and_cycles(dbg):
@@ -63,7 +65,8 @@ def test_bucketed_ranking_long_lists_and_cycles(dbg):
     circ2 = circ + circ[:60]
     reads += [circ2[i:i + 80] for i in range(0, 3000, 30)]  # a long cycle
     r, l = as_input(reads)
-    want = check(dbg, ctx, r, l, 21, [0, 300_000, 100_000])
+    want, launches = check(dbg, ctx, r, l, 21, [0, 300_000, 100_000])
+    assert min(launches) > 0
     assert int(want["circular"].sum()) >= 2
 
 
