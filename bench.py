@@ -399,6 +399,7 @@ def run_ours(args):
     dbg.dbg_sort_partition_first_set(ctx, bool(args.partition_first))
     dbg.dbg_node_mult_set(ctx, bool(args.node_mult))
     variants = {kd: dbg.dbg_sort_variant_name(kd, dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(6)}
+    variant_ids = ",".join(str(dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(6))
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -538,7 +539,8 @@ def run_ours(args):
                        "nodes": info.get("nodes"), "edges": info.get("edges"), "unitigs": info.get("unitigs"),
                        "l2": "inputs and sort buffers far larger than L2 (1.5 GB reads, 8.3 GB keys)",
                        "parallelism": f"replicas x{ws}",
-                       "sort_variants": variants, "count_first": bool(args.count_first),
+                       "sort_variants": variants, "sort_variant_ids": variant_ids,
+                       "count_first": bool(args.count_first),
                        "partition_first": bool(args.partition_first), "node_mult": bool(args.node_mult),
                        "autotune_pass_ms": {kd: [round(x, 4) for x in v] for kd, v in tune_ms.items()}},
             "roofline": {"bound": "hbm",

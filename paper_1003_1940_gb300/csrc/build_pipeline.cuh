@@ -116,6 +116,8 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SVP(uint64_t, false, 1024, 8, RANK_ATOMIC, 1, 4, "1024x8 atomic persistent occ1 lb4"),
         DBG_SVP(uint64_t, false, 1024, 8, RANK_ATOMIC, 1, 8, "1024x8 atomic persistent occ1 lb8"),
         DBG_SVP(uint64_t, false, 768, 8, RANK_ATOMIC, 1, 4, "768x8 atomic persistent occ1 lb4"),
+        DBG_SVP(uint64_t, false, 1024, 10, RANK_ATOMIC, 1, 8, "1024x10 atomic persistent occ1 lb8"),
+        DBG_SVP(uint64_t, false, 1024, 9, RANK_ATOMIC, 1, 8, "1024x9 atomic persistent occ1 lb8"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -143,6 +145,7 @@ template <> struct SortKind<uint64_t, true> {
         DBG_SVP(uint64_t, true, 256, 10, RANK_ATOMIC, 2, 4, "256x10 atomic persistent occ2 lb4"),
         DBG_SVP(uint64_t, true, 256, 6, RANK_ATOMIC, 4, 4, "256x6 atomic persistent occ4 lb4"),
         DBG_SVP(uint64_t, true, 1024, 6, RANK_ATOMIC, 1, 4, "1024x6 atomic persistent occ1 lb4"),
+        DBG_SVP(uint64_t, true, 1024, 6, RANK_ATOMIC, 1, 8, "1024x6 atomic persistent occ1 lb8"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -164,6 +167,7 @@ template <> struct SortKind<Key128, false> {
         DBG_SVP(Key128, false, 256, 6, RANK_ATOMIC, 3, 4, "256x6 atomic persistent occ3 lb4"),
         DBG_SVP(Key128, false, 256, 8, RANK_ATOMIC, 2, 4, "256x8 atomic persistent occ2 lb4"),
         DBG_SVP(Key128, false, 1024, 4, RANK_ATOMIC, 1, 4, "1024x4 atomic persistent occ1 lb4"),
+        DBG_SVP(Key128, false, 1024, 5, RANK_ATOMIC, 1, 8, "1024x5 atomic persistent occ1 lb8"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
