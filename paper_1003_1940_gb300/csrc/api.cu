@@ -620,10 +620,12 @@ static const char *variant_name_of(uint32_t kind, uint32_t v, uint32_t *count) {
     case 3: return sort_variant_name_u128(true, v, count);
     case 4:
     case 5: {
-      // the local sort's ranking methods (same order as local_rank_method)
-      static const char *const names[] = {"local match", "local atomic", "local ballot"};
-      *count = 3;
-      return v < 3 ? names[v] : nullptr;
+      // the local sort's ranking methods (same order as local_rank_method);
+      // 3-5: the same with the node records' local sort in its wide form
+      static const char *const names[] = {"local match", "local atomic", "local ballot",
+                                          "local match wide", "local atomic wide", "local ballot wide"};
+      *count = 6;
+      return v < 6 ? names[v] : nullptr;
     }
     default: return nullptr;
   }

@@ -47,11 +47,11 @@ void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *
                                                       epoch, ctx->spin_limit, ctx->d_err);
 }
 
-template <class K, bool V, int BLOCK, int ITEMS, int RANK, int MINB, int LB>
+template <class K, bool V, int BLOCK, int ITEMS, int RANK, int MINB, int LB, int HB = 4>
 void launch_onesweep_p(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *vin, uint32_t *vout, uint64_t n,
                        int shift, const uint64_t *digit_base, uint32_t epoch) {
-  auto kern = k_onesweep_p<K, V, BLOCK, ITEMS, RANK, MINB, LB>;
-  constexpr size_t smem = sizeof(OnesweepPSmem<K, V, BLOCK, ITEMS>);
+  auto kern = k_onesweep_p<K, V, BLOCK, ITEMS, RANK, MINB, LB, HB>;
+  constexpr size_t smem = sizeof(OnesweepPSmem<K, V, BLOCK, ITEMS, RANK, HB>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   const uint64_t tiles = (n + BLOCK * ITEMS - 1) / (BLOCK * ITEMS);
@@ -63,6 +63,8 @@ void launch_onesweep_p(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t
 
 #define DBG_SVP(K, V, B, I, R, M, L, NAME) \
   SortVariant { NAME, (B) * (I), &launch_onesweep_p<K, V, B, I, R, M, L> }
+#define DBG_SVH(K, V, B, I, R, M, L, NAME) \
+  SortVariant { NAME, (B) * (I), &launch_onesweep_p<K, V, B, I, R, M, L, 2> }
 #define DBG_SV(K, V, B, I, R, T, M, NAME) \
   SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, false> }
 #define DBG_SVE(K, V, B, I, R, T, M, NAME) \
@@ -118,6 +120,9 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SVP(uint64_t, false, 768, 8, RANK_ATOMIC, 1, 4, "768x8 atomic persistent occ1 lb4"),
         DBG_SVP(uint64_t, false, 1024, 10, RANK_ATOMIC, 1, 8, "1024x10 atomic persistent occ1 lb8"),
         DBG_SVP(uint64_t, false, 1024, 9, RANK_ATOMIC, 1, 8, "1024x9 atomic persistent occ1 lb8"),
+        DBG_SVH(uint64_t, false, 1024, 10, RANK_ATOMIC, 1, 8, "1024x10 atomic persistent occ1 lb8 h16"),
+        DBG_SVH(uint64_t, false, 1024, 11, RANK_ATOMIC, 1, 8, "1024x11 atomic persistent occ1 lb8 h16"),
+        DBG_SVH(uint64_t, false, 1024, 12, RANK_MATCH, 1, 8, "1024x12 match persistent occ1 lb8 h16"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -146,6 +151,7 @@ template <> struct SortKind<uint64_t, true> {
         DBG_SVP(uint64_t, true, 256, 6, RANK_ATOMIC, 4, 4, "256x6 atomic persistent occ4 lb4"),
         DBG_SVP(uint64_t, true, 1024, 6, RANK_ATOMIC, 1, 4, "1024x6 atomic persistent occ1 lb4"),
         DBG_SVP(uint64_t, true, 1024, 6, RANK_ATOMIC, 1, 8, "1024x6 atomic persistent occ1 lb8"),
+        DBG_SVH(uint64_t, true, 1024, 7, RANK_ATOMIC, 1, 8, "1024x7 atomic persistent occ1 lb8 h16"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -168,6 +174,7 @@ template <> struct SortKind<Key128, false> {
         DBG_SVP(Key128, false, 256, 8, RANK_ATOMIC, 2, 4, "256x8 atomic persistent occ2 lb4"),
         DBG_SVP(Key128, false, 1024, 4, RANK_ATOMIC, 1, 4, "1024x4 atomic persistent occ1 lb4"),
         DBG_SVP(Key128, false, 1024, 5, RANK_ATOMIC, 1, 8, "1024x5 atomic persistent occ1 lb8"),
+        DBG_SVH(Key128, false, 1024, 6, RANK_MATCH, 1, 8, "1024x6 match persistent occ1 lb8 h16"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -193,6 +200,7 @@ template <> struct SortKind<Key128, true> {
 };
 #undef DBG_SV
 #undef DBG_SVP
+#undef DBG_SVH
 #undef DBG_SVE
 #undef DBG_SVD
 #undef DBG_SVL
@@ -297,7 +305,7 @@ int hybrid_first_pass(uint64_t n, int bits) {
 inline int local_rank_method(dbg_ctx *ctx, bool wide) {
   static const int methods[] = {RANK_MATCH, RANK_ATOMIC, RANK_BALLOT};
   const int v = ctx->sort_variant[wide ? 5 : 4];
-  return methods[(v >= 0 && v < 3) ? v : 0];
+  return methods[(v >= 0 && v < 6) ? v % 3 : 0];
 }
 
 inline unsigned grid_for(uint64_t n, int per_block) {
@@ -405,12 +413,29 @@ dbg_status seg_sort_records(dbg_ctx *ctx, const K *kin, const uint32_t *vin, K *
   DBG_TRY((seg_prepare<K, true>(ctx, kin, vin, n, low_bits, key_bits, bound, osize, ooff, gk, gv, &G,
                                 ST_LOCAL_SORT_NODES)));
   const int rank = local_rank_method(ctx, sizeof(K) == 16);
+  const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
+  const int v = ctx->sort_variant[sizeof(K) == 16 ? 5 : 4];
+  if (v >= 3) {
+    // the wide form: 384 threads x (2/3 of the items), the same capacity
+    constexpr int WB = 384, WI = Sh::ITEMS * SEG_BLOCK / WB;
+    static_assert(WB * WI == SEG_BLOCK * Sh::ITEMS, "same tile capacity");
+    auto kern = rank == RANK_MATCH    ? k_seg_sort<K, WI, RANK_MATCH, WB>
+                : rank == RANK_ATOMIC ? k_seg_sort<K, WI, RANK_ATOMIC, WB>
+                                      : k_seg_sort<K, WI, RANK_BALLOT, WB>;
+    constexpr size_t smem = sizeof(SegSortSmem<K, true, WI, WB>);
+    set_smem_attrs(kern, smem);
+    DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 2.0 * (double)n * (sizeof(K) + 4),
+               kern<<<(unsigned)tiles, WB, smem, ctx->stream>>>(
+                   kin, vin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), gk.as<K>(),
+                   gv.as<uint32_t>(), kout, vout, low_bits, key_bits));
+    DBG_CUDA_TRY(cudaGetLastError());
+    return DBG_OK;
+  }
   auto kern = rank == RANK_MATCH    ? k_seg_sort<K, Sh::ITEMS, RANK_MATCH>
               : rank == RANK_ATOMIC ? k_seg_sort<K, Sh::ITEMS, RANK_ATOMIC>
                                     : k_seg_sort<K, Sh::ITEMS, RANK_BALLOT>;
   constexpr size_t smem = sizeof(SegSortSmem<K, true, Sh::ITEMS>);
   set_smem_attrs(kern, smem);
-  const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
   DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 2.0 * (double)n * (sizeof(K) + 4),
              kern<<<(unsigned)tiles, SEG_BLOCK, smem, ctx->stream>>>(
                  kin, vin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), gk.as<K>(),

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "dbg_device.cuh"
 #include "dbg_internal.h"
@@ -814,26 +815,32 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
 // ticket is taken only by a CTA that holds no unpublished tile, so every
 // look-back ends.  Ranking and look-back are those of k_onesweep.
 // ---------------------------------------------------------------------------
-template <class K, bool HAS_VAL, int BLOCK, int ITEMS>
+// HB: bytes of a per-warp digit counter (2 halves the counters' shared
+// memory; a tile holds fewer than 2^16 keys); the lane-mask rows exist for
+// shared-memory atomicOr ranking only.
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK = RANK_ATOMIC, int HB = 4>
 struct OnesweepPSmem {
   static constexpr int WARPS = BLOCK / 32;
   static constexpr int TILE = BLOCK * ITEMS;
+  static_assert(HB == 4 || (HB == 2 && TILE < 65536), "digit counters must hold a tile's keys");
+  using Hist = std::conditional_t<HB == 2, uint16_t, uint32_t>;
   K keys[2][TILE];
   uint32_t vals[2][HAS_VAL ? TILE : 1];
-  uint32_t whist[WARPS][RADIX];
-  uint32_t match[WARPS][RADIX + 1];
+  Hist whist[WARPS][RADIX];
+  uint32_t match[RANK == RANK_ATOMIC ? WARPS : 1][RADIX + 1];
   uint64_t gbase[RADIX];
   uint64_t bar[2];
   uint32_t tmp[8];
   uint32_t tnext;
 };
 
-template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, int MIN_BLOCKS, int LB>
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, int MIN_BLOCKS, int LB, int HB = 4>
 __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
     const K *__restrict__ kin, K *__restrict__ kout, const uint32_t *__restrict__ vin, uint32_t *__restrict__ vout,
     uint64_t n, int shift, const uint64_t *__restrict__ digit_base, uint64_t *__restrict__ status,
     uint32_t *ticket, uint32_t epoch, uint32_t spin_limit, uint32_t *err) {
-  using S = OnesweepPSmem<K, HAS_VAL, BLOCK, ITEMS>;
+  using S = OnesweepPSmem<K, HAS_VAL, BLOCK, ITEMS, RANK, HB>;
+  using Hist = typename S::Hist;
   constexpr int WARPS = S::WARPS;
   constexpr int TILE = S::TILE;
   constexpr uint32_t KB = TILE * sizeof(K), VB = HAS_VAL ? TILE * sizeof(uint32_t) : 0;
@@ -918,7 +925,7 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
       uint32_t before = 0;
       if (lane == leader && valid) {
         before = sm.whist[warp][d];
-        sm.whist[warp][d] = before + __popc(peers);
+        sm.whist[warp][d] = (Hist)(before + __popc(peers));
       }
       before = __shfl_sync(0xffffffffu, before, leader);
       rank[i] = ((before + __popc(peers & lt_mask)) << 9) | d;
@@ -937,7 +944,7 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
 #pragma unroll
       for (int w = 0; w < WARPS; w++) {
         const uint32_t c = sm.whist[w][tid];
-        sm.whist[w][tid] = run;
+        sm.whist[w][tid] = (Hist)run;
         run += c;
       }
       uint32_t excl = 0;

@@ -15,7 +15,9 @@
 // passes over every digit, and the local kernels copy those results into
 // place instead of sorting.
 //
-// k_seg_sort sorts (key, payload) records (STEP-3's node records).
+// k_seg_sort sorts (key, payload) records (STEP-3's node records), with 256
+// threads of 24 items (126 registers, 2 CTAs per SM) or, in its wide form,
+// 384 threads of 16 items: the same capacity with half again the warps.
 // k_seg_rle finishes STEP-2 on the edge keys: it sorts them and writes each
 // distinct key once with the length of its run (its multiplicity) into the
 // tile's own range; k_seg_compact then packs the tiles' outputs.  Equal keys share their high bits, so no run of
@@ -30,10 +32,10 @@ namespace dbg {
 
 constexpr int SEG_BLOCK = 256;
 
-template <class K, bool HAS_VAL, int ITEMS>
+template <class K, bool HAS_VAL, int ITEMS, int BLOCK = SEG_BLOCK>
 struct SegSortSmem {
-  static constexpr int WARPS = SEG_BLOCK / 32;
-  static constexpr int CAP = SEG_BLOCK * ITEMS;
+  static constexpr int WARPS = BLOCK / 32;
+  static constexpr int CAP = BLOCK * ITEMS;
   K keys[CAP];
   uint32_t vals[HAS_VAL ? CAP : 1];
   uint32_t whist[WARPS][RADIX];
@@ -236,32 +238,32 @@ __device__ __forceinline__ void reload_items(S &sm, K (&key)[ITEMS], uint32_t (&
       if (HAS_VAL) val[i] = sm.vals[j];
     }
   }
-  for (int i = threadIdx.x; i < S::WARPS * RADIX; i += SEG_BLOCK) (&sm.whist[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < S::WARPS * RADIX; i += S::WARPS * 32) (&sm.whist[0][0])[i] = 0;
 }
 
 // Records: tile t sorted in shared memory into kout / vout at its own range;
 // an oversize tile copies its slice of the gathered, globally sorted records
 // (gk / gv at ooff[t]).
-template <class K, int ITEMS, int RANK>
-__global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_sort(
+template <class K, int ITEMS, int RANK, int BLOCK = SEG_BLOCK>
+__global__ __launch_bounds__(BLOCK, 2) void k_seg_sort(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, const uint64_t *__restrict__ bound,
     const uint32_t *__restrict__ osize, const uint64_t *__restrict__ ooff, const K *__restrict__ gk,
     const uint32_t *__restrict__ gv, K *__restrict__ kout, uint32_t *__restrict__ vout, int low_bits, int key_bits) {
-  using S = SegSortSmem<K, true, ITEMS>;
+  using S = SegSortSmem<K, true, ITEMS, BLOCK>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   S &sm = *reinterpret_cast<S *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t tile = blockIdx.x;
   if (osize[tile]) {
     const uint64_t s = bound[tile], o = ooff[tile];
-    for (uint32_t j = tid; j < osize[tile]; j += SEG_BLOCK) {
+    for (uint32_t j = tid; j < osize[tile]; j += BLOCK) {
       kout[s + j] = gk[o + j];
       vout[s + j] = gv[o + j];
     }
     return;
   }
-  for (int i = tid; i < S::WARPS * RADIX; i += SEG_BLOCK) (&sm.whist[0][0])[i] = 0;
-  for (int i = tid; i < S::WARPS * (RADIX + 1); i += SEG_BLOCK) (&sm.match[0][0])[i] = 0;
+  for (int i = tid; i < S::WARPS * RADIX; i += BLOCK) (&sm.whist[0][0])[i] = 0;
+  for (int i = tid; i < S::WARPS * (RADIX + 1); i += BLOCK) (&sm.match[0][0])[i] = 0;
   seg_setup<K>(sm, kin, bound, tile, low_bits, key_bits);
   const uint64_t s = sm.bound[0];
   const uint32_t cnt = (uint32_t)(sm.bound[1] - s);
@@ -270,7 +272,7 @@ __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_sort(
   const int passes = (int)sm.passes;
   // the keys spread evenly over the warps: warp w holds the consecutive
   // keys [w * 32 * ipw, (w + 1) * 32 * ipw), item-major
-  const int ipw = (int)((cnt + SEG_BLOCK - 1) / SEG_BLOCK);
+  const int ipw = (int)((cnt + BLOCK - 1) / BLOCK);
   const uint32_t wofs = (uint32_t)warp * 32u * ipw;
   K key[ITEMS];
   uint32_t val[ITEMS];
@@ -292,7 +294,7 @@ __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_sort(
     scatter_items<K, true, ITEMS>(sm, key, val, rank, ipw);
   }
   __syncthreads();
-  for (uint32_t j = tid; j < cnt; j += SEG_BLOCK) {
+  for (uint32_t j = tid; j < cnt; j += BLOCK) {
     kout[s + j] = KeyOps<K>::add(sm.keys[j], base);
     vout[s + j] = sm.vals[j];
   }
