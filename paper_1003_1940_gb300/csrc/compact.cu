@@ -381,6 +381,125 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_fast_measure(const uint32_t *__r
   }
 }
 
+// Measuring with half the walking: both walkers of a unitig (its two list
+// heads, one per mirrored copy) walk towards each other and stop where they
+// meet.  A walker at strand-node y loads its successor word succ[y]; if the
+// other walker has marked it (bit 31, with the other walker's head in the
+// low bits) the node is the other's and the walk stops; else the walker
+// marks the word the other walker would load at this node, succ[y ^ 1], and
+// goes on.  Plain loads and stores: two walkers arriving together may both
+// take a few nodes, which the pairing step measures.  hrec[x] = (nodes
+// walker x took, its last strand-node, the other walker's head).  The
+// successor words are spoiled for anything but this walk (the list heads are
+// read from succ_base, which stays intact).
+constexpr uint32_t MARK = 0x80000000u;
+
+__global__ __launch_bounds__(WALK_BLOCK) void k_mark_measure(uint32_t *__restrict__ succ,
+                                                             const uint64_t *__restrict__ succ_base, uint64_t n,
+                                                             uint32_t cap, uint4 *__restrict__ hrec,
+                                                             uint32_t *too_long) {
+  __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
+  __shared__ uint32_t s_next[WALK_WARPS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
+  uint32_t lng = 0;
+  for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
+    const uint32_t cnt =
+        queue_heads(c * WALK_CHUNK, n, s_q[w], [&](uint64_t x) { return succ_base[x ^ 1] == ~0ull; });
+    if (lane == 0) s_next[w] = 0;
+    __syncwarp();
+    for (;;) {
+      const uint32_t qi = atomicAdd(&s_next[w], 1u);
+      if (qi >= cnt) break;
+      const uint32_t x = s_q[w][qi];
+      uint32_t y = x, d = 0, last = NONE32, partner = NONE32;
+      for (;;) {
+        const uint32_t nx = __ldcg(succ + y);  // from L2: another SM's mark may be there
+        if (nx != NONE32 && (nx & MARK)) {
+          partner = nx & ~MARK;
+          break;
+        }
+        __stcg(succ + (y ^ 1u), MARK | x);
+        d++;
+        last = y;
+        if (nx == NONE32) {
+          partner = y ^ 1u;
+          break;
+        }
+        if (d >= cap) {
+          lng++;
+          break;
+        }
+        y = nx;
+      }
+      hrec[x] = make_uint4(d, last, partner, 0u);
+    }
+    __syncwarp();
+  }
+  lng = __reduce_add_sync(0xffffffffu, lng);
+  if (lane == 0 && lng) atomicAdd(too_long, lng);
+}
+
+// Per pair of walkers (handled by the smaller head): the unitig's length
+// L = d_a + d_b - o, o the nodes both took (found by stepping from the
+// second walker's last node, read on the first walker's strands, to the
+// first walker's last node); the copy kept (the one whose first k-mer is
+// smaller) and its first node's tables, as k_fast_measure writes them.
+template <class K>
+__global__ void k_mark_pair(const uint64_t *__restrict__ succ_base, uint64_t n, const uint4 *__restrict__ hrec,
+                            const uint64_t *__restrict__ node_keys, int k, uint32_t cap,
+                            uint32_t *__restrict__ is_head, uint32_t *__restrict__ len_at_head,
+                            uint8_t *__restrict__ hstrand, unsigned long long *covered, uint32_t *err) {
+  unsigned long long cov = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (succ_base[i ^ 1] != ~0ull) continue;  // not a list head
+    const uint32_t x = (uint32_t)i;
+    const uint4 ra = hrec[x];
+    const uint32_t p = ra.z;
+    if (p >= n || p == x) {
+      atomicOr(err, ERR_INTERNAL);
+      continue;
+    }
+    if (x > p) continue;
+    const uint4 rb = hrec[p];
+    if (rb.z != x) {
+      atomicOr(err, ERR_INTERNAL);
+      continue;
+    }
+    uint32_t o = 0;
+    if (ra.x > 0 && rb.x > 0 && (uint32_t)succ_base[ra.y] != (rb.y ^ 1u)) {
+      // the walks overlap: step from b's last node (on a's strands) to a's last
+      uint32_t y = rb.y ^ 1u, steps = 0;
+      while (y != ra.y && steps <= cap) {
+        y = (uint32_t)succ_base[y];
+        steps++;
+      }
+      if (y != ra.y) {
+        atomicOr(err, ERR_INTERNAL);
+        continue;
+      }
+      o = steps + 1;
+    }
+    const uint32_t L = ra.x + rb.x - o;
+    const uint32_t kept = KeyOps<K>::less(strand_kmer<K>(node_keys, p, k), strand_kmer<K>(node_keys, x, k)) ? p : x;
+    const uint32_t h = kept >> 1;
+    is_head[h] = 1;
+    len_at_head[h] = L;
+    hstrand[h] = (uint8_t)(kept & 1u);
+    cov += L;
+  }
+  cov = __reduce_add_sync(0xffffffffu, (unsigned)cov);
+  if ((threadIdx.x & 31) == 0 && cov) atomicAdd(covered, cov);
+}
+
+// The successor words again, from succ_base (after a measuring walk spoiled them).
+__global__ void k_restore_succ(const uint64_t *__restrict__ succ_base, uint64_t n, uint32_t *__restrict__ succ) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b = succ_base[x];
+    succ[x] = b == ~0ull ? NONE32 : (uint32_t)b;
+  }
+}
+
 // The first node of every kept unitig: its tables, node entry and first
 // k-mer, and where its walk continues (walk[u] = succ_base of the first
 // strand-node: the second one and the base it appends, or all ones).
@@ -614,17 +733,33 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
       DBG_TRY(alloc_buf(ctx, f_strand, V1));
       DBG_CUDA_TRY(cudaMemsetAsync(f_is_head.p, 0, V1 * 4, s));
       DBG_CUDA_TRY(cudaMemsetAsync(f_len.p, 0, V1 * 4, s));
-      DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 10, 0, 2 * sizeof(uint32_t), s));
-      DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 32.0 * n + 16.0 * V,
-                 k_fast_measure<K><<<walk_grid(ctx, n), WALK_BLOCK, 0, s>>>(succ.as<uint32_t>(), n,
-                                                                            g->node_keys.as<uint64_t>(), k,
-                                                              kWalkCap, f_is_head.as<uint32_t>(),
-                                                              f_len.as<uint32_t>(), f_strand.as<uint8_t>(),
-                                                              ctx->d_counters + 10, ctx->d_counters + 11));
+      // the two walkers of each unitig meet half way (k_mark_measure), then
+      // each pair gives its unitig's length and kept copy (k_mark_pair)
+      DevBuf hrec;
+      DBG_TRY(alloc_buf(ctx, hrec, n1 * sizeof(uint4)));
+      DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 10, 0, 4 * sizeof(uint32_t), s));
+      DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 24.0 * V,
+                 k_mark_measure<<<walk_grid(ctx, n), WALK_BLOCK, 0, s>>>(succ.as<uint32_t>(), word.as<uint64_t>(),
+                                                                         n, kWalkCap, hrec.as<uint4>(),
+                                                                         ctx->d_counters + 11));
       DBG_CUDA_TRY(cudaGetLastError());
-      uint32_t cnt[2] = {0, 0};
-      DBG_TRY(read_small(ctx, ctx->d_counters + 10, sizeof(cnt), cnt));
-      if (cnt[1] == 0 && cnt[0] == n) {
+      uint32_t too_long = 0;
+      DBG_TRY(read_small(ctx, ctx->d_counters + 11, sizeof(uint32_t), &too_long));
+      uint64_t covered = 0;
+      if (too_long == 0) {
+        DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 32.0 * V,
+                   k_mark_pair<K><<<grid_of(n), 256, 0, s>>>(word.as<uint64_t>(), n, hrec.as<uint4>(),
+                                                             g->node_keys.as<uint64_t>(), k, kWalkCap,
+                                                             f_is_head.as<uint32_t>(), f_len.as<uint32_t>(),
+                                                             f_strand.as<uint8_t>(),
+                                                             reinterpret_cast<unsigned long long *>(ctx->d_counters + 12),
+                                                             ctx->d_err));
+        DBG_CUDA_TRY(cudaGetLastError());
+        DBG_TRY(read_small(ctx, ctx->d_counters + 12, sizeof(uint64_t), &covered));
+        DBG_TRY(check_device_error(ctx));
+      }
+      hrec.release();
+      if (too_long == 0 && covered == V) {
         DBG_TRY(alloc_buf(ctx, f_uidx, (V + 1) * 8));
         DBG_TRY(alloc_buf(ctx, f_off, (V + 1) * 8));
         uint32_t U32 = 0, total = 0;
@@ -661,6 +796,9 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
       }
     }
     // ---- general path: long lists or cycles present ----
+    // (the measuring walk marked the successor words: rebuild them)
+    DBG_LAUNCH(ctx, ST_COMPACT_RANK, 12.0 * n,
+               k_restore_succ<<<grid_of(n), 256, 0, s>>>(word.as<uint64_t>(), n, succ.as<uint32_t>()));
     DBG_CUDA_TRY(cudaMemsetAsync(word.p, 0xff, n * 8, s));
     DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 12.0 * n,
                k_walk_lists<<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n, kWalkCap,
