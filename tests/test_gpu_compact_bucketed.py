@@ -81,3 +81,19 @@ def test_bucketed_ranking_low_complexity_and_tiny(dbg):
     check(dbg, ctx, r, l, 21, [0])
     r, l = as_input(["ACGTACGTAACCGGTT"])
     check(dbg, ctx, r, l, 5, [0, 4096])
+
+
+def test_bucketed_ranking_mid_size(dbg):
+    """750 K reads of the large workload's recipe (52 M edge instances): the
+    out-of-core ranking in 1 GB of device memory gives dbg_compact's unitigs."""
+    import torch
+    spec = readgen.large_spec(0.05)
+    reads, lengths = readgen.generate(spec)
+    ctx = dbg.Context()
+    g = dbg.dbg_build(ctx, torch.from_numpy(reads).cuda(), torch.from_numpy(lengths.view(np.int32)).cuda(), 31)
+    want = dbg.dbg_unitigs_get(dbg.dbg_compact(ctx, g))
+    u, launches = dbg.dbg_compact_bucketed(ctx, g, 1 << 30)
+    got = dbg.dbg_unitigs_get(u)
+    for f in ("node_off", "nodes", "seq_off", "circular"):
+        np.testing.assert_array_equal(got[f], want[f], err_msg=f)
+    assert got["seq"] == want["seq"] and launches > 10

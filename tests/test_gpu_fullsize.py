@@ -173,3 +173,22 @@ def test_full_size_compaction_is_maximal(built):
     u = dbg.dbg_compact(ctx, g)
     res = check_unitigs_maximal(dbg, g, dbg.dbg_unitigs_get(u))
     assert res["unitigs"] == dbg.dbg_unitigs_count(u) and res["mergeable"] > 0
+
+
+def test_full_size_bucketed_equals_in_memory(built):
+    """The key-range bucket path (Section 5) on the full-size workload, with
+    a budget that cuts the edge and node keys into several ranges and with
+    host-resident reads streamed in: array for array the in-memory graph
+    (itself compared with the oracle above)."""
+    import torch
+    dbg, ctx, g, reads, lengths = built
+    gb = dbg.dbg_build_bucketed(ctx, reads, lengths, K, 6 << 30)
+    eb, nb = dbg.dbg_graph_buckets(gb)
+    assert eb > 1 and nb > 1, (eb, nb)
+    V, E = dbg.dbg_graph_num_nodes(g), dbg.dbg_graph_num_edges(g)
+    assert (dbg.dbg_graph_num_nodes(gb), dbg.dbg_graph_num_edges(gb)) == (V, E)
+    for f, n, ty in (("node_keys", V, "<u8"), ("edge_keys", E, "<u8"), ("src", E, "<u4"), ("dst", E, "<u4"),
+                     ("orient", E, "|u1"), ("mult", E, "<u4"), ("row_ptr", V + 1, "<u8"),
+                     ("adj_nbr", 2 * E, "<u4"), ("adj_edge", 2 * E, "<u4"), ("adj_role", 2 * E, "|u1")):
+        assert torch.equal(dbg.device_tensor(g, f, n, ty), dbg.device_tensor(gb, f, n, ty)), f
+    gb.free()
