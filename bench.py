@@ -60,6 +60,8 @@ def parse():
                     help="1: the edge keys' local pass counts copies in a hash table before sorting")
     ap.add_argument("--partition-first", type=int, default=1, choices=(0, 1),
                     help="1: the edge keys' first global pass is an unordered partition")
+    ap.add_argument("--local-rank", type=int, default=1, choices=(0, 1),
+                    help="1: the local passes rank keys within their groups instead of digit passes")
     ap.add_argument("--node-mult", action="store_true",
                     help="the build also counts node multiplicities (an extra k-mer sort)")
     ap.add_argument("--sort-variant", default="", help="a,b,c,d: fixed radix variants per key kind instead "
@@ -397,6 +399,7 @@ def run_ours(args):
             dbg.dbg_sort_variant_set(ctx, kd, args.local_variant)
     dbg.dbg_sort_count_first_set(ctx, bool(args.count_first))
     dbg.dbg_sort_partition_first_set(ctx, bool(args.partition_first))
+    dbg.dbg_sort_local_rank_set(ctx, bool(args.local_rank))
     dbg.dbg_node_mult_set(ctx, bool(args.node_mult))
     variants = {kd: dbg.dbg_sort_variant_name(kd, dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(6)}
     variant_ids = ",".join(str(dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(6))
@@ -541,7 +544,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}",
                        "sort_variants": variants, "sort_variant_ids": variant_ids,
                        "count_first": bool(args.count_first),
-                       "partition_first": bool(args.partition_first), "node_mult": bool(args.node_mult),
+                       "partition_first": bool(args.partition_first), "local_rank": bool(args.local_rank),
+                       "node_mult": bool(args.node_mult),
                        "autotune_pass_ms": {kd: [round(x, 4) for x in v] for kd, v in tune_ms.items()}},
             "roofline": {"bound": "hbm",
                          "kernel": f"{'k_onesweep_p' if 'persistent' in (variants.get(ekind) or '') else 'k_onesweep'}"

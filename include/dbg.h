@@ -470,6 +470,22 @@ uint64_t dbg_sort_count_overflows(const dbg_ctx *ctx);
 dbg_status dbg_sort_partition_first_set(dbg_ctx *ctx, int on);
 
 /* ----------------------------------------------------------------------
+ * Group-ranking switch for the local passes of the hybrid sort.  The
+ * global passes leave keys with equal high bits (a group) contiguous; with
+ * the switch on (the default) a local pass places each key at its group's
+ * start plus the number of the group's keys that precede it (for the
+ * count-first edge pass, the distinct keys below it; for 64-bit node
+ * records, the records with smaller low bits or an equal key and an
+ * earlier position, which keeps the sort stable).  Tiles holding a group
+ * too long for that (over 256 distinct edge keys or 512 records) take the
+ * shared-memory digit passes, as every tile does with the switch off.
+ * The graph is the same either way.
+ * -------------------------------------------------------------------- */
+dbg_status dbg_sort_local_rank_set(dbg_ctx *ctx, int on);
+/* Tiles that met such a group, over the context's builds. */
+uint64_t dbg_sort_rank_fallbacks(const dbg_ctx *ctx);
+
+/* ----------------------------------------------------------------------
  * Failure detection.  Every device-side wait of the library (decoupled
  * look-back, TMA completion) spins at most spin_limit times, then records
  * DBG_ETIMEOUT in the context's device error word and returns; the call

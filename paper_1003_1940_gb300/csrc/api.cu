@@ -677,6 +677,8 @@ uint64_t dbg_sort_fallbacks(const dbg_ctx *ctx) { return ctx ? ctx->local_sort_f
 
 uint64_t dbg_sort_count_overflows(const dbg_ctx *ctx) { return ctx ? ctx->count_overflow_tiles : 0; }
 
+uint64_t dbg_sort_rank_fallbacks(const dbg_ctx *ctx) { return ctx ? ctx->rank_fallback_tiles : 0; }
+
 dbg_status dbg_node_mult_set(dbg_ctx *ctx, int on) {
   if (!ctx) {
     set_error("null context");
@@ -740,6 +742,15 @@ dbg_status dbg_sort_partition_first_set(dbg_ctx *ctx, int on) {
     return DBG_EINVAL;
   }
   ctx->partition_first = on ? 1 : 0;
+  return DBG_OK;
+}
+
+dbg_status dbg_sort_local_rank_set(dbg_ctx *ctx, int on) {
+  if (!ctx) {
+    set_error("null context");
+    return DBG_EINVAL;
+  }
+  ctx->seg_rank = on ? 1 : 0;
   return DBG_OK;
 }
 

@@ -224,13 +224,16 @@ inline void set_smem_attrs(F kern, size_t smem) {
 // significant bits are the low `bits`.  `hist` holds the per-pass digit
 // histograms (passes x 256), already accumulated by the producer kernel.
 // Passes below first_pass are skipped: the keys are then sorted by their
-// bits from 8 * first_pass up (stably; for keys without payload, with the
-// partition-first switch on, keys equal in those bits end in no particular
-// order).  On return the data is in *keys / *vals (the buffers may have
+// bits from 8 * first_pass - adj up (stably; for keys without payload, with
+// the partition-first switch on, keys equal in those bits end in no
+// particular order).  Pass p takes the 8 bits from 8 p - adj up: adj > 0
+// aligns the top pass with the top of a key of 8 P - adj bits, so that the
+// passes from first_pass up resolve whole bytes of it.  On return the data is in *keys / *vals (the buffers may have
 // been swapped with *alt_keys / *alt_vals).
 template <class K, bool HAS_VAL>
 dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uint32_t **alt_vals, uint64_t n,
-                      int bits, const unsigned long long *d_hist, uint64_t *d_digit_base, int first_pass = 0) {
+                      int bits, const unsigned long long *d_hist, uint64_t *d_digit_base, int first_pass = 0,
+                      int adj = 0) {
   if (n <= 1) return DBG_OK;
   const SortVariant &sv = chosen_variant<K, HAS_VAL>(ctx);
   const int passes = passes_for_bits(bits);
@@ -250,7 +253,7 @@ dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uin
     const unsigned grid = (unsigned)std::min<uint64_t>(tiles, 3ull * (uint64_t)ctx->num_sms);
     DBG_LAUNCH(ctx, ST_PARTITION_EDGES, 2.0 * (double)n * (double)sizeof(K),
                k_partition<K><<<grid, PART_BLOCK, smem, s>>>(
-                   *keys, *alt_keys, n, p * RADIX_BITS,
+                   *keys, *alt_keys, n, p * RADIX_BITS - adj,
                    reinterpret_cast<unsigned long long *>(d_digit_base + p * RADIX), ctx->spin_limit, ctx->d_err));
     std::swap(*keys, *alt_keys);
     p++;
@@ -262,7 +265,7 @@ dbg_status radix_sort(dbg_ctx *ctx, K **keys, K **alt_keys, uint32_t **vals, uin
     DBG_LAUNCH(ctx, HAS_VAL ? ST_SORT_NODES : ST_SORT_EDGES,
                2.0 * (double)n * (double)(sizeof(K) + (HAS_VAL ? sizeof(uint32_t) : 0)),
                sv.launch(ctx, *keys, *alt_keys, HAS_VAL ? *vals : nullptr, HAS_VAL ? *alt_vals : nullptr, n,
-                         p * RADIX_BITS, d_digit_base + p * RADIX, epoch));
+                         p * RADIX_BITS - adj, d_digit_base + p * RADIX, epoch));
     std::swap(*keys, *alt_keys);
     if (HAS_VAL) std::swap(*vals, *alt_vals);
   }
@@ -414,6 +417,39 @@ dbg_status seg_sort_records(dbg_ctx *ctx, const K *kin, const uint32_t *vin, K *
                                 ST_LOCAL_SORT_NODES)));
   const int rank = local_rank_method(ctx, sizeof(K) == 16);
   const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
+  if constexpr (sizeof(K) == 8) {
+    if (ctx->seg_rank && low_bits + 13 <= 64) {
+      // ranking within groups; tiles with a long group are listed and
+      // sorted by the digit passes
+      static_assert(RANK_CAP == SEG_BLOCK * Sh::ITEMS, "same tile capacity as the digit-pass kernel");
+      set_smem_attrs(k_seg_rank, sizeof(SegRankSmem));
+      DevBuf fb;
+      DBG_TRY(alloc_buf(ctx, fb, (tiles + 1) * 4));
+      uint32_t *fb_count = fb.as<uint32_t>(), *fb_list = fb_count + 1;
+      DBG_CUDA_TRY(cudaMemsetAsync(fb_count, 0, 4, ctx->stream));
+      DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 2.0 * (double)n * (sizeof(K) + 4),
+                 k_seg_rank<<<(unsigned)tiles, RANK_BLOCK, sizeof(SegRankSmem), ctx->stream>>>(
+                     kin, vin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), gk.as<K>(),
+                     gv.as<uint32_t>(), kout, vout, low_bits, fb_list, fb_count));
+      DBG_CUDA_TRY(cudaGetLastError());
+      uint32_t nfb = 0;
+      DBG_TRY(read_small(ctx, fb_count, sizeof(uint32_t), &nfb));
+      ctx->rank_fallback_tiles += nfb;
+      if (nfb == 0) return DBG_OK;
+      auto kern = rank == RANK_MATCH    ? k_seg_sort<K, Sh::ITEMS, RANK_MATCH>
+                  : rank == RANK_ATOMIC ? k_seg_sort<K, Sh::ITEMS, RANK_ATOMIC>
+                                        : k_seg_sort<K, Sh::ITEMS, RANK_BALLOT>;
+      constexpr size_t smem = sizeof(SegSortSmem<K, true, Sh::ITEMS>);
+      set_smem_attrs(kern, smem);
+      const unsigned grid = (unsigned)std::min<uint64_t>(nfb, 2ull * (uint64_t)std::max(1, ctx->num_sms));
+      DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 0.0,
+                 kern<<<grid, SEG_BLOCK, smem, ctx->stream>>>(
+                     kin, vin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), gk.as<K>(),
+                     gv.as<uint32_t>(), kout, vout, low_bits, key_bits, fb_list, fb_count));
+      DBG_CUDA_TRY(cudaGetLastError());
+      return DBG_OK;
+    }
+  }
   const int v = ctx->sort_variant[sizeof(K) == 16 ? 5 : 4];
   if (v >= 3) {
     // the wide form: 384 threads x (2/3 of the items), the same capacity
@@ -427,7 +463,7 @@ dbg_status seg_sort_records(dbg_ctx *ctx, const K *kin, const uint32_t *vin, K *
     DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 2.0 * (double)n * (sizeof(K) + 4),
                kern<<<(unsigned)tiles, WB, smem, ctx->stream>>>(
                    kin, vin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), gk.as<K>(),
-                   gv.as<uint32_t>(), kout, vout, low_bits, key_bits));
+                   gv.as<uint32_t>(), kout, vout, low_bits, key_bits, nullptr, nullptr));
     DBG_CUDA_TRY(cudaGetLastError());
     return DBG_OK;
   }
@@ -439,7 +475,7 @@ dbg_status seg_sort_records(dbg_ctx *ctx, const K *kin, const uint32_t *vin, K *
   DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 2.0 * (double)n * (sizeof(K) + 4),
              kern<<<(unsigned)tiles, SEG_BLOCK, smem, ctx->stream>>>(
                  kin, vin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), gk.as<K>(),
-                 gv.as<uint32_t>(), kout, vout, low_bits, key_bits));
+                 gv.as<uint32_t>(), kout, vout, low_bits, key_bits, nullptr, nullptr));
   DBG_CUDA_TRY(cudaGetLastError());
   return DBG_OK;
 }
@@ -486,18 +522,20 @@ dbg_status seg_rle(dbg_ctx *ctx, K *kin, K *kstage, uint64_t n, int low_bits, in
                                                  : sizeof(SegCountSmem<K, RANK_BALLOT>);
       set_smem_attrs(count, csmem);
       DevBuf over;
-      DBG_TRY(alloc_buf(ctx, over, (tiles + 1) * 4));
-      uint32_t *over_count = over.as<uint32_t>(), *over_list = over_count + 1;
-      DBG_CUDA_TRY(cudaMemsetAsync(over_count, 0, 4, s));
+      DBG_TRY(alloc_buf(ctx, over, (tiles + 2) * 4));
+      uint32_t *over_count = over.as<uint32_t>(), *rank_fb = over_count + 1, *over_list = over_count + 2;
+      DBG_CUDA_TRY(cudaMemsetAsync(over_count, 0, 8, s));
       DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, (double)n * sizeof(K),
                  count<<<(unsigned)tiles, SEG_BLOCK, csmem, s>>>(
                      kin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), guniq.as<K>(),
                      gheads.as<uint32_t>(), (uint32_t)H, kstage, mstage.as<uint32_t>(), tcount.as<uint32_t>(),
-                     over_list, over_count, low_bits, key_bits));
+                     over_list, over_count, low_bits, key_bits, ctx->seg_rank, rank_fb));
       DBG_CUDA_TRY(cudaGetLastError());
-      uint32_t nover = 0;
-      DBG_TRY(read_small(ctx, over_count, sizeof(uint32_t), &nover));
+      uint32_t nover_fb[2] = {0, 0};
+      DBG_TRY(read_small(ctx, over_count, 2 * sizeof(uint32_t), nover_fb));
+      const uint32_t nover = nover_fb[0];
       ctx->count_overflow_tiles += nover;
+      ctx->rank_fallback_tiles += nover_fb[1];
       if (nover > 0)
         DBG_LAUNCH(ctx, ST_LOCAL_SORT_EDGES, 0.0,
                    radix<<<nover, SEG_BLOCK, rsmem, s>>>(
@@ -528,13 +566,14 @@ dbg_status seg_rle(dbg_ctx *ctx, K *kin, K *kstage, uint64_t n, int low_bits, in
 
 // STEP-3's stable sort of R node records: hybrid (global passes from q0
 // up, then the local pass) when q0 > 0, else every digit globally.  The
-// producers accumulated the histograms of passes q0 and up only.
+// producers accumulated the histograms of passes q0 and up only (with the
+// digit alignment adj, which needs q0 > 0).
 template <class K>
 dbg_status sort_records(dbg_ctx *ctx, K **rk, K **rk_alt, uint32_t **rv, uint32_t **rv_alt, uint64_t R, int nbits,
-                        int q0, unsigned long long *d_hist, uint64_t *d_digit_base) {
+                        int q0, unsigned long long *d_hist, uint64_t *d_digit_base, int adj = 0) {
   if (q0 > 0 && R > 1) {
-    DBG_TRY((radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base, q0)));
-    DBG_TRY(seg_sort_records<K>(ctx, *rk, *rv, *rk_alt, *rv_alt, R, RADIX_BITS * q0, nbits));
+    DBG_TRY((radix_sort<K, true>(ctx, rk, rk_alt, rv, rv_alt, R, nbits, d_hist, d_digit_base, q0, adj)));
+    DBG_TRY(seg_sort_records<K>(ctx, *rk, *rv, *rk_alt, *rv_alt, R, RADIX_BITS * q0 - adj, nbits));
     std::swap(*rk, *rk_alt);
     std::swap(*rv, *rv_alt);
     return DBG_OK;
@@ -900,13 +939,21 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   DBG_TRY(alloc_buf(ctx, rv_a, std::max<uint64_t>(1, R) * sizeof(uint32_t)));
   DBG_TRY(alloc_buf(ctx, rv_b, std::max<uint64_t>(1, R) * sizeof(uint32_t)));
   DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
-  const int q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(R, nbits) : 0;
+  // 64-bit records ranked within groups: align the digits with the top of
+  // the 2k-bit key, so that the global passes resolve 8 bits each of it and
+  // leave short groups
+  int adj = (sizeof(K) == 8 && ctx->seg_rank) ? (8 - nbits % 8) % 8 : 0;
+  int q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(R, nbits + adj) : 0;
+  if (q0 == 0) {
+    adj = 0;
+    q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(R, nbits) : 0;
+  }
   if (E > 0) {
     DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)E * (3 * sizeof(K) + 4 + 4 + 1 + 8),
                k_endpoints<K><<<grid_for(E, EMIT_TILE), EMIT_BLOCK, 0, s>>>(
         uniq.as<K>(), headpos.p ? headpos.as<uint32_t>() : nullptr, mult_tmp.as<uint32_t>(), E, k,
         g->edge_keys.as<K>(), g->mult.as<uint32_t>(),
-        g->orient.as<uint8_t>(), rk_a.as<K>(), rv_a.as<uint32_t>(), q0, npasses, d_hist));
+        g->orient.as<uint8_t>(), rk_a.as<K>(), rv_a.as<uint32_t>(), q0, npasses, d_hist, adj));
   }
   if (I > 0) {
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 2, 0, sizeof(uint32_t), s));
@@ -914,7 +961,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
                k_isolated<K><<<grid_for(n, 256), 256, 0, s>>>(packed.as<uint64_t>(), base_off.as<uint64_t>(),
                                                    in.d_lengths, n, k, rk_a.as<K>() + 2 * E,
                                                    rv_a.as<uint32_t>() + 2 * E, ctx->d_counters + 2, q0, npasses,
-                                                   d_hist));
+                                                   d_hist, adj));
   }
   DBG_CUDA_TRY(cudaGetLastError());
   uniq.release();
@@ -927,7 +974,7 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   // ---- STEP-3 sort of the node records (stable: payload order kept) ----
   K *rk = rk_a.as<K>(), *rk_alt = rk_b.as<K>();
   uint32_t *rv = rv_a.as<uint32_t>(), *rv_alt = rv_b.as<uint32_t>();
-  DBG_TRY((sort_records<K>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, q0, d_hist, d_digit_base)));
+  DBG_TRY((sort_records<K>(ctx, &rk, &rk_alt, &rv, &rv_alt, R, nbits, q0, d_hist, d_digit_base, adj)));
 
   // ---- K6 node IDs + adjacency rows, K7 neighbours ----
   DevBuf row_tmp;

@@ -83,10 +83,12 @@ struct dbg_ctx {
   int hybrid_sort = 1;                 // high digits globally + local sort of group-aligned tiles
   int count_first = 1;                 // local pass of the edge keys counts copies before sorting
   int partition_first = 1;             // first global pass of keys without payload: unordered partition
+  int seg_rank = 1;                    // local passes rank within groups instead of digit passes
   int node_mult = 0;                   // dbg_build also counts every node's k-mer occurrences
   int node_reads = 0;                  // dbg_build also counts the distinct reads holding every node
   uint64_t count_overflow_tiles = 0;  // count-first tiles whose keys did not fit the hash table
   uint64_t local_sort_fallbacks = 0;   // local sorts that met a group longer than their window
+  uint64_t rank_fallback_tiles = 0;    // tiles with a group too long to rank, sorted by digit passes
   int num_sms = 0;
   // persistent scratch: the look-back status words of every scan and sort
   // pass, tagged by epoch so they never need clearing between uses

@@ -1152,8 +1152,9 @@ static __global__ __launch_bounds__(SCAN_BLOCK) void k_scan_excl(const uint32_t 
 // negative strand, STEP-1's table gives (x^, y^, o1, o2) if x^ <= y^ and
 // (y^, x^, not o2, not o1) otherwise.  Writes orient, mult, a copy of the
 // key into the graph, and two node records per edge (payload e<<1 | role),
-// and accumulates the digit histograms of the node sort.  The multiplicity
-// comes from the run heads (headpos) or directly from mult_in.
+// and accumulates the digit histograms of the node sort (pass ps takes the
+// 8 bits from 8 ps - adj up).  The multiplicity comes from the run heads
+// (headpos) or directly from mult_in.
 // ---------------------------------------------------------------------------
 template <class K>
 __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ uniq,
@@ -1163,7 +1164,7 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ 
                                                           uint32_t *__restrict__ mult,
                                                           uint8_t *__restrict__ orient, K *__restrict__ rkeys,
                                                           uint32_t *__restrict__ rvals, int first, int passes,
-                                                          unsigned long long *__restrict__ hist) {
+                                                          unsigned long long *__restrict__ hist, int adj = 0) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK) s_hist[i] = 0;
   __syncthreads();
@@ -1188,8 +1189,8 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ 
     rkeys[2 * e + 1] = d;
     rvals[2 * e + 1] = (uint32_t)(e << 1) | 1u;
     for (int ps = first; ps < passes; ps++) {
-      atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(s, ps * RADIX_BITS, RADIX_BITS)], 1u);
-      atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(d, ps * RADIX_BITS, RADIX_BITS)], 1u);
+      atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(s, ps * RADIX_BITS - adj, RADIX_BITS)], 1u);
+      atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(d, ps * RADIX_BITS - adj, RADIX_BITS)], 1u);
     }
   }
   __syncthreads();
@@ -1204,7 +1205,7 @@ template <class K>
 __global__ void k_isolated(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ base_off,
                            const uint32_t *__restrict__ len, uint64_t n, uint32_t k, K *__restrict__ rkeys,
                            uint32_t *__restrict__ rvals, uint32_t *slot, int first, int passes,
-                           unsigned long long *__restrict__ hist) {
+                           unsigned long long *__restrict__ hist, int adj = 0) {
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
     if (len[r] != k) continue;
     const K x = load_window<K>(packed, base_off[r], (int)k);
@@ -1213,7 +1214,7 @@ __global__ void k_isolated(const uint64_t *__restrict__ packed, const uint64_t *
     rkeys[i] = xh;
     rvals[i] = REC_NONE;
     for (int ps = first; ps < passes; ps++)
-      atomicAdd(hist + ps * RADIX + KeyOps<K>::digit(xh, ps * RADIX_BITS, RADIX_BITS), 1ull);
+      atomicAdd(hist + ps * RADIX + KeyOps<K>::digit(xh, ps * RADIX_BITS - adj, RADIX_BITS), 1ull);
   }
 }
 

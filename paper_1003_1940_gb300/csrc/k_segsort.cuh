@@ -244,16 +244,14 @@ __device__ __forceinline__ void reload_items(S &sm, K (&key)[ITEMS], uint32_t (&
 // Records: tile t sorted in shared memory into kout / vout at its own range;
 // an oversize tile copies its slice of the gathered, globally sorted records
 // (gk / gv at ooff[t]).
-template <class K, int ITEMS, int RANK, int BLOCK = SEG_BLOCK>
-__global__ __launch_bounds__(BLOCK, 2) void k_seg_sort(
-    const K *__restrict__ kin, const uint32_t *__restrict__ vin, const uint64_t *__restrict__ bound,
-    const uint32_t *__restrict__ osize, const uint64_t *__restrict__ ooff, const K *__restrict__ gk,
-    const uint32_t *__restrict__ gv, K *__restrict__ kout, uint32_t *__restrict__ vout, int low_bits, int key_bits) {
+template <class K, int ITEMS, int RANK, int BLOCK>
+__device__ __forceinline__ void seg_sort_tile(
+    SegSortSmem<K, true, ITEMS, BLOCK> &sm, uint32_t tile, const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+    const uint64_t *__restrict__ bound, const uint32_t *__restrict__ osize, const uint64_t *__restrict__ ooff,
+    const K *__restrict__ gk, const uint32_t *__restrict__ gv, K *__restrict__ kout, uint32_t *__restrict__ vout,
+    int low_bits, int key_bits) {
   using S = SegSortSmem<K, true, ITEMS, BLOCK>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  S &sm = *reinterpret_cast<S *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t tile = blockIdx.x;
   if (osize[tile]) {
     const uint64_t s = bound[tile], o = ooff[tile];
     for (uint32_t j = tid; j < osize[tile]; j += BLOCK) {
@@ -297,6 +295,122 @@ __global__ __launch_bounds__(BLOCK, 2) void k_seg_sort(
   for (uint32_t j = tid; j < cnt; j += BLOCK) {
     kout[s + j] = KeyOps<K>::add(sm.keys[j], base);
     vout[s + j] = sm.vals[j];
+  }
+}
+
+// One CTA per tile; or, with a tile list, a grid of CTAs that take the
+// *list_count listed tiles in turn.
+template <class K, int ITEMS, int RANK, int BLOCK = SEG_BLOCK>
+__global__ __launch_bounds__(BLOCK, 2) void k_seg_sort(
+    const K *__restrict__ kin, const uint32_t *__restrict__ vin, const uint64_t *__restrict__ bound,
+    const uint32_t *__restrict__ osize, const uint64_t *__restrict__ ooff, const K *__restrict__ gk,
+    const uint32_t *__restrict__ gv, K *__restrict__ kout, uint32_t *__restrict__ vout, int low_bits, int key_bits,
+    const uint32_t *__restrict__ tile_list = nullptr, const uint32_t *__restrict__ list_count = nullptr) {
+  using S = SegSortSmem<K, true, ITEMS, BLOCK>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  S &sm = *reinterpret_cast<S *>(smem_raw);
+  if (!tile_list) {
+    seg_sort_tile<K, ITEMS, RANK, BLOCK>(sm, blockIdx.x, kin, vin, bound, osize, ooff, gk, gv, kout, vout, low_bits,
+                                         key_bits);
+    return;
+  }
+  const uint32_t n = *list_count;
+  for (uint32_t q = blockIdx.x; q < n; q += gridDim.x) {
+    seg_sort_tile<K, ITEMS, RANK, BLOCK>(sm, tile_list[q], kin, vin, bound, osize, ooff, gk, gv, kout, vout,
+                                         low_bits, key_bits);
+    __syncthreads();
+  }
+}
+
+// Records by ranking within groups (64-bit keys).  The tile's keys are
+// already ordered by their high bits (from low_bits up), so a record's place
+// in the sorted tile is its group's start plus the number of records of its
+// group that precede it: those with smaller low bits, or equal low bits and
+// an earlier position (which keeps the sort stable).  Each record is staged
+// in shared memory as one word, (low bits << 13) | position, and ranked by
+// comparing that word with the group's others; no digit pass and no block
+// barrier is needed past the staging.  The work is the sum of the squared
+// group lengths, small when the global passes leave groups of a few dozen
+// records.  A tile with a group longer than RANK_GROUP_MAX is listed in
+// fb_list for the digit-pass kernel instead.
+constexpr int RANK_BLOCK = 512, RANK_CAP = SEG_BLOCK * 24, RANK_ITEMS = RANK_CAP / RANK_BLOCK;
+constexpr uint32_t RANK_GROUP_MAX = 512;
+static_assert(RANK_CAP <= 8192, "positions fit 13 bits");
+
+struct SegRankSmem {
+  uint64_t pk[RANK_CAP];  // (low bits << 13) | position
+  uint32_t val[RANK_CAP];
+  uint16_t ord[RANK_CAP];           // group of each record
+  uint16_t gstart[RANK_CAP + 1];    // first position of each group, then cnt
+  uint32_t cnt[RANK_ITEMS * (RANK_BLOCK / 32) + 1];
+  uint32_t maxg;
+};
+
+static __global__ __launch_bounds__(RANK_BLOCK, 2) void k_seg_rank(
+    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, const uint64_t *__restrict__ bound,
+    const uint32_t *__restrict__ osize, const uint64_t *__restrict__ ooff, const uint64_t *__restrict__ gk,
+    const uint32_t *__restrict__ gv, uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int low_bits,
+    uint32_t *__restrict__ fb_list, uint32_t *__restrict__ fb_count) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SegRankSmem &sm = *reinterpret_cast<SegRankSmem *>(smem_raw);
+  const int tid = threadIdx.x;
+  const uint32_t tile = blockIdx.x;
+  const uint64_t s = bound[tile];
+  if (osize[tile]) {
+    const uint64_t o = ooff[tile];
+    for (uint32_t j = tid; j < osize[tile]; j += RANK_BLOCK) {
+      kout[s + j] = gk[o + j];
+      vout[s + j] = gv[o + j];
+    }
+    return;
+  }
+  const uint32_t cnt = (uint32_t)(bound[tile + 1] - s);
+  if (cnt == 0) return;
+  const uint64_t low_mask = (1ull << low_bits) - 1ull;
+  if (tid == 0) sm.maxg = 0;
+  // stage the records; a group starts where the high bits change
+  bool head[RANK_ITEMS];
+  uint32_t rk[RANK_ITEMS];
+#pragma unroll
+  for (int i = 0; i < RANK_ITEMS; i++) {
+    const uint32_t j = (uint32_t)i * RANK_BLOCK + tid;
+    head[i] = false;
+    if (j < cnt) {
+      const uint64_t x = kin[s + j];
+      head[i] = j == 0 || ((x ^ kin[s + j - 1]) >> low_bits) != 0;
+      sm.pk[j] = ((x & low_mask) << 13) | j;
+      sm.val[j] = vin[s + j];
+    }
+  }
+  const uint32_t G = tile_flag_ranks<RANK_BLOCK, RANK_ITEMS>(head, rk, sm.cnt);
+#pragma unroll
+  for (int i = 0; i < RANK_ITEMS; i++) {
+    const uint32_t j = (uint32_t)i * RANK_BLOCK + tid;
+    if (j < cnt) {
+      const uint32_t o = rk[i] + (head[i] ? 1u : 0u) - 1u;
+      sm.ord[j] = (uint16_t)o;
+      if (head[i]) sm.gstart[o] = (uint16_t)j;
+    }
+  }
+  if (tid == 0) sm.gstart[G] = (uint16_t)cnt;
+  __syncthreads();
+  uint32_t mg = 0;
+  for (uint32_t o = tid; o < G; o += RANK_BLOCK) mg = max(mg, (uint32_t)sm.gstart[o + 1] - sm.gstart[o]);
+  mg = __reduce_max_sync(0xffffffffu, mg);
+  if ((tid & 31) == 0 && mg) atomicMax(&sm.maxg, mg);
+  __syncthreads();
+  if (sm.maxg > RANK_GROUP_MAX) {
+    if (tid == 0) fb_list[atomicAdd(fb_count, 1u)] = tile;
+    return;
+  }
+  for (uint32_t i = tid; i < cnt; i += RANK_BLOCK) {
+    const uint32_t o = sm.ord[i], a = sm.gstart[o], b = sm.gstart[o + 1];
+    const uint64_t p = sm.pk[i];
+    uint32_t r = 0;
+#pragma unroll 4
+    for (uint32_t t = a; t < b; t++) r += sm.pk[t] < p ? 1u : 0u;
+    kout[s + a + r] = kin[s + i];
+    vout[s + a + r] = sm.val[i];
   }
 }
 
@@ -404,7 +518,13 @@ __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_rle(
 // occupied slots to the front of the table in slot order, and radix-sorts
 // only the distinct keys with their counts as payload.  The output is that
 // of k_seg_rle: each distinct key once, in order, with its multiplicity
-// (STEP-2), staged in the tile's own range.  The table is small so that
+// (STEP-2), staged in the tile's own range.  With rank_groups set, the
+// distinct keys are not radix-sorted but ranked: each slot also records the
+// ordinal of its key's group (keys of equal high bits, numbered in tile
+// order while the keys are counted), the distinct keys are bucketed by
+// group, and a key's place is its group's start plus the number of the
+// group's keys below it (a tile with a group of more than
+// COUNT_GROUP_MAX distinct keys takes the radix sort).  The table is small so that
 // several CTAs share an SM; a tile whose keys do not fit (a probe longer
 // than PROBES slots) is listed in over_list and sorted by k_seg_rle instead.
 
@@ -452,6 +572,8 @@ struct SlotOps<Key128> {
   }
 };
 
+constexpr uint32_t COUNT_GROUP_MAX = 256;
+
 template <class K, int RANK>
 struct SegCountSmem {
   static constexpr int WARPS = SEG_BLOCK / 32;
@@ -463,6 +585,10 @@ struct SegCountSmem {
   static_assert((1 << TBITS) == TBL, "table size");
   K keys[TBL];         // hash slots; then the distinct keys, packed and sorted
   uint32_t vals[TBL];  // copies per slot; then per distinct key
+  uint16_t sord[TBL];  // group ordinal per slot; then per distinct key
+  uint16_t perm[TBL];  // distinct keys bucketed by group
+  uint32_t gst[TBL + 1];
+  uint32_t maxg;
   uint32_t whist[WARPS][RADIX];
   uint32_t match[RANK == RANK_ATOMIC ? WARPS : 1][RADIX + 1];
   uint32_t cnt[ITEMS * WARPS + 1];
@@ -477,7 +603,8 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
     const K *__restrict__ kin, const uint64_t *__restrict__ bound, const uint32_t *__restrict__ osize,
     const uint64_t *__restrict__ ooff, const K *__restrict__ guniq, const uint32_t *__restrict__ gheads, uint32_t H,
     K *__restrict__ ustage, uint32_t *__restrict__ mstage, uint32_t *__restrict__ tcount,
-    uint32_t *__restrict__ over_list, uint32_t *__restrict__ over_count, int low_bits, int key_bits) {
+    uint32_t *__restrict__ over_list, uint32_t *__restrict__ over_count, int low_bits, int key_bits,
+    int rank_groups, uint32_t *__restrict__ rank_fb) {
   using S = SegCountSmem<K, RANK>;
   using O = SlotOps<K>;
   constexpr int ITEMS = S::ITEMS;
@@ -501,24 +628,40 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
   const uint64_t s = sm.bound[0];
   const uint32_t cnt = (uint32_t)(sm.bound[1] - s);
   const K base = sm.base;
-  // count: each key into its slot, LOAD keys per thread at a time
+  // count: each key into its slot, LOAD keys per thread at a time; with
+  // rank_groups, each slot also gets its key's group ordinal (the number of
+  // group starts up to the key, less one; every copy writes the same value)
+  uint32_t groups = 0;
   for (uint32_t j0 = 0; j0 < cnt; j0 += S::LOAD * SEG_BLOCK) {
     K d[S::LOAD];
+    bool hd[S::LOAD];
+    uint32_t hr[S::LOAD];
 #pragma unroll
     for (int i = 0; i < S::LOAD; i++) {
       const uint32_t j = j0 + (uint32_t)i * SEG_BLOCK + tid;
-      d[i] = j < cnt ? KeyOps<K>::sub(kin[s + j], base) : O::empty();
+      hd[i] = false;
+      if (j < cnt) {
+        const K x = kin[s + j];
+        d[i] = KeyOps<K>::sub(x, base);
+        if (rank_groups)
+          hd[i] = j == 0 || !KeyOps<K>::eq(KeyOps<K>::shr(x, low_bits), KeyOps<K>::shr(kin[s + j - 1], low_bits));
+      } else {
+        d[i] = O::empty();
+      }
     }
-    if (*reinterpret_cast<volatile uint32_t *>(&sm.overflow)) break;
+    uint32_t ng = 0;
+    if (rank_groups) ng = tile_flag_ranks<SEG_BLOCK, S::LOAD>(hd, hr, sm.cnt);  // synchronises
+    const bool stop = *reinterpret_cast<volatile uint32_t *>(&sm.overflow) != 0;
 #pragma unroll
     for (int i = 0; i < S::LOAD; i++) {
-      if (KeyOps<K>::eq(d[i], O::empty())) continue;
+      if (stop || KeyOps<K>::eq(d[i], O::empty())) continue;
       uint32_t h = O::hash(d[i]) >> (32 - S::TBITS);
       bool done = false;
       for (uint32_t probe = 0; probe < S::PROBES; probe++) {
         const K cur = O::claim(&sm.keys[h], d[i]);
         if (KeyOps<K>::eq(cur, O::empty()) || KeyOps<K>::eq(cur, d[i])) {
           atomicAdd(&sm.vals[h], 1u);
+          if (rank_groups) sm.sord[h] = (uint16_t)(groups + hr[i] + (hd[i] ? 1u : 0u) - 1u);
           done = true;
           break;
         }
@@ -526,8 +669,9 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
       }
       if (!done) sm.overflow = 1;
     }
+    groups += ng;
+    __syncthreads();  // sm.cnt is reused by the next batch
   }
-  __syncthreads();
   if (sm.overflow) {
     if (tid == 0) over_list[atomicAdd(over_count, 1u)] = tile;
     return;
@@ -539,12 +683,14 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
   {
     K pk[ITEMS];
     uint32_t pc[ITEMS], pr[ITEMS];
+    uint16_t po[ITEMS];
     bool occ[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
       const uint32_t j = (uint32_t)i * SEG_BLOCK + tid;
       pk[i] = sm.keys[j];
       pc[i] = sm.vals[j];
+      po[i] = sm.sord[j];
       occ[i] = !KeyOps<K>::eq(pk[i], O::empty());
     }
     D = tile_flag_ranks<SEG_BLOCK, ITEMS>(occ, pr, sm.cnt);
@@ -553,12 +699,57 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
       if (occ[i]) {
         sm.keys[pr[i]] = pk[i];
         sm.vals[pr[i]] = pc[i];
+        sm.sord[pr[i]] = po[i];
       }
     }
   }
   __syncthreads();
+  bool ranked = false;
+  if (rank_groups && D > 0) {
+    // bucket the distinct keys by group: counts, exclusive scan (ITEMS
+    // consecutive groups per thread), then placement
+    for (uint32_t o = tid; o < groups; o += SEG_BLOCK) sm.gst[o] = 0;
+    if (tid == 0) sm.maxg = 0;
+    __syncthreads();
+    for (uint32_t r = tid; r < D; r += SEG_BLOCK) atomicAdd(&sm.gst[sm.sord[r]], 1u);
+    __syncthreads();
+    uint32_t gv[ITEMS], sum = 0, mx = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const uint32_t o = (uint32_t)tid * ITEMS + i;
+      gv[i] = o < groups ? sm.gst[o] : 0u;
+      sum += gv[i];
+      mx = max(mx, gv[i]);
+    }
+    uint32_t run = block_excl_scan_256(sum, sm.tmp);
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+      const uint32_t o = (uint32_t)tid * ITEMS + i;
+      if (o < groups) sm.gst[o] = run;
+      run += gv[i];
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0 && mx) atomicMax(&sm.maxg, mx);
+    __syncthreads();
+    if (sm.maxg <= COUNT_GROUP_MAX) {
+      for (uint32_t r = tid; r < D; r += SEG_BLOCK) sm.perm[atomicAdd(&sm.gst[sm.sord[r]], 1u)] = (uint16_t)r;
+      __syncthreads();
+      // group o now spans [gst[o - 1], gst[o]) (from 0 for o = 0)
+      for (uint32_t q = tid; q < D; q += SEG_BLOCK) {
+        const uint32_t r = sm.perm[q], o = sm.sord[r];
+        const uint32_t a = o ? sm.gst[o - 1] : 0u, b = sm.gst[o];
+        const K x = sm.keys[r];
+        uint32_t below = 0;
+        for (uint32_t t = a; t < b; t++) below += KeyOps<K>::less(sm.keys[sm.perm[t]], x) ? 1u : 0u;
+        ustage[s + a + below] = KeyOps<K>::add(x, base);
+        mstage[s + a + below] = sm.vals[r];
+      }
+      ranked = true;
+    }
+  }
+  if (rank_groups && !ranked && D > 0 && tid == 0) atomicAdd(rank_fb, 1u);
   // sort the D distinct keys (with their counts) by their offset bits
-  if (D > 0) {
+  if (!ranked && D > 0) {
     const int passes = (int)sm.passes;
     const int ipw = (int)((D + SEG_BLOCK - 1) / SEG_BLOCK);
     const uint32_t wofs = (uint32_t)warp * 32u * ipw;

@@ -109,6 +109,8 @@ _SIGNATURES = [
     ("dbg_sort_count_first_set", ctypes.c_int, [_P, ctypes.c_int]),
     ("dbg_sort_count_overflows", ctypes.c_uint64, [_P]),
     ("dbg_sort_partition_first_set", ctypes.c_int, [_P, ctypes.c_int]),
+    ("dbg_sort_local_rank_set", ctypes.c_int, [_P, ctypes.c_int]),
+    ("dbg_sort_rank_fallbacks", ctypes.c_uint64, [_P]),
     ("dbg_sort_fallbacks", ctypes.c_uint64, [_P]),
     ("dbg_autotune", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_char_p, _P]),
 ]
@@ -566,6 +568,14 @@ def dbg_sort_count_overflows(ctx: Context) -> int:
 
 def dbg_sort_partition_first_set(ctx: Context, on: bool) -> None:
     _check(_lib.dbg_sort_partition_first_set(ctx.handle, 1 if on else 0), "dbg_sort_partition_first_set")
+
+
+def dbg_sort_local_rank_set(ctx: Context, on: bool) -> None:
+    _check(_lib.dbg_sort_local_rank_set(ctx.handle, 1 if on else 0), "dbg_sort_local_rank_set")
+
+
+def dbg_sort_rank_fallbacks(ctx: Context) -> int:
+    return int(_lib.dbg_sort_rank_fallbacks(ctx.handle))
 
 
 def dbg_sort_fallbacks(ctx: Context) -> int:

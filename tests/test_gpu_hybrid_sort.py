@@ -152,8 +152,9 @@ def test_partition_first_equals_stable_first_pass(dbg, k, hybrid):
 @pytest.mark.parametrize("k,n_reads,L", [(21, 30_000, 100), (31, 40_000, 100), (55, 12_000, 150)])
 def test_local_sort_variants_identical(dbg, k, n_reads, L):
     """Every local ranking method, in the 256-thread and the wide (384-
-    thread) form of the node records' local sort, gives the same graph, and
-    the oracle's; a group longer than a tile is in the input too."""
+    thread) form of the node records' local sort (the digit passes: ranking
+    within groups switched off), gives the same graph, and the oracle's; a
+    group longer than a tile is in the input too."""
     reads, lengths = readgen.generate(readgen.ReadSetSpec(200_000, n_reads, L, 0.01, k, 600 + k))
     rep = "ACGTTGCA" * 40
     reads = np.concatenate([reads, np.frombuffer((rep[:k + 3] * 7_000).encode(), dtype=np.uint8)])
@@ -162,6 +163,7 @@ def test_local_sort_variants_identical(dbg, k, n_reads, L):
     ref = None
     for v in range(dbg.dbg_sort_variant_count(kind)):
         ctx = dbg.Context()
+        dbg.dbg_sort_local_rank_set(ctx, False)
         dbg.dbg_sort_variant_set(ctx, kind, v)
         _, got = gpu_graph(dbg, ctx, reads, lengths, k)
         if ref is None:
