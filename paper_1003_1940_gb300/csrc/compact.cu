@@ -79,14 +79,52 @@ __global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_
   }
 }
 
+// A meeting walk's word per strand-node: its successor and the base that
+// arc appends, or "tail", or a mark (the head of the walker that took the
+// node on the other strand).  32-bit words for up to 2^29 - 1 strand-nodes
+// (successor in bits 0-28, all ones for a tail; base in bits 29-30; mark in
+// bit 31), 64-bit words above (successor and base as in succ_base, a mark
+// as 2^62 | head).
+template <class W>
+struct WalkWord;
+template <>
+struct WalkWord<uint32_t> {
+  static constexpr uint64_t MAX_N = (1ull << 29) - 1;
+  __host__ __device__ static uint32_t make(uint32_t next, uint32_t base) {
+    return next == NONE32 ? 0x1fffffffu : ((base & 3u) << 29) | next;
+  }
+  __device__ static bool marked(uint32_t w) { return (w >> 31) != 0; }
+  __device__ static uint32_t mark(uint32_t head) { return 0x80000000u | head; }
+  __device__ static uint32_t head(uint32_t w) { return w & 0x7fffffffu; }
+  __device__ static bool tail(uint32_t w) { return (w & 0x1fffffffu) == 0x1fffffffu; }
+  __device__ static uint32_t next(uint32_t w) { return w & 0x1fffffffu; }
+  __device__ static uint32_t base(uint32_t w) { return (w >> 29) & 3u; }
+};
+template <>
+struct WalkWord<uint64_t> {
+  static constexpr uint64_t MAX_N = 1ull << 30;  // a staged entry holds the strand-node in 30 bits
+  __host__ __device__ static uint64_t make(uint32_t next, uint32_t base) {
+    return next == NONE32 ? ~0ull : ((uint64_t)(base & 3u) << 32) | next;
+  }
+  __device__ static bool marked(uint64_t w) { return (w >> 62) == 1ull; }
+  __device__ static uint64_t mark(uint32_t head) { return (1ull << 62) | head; }
+  __device__ static uint32_t head(uint64_t w) { return (uint32_t)w; }
+  __device__ static bool tail(uint64_t w) { return w == ~0ull; }
+  __device__ static uint32_t next(uint64_t w) { return (uint32_t)w; }
+  __device__ static uint32_t base(uint64_t w) { return (uint32_t)(w >> 32) & 3u; }
+};
+
 // ListRankingTransform arcs.  Strand-node x = 2v + s leaves v by its right
 // side (s = 0) or its left side (s = 1); the arc exists when the edge there
 // joins two distinct nodes and is alone on the far node's side too.  It
 // enters w on side sw: strand 0 when that is w's left side, 1 otherwise.
 // succ_base[x] = succ[x] | (the base appended on that arc) << 32, or all
-// ones, for the walks that write the unitigs' strings.
+// ones, for the walks that write the unitigs' strings; mk, when given,
+// receives the same successor and base as a walk word (the meeting walks'
+// working copy, which they mark).
+template <class W>
 __global__ void k_successors(const uint32_t *__restrict__ link_node, const uint64_t *__restrict__ link_edge,
-                             uint64_t V, uint32_t *__restrict__ succ, uint64_t *__restrict__ succ_base) {
+                             uint64_t V, uint64_t *__restrict__ succ_base, W *__restrict__ mk) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * V; x += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t v = x >> 1;
     const uint32_t leave = (x & 1) ? 0u : 1u;
@@ -98,8 +136,8 @@ __global__ void k_successors(const uint32_t *__restrict__ link_node, const uint6
       far = link_edge[2 * (uint64_t)w + sw];
       if (w != (uint32_t)v && (uint32_t)far == (uint32_t)link_edge[2 * v + leave]) out = 2 * w + (sw == 0 ? 0u : 1u);
     }
-    succ[x] = out;
     succ_base[x] = out == NONE32 ? ~0ull : ((far >> 32) << 32) | out;
+    if (mk) mk[x] = WalkWord<W>::make(out, (uint32_t)(far >> 32));
   }
 }
 
@@ -296,9 +334,12 @@ __global__ void k_unitig_write(const uint32_t *__restrict__ head, const uint32_t
 
 // ---------------------------------------------------------------------------
 // Fast path, for graphs whose lists are all at most `cap` strand-nodes long
-// and acyclic (the usual case): one walk per list head measures the list
-// and picks the copy to keep; a second walk writes each kept unitig's nodes
-// and bases in order.  No per-strand-node ranking state is written.
+// and acyclic (the usual case): the two walkers of each unitig (its two list
+// heads, one per mirrored copy) walk towards each other, meet half way, and
+// stage the strand-nodes they take in walk order; per pair of walkers the
+// unitig's length and kept copy follow, and one copy pass writes each kept
+// unitig's nodes and bases from the two staged halves.  Every strand-node's
+// successor word is loaded once; no per-strand-node ranking state is written.
 // ---------------------------------------------------------------------------
 template <class K>
 __device__ __forceinline__ K strand_kmer(const uint64_t *node_keys, uint32_t x, int k) {
@@ -327,82 +368,76 @@ __device__ __forceinline__ uint32_t queue_heads(uint64_t base, uint64_t n, uint3
   return cnt;
 }
 
-template <class K>
-__global__ __launch_bounds__(WALK_BLOCK) void k_fast_measure(const uint32_t *__restrict__ succ, uint64_t n,
-                                                             const uint64_t *__restrict__ node_keys, int k,
-                                                             uint32_t cap, uint32_t *__restrict__ is_head,
-                                                             uint32_t *__restrict__ len_at_head,
-                                                             uint8_t *__restrict__ hstrand, uint32_t *covered,
-                                                             uint32_t *too_long) {
-  __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
-  __shared__ uint32_t s_next[WALK_WARPS];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint64_t chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
-  uint32_t cov = 0, lng = 0;
-  for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
-    const uint32_t cnt = queue_heads(c * WALK_CHUNK, n, s_q[w], [&](uint64_t x) { return succ[x ^ 1] == NONE32; });
-    if (lane == 0) s_next[w] = 0;
-    __syncwarp();
-    uint32_t head = NONE32, y = 0, L = 0;
-    for (;;) {
-      if (head == NONE32) {
-        const uint32_t qi = atomicAdd(&s_next[w], 1u);
-        if (qi >= cnt) break;
-        head = s_q[w][qi];
-        y = head;
-        L = 1;
-      }
-      const uint32_t ny = succ[y];
-      if (ny != NONE32 && L < cap) {
-        y = ny;
-        L++;
-        continue;
-      }
-      if (ny != NONE32) {
-        lng++;
-      } else if (KeyOps<K>::less(strand_kmer<K>(node_keys, head, k), strand_kmer<K>(node_keys, y ^ 1u, k))) {
-        // the mirror copy starts at the tail on the other strand; the copy
-        // whose first k-mer is smaller spells the smaller string
-        const uint32_t v = head >> 1;
-        is_head[v] = 1;
-        len_at_head[v] = L;
-        hstrand[v] = (uint8_t)(head & 1u);
-        cov += 2 * L;
-      }
-      head = NONE32;
+// The meeting walks.  A walker at strand-node y loads y's word from mk, the
+// working copy of the successor words; if the other walker has marked it
+// (with the other walker's head) the node is the other's and the walk
+// stops; else the walker marks the word the other walker would load at
+// this node, mk[y ^ 1], takes y and goes on.  Plain loads and stores: two
+// walkers arriving together may both take a few nodes, which the pairing
+// step measures.  hrec[x] = (nodes walker x took, its last strand-node, the
+// other walker's head, the index of its first staged entry).
+//
+// Staging: each lane stages the strand-nodes its walks take, in walk order,
+// as entries (y << 2) | the base the arc into y appends (0 for a head), at
+// consecutive indices of lane-private pages of STAGE_PAGE entries taken
+// from a global cursor; page_next[page] is the page the lane went on to.
+// The entries pass through eight registers and are stored eight at a time,
+// one whole 32-byte sector per store pair (entries stored one by one left
+// sectors half written in L2 under the walks' random traffic).  If the
+// staging area runs out, *overflow is set and the walks only measure.
+constexpr uint32_t STAGE_PAGE = 256;
+
+struct StageLane {
+  uint32_t b[8];
+  uint32_t nb = 0;         // entries held in b
+  uint64_t idx = 0, end = 0;  // the next entry's index; the current page's end
+  bool full = false;
+};
+
+// The entry at lane.idx; a fresh page when the current one is used up.
+__device__ __forceinline__ void stage_push(StageLane &ln, uint32_t e, uint32_t *__restrict__ stage,
+                                           uint32_t *__restrict__ page_next, unsigned long long *cursor,
+                                           uint64_t stage_cap, uint32_t *overflow) {
+  if (ln.full) return;
+  if (ln.idx == ln.end) {  // (the buffer is empty here: pages hold whole groups of eight)
+    const uint64_t np = atomicAdd(cursor, (unsigned long long)STAGE_PAGE);
+    if (np + STAGE_PAGE > stage_cap) {
+      ln.full = true;
+      atomicOr(overflow, 1u);
+      return;
     }
-    __syncwarp();
+    if (ln.end) page_next[ln.end / STAGE_PAGE - 1] = (uint32_t)(np / STAGE_PAGE);
+    ln.idx = np;
+    ln.end = np + STAGE_PAGE;
   }
-  cov = __reduce_add_sync(0xffffffffu, cov);
-  lng = __reduce_add_sync(0xffffffffu, lng);
-  if (lane == 0) {
-    if (cov) atomicAdd(covered, cov);
-    if (lng) atomicAdd(too_long, lng);
+#pragma unroll
+  for (int j = 0; j < 8; j++)
+    if (ln.nb == (uint32_t)j) ln.b[j] = e;
+  ln.nb++;
+  ln.idx++;
+  if (ln.nb == 8) {
+    uint4 *dst = reinterpret_cast<uint4 *>(stage + (ln.idx - 8));
+    dst[0] = make_uint4(ln.b[0], ln.b[1], ln.b[2], ln.b[3]);
+    dst[1] = make_uint4(ln.b[4], ln.b[5], ln.b[6], ln.b[7]);
+    ln.nb = 0;
   }
 }
 
-// Measuring with half the walking: both walkers of a unitig (its two list
-// heads, one per mirrored copy) walk towards each other and stop where they
-// meet.  A walker at strand-node y loads its successor word succ[y]; if the
-// other walker has marked it (bit 31, with the other walker's head in the
-// low bits) the node is the other's and the walk stops; else the walker
-// marks the word the other walker would load at this node, succ[y ^ 1], and
-// goes on.  Plain loads and stores: two walkers arriving together may both
-// take a few nodes, which the pairing step measures.  hrec[x] = (nodes
-// walker x took, its last strand-node, the other walker's head).  The
-// successor words are spoiled for anything but this walk (the list heads are
-// read from succ_base, which stays intact).
-constexpr uint32_t MARK = 0x80000000u;
-
-__global__ __launch_bounds__(WALK_BLOCK) void k_mark_measure(uint32_t *__restrict__ succ,
-                                                             const uint64_t *__restrict__ succ_base, uint64_t n,
-                                                             uint32_t cap, uint4 *__restrict__ hrec,
-                                                             uint32_t *too_long) {
+template <class W>
+__global__ __launch_bounds__(WALK_BLOCK) void k_mark_stage(W *__restrict__ mk,
+                                                           const uint64_t *__restrict__ succ_base, uint64_t n,
+                                                           uint32_t cap, uint4 *__restrict__ hrec,
+                                                           uint32_t *__restrict__ stage,
+                                                           uint32_t *__restrict__ page_next,
+                                                           unsigned long long *__restrict__ cursor,
+                                                           uint64_t stage_cap, uint32_t *too_long,
+                                                           uint32_t *overflow) {
   __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
   __shared__ uint32_t s_next[WALK_WARPS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
   uint32_t lng = 0;
+  StageLane ln;
   for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
     const uint32_t cnt =
         queue_heads(c * WALK_CHUNK, n, s_q[w], [&](uint64_t x) { return succ_base[x ^ 1] == ~0ull; });
@@ -412,17 +447,19 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_mark_measure(uint32_t *__restric
       const uint32_t qi = atomicAdd(&s_next[w], 1u);
       if (qi >= cnt) break;
       const uint32_t x = s_q[w][qi];
-      uint32_t y = x, d = 0, last = NONE32, partner = NONE32;
+      uint32_t y = x, d = 0, last = NONE32, partner = NONE32, first = NONE32, base = 0;
       for (;;) {
-        const uint32_t nx = __ldcg(succ + y);  // from L2: another SM's mark may be there
-        if (nx != NONE32 && (nx & MARK)) {
-          partner = nx & ~MARK;
+        const W wd = __ldcg(mk + y);  // from L2: another SM's mark may be there
+        if (WalkWord<W>::marked(wd)) {
+          partner = WalkWord<W>::head(wd);
           break;
         }
-        __stcg(succ + (y ^ 1u), MARK | x);
+        __stcg(mk + (y ^ 1u), WalkWord<W>::mark(x));
+        stage_push(ln, (y << 2) | base, stage, page_next, cursor, stage_cap, overflow);
+        if (first == NONE32 && !ln.full) first = (uint32_t)(ln.idx - 1);
         d++;
         last = y;
-        if (nx == NONE32) {
+        if (WalkWord<W>::tail(wd)) {
           partner = y ^ 1u;
           break;
         }
@@ -430,12 +467,22 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_mark_measure(uint32_t *__restric
           lng++;
           break;
         }
-        y = nx;
+        base = WalkWord<W>::base(wd);
+        y = WalkWord<W>::next(wd);
       }
-      hrec[x] = make_uint4(d, last, partner, 0u);
+      hrec[x] = make_uint4(d, last, partner, first);
     }
     __syncwarp();
   }
+  // the last, partly filled group
+  if (!ln.full)
+    for (uint32_t j = 0; j < ln.nb; j++) {
+      uint32_t v = ln.b[0];
+#pragma unroll
+      for (int t = 1; t < 8; t++)
+        if (j == (uint32_t)t) v = ln.b[t];
+      stage[ln.idx - ln.nb + j] = v;
+    }
   lng = __reduce_add_sync(0xffffffffu, lng);
   if (lane == 0 && lng) atomicAdd(too_long, lng);
 }
@@ -444,7 +491,8 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_mark_measure(uint32_t *__restric
 // L = d_a + d_b - o, o the nodes both took (found by stepping from the
 // second walker's last node, read on the first walker's strands, to the
 // first walker's last node); the copy kept (the one whose first k-mer is
-// smaller) and its first node's tables, as k_fast_measure writes them.
+// smaller) and its first node's tables: is_head, the unitig's length, the
+// kept copy's strand.
 template <class K>
 __global__ void k_mark_pair(const uint64_t *__restrict__ succ_base, uint64_t n, const uint4 *__restrict__ hrec,
                             const uint64_t *__restrict__ node_keys, int k, uint32_t cap,
@@ -492,7 +540,8 @@ __global__ void k_mark_pair(const uint64_t *__restrict__ succ_base, uint64_t n, 
   if ((threadIdx.x & 31) == 0 && cov) atomicAdd(covered, cov);
 }
 
-// The successor words again, from succ_base (after a measuring walk spoiled them).
+// The 32-bit successor words (the general path's and the out-of-core
+// ranking's form), from succ_base.
 __global__ void k_restore_succ(const uint64_t *__restrict__ succ_base, uint64_t n, uint32_t *__restrict__ succ) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t b = succ_base[x];
@@ -500,71 +549,95 @@ __global__ void k_restore_succ(const uint64_t *__restrict__ succ_base, uint64_t 
   }
 }
 
-// The first node of every kept unitig: its tables, node entry and first
-// k-mer, and where its walk continues (walk[u] = succ_base of the first
-// strand-node: the second one and the base it appends, or all ones).
-template <class K>
-__global__ void k_fast_heads(const uint64_t *__restrict__ succ_base, const uint32_t *__restrict__ is_head,
-                             const uint8_t *__restrict__ hstrand, const uint64_t *__restrict__ uidx,
-                             const uint64_t *__restrict__ off_by_v, const uint64_t *__restrict__ node_keys,
-                             uint64_t V, uint64_t U, int k, uint64_t *__restrict__ nodes_out, char *__restrict__ seq,
-                             uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
-                             uint8_t *__restrict__ circular, uint64_t *__restrict__ walk) {
-  const char *acgt = "ACGT";
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= V; v += (uint64_t)gridDim.x * blockDim.x) {
-    if (v == V) {
-      node_off[U] = V;
-      seq_off[U] = V + U * (uint64_t)(k - 1);
-      continue;
-    }
-    if (!is_head[v]) continue;
-    const uint64_t u = uidx[v], off = off_by_v[v], so = off + u * (uint64_t)(k - 1);
-    const uint32_t y = 2 * (uint32_t)v + hstrand[v];
-    node_off[u] = off;
-    seq_off[u] = so;
-    circular[u] = 0;
-    nodes_out[off] = y;  // (node ID << 1) | strand
-    const K km = strand_kmer<K>(node_keys, y, k);
-    for (int j = 0; j < k; j++) seq[so + j] = acgt[KeyOps<K>::digit(km, 2 * (k - 1 - j), 2)];
-    walk[u] = succ_base[y];
+// The index s entries after index q of the same walk (following the lanes'
+// page links).
+__device__ __forceinline__ uint64_t stage_advance(const uint32_t *__restrict__ page_next, uint64_t q, uint32_t s) {
+  while (s > 0) {
+    const uint32_t room = STAGE_PAGE - (uint32_t)(q % STAGE_PAGE);
+    if (s < room) return q + s;
+    s -= room;
+    q = (uint64_t)page_next[q / STAGE_PAGE] * STAGE_PAGE;
   }
+  return q;
 }
 
-// The rest of every kept unitig: lanes take unitigs in turn (per-warp
-// chunks, a shared-memory counter) and walk them, writing each node's entry
-// and the base its arc appends; only the successor words are loaded at random.
-__global__ __launch_bounds__(WALK_BLOCK) void k_fast_walk(const uint64_t *__restrict__ succ_base,
-                                                          const uint64_t *__restrict__ walk,
-                                                          const uint64_t *__restrict__ node_off,
-                                                          const uint64_t *__restrict__ seq_off, uint64_t U, int k,
-                                                          uint64_t *__restrict__ nodes_out, char *__restrict__ seq) {
+// 'A', 'C', 'G', 'T' for 2-bit codes 0..3
+__device__ __forceinline__ char base_char(uint32_t b) { return (char)((0x54474341u >> (8 * (b & 3u))) & 0xffu); }
+
+// Every kept unitig from its two staged halves.  With the kept walker's
+// head y (the unitig's first strand-node), a nodes taken by it and L in
+// all, the first a nodes are its entries in order; the other L - a are the
+// first L - a entries of the other walker, read backwards on the other
+// strand.  The string S (k + L - 1 bases) starts with y's k-mer, then the
+// bases the kept walker's arcs appended; the rest is the reverse complement
+// of the first L - a characters of the other walker's string T (its head's
+// k-mer, then its arcs' bases): S[k - 2 + L - m] is the complement of T[m].
+// Groups of CG lanes take the unitigs of their warp's chunk of nodes in
+// turn, and each group writes a unitig's nodes and bases CG at a time, so
+// that every store of the group covers consecutive addresses.
+constexpr int CG = 8;
+
+template <class K>
+__global__ __launch_bounds__(WALK_BLOCK) void k_stage_copy(
+    const uint32_t *__restrict__ is_head, const uint8_t *__restrict__ hstrand, const uint32_t *__restrict__ ulen,
+    const uint64_t *__restrict__ uidx, const uint64_t *__restrict__ off_by_v, const uint4 *__restrict__ hrec,
+    const uint32_t *__restrict__ stage, const uint32_t *__restrict__ page_next,
+    const uint64_t *__restrict__ node_keys, uint64_t V, uint64_t U, int k, uint64_t *__restrict__ nodes_out,
+    char *__restrict__ seq, uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
+    uint8_t *__restrict__ circular) {
+  __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
   __shared__ uint32_t s_next[WALK_WARPS];
-  const char *acgt = "ACGT";
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint64_t chunks = (U + WALK_CHUNK - 1) / WALK_CHUNK;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, gl = lane % CG;
+  const unsigned gmask = ((1u << CG) - 1u) << (lane - gl);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    node_off[U] = V;
+    seq_off[U] = V + U * (uint64_t)(k - 1);
+  }
+  const uint64_t chunks = (V + WALK_CHUNK - 1) / WALK_CHUNK;
   for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
-    const uint64_t u0 = c * WALK_CHUNK;
-    const uint32_t cnt = (uint32_t)min((uint64_t)WALK_CHUNK, U - u0);
+    const uint32_t cnt = queue_heads(c * WALK_CHUNK, V, s_q[w], [&](uint64_t v) { return is_head[v] != 0; });
     if (lane == 0) s_next[w] = 0;
     __syncwarp();
-    bool busy = false;
-    uint64_t nb = 0, pos = 0, spos = 0;
     for (;;) {
-      if (!busy) {
-        const uint32_t qi = atomicAdd(&s_next[w], 1u);
-        if (qi >= cnt) break;
-        const uint64_t u = u0 + qi;
-        nb = walk[u];
-        if (nb == ~0ull) continue;  // a single node
-        pos = node_off[u] + 1;
-        spos = seq_off[u] + k;
-        busy = true;
+      uint32_t qi = 0;
+      if (gl == 0) qi = atomicAdd(&s_next[w], 1u);
+      qi = __shfl_sync(gmask, qi, 0, CG);
+      if (qi >= cnt) break;
+      const uint32_t v = s_q[w][qi];
+      const uint32_t y = 2 * v + hstrand[v];
+      const uint4 ra = hrec[y];
+      const uint32_t L = ulen[v], a = ra.x, bp = L - a;
+      const uint64_t u = uidx[v], off = off_by_v[v], so = off + u * (uint64_t)(k - 1);
+      if (gl == 0) {
+        node_off[u] = off;
+        seq_off[u] = so;
+        circular[u] = 0;
       }
-      const uint32_t y = (uint32_t)nb;
-      nodes_out[pos++] = y;
-      seq[spos++] = acgt[nb >> 32];
-      nb = succ_base[y];
-      busy = nb != ~0ull;
+      const K km = strand_kmer<K>(node_keys, y, k);
+      for (int j = gl; j < k; j += CG) seq[so + j] = base_char(KeyOps<K>::digit(km, 2 * (k - 1 - j), 2));
+      // (a lane follows a walk's entries only while it has one to read: a
+      // walk that took no node has no first entry)
+      uint64_t q = (uint32_t)gl < a ? stage_advance(page_next, ra.w, (uint32_t)gl) : 0;
+      for (uint32_t e = gl; e < a; e += CG) {
+        const uint32_t t = stage[q];
+        nodes_out[off + e] = t >> 2;
+        if (e > 0) seq[so + k - 1 + e] = base_char(t);
+        if (e + CG < a) q = stage_advance(page_next, q, CG);
+      }
+      if (bp > 0) {
+        const uint32_t zb = ra.z;
+        const K kb = strand_kmer<K>(node_keys, zb, k);
+        const uint32_t mk_end = min((uint32_t)k, bp);
+        for (uint32_t m = gl; m < mk_end; m += CG)
+          seq[so + k - 2 + L - m] = base_char(3u - KeyOps<K>::digit(kb, 2 * (k - 1 - (int)m), 2));
+        q = (uint32_t)gl < bp ? stage_advance(page_next, hrec[zb].w, (uint32_t)gl) : 0;
+        for (uint32_t e = gl; e < bp; e += CG) {
+          const uint32_t t = stage[q];
+          nodes_out[off + L - 1 - e] = (t >> 2) ^ 1u;
+          if (e >= 1 && e + (uint32_t)k - 1 < bp) seq[so + L - 1 - e] = base_char(3u - t);
+          if (e + CG < bp) q = stage_advance(page_next, q, CG);
+        }
+      }
     }
     __syncwarp();
   }
@@ -710,43 +783,70 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
   DevBuf link_node, link_edge, succ, word, active, cycl, lab, cyc;
   bool have_cycles = false;
   if (V > 0) {
+    // the meeting walks' words: 32-bit up to 2^29 - 1 strand-nodes, 64-bit
+    // up to 2^30 (their staged entries hold a strand-node in 30 bits)
+    const bool w32 = n <= WalkWord<uint32_t>::MAX_N, fast = n <= WalkWord<uint64_t>::MAX_N;
+    DevBuf mk;
     DBG_TRY(alloc_buf(ctx, link_node, n1 * 4));
     DBG_TRY(alloc_buf(ctx, link_edge, n1 * 8));
-    DBG_TRY(alloc_buf(ctx, succ, n1 * 4));
     DBG_TRY(alloc_buf(ctx, word, n1 * 8));
+    if (fast) DBG_TRY(alloc_buf(ctx, mk, n1 * (w32 ? 4 : 8)));
     DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + (double)E2 * 10 + 8.0 * V * g->key_words + 12.0 * n,
                k_side_links<K><<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
                                                           g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
                                                           g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
                                                           literal, link_node.as<uint32_t>(), link_edge.as<uint64_t>()));
     // succ_base goes to the ranking words' buffer (free until the general path)
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n + 8.0 * n + 12.0 * n,
-               k_successors<<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(), V,
-                                                       succ.as<uint32_t>(), word.as<uint64_t>()));
+    if (w32)
+      DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n + 8.0 * n + 12.0 * n,
+                 k_successors<uint32_t><<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(),
+                                                                   V, word.as<uint64_t>(), mk.as<uint32_t>()));
+    else
+      DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n + 8.0 * n + (fast ? 16.0 : 8.0) * n,
+                 k_successors<uint64_t><<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(),
+                                                                   V, word.as<uint64_t>(),
+                                                                   fast ? mk.as<uint64_t>() : nullptr));
     link_node.release();
     link_edge.release();
     // ---- fast path: short acyclic lists only ----
-    {
-      DevBuf f_is_head, f_len, f_strand, f_uidx, f_off;
+    if (fast) {
+      DevBuf f_is_head, f_len, f_strand, f_uidx, f_off, hrec, stage, page_next;
       DBG_TRY(alloc_buf(ctx, f_is_head, V1 * 4));
       DBG_TRY(alloc_buf(ctx, f_len, V1 * 4));
       DBG_TRY(alloc_buf(ctx, f_strand, V1));
       DBG_CUDA_TRY(cudaMemsetAsync(f_is_head.p, 0, V1 * 4, s));
       DBG_CUDA_TRY(cudaMemsetAsync(f_len.p, 0, V1 * 4, s));
-      // the two walkers of each unitig meet half way (k_mark_measure), then
-      // each pair gives its unitig's length and kept copy (k_mark_pair)
-      DevBuf hrec;
+      // the two walkers of each unitig meet half way and stage what they
+      // take (k_mark_stage); each pair gives its unitig's length and kept
+      // copy (k_mark_pair).  Staging room: every node once (the few that
+      // both walkers of a pair take within the margin), plus two partly
+      // used pages per lane.
+      const unsigned wgrid = walk_grid(ctx, n);
+      const uint64_t lanes = (uint64_t)wgrid * WALK_BLOCK;
+      const uint64_t stage_cap = ((V + V / 4 + 2 * lanes * STAGE_PAGE) / STAGE_PAGE + 1) * STAGE_PAGE;
       DBG_TRY(alloc_buf(ctx, hrec, n1 * sizeof(uint4)));
-      DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 10, 0, 4 * sizeof(uint32_t), s));
-      DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 24.0 * V,
-                 k_mark_measure<<<walk_grid(ctx, n), WALK_BLOCK, 0, s>>>(succ.as<uint32_t>(), word.as<uint64_t>(),
-                                                                         n, kWalkCap, hrec.as<uint4>(),
-                                                                         ctx->d_counters + 11));
+      DBG_TRY(alloc_buf(ctx, stage, stage_cap * 4));
+      DBG_TRY(alloc_buf(ctx, page_next, stage_cap / STAGE_PAGE * 4));
+      // counters: 11 too_long, 12-13 covered, 14-15 page cursor, 16 overflow
+      DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 10, 0, 8 * sizeof(uint32_t), s));
+      unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ctx->d_counters + 14);
+      if (w32)
+        DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 16.0 * V + 4.0 * V,
+                   k_mark_stage<uint32_t><<<wgrid, WALK_BLOCK, 0, s>>>(
+                       mk.as<uint32_t>(), word.as<uint64_t>(), n, kWalkCap, hrec.as<uint4>(), stage.as<uint32_t>(),
+                       page_next.as<uint32_t>(), cursor, stage_cap, ctx->d_counters + 11, ctx->d_counters + 16));
+      else
+        DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 24.0 * V + 4.0 * V,
+                   k_mark_stage<uint64_t><<<wgrid, WALK_BLOCK, 0, s>>>(
+                       mk.as<uint64_t>(), word.as<uint64_t>(), n, kWalkCap, hrec.as<uint4>(), stage.as<uint32_t>(),
+                       page_next.as<uint32_t>(), cursor, stage_cap, ctx->d_counters + 11, ctx->d_counters + 16));
       DBG_CUDA_TRY(cudaGetLastError());
-      uint32_t too_long = 0;
-      DBG_TRY(read_small(ctx, ctx->d_counters + 11, sizeof(uint32_t), &too_long));
+      uint32_t flags[6] = {0, 0, 0, 0, 0, 0};  // counters 11..16
+      DBG_TRY(read_small(ctx, ctx->d_counters + 11, sizeof(flags), flags));
+      const uint32_t too_long = flags[0], overflow = flags[5];
+      mk.release();
       uint64_t covered = 0;
-      if (too_long == 0) {
+      if (too_long == 0 && overflow == 0) {
         DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 32.0 * V,
                    k_mark_pair<K><<<grid_of(n), 256, 0, s>>>(word.as<uint64_t>(), n, hrec.as<uint4>(),
                                                              g->node_keys.as<uint64_t>(), k, kWalkCap,
@@ -758,8 +858,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
         DBG_TRY(read_small(ctx, ctx->d_counters + 12, sizeof(uint64_t), &covered));
         DBG_TRY(check_device_error(ctx));
       }
-      hrec.release();
-      if (too_long == 0 && covered == V) {
+      if (too_long == 0 && overflow == 0 && covered == V) {
         DBG_TRY(alloc_buf(ctx, f_uidx, (V + 1) * 8));
         DBG_TRY(alloc_buf(ctx, f_off, (V + 1) * 8));
         uint32_t U32 = 0, total = 0;
@@ -777,26 +876,20 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
         DBG_TRY(alloc_buf(ctx, u->nodes, V1 * 8));
         u->total_bases = V + Uf * (uint64_t)(k - 1);
         DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
-        DevBuf walk;
-        DBG_TRY(alloc_buf(ctx, walk, std::max<uint64_t>(1, Uf) * 8));
-        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)V * (4 + 1) + (double)Uf * (16 + 8 + 8 * g->key_words + 8 + 25 + k),
-                   k_fast_heads<K><<<grid_of(V + 1), 256, 0, s>>>(
-                       word.as<uint64_t>(), f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_uidx.as<uint64_t>(),
-                       f_off.as<uint64_t>(), g->node_keys.as<uint64_t>(), V, Uf, k, u->nodes.as<uint64_t>(),
-                       u->seq.as<char>(), u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(),
-                       u->circular.as<uint8_t>(), walk.as<uint64_t>()));
-        if (Uf > 0)
-          DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, (double)(V - Uf) * (8 + 8 + 1) + (double)Uf * 24,
-                     k_fast_walk<<<walk_grid(ctx, Uf), WALK_BLOCK, 0, s>>>(
-                         word.as<uint64_t>(), walk.as<uint64_t>(), u->node_off.as<uint64_t>(),
-                         u->seq_off.as<uint64_t>(), Uf, k, u->nodes.as<uint64_t>(), u->seq.as<char>()));
+        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT,
+                   (double)V * (4 + 1 + 4 + 8 + 1) + (double)Uf * (16 + 32 + 8 * g->key_words * 2 + 16 + k),
+                   k_stage_copy<K><<<walk_grid(ctx, V), WALK_BLOCK, 0, s>>>(
+                       f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_len.as<uint32_t>(), f_uidx.as<uint64_t>(),
+                       f_off.as<uint64_t>(), hrec.as<uint4>(), stage.as<uint32_t>(), page_next.as<uint32_t>(),
+                       g->node_keys.as<uint64_t>(), V, Uf, k, u->nodes.as<uint64_t>(), u->seq.as<char>(),
+                       u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(), u->circular.as<uint8_t>()));
         DBG_CUDA_TRY(cudaGetLastError());
         DBG_CUDA_TRY(cudaStreamSynchronize(s));
         return check_device_error(ctx);
       }
     }
     // ---- general path: long lists or cycles present ----
-    // (the measuring walk marked the successor words: rebuild them)
+    DBG_TRY(alloc_buf(ctx, succ, n1 * 4));
     DBG_LAUNCH(ctx, ST_COMPACT_RANK, 12.0 * n,
                k_restore_succ<<<grid_of(n), 256, 0, s>>>(word.as<uint64_t>(), n, succ.as<uint32_t>()));
     DBG_CUDA_TRY(cudaMemsetAsync(word.p, 0xff, n * 8, s));
@@ -1022,9 +1115,11 @@ static dbg_status compact_bucketed_impl(dbg_ctx *ctx, const dbg_graph *g, uint64
                                                           g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
                                                           g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
                                                           false, link_node.as<uint32_t>(), link_edge.as<uint64_t>()));
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 32.0 * n,
-               k_successors<<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(), V,
-                                                       succ.as<uint32_t>(), word.as<uint64_t>()));
+    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 28.0 * n,
+               k_successors<uint64_t><<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(),
+                                                                 V, word.as<uint64_t>(), nullptr));
+    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n,
+               k_restore_succ<<<grid_of(n), 256, 0, s>>>(word.as<uint64_t>(), n, succ.as<uint32_t>()));
     DBG_CUDA_TRY(cudaGetLastError());
   }
   word.release();

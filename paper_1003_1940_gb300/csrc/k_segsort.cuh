@@ -45,7 +45,7 @@ struct SegSortSmem {
   uint32_t tmp[8];
   uint64_t bound[2];
   K base;
-  uint32_t tile, passes, excl, total;
+  uint32_t tile, passes, excl, total, spread_bits;
 };
 
 // bound[t] for t in [0, tiles]: the first index of the group holding
@@ -120,6 +120,7 @@ __device__ __forceinline__ void seg_setup(S &sm, const K *__restrict__ kin, cons
       const int spread_bits =
           KeyOps<K>::bitlen(KeyOps<K>::sub(KeyOps<K>::shr(last, low_bits), KeyOps<K>::shr(first, low_bits)));
       sm.passes = (uint32_t)((min(low_bits + spread_bits, key_bits) + RADIX_BITS - 1) / RADIX_BITS);
+      sm.spread_bits = (uint32_t)spread_bits;
     }
   }
   __syncthreads();
@@ -515,18 +516,24 @@ __global__ __launch_bounds__(SEG_BLOCK, 2) void k_seg_rle(
 // keys holds about n / c distinct ones, so k_seg_count counts the copies
 // first, in a shared-memory hash table of TBL slots (linear probing; a slot
 // is claimed by compare-and-swap and counted by atomic add), packs the
-// occupied slots to the front of the table in slot order, and radix-sorts
-// only the distinct keys with their counts as payload.  The output is that
-// of k_seg_rle: each distinct key once, in order, with its multiplicity
-// (STEP-2), staged in the tile's own range.  With rank_groups set, the
-// distinct keys are not radix-sorted but ranked: each slot also records the
-// ordinal of its key's group (keys of equal high bits, numbered in tile
-// order while the keys are counted), the distinct keys are bucketed by
-// group, and a key's place is its group's start plus the number of the
-// group's keys below it (a tile with a group of more than
-// COUNT_GROUP_MAX distinct keys takes the radix sort).  The table is small so that
-// several CTAs share an SM; a tile whose keys do not fit (a probe longer
-// than PROBES slots) is listed in over_list and sorted by k_seg_rle instead.
+// occupied slots to the front of the table in slot order, and then orders
+// only the distinct keys.  The output is that of k_seg_rle: each distinct
+// key once, in order, with its multiplicity (STEP-2), staged in the tile's
+// own range.  The table is small so that several CTAs share an SM; a tile
+// whose keys do not fit (a probe longer than PROBES slots) is listed in
+// over_list and sorted by k_seg_rle instead.
+//
+// Ordering the distinct keys.  With rank_groups set, the distinct keys are
+// bucketed by their high bits (from low_bits up) -- the tile's groups, in
+// order; where those bits span more than TBL values, by their top bits, so
+// that a bucket holds 2, 4, ... adjacent groups -- and each key goes to its
+// bucket's start plus the number of the bucket's keys below it; a tile
+// with a bucket of more than COUNT_GROUP_MAX distinct keys is radix-sorted
+// by the 8-bit passes instead (and counted in rank_fb).  (Packing a 64-bit
+// key's offset and its count into one slot word, counted by 64-bit shared
+// atomic adds, measured 1.9x slower: the hot slots of a 30x-covered key
+// serialise.)
+constexpr uint32_t COUNT_GROUP_MAX = 256;
 
 // Hash-table slots of the counting pass.  The empty mark is the all-ones
 // key, which no key offset reaches: an offset is key - base <= key, and the
@@ -572,8 +579,6 @@ struct SlotOps<Key128> {
   }
 };
 
-constexpr uint32_t COUNT_GROUP_MAX = 256;
-
 template <class K, int RANK>
 struct SegCountSmem {
   static constexpr int WARPS = SEG_BLOCK / 32;
@@ -585,18 +590,22 @@ struct SegCountSmem {
   static_assert((1 << TBITS) == TBL, "table size");
   K keys[TBL];         // hash slots; then the distinct keys, packed and sorted
   uint32_t vals[TBL];  // copies per slot; then per distinct key
-  uint16_t sord[TBL];  // group ordinal per slot; then per distinct key
   uint16_t perm[TBL];  // distinct keys bucketed by group
-  uint32_t gst[TBL + 1];
-  uint32_t maxg;
+  uint32_t gst[TBL];   // distinct keys per group, then where each group ends
   uint32_t whist[WARPS][RADIX];
   uint32_t match[RANK == RANK_ATOMIC ? WARPS : 1][RADIX + 1];
   uint32_t cnt[ITEMS * WARPS + 1];
   uint32_t tmp[8];
   uint64_t bound[2];
   K base;
-  uint32_t tile, passes, excl, total, overflow;
+  uint32_t tile, passes, excl, total, spread_bits, overflow, maxg;
 };
+
+// high bits of a key offset, as a group index within the tile
+template <class K>
+__device__ __forceinline__ uint32_t group_of(K d, int low_bits) {
+  return (uint32_t)KeyOps<K>::words_lo(KeyOps<K>::shr(d, low_bits));
+}
 
 template <class K, int RANK>
 __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
@@ -628,40 +637,27 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
   const uint64_t s = sm.bound[0];
   const uint32_t cnt = (uint32_t)(sm.bound[1] - s);
   const K base = sm.base;
-  // count: each key into its slot, LOAD keys per thread at a time; with
-  // rank_groups, each slot also gets its key's group ordinal (the number of
-  // group starts up to the key, less one; every copy writes the same value)
-  uint32_t groups = 0;
+  // the tile's path (uniform): ranked by buckets of groups
+  const bool by_groups = rank_groups && cnt > 0;
+  const int bshift = (int)sm.spread_bits > S::TBITS ? (int)sm.spread_bits - S::TBITS : 0;
+  // count: each key into its slot, LOAD keys per thread at a time
   for (uint32_t j0 = 0; j0 < cnt; j0 += S::LOAD * SEG_BLOCK) {
     K d[S::LOAD];
-    bool hd[S::LOAD];
-    uint32_t hr[S::LOAD];
 #pragma unroll
     for (int i = 0; i < S::LOAD; i++) {
       const uint32_t j = j0 + (uint32_t)i * SEG_BLOCK + tid;
-      hd[i] = false;
-      if (j < cnt) {
-        const K x = kin[s + j];
-        d[i] = KeyOps<K>::sub(x, base);
-        if (rank_groups)
-          hd[i] = j == 0 || !KeyOps<K>::eq(KeyOps<K>::shr(x, low_bits), KeyOps<K>::shr(kin[s + j - 1], low_bits));
-      } else {
-        d[i] = O::empty();
-      }
+      d[i] = j < cnt ? KeyOps<K>::sub(kin[s + j], base) : O::empty();
     }
-    uint32_t ng = 0;
-    if (rank_groups) ng = tile_flag_ranks<SEG_BLOCK, S::LOAD>(hd, hr, sm.cnt);  // synchronises
-    const bool stop = *reinterpret_cast<volatile uint32_t *>(&sm.overflow) != 0;
+    if (*reinterpret_cast<volatile uint32_t *>(&sm.overflow)) break;
 #pragma unroll
     for (int i = 0; i < S::LOAD; i++) {
-      if (stop || KeyOps<K>::eq(d[i], O::empty())) continue;
+      if (KeyOps<K>::eq(d[i], O::empty())) continue;
       uint32_t h = O::hash(d[i]) >> (32 - S::TBITS);
       bool done = false;
       for (uint32_t probe = 0; probe < S::PROBES; probe++) {
         const K cur = O::claim(&sm.keys[h], d[i]);
         if (KeyOps<K>::eq(cur, O::empty()) || KeyOps<K>::eq(cur, d[i])) {
           atomicAdd(&sm.vals[h], 1u);
-          if (rank_groups) sm.sord[h] = (uint16_t)(groups + hr[i] + (hd[i] ? 1u : 0u) - 1u);
           done = true;
           break;
         }
@@ -669,9 +665,8 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
       }
       if (!done) sm.overflow = 1;
     }
-    groups += ng;
-    __syncthreads();  // sm.cnt is reused by the next batch
   }
+  __syncthreads();
   if (sm.overflow) {
     if (tid == 0) over_list[atomicAdd(over_count, 1u)] = tile;
     return;
@@ -683,14 +678,12 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
   {
     K pk[ITEMS];
     uint32_t pc[ITEMS], pr[ITEMS];
-    uint16_t po[ITEMS];
     bool occ[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
       const uint32_t j = (uint32_t)i * SEG_BLOCK + tid;
       pk[i] = sm.keys[j];
       pc[i] = sm.vals[j];
-      po[i] = sm.sord[j];
       occ[i] = !KeyOps<K>::eq(pk[i], O::empty());
     }
     D = tile_flag_ranks<SEG_BLOCK, ITEMS>(occ, pr, sm.cnt);
@@ -699,44 +692,46 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
       if (occ[i]) {
         sm.keys[pr[i]] = pk[i];
         sm.vals[pr[i]] = pc[i];
-        sm.sord[pr[i]] = po[i];
       }
     }
   }
   __syncthreads();
+  const int gshift = low_bits + bshift;  // a key offset's bucket bits
   bool ranked = false;
-  if (rank_groups && D > 0) {
-    // bucket the distinct keys by group: counts, exclusive scan (ITEMS
-    // consecutive groups per thread), then placement
-    for (uint32_t o = tid; o < groups; o += SEG_BLOCK) sm.gst[o] = 0;
+  if (by_groups && D > 0) {
+    // bucket the distinct keys: counts, exclusive scan (ITEMS consecutive
+    // buckets per thread), then placement
+    const uint32_t G = 1u << ((int)sm.spread_bits - bshift);
+    for (uint32_t o = tid; o < G; o += SEG_BLOCK) sm.gst[o] = 0;
     if (tid == 0) sm.maxg = 0;
     __syncthreads();
-    for (uint32_t r = tid; r < D; r += SEG_BLOCK) atomicAdd(&sm.gst[sm.sord[r]], 1u);
+    for (uint32_t r = tid; r < D; r += SEG_BLOCK) atomicAdd(&sm.gst[group_of<K>(sm.keys[r], gshift)], 1u);
     __syncthreads();
-    uint32_t gv[ITEMS], sum = 0, mx = 0;
+    uint32_t gc[ITEMS], sum = 0, mx = 0;
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
       const uint32_t o = (uint32_t)tid * ITEMS + i;
-      gv[i] = o < groups ? sm.gst[o] : 0u;
-      sum += gv[i];
-      mx = max(mx, gv[i]);
+      gc[i] = o < G ? sm.gst[o] : 0u;
+      sum += gc[i];
+      mx = max(mx, gc[i]);
     }
     uint32_t run = block_excl_scan_256(sum, sm.tmp);
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
       const uint32_t o = (uint32_t)tid * ITEMS + i;
-      if (o < groups) sm.gst[o] = run;
-      run += gv[i];
+      if (o < G) sm.gst[o] = run;
+      run += gc[i];
     }
     mx = __reduce_max_sync(0xffffffffu, mx);
     if (lane == 0 && mx) atomicMax(&sm.maxg, mx);
     __syncthreads();
     if (sm.maxg <= COUNT_GROUP_MAX) {
-      for (uint32_t r = tid; r < D; r += SEG_BLOCK) sm.perm[atomicAdd(&sm.gst[sm.sord[r]], 1u)] = (uint16_t)r;
+      for (uint32_t r = tid; r < D; r += SEG_BLOCK)
+        sm.perm[atomicAdd(&sm.gst[group_of<K>(sm.keys[r], gshift)], 1u)] = (uint16_t)r;
       __syncthreads();
-      // group o now spans [gst[o - 1], gst[o]) (from 0 for o = 0)
+      // bucket o now spans [gst[o - 1], gst[o]) (from 0 for o = 0)
       for (uint32_t q = tid; q < D; q += SEG_BLOCK) {
-        const uint32_t r = sm.perm[q], o = sm.sord[r];
+        const uint32_t r = sm.perm[q], o = group_of<K>(sm.keys[r], gshift);
         const uint32_t a = o ? sm.gst[o - 1] : 0u, b = sm.gst[o];
         const K x = sm.keys[r];
         uint32_t below = 0;
@@ -747,9 +742,9 @@ __global__ __launch_bounds__(SEG_BLOCK, 4) void k_seg_count(
       ranked = true;
     }
   }
-  if (rank_groups && !ranked && D > 0 && tid == 0) atomicAdd(rank_fb, 1u);
-  // sort the D distinct keys (with their counts) by their offset bits
   if (!ranked && D > 0) {
+    if (rank_groups && tid == 0) atomicAdd(rank_fb, 1u);
+    // sort the D distinct keys (with their counts) by their offset bits
     const int passes = (int)sm.passes;
     const int ipw = (int)((D + SEG_BLOCK - 1) / SEG_BLOCK);
     const uint32_t wofs = (uint32_t)warp * 32u * ipw;
