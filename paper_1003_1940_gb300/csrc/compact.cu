@@ -79,19 +79,20 @@ __global__ void k_side_links(const uint64_t *__restrict__ row_ptr, const uint32_
   }
 }
 
-// A meeting walk's word per strand-node: its successor and the base that
-// arc appends, or "tail", or a mark (the head of the walker that took the
-// node on the other strand).  32-bit words for up to 2^29 - 1 strand-nodes
-// (successor in bits 0-28, all ones for a tail; base in bits 29-30; mark in
-// bit 31), 64-bit words above (successor and base as in succ_base, a mark
-// as 2^62 | head).
+// A meeting walk's word per strand-node: its successor (or "tail") and its
+// entry base -- the base a walk appends on arriving at it, the last base of
+// its k-mer on its strand -- or a mark (the head of the walker that took
+// the node on the other strand).  32-bit words for up to 2^29 - 1
+// strand-nodes (successor in bits 0-28, all ones for a tail; base in bits
+// 29-30; mark in bit 31), 64-bit words above (successor in the low word,
+// all ones for a tail; base in bits 32-33; a mark as 2^62 | head).
 template <class W>
 struct WalkWord;
 template <>
 struct WalkWord<uint32_t> {
   static constexpr uint64_t MAX_N = (1ull << 29) - 1;
   __host__ __device__ static uint32_t make(uint32_t next, uint32_t base) {
-    return next == NONE32 ? 0x1fffffffu : ((base & 3u) << 29) | next;
+    return ((base & 3u) << 29) | (next == NONE32 ? 0x1fffffffu : next);
   }
   __device__ static bool marked(uint32_t w) { return (w >> 31) != 0; }
   __device__ static uint32_t mark(uint32_t head) { return 0x80000000u | head; }
@@ -104,12 +105,12 @@ template <>
 struct WalkWord<uint64_t> {
   static constexpr uint64_t MAX_N = 1ull << 30;  // a staged entry holds the strand-node in 30 bits
   __host__ __device__ static uint64_t make(uint32_t next, uint32_t base) {
-    return next == NONE32 ? ~0ull : ((uint64_t)(base & 3u) << 32) | next;
+    return ((uint64_t)(base & 3u) << 32) | next;
   }
   __device__ static bool marked(uint64_t w) { return (w >> 62) == 1ull; }
   __device__ static uint64_t mark(uint32_t head) { return (1ull << 62) | head; }
   __device__ static uint32_t head(uint64_t w) { return (uint32_t)w; }
-  __device__ static bool tail(uint64_t w) { return w == ~0ull; }
+  __device__ static bool tail(uint64_t w) { return (uint32_t)w == NONE32; }
   __device__ static uint32_t next(uint64_t w) { return (uint32_t)w; }
   __device__ static uint32_t base(uint64_t w) { return (uint32_t)(w >> 32) & 3u; }
 };
@@ -118,13 +119,12 @@ struct WalkWord<uint64_t> {
 // side (s = 0) or its left side (s = 1); the arc exists when the edge there
 // joins two distinct nodes and is alone on the far node's side too.  It
 // enters w on side sw: strand 0 when that is w's left side, 1 otherwise.
-// succ_base[x] = succ[x] | (the base appended on that arc) << 32, or all
-// ones, for the walks that write the unitigs' strings; mk, when given,
-// receives the same successor and base as a walk word (the meeting walks'
-// working copy, which they mark).
+// succ[x] = the successor or NONE; mk, when given, receives x's walk word
+// (the meeting walks' working copy, which they mark), with x's entry base
+// (entering v by side s).
 template <class W>
 __global__ void k_successors(const uint32_t *__restrict__ link_node, const uint64_t *__restrict__ link_edge,
-                             uint64_t V, uint64_t *__restrict__ succ_base, W *__restrict__ mk) {
+                             uint64_t V, uint32_t *__restrict__ succ, W *__restrict__ mk) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * V; x += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t v = x >> 1;
     const uint32_t leave = (x & 1) ? 0u : 1u;
@@ -136,8 +136,76 @@ __global__ void k_successors(const uint32_t *__restrict__ link_node, const uint6
       far = link_edge[2 * (uint64_t)w + sw];
       if (w != (uint32_t)v && (uint32_t)far == (uint32_t)link_edge[2 * v + leave]) out = 2 * w + (sw == 0 ? 0u : 1u);
     }
-    succ_base[x] = out == NONE32 ? ~0ull : ((far >> 32) << 32) | out;
-    if (mk) mk[x] = WalkWord<W>::make(out, (uint32_t)(far >> 32));
+    succ[x] = out;
+    if (mk) mk[x] = WalkWord<W>::make(out, (uint32_t)(link_edge[2 * v + (x & 1)] >> 32));
+  }
+}
+
+// The same arcs, for up to 2^29 - 1 strand-nodes, through a bitmap small
+// enough for L2 instead of a random load of the far node's link.  Per node
+// v (warps on 32 consecutive nodes): the lone end of each side as in
+// k_side_links; bit 2v + sd of `lone` set when side sd holds exactly one
+// end (and, with `literal`, each side of v holds one); and for x = 2v + s
+// the candidate word (its would-be successor, entering the far node w by
+// the far end's side, unless that is v itself, with x's entry base).
+// Bit 2w + sw is the bit of that successor itself, so k_succ_lone keeps a
+// candidate when the bit of its successor is set.
+template <class K>
+__global__ void k_side_cand(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ adj_nbr,
+                            const uint32_t *__restrict__ adj_edge, const uint8_t *__restrict__ adj_role,
+                            const uint8_t *__restrict__ orient, const uint64_t *__restrict__ node_keys, uint64_t V,
+                            int k, bool literal, uint32_t *__restrict__ cand, uint32_t *__restrict__ lone) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g < V;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t v = g + lane;
+    uint32_t pair = 0;
+    if (v < V) {
+      uint32_t cnt[2] = {0, 0}, far[2] = {NONE32, NONE32};
+      const uint64_t p0 = row_ptr[v], p1 = row_ptr[v + 1];
+      for (uint64_t p = p0; p < p1; p++) {
+        const uint32_t e = adj_edge[p], role = adj_role[p];
+        const uint8_t o = orient[e];
+        const uint32_t sd = end_side(o, role);
+        cnt[sd]++;
+        far[sd] = (adj_nbr[p] << 1) | end_side(o, 1u - role);
+      }
+      const K kv = load_node_key<K>(node_keys, v);
+      const uint32_t entry[2] = {(uint32_t)KeyOps<K>::low2(kv), 3u - KeyOps<K>::digit(kv, 2 * (k - 1), 2)};
+      const bool ok = !literal || (cnt[0] == 1 && cnt[1] == 1);
+      const bool one[2] = {ok && cnt[0] == 1, ok && cnt[1] == 1};
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        const int leave = 1 - s;
+        uint32_t next = NONE32;
+        if (one[leave] && (far[leave] >> 1) != (uint32_t)v) next = far[leave];  // = 2w + sw
+        cand[2 * v + s] = WalkWord<uint32_t>::make(next, entry[s]);
+      }
+      pair = (one[0] ? 1u : 0u) | (one[1] ? 2u : 0u);
+    }
+    const uint32_t lo = __reduce_or_sync(0xffffffffu, lane < 16 ? pair << (2 * lane) : 0u);
+    const uint32_t hi = __reduce_or_sync(0xffffffffu, lane >= 16 ? pair << (2 * (lane - 16)) : 0u);
+    if (lane == 0) {
+      lone[g / 16] = lo;
+      if (g + 16 < V) lone[g / 16 + 1] = hi;
+    }
+  }
+}
+
+// Keeps the candidates whose successor's side is lone too: mk[x] (in
+// place) and succ[x].
+__global__ void k_succ_lone(uint32_t *__restrict__ mk, const uint32_t *__restrict__ lone, uint64_t n,
+                            uint32_t *__restrict__ succ) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t c = mk[x];
+    uint32_t out = NONE32;
+    if (!WalkWord<uint32_t>::tail(c)) {
+      const uint32_t y = WalkWord<uint32_t>::next(c);
+      if ((__ldg(lone + (y >> 5)) >> (y & 31)) & 1u) out = y;
+      else c = WalkWord<uint32_t>::make(NONE32, WalkWord<uint32_t>::base(c));
+    }
+    mk[x] = c;
+    succ[x] = out;
   }
 }
 
@@ -378,7 +446,7 @@ __device__ __forceinline__ uint32_t queue_heads(uint64_t base, uint64_t n, uint3
 // other walker's head, the index of its first staged entry).
 //
 // Staging: each lane stages the strand-nodes its walks take, in walk order,
-// as entries (y << 2) | the base the arc into y appends (0 for a head), at
+// as entries (y << 2) | y's entry base (the base the arc into y appends), at
 // consecutive indices of lane-private pages of STAGE_PAGE entries taken
 // from a global cursor; page_next[page] is the page the lane went on to.
 // The entries pass through eight registers and are stored eight at a time,
@@ -424,8 +492,8 @@ __device__ __forceinline__ void stage_push(StageLane &ln, uint32_t e, uint32_t *
 }
 
 template <class W>
-__global__ __launch_bounds__(WALK_BLOCK) void k_mark_stage(W *__restrict__ mk,
-                                                           const uint64_t *__restrict__ succ_base, uint64_t n,
+__global__ __launch_bounds__(WALK_BLOCK, 6) void k_mark_stage(W *__restrict__ mk,
+                                                           const uint32_t *__restrict__ succ, uint64_t n,
                                                            uint32_t cap, uint4 *__restrict__ hrec,
                                                            uint32_t *__restrict__ stage,
                                                            uint32_t *__restrict__ page_next,
@@ -439,15 +507,14 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_mark_stage(W *__restrict__ mk,
   uint32_t lng = 0;
   StageLane ln;
   for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
-    const uint32_t cnt =
-        queue_heads(c * WALK_CHUNK, n, s_q[w], [&](uint64_t x) { return succ_base[x ^ 1] == ~0ull; });
+    const uint32_t cnt = queue_heads(c * WALK_CHUNK, n, s_q[w], [&](uint64_t x) { return succ[x ^ 1] == NONE32; });
     if (lane == 0) s_next[w] = 0;
     __syncwarp();
     for (;;) {
       const uint32_t qi = atomicAdd(&s_next[w], 1u);
       if (qi >= cnt) break;
       const uint32_t x = s_q[w][qi];
-      uint32_t y = x, d = 0, last = NONE32, partner = NONE32, first = NONE32, base = 0;
+      uint32_t y = x, d = 0, last = NONE32, partner = NONE32, first = NONE32;
       for (;;) {
         const W wd = __ldcg(mk + y);  // from L2: another SM's mark may be there
         if (WalkWord<W>::marked(wd)) {
@@ -455,7 +522,7 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_mark_stage(W *__restrict__ mk,
           break;
         }
         __stcg(mk + (y ^ 1u), WalkWord<W>::mark(x));
-        stage_push(ln, (y << 2) | base, stage, page_next, cursor, stage_cap, overflow);
+        stage_push(ln, (y << 2) | WalkWord<W>::base(wd), stage, page_next, cursor, stage_cap, overflow);
         if (first == NONE32 && !ln.full) first = (uint32_t)(ln.idx - 1);
         d++;
         last = y;
@@ -467,7 +534,6 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_mark_stage(W *__restrict__ mk,
           lng++;
           break;
         }
-        base = WalkWord<W>::base(wd);
         y = WalkWord<W>::next(wd);
       }
       hrec[x] = make_uint4(d, last, partner, first);
@@ -494,13 +560,13 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_mark_stage(W *__restrict__ mk,
 // smaller) and its first node's tables: is_head, the unitig's length, the
 // kept copy's strand.
 template <class K>
-__global__ void k_mark_pair(const uint64_t *__restrict__ succ_base, uint64_t n, const uint4 *__restrict__ hrec,
+__global__ void k_mark_pair(const uint32_t *__restrict__ succ, uint64_t n, const uint4 *__restrict__ hrec,
                             const uint64_t *__restrict__ node_keys, int k, uint32_t cap,
                             uint32_t *__restrict__ is_head, uint32_t *__restrict__ len_at_head,
                             uint8_t *__restrict__ hstrand, unsigned long long *covered, uint32_t *err) {
   unsigned long long cov = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    if (succ_base[i ^ 1] != ~0ull) continue;  // not a list head
+    if (succ[i ^ 1] != NONE32) continue;  // not a list head
     const uint32_t x = (uint32_t)i;
     const uint4 ra = hrec[x];
     const uint32_t p = ra.z;
@@ -515,11 +581,11 @@ __global__ void k_mark_pair(const uint64_t *__restrict__ succ_base, uint64_t n, 
       continue;
     }
     uint32_t o = 0;
-    if (ra.x > 0 && rb.x > 0 && (uint32_t)succ_base[ra.y] != (rb.y ^ 1u)) {
+    if (ra.x > 0 && rb.x > 0 && succ[ra.y] != (rb.y ^ 1u)) {
       // the walks overlap: step from b's last node (on a's strands) to a's last
       uint32_t y = rb.y ^ 1u, steps = 0;
       while (y != ra.y && steps <= cap) {
-        y = (uint32_t)succ_base[y];
+        y = succ[y];
         steps++;
       }
       if (y != ra.y) {
@@ -538,15 +604,6 @@ __global__ void k_mark_pair(const uint64_t *__restrict__ succ_base, uint64_t n, 
   }
   cov = __reduce_add_sync(0xffffffffu, (unsigned)cov);
   if ((threadIdx.x & 31) == 0 && cov) atomicAdd(covered, cov);
-}
-
-// The 32-bit successor words (the general path's and the out-of-core
-// ranking's form), from succ_base.
-__global__ void k_restore_succ(const uint64_t *__restrict__ succ_base, uint64_t n, uint32_t *__restrict__ succ) {
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t b = succ_base[x];
-    succ[x] = b == ~0ull ? NONE32 : (uint32_t)b;
-  }
 }
 
 // The index s entries after index q of the same walk (following the lanes'
@@ -578,7 +635,7 @@ __device__ __forceinline__ char base_char(uint32_t b) { return (char)((0x5447434
 constexpr int CG = 8;
 
 template <class K>
-__global__ __launch_bounds__(WALK_BLOCK) void k_stage_copy(
+__global__ __launch_bounds__(WALK_BLOCK, 6) void k_stage_copy(
     const uint32_t *__restrict__ is_head, const uint8_t *__restrict__ hstrand, const uint32_t *__restrict__ ulen,
     const uint64_t *__restrict__ uidx, const uint64_t *__restrict__ off_by_v, const uint4 *__restrict__ hrec,
     const uint32_t *__restrict__ stage, const uint32_t *__restrict__ page_next,
@@ -643,11 +700,21 @@ __global__ __launch_bounds__(WALK_BLOCK) void k_stage_copy(
   }
 }
 
-// enough warps to fill the device, at most one per chunk
-static unsigned walk_grid(const dbg_ctx *ctx, uint64_t n) {
+// enough warps to fill the device in one wave (a block beyond the resident
+// ones would start its fixed share of chunks only when another ends), at
+// most one per chunk
+template <class F>
+static unsigned walk_grid(const dbg_ctx *ctx, uint64_t n, F kern) {
   const uint64_t chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
   const uint64_t blocks = (chunks + WALK_WARPS - 1) / WALK_WARPS;
-  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)std::max(1, ctx->num_sms) * 6));
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WALK_BLOCK, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return (unsigned)std::max<uint64_t>(
+      1, std::min<uint64_t>(blocks, (uint64_t)std::max(1, ctx->num_sms) * (uint64_t)per_sm));
 }
 
 static unsigned grid_of(uint64_t n) {
@@ -787,27 +854,37 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
     // up to 2^30 (their staged entries hold a strand-node in 30 bits)
     const bool w32 = n <= WalkWord<uint32_t>::MAX_N, fast = n <= WalkWord<uint64_t>::MAX_N;
     DevBuf mk;
-    DBG_TRY(alloc_buf(ctx, link_node, n1 * 4));
-    DBG_TRY(alloc_buf(ctx, link_edge, n1 * 8));
-    DBG_TRY(alloc_buf(ctx, word, n1 * 8));
+    DBG_TRY(alloc_buf(ctx, succ, n1 * 4));
     if (fast) DBG_TRY(alloc_buf(ctx, mk, n1 * (w32 ? 4 : 8)));
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + (double)E2 * 10 + 8.0 * V * g->key_words + 12.0 * n,
-               k_side_links<K><<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
-                                                          g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
-                                                          g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
-                                                          literal, link_node.as<uint32_t>(), link_edge.as<uint64_t>()));
-    // succ_base goes to the ranking words' buffer (free until the general path)
-    if (w32)
-      DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n + 8.0 * n + 12.0 * n,
-                 k_successors<uint32_t><<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(),
-                                                                   V, word.as<uint64_t>(), mk.as<uint32_t>()));
-    else
-      DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n + 8.0 * n + (fast ? 16.0 : 8.0) * n,
+    if (w32) {
+      // per side the lone end, a bitmap of the lone sides, the candidate
+      // words; then the arcs whose far side is lone too
+      DevBuf lone;
+      DBG_TRY(alloc_buf(ctx, lone, (V / 16 + 2) * 4));
+      DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + (double)E2 * 10 + 8.0 * V * g->key_words + 8.0 * V + V / 4.0,
+                 k_side_cand<K><<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
+                                                           g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
+                                                           g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
+                                                           literal, mk.as<uint32_t>(), lone.as<uint32_t>()));
+      DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n,
+                 k_succ_lone<<<grid_of(n), 256, 0, s>>>(mk.as<uint32_t>(), lone.as<uint32_t>(), n,
+                                                        succ.as<uint32_t>()));
+    } else {
+      DBG_TRY(alloc_buf(ctx, link_node, n1 * 4));
+      DBG_TRY(alloc_buf(ctx, link_edge, n1 * 8));
+      DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + (double)E2 * 10 + 8.0 * V * g->key_words + 12.0 * n,
+                 k_side_links<K><<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
+                                                            g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
+                                                            g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V,
+                                                            k, literal, link_node.as<uint32_t>(),
+                                                            link_edge.as<uint64_t>()));
+      DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n + 8.0 * n + (fast ? 12.0 : 4.0) * n,
                  k_successors<uint64_t><<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(),
-                                                                   V, word.as<uint64_t>(),
+                                                                   V, succ.as<uint32_t>(),
                                                                    fast ? mk.as<uint64_t>() : nullptr));
-    link_node.release();
-    link_edge.release();
+      link_node.release();
+      link_edge.release();
+    }
     // ---- fast path: short acyclic lists only ----
     if (fast) {
       DevBuf f_is_head, f_len, f_strand, f_uidx, f_off, hrec, stage, page_next;
@@ -821,7 +898,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
       // copy (k_mark_pair).  Staging room: every node once (the few that
       // both walkers of a pair take within the margin), plus two partly
       // used pages per lane.
-      const unsigned wgrid = walk_grid(ctx, n);
+      const unsigned wgrid = w32 ? walk_grid(ctx, n, k_mark_stage<uint32_t>) : walk_grid(ctx, n, k_mark_stage<uint64_t>);
       const uint64_t lanes = (uint64_t)wgrid * WALK_BLOCK;
       const uint64_t stage_cap = ((V + V / 4 + 2 * lanes * STAGE_PAGE) / STAGE_PAGE + 1) * STAGE_PAGE;
       DBG_TRY(alloc_buf(ctx, hrec, n1 * sizeof(uint4)));
@@ -833,12 +910,12 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
       if (w32)
         DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 16.0 * V + 4.0 * V,
                    k_mark_stage<uint32_t><<<wgrid, WALK_BLOCK, 0, s>>>(
-                       mk.as<uint32_t>(), word.as<uint64_t>(), n, kWalkCap, hrec.as<uint4>(), stage.as<uint32_t>(),
+                       mk.as<uint32_t>(), succ.as<uint32_t>(), n, kWalkCap, hrec.as<uint4>(), stage.as<uint32_t>(),
                        page_next.as<uint32_t>(), cursor, stage_cap, ctx->d_counters + 11, ctx->d_counters + 16));
       else
         DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 24.0 * V + 4.0 * V,
                    k_mark_stage<uint64_t><<<wgrid, WALK_BLOCK, 0, s>>>(
-                       mk.as<uint64_t>(), word.as<uint64_t>(), n, kWalkCap, hrec.as<uint4>(), stage.as<uint32_t>(),
+                       mk.as<uint64_t>(), succ.as<uint32_t>(), n, kWalkCap, hrec.as<uint4>(), stage.as<uint32_t>(),
                        page_next.as<uint32_t>(), cursor, stage_cap, ctx->d_counters + 11, ctx->d_counters + 16));
       DBG_CUDA_TRY(cudaGetLastError());
       uint32_t flags[6] = {0, 0, 0, 0, 0, 0};  // counters 11..16
@@ -848,7 +925,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
       uint64_t covered = 0;
       if (too_long == 0 && overflow == 0) {
         DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 32.0 * V,
-                   k_mark_pair<K><<<grid_of(n), 256, 0, s>>>(word.as<uint64_t>(), n, hrec.as<uint4>(),
+                   k_mark_pair<K><<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n, hrec.as<uint4>(),
                                                              g->node_keys.as<uint64_t>(), k, kWalkCap,
                                                              f_is_head.as<uint32_t>(), f_len.as<uint32_t>(),
                                                              f_strand.as<uint8_t>(),
@@ -878,7 +955,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
         DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
         DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT,
                    (double)V * (4 + 1 + 4 + 8 + 1) + (double)Uf * (16 + 32 + 8 * g->key_words * 2 + 16 + k),
-                   k_stage_copy<K><<<walk_grid(ctx, V), WALK_BLOCK, 0, s>>>(
+                   k_stage_copy<K><<<walk_grid(ctx, V, k_stage_copy<K>), WALK_BLOCK, 0, s>>>(
                        f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_len.as<uint32_t>(), f_uidx.as<uint64_t>(),
                        f_off.as<uint64_t>(), hrec.as<uint4>(), stage.as<uint32_t>(), page_next.as<uint32_t>(),
                        g->node_keys.as<uint64_t>(), V, Uf, k, u->nodes.as<uint64_t>(), u->seq.as<char>(),
@@ -889,9 +966,8 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
       }
     }
     // ---- general path: long lists or cycles present ----
-    DBG_TRY(alloc_buf(ctx, succ, n1 * 4));
-    DBG_LAUNCH(ctx, ST_COMPACT_RANK, 12.0 * n,
-               k_restore_succ<<<grid_of(n), 256, 0, s>>>(word.as<uint64_t>(), n, succ.as<uint32_t>()));
+    mk.release();
+    DBG_TRY(alloc_buf(ctx, word, n1 * 8));
     DBG_CUDA_TRY(cudaMemsetAsync(word.p, 0xff, n * 8, s));
     DBG_LAUNCH(ctx, ST_COMPACT_RANK, 4.0 * n + 12.0 * n,
                k_walk_lists<<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n, kWalkCap,
@@ -1109,20 +1185,16 @@ static dbg_status compact_bucketed_impl(dbg_ctx *ctx, const dbg_graph *g, uint64
     DBG_TRY(alloc_buf(ctx, link_node, n * 4));
     DBG_TRY(alloc_buf(ctx, link_edge, n * 8));
     DBG_TRY(alloc_buf(ctx, succ, n * 4));
-    DBG_TRY(alloc_buf(ctx, word, n * 8));
     DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + 20.0 * g->num_edges + 8.0 * V * g->key_words + 12.0 * n,
                k_side_links<K><<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
                                                           g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
                                                           g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
                                                           false, link_node.as<uint32_t>(), link_edge.as<uint64_t>()));
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 28.0 * n,
+    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 24.0 * n,
                k_successors<uint64_t><<<grid_of(n), 256, 0, s>>>(link_node.as<uint32_t>(), link_edge.as<uint64_t>(),
-                                                                 V, word.as<uint64_t>(), nullptr));
-    DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n,
-               k_restore_succ<<<grid_of(n), 256, 0, s>>>(word.as<uint64_t>(), n, succ.as<uint32_t>()));
+                                                                 V, succ.as<uint32_t>(), nullptr));
     DBG_CUDA_TRY(cudaGetLastError());
   }
-  word.release();
   PinnedBuf h_succ, h_W, h_lab, h_req, h_out, h_moved;
   DBG_TRY(h_succ.alloc(n * 4));
   DBG_TRY(h_W.alloc(n * 8));
