@@ -60,6 +60,8 @@ def parse():
                     help="1: the edge keys' local pass counts copies in a hash table before sorting")
     ap.add_argument("--partition-first", type=int, default=1, choices=(0, 1),
                     help="1: the edge keys' first global pass is an unordered partition")
+    ap.add_argument("--copy-streams", type=int, default=0,
+                    help="streams the end-to-end read-back is spread over (0: the library's default)")
     ap.add_argument("--local-rank", type=int, default=1, choices=(0, 1),
                     help="1: the local passes rank keys within their groups instead of digit passes")
     ap.add_argument("--node-mult", action="store_true",
@@ -400,6 +402,8 @@ def run_ours(args):
     dbg.dbg_sort_count_first_set(ctx, bool(args.count_first))
     dbg.dbg_sort_partition_first_set(ctx, bool(args.partition_first))
     dbg.dbg_sort_local_rank_set(ctx, bool(args.local_rank))
+    if args.copy_streams:
+        dbg.dbg_copy_streams_set(ctx, args.copy_streams)
     dbg.dbg_node_mult_set(ctx, bool(args.node_mult))
     variants = {kd: dbg.dbg_sort_variant_name(kd, dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(6)}
     variant_ids = ",".join(str(dbg.dbg_sort_variant_get(ctx, kd)) for kd in range(6))
@@ -545,6 +549,7 @@ def run_ours(args):
                        "sort_variants": variants, "sort_variant_ids": variant_ids,
                        "count_first": bool(args.count_first),
                        "partition_first": bool(args.partition_first), "local_rank": bool(args.local_rank),
+                       "copy_streams": args.copy_streams or 1,
                        "node_mult": bool(args.node_mult),
                        "autotune_pass_ms": {kd: [round(x, 4) for x in v] for kd, v in tune_ms.items()}},
             "roofline": {"bound": "hbm",

@@ -210,6 +210,19 @@ void dbg_graph_free(dbg_graph *g);
  * -------------------------------------------------------------------- */
 dbg_status dbg_compact(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs **out);
 
+/* How dbg_compact ranks the lists.  0 (the default): the meeting walks
+ * with staged halves when every list is short and acyclic, with 32-bit walk
+ * words up to 2^29 - 1 strand-nodes and 64-bit words up to 2^30, else
+ * pointer jumping with cycle breaking; 1: the walks with 64-bit words at
+ * any size they allow; 2: pointer jumping only.  The unitigs are the same
+ * either way.  DBG_EINVAL for another mode. */
+dbg_status dbg_compact_mode_set(dbg_ctx *ctx, int mode);
+
+/* Streams over which the read-back of a graph (dbg_graph_*_async) or of
+ * unitigs (dbg_unitigs_get) built with this context is spread, in chunks
+ * of at least 32 MB: 1 (the default) to 8.  DBG_EINVAL outside. */
+dbg_status dbg_copy_streams_set(dbg_ctx *ctx, int n);
+
 /* ----------------------------------------------------------------------
  * dbg_compact_bucketed -- dbg_compact with the out-of-core list ranking of
  * Section 6.2: the ranking words of the 2|V| strand-nodes (list head,

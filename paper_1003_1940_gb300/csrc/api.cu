@@ -67,6 +67,18 @@ dbg_status ensure_status(dbg_ctx *ctx, size_t words) {
   return DBG_OK;
 }
 
+dbg_status copy_spread(cudaStream_t *streams, int n_streams, int *next, void *dst, const void *src, size_t bytes) {
+  // chunks of at least 32 MB, at most one per stream and array
+  const size_t chunk = std::max<size_t>((size_t)32 << 20, (bytes + n_streams - 1) / n_streams);
+  for (size_t off = 0; off < bytes; off += chunk) {
+    const size_t b = std::min(chunk, bytes - off);
+    DBG_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, b,
+                                 cudaMemcpyDefault, streams[*next]));
+    *next = (*next + 1) % n_streams;
+  }
+  return DBG_OK;
+}
+
 dbg_status ensure_copy_stream(dbg_ctx *ctx) {
   if (!ctx->copy_stream) DBG_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
   return DBG_OK;
@@ -345,6 +357,7 @@ dbg_status dbg_build(dbg_ctx *ctx, const char *reads, const uint32_t *lengths, u
   if (!g) return DBG_ENOMEM;
   g->al = ctx->al;
   g->device = ctx->device;
+  g->n_copy = ctx->copy_streams;
   // graph arrays must be freed through the graph's own allocator copy
   auto rebind = [&](DevBuf &b) { b.al = &g->al; };
 
@@ -418,6 +431,7 @@ dbg_status dbg_build_bucketed(dbg_ctx *ctx, const char *reads, const uint32_t *l
   if (!g) return DBG_ENOMEM;
   g->al = ctx->al;
   g->device = ctx->device;
+  g->n_copy = ctx->copy_streams;
   dbg_status st = DBG_OK;
   DevBuf d_len;
   const uint32_t *len_dev = lengths;
@@ -525,15 +539,18 @@ struct CopyPart {
   const void *src;
   size_t bytes;
 };
-// starts the copies of the given parts on the graph's own copy stream
+// starts the copies of the given parts on the graph's own copy streams
 dbg_status copy_parts_async(dbg_graph *g, std::initializer_list<CopyPart> parts) {
   DeviceScope scope(g->device);
-  if (!g->copy_stream) DBG_CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+  for (int i = 0; i < g->n_copy; i++)
+    if (!g->copy_streams[i]) DBG_CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_streams[i], cudaStreamNonBlocking));
   for (const CopyPart &c : parts)
-    if (c.dst && c.bytes) DBG_CUDA_TRY(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, g->copy_stream));
+    if (c.dst && c.bytes) DBG_TRY(copy_spread(g->copy_streams, g->n_copy, &g->copy_next, c.dst, c.src, c.bytes));
   return DBG_OK;
 }
 }  // namespace
+
+
 
 dbg_status dbg_graph_edges_async(dbg_graph *g, uint64_t *keys, uint32_t *src, uint32_t *dst, uint8_t *orient,
                                  uint32_t *mult) {
@@ -562,9 +579,9 @@ dbg_status dbg_graph_csr_async(dbg_graph *g, uint64_t *row_ptr, uint32_t *nbr, u
 
 dbg_status dbg_graph_wait(dbg_graph *g) {
   if (!g) return DBG_EINVAL;
-  if (!g->copy_stream) return DBG_OK;
   DeviceScope scope(g->device);
-  DBG_CUDA_TRY(cudaStreamSynchronize(g->copy_stream));
+  for (cudaStream_t cs : g->copy_streams)
+    if (cs) DBG_CUDA_TRY(cudaStreamSynchronize(cs));
   return DBG_OK;
 }
 
@@ -601,10 +618,11 @@ dbg_status dbg_graph_device_view(const dbg_graph *g, dbg_graph_view *v) {
 void dbg_graph_free(dbg_graph *g) {
   if (!g) return;
   DeviceScope scope(g->device);
-  if (g->copy_stream) {  // read-backs in flight finish before the arrays go
-    cudaStreamSynchronize(g->copy_stream);
-    cudaStreamDestroy(g->copy_stream);
-  }
+  for (cudaStream_t cs : g->copy_streams)
+    if (cs) {  // read-backs in flight finish before the arrays go
+      cudaStreamSynchronize(cs);
+      cudaStreamDestroy(cs);
+    }
   std::shared_ptr<BudgetShare> budget = std::move(g->budget);
   const uint64_t charged = g->charged;
   delete g;  // DevBuf destructors release in stream order
@@ -678,6 +696,24 @@ uint64_t dbg_sort_fallbacks(const dbg_ctx *ctx) { return ctx ? ctx->local_sort_f
 uint64_t dbg_sort_count_overflows(const dbg_ctx *ctx) { return ctx ? ctx->count_overflow_tiles : 0; }
 
 uint64_t dbg_sort_rank_fallbacks(const dbg_ctx *ctx) { return ctx ? ctx->rank_fallback_tiles : 0; }
+
+dbg_status dbg_copy_streams_set(dbg_ctx *ctx, int n) {
+  if (!ctx || n < 1 || n > kCopyStreams) {
+    set_error("copy streams: null context or %d not in 1..%d", n, kCopyStreams);
+    return DBG_EINVAL;
+  }
+  ctx->copy_streams = n;
+  return DBG_OK;
+}
+
+dbg_status dbg_compact_mode_set(dbg_ctx *ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 2) {
+    set_error("compact mode: null context or mode %d not in 0..2", mode);
+    return DBG_EINVAL;
+  }
+  ctx->compact_mode = mode;
+  return DBG_OK;
+}
 
 dbg_status dbg_node_mult_set(dbg_ctx *ctx, int on) {
   if (!ctx) {

@@ -852,7 +852,8 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
   if (V > 0) {
     // the meeting walks' words: 32-bit up to 2^29 - 1 strand-nodes, 64-bit
     // up to 2^30 (their staged entries hold a strand-node in 30 bits)
-    const bool w32 = n <= WalkWord<uint32_t>::MAX_N, fast = n <= WalkWord<uint64_t>::MAX_N;
+    const bool fast = ctx->compact_mode != 2 && n <= WalkWord<uint64_t>::MAX_N;
+    const bool w32 = fast && ctx->compact_mode == 0 && n <= WalkWord<uint32_t>::MAX_N;
     DevBuf mk;
     DBG_TRY(alloc_buf(ctx, succ, n1 * 4));
     if (fast) DBG_TRY(alloc_buf(ctx, mk, n1 * (w32 ? 4 : 8)));
@@ -1303,6 +1304,7 @@ dbg_status dbg_compact(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs **out) {
   if (!u) return DBG_ENOMEM;
   u->al = ctx->al;
   u->device = ctx->device;
+  u->n_copy = ctx->copy_streams;
   dbg_status st = compact_chains(ctx, g, u, false);
   for (DevBuf *b : {&u->node_off, &u->nodes, &u->seq_off, &u->seq, &u->circular}) b->al = &u->al;
   cudaStreamSynchronize(ctx->stream);
@@ -1342,6 +1344,7 @@ dbg_status dbg_compact_bucketed(dbg_ctx *ctx, const dbg_graph *g, uint64_t mem_b
   if (!u) return DBG_ENOMEM;
   u->al = ctx->al;
   u->device = ctx->device;
+  u->n_copy = ctx->copy_streams;
   uint32_t launches = 0;
   dbg_status st = g->key_words == 1 ? compact_bucketed_impl<uint64_t>(ctx, g, mem_budget, u, &launches)
                                     : compact_bucketed_impl<Key128>(ctx, g, mem_budget, u, &launches);
@@ -1373,15 +1376,27 @@ dbg_status dbg_unitigs_get(const dbg_unitigs *u, uint64_t *node_off, uint64_t *n
       {node_off, u->node_off.p, (u->count + 1) * 8}, {nodes, u->nodes.p, u->num_nodes * 8},
       {seq_off, u->seq_off.p, (u->count + 1) * 8},   {seq, u->seq.p, u->total_bases},
       {circular, u->circular.p, u->count}};
+  // the arrays in chunks over several streams (the copy engines side by side)
   dbg_status st = DBG_OK;
-  for (auto &it : items) {
-    if (!it.dst || !it.bytes) continue;
-    cudaError_t e = cudaMemcpy(it.dst, it.src, it.bytes, cudaMemcpyDefault);
-    if (e != cudaSuccess) {
-      set_error("cudaMemcpy failed: %s", cudaGetErrorString(e));
+  cudaStream_t streams[kCopyStreams] = {};
+  const int ns = std::max(1, std::min(u->n_copy, kCopyStreams));
+  for (int i = 0; i < ns; i++)
+    if (st == DBG_OK && cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaStreamCreate failed");
       st = DBG_ECUDA;
-      break;
     }
+  int next = 0;
+  for (auto &it : items)
+    if (st == DBG_OK && it.dst && it.bytes) st = copy_spread(streams, ns, &next, it.dst, it.src, it.bytes);
+  for (cudaStream_t cs : streams) {
+    if (!cs) continue;
+    const cudaError_t e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess && st == DBG_OK) {
+      set_error("copy failed: %s", cudaGetErrorString(e));
+      st = DBG_ECUDA;
+    }
+    cudaStreamDestroy(cs);
   }
   if (prev >= 0 && prev != u->device) cudaSetDevice(prev);
   return st;

@@ -84,6 +84,8 @@ struct dbg_ctx {
   int count_first = 1;                 // local pass of the edge keys counts copies before sorting
   int partition_first = 1;             // first global pass of keys without payload: unordered partition
   int seg_rank = 1;                    // local passes rank within groups instead of digit passes
+  int compact_mode = 0;                // 0 auto, 1 walks with 64-bit words, 2 pointer jumping only
+  int copy_streams = 1;                // streams a graph's or unitigs' read-back is spread over
   int node_mult = 0;                   // dbg_build also counts every node's k-mer occurrences
   int node_reads = 0;                  // dbg_build also counts the distinct reads holding every node
   uint64_t count_overflow_tiles = 0;  // count-first tiles whose keys did not fit the hash table
@@ -126,6 +128,10 @@ struct BudgetShare {
 };
 }  // namespace dbg
 
+namespace dbg {
+constexpr int kCopyStreams = 8;  // most streams a result read-back is spread over
+}  // namespace dbg
+
 struct dbg_graph {
   uint32_t k = 0, key_words = 1;
   uint64_t num_nodes = 0, num_edges = 0, num_instances = 0;
@@ -135,7 +141,9 @@ struct dbg_graph {
   dbg::DevBuf node_keys, edge_keys, src, dst, orient, mult, row_ptr, adj_nbr, adj_edge, adj_role;
   dbg::DevBuf node_mult;   // k-mer occurrences per node, when the build counted them
   dbg::DevBuf node_reads;  // distinct reads per node, when the build counted them
-  cudaStream_t copy_stream = nullptr;  // read-backs started by dbg_graph_edges_async
+  cudaStream_t copy_streams[dbg::kCopyStreams] = {};  // read-backs started by dbg_graph_*_async
+  int copy_next = 0;                                   // the stream that takes the next chunk
+  int n_copy = 1;                                      // streams in use (the context's setting)
   std::shared_ptr<dbg::BudgetShare> budget;  // the server budget this graph is charged to, if any
   uint64_t charged = 0;
   // device bytes of the graph's arrays
@@ -152,6 +160,7 @@ struct dbg_unitigs {
   uint64_t count = 0, num_nodes = 0, total_bases = 0;
   dbg::Allocator al;
   int device = 0;
+  int n_copy = 1;  // streams its read-back is spread over (the context's setting)
   dbg::DevBuf node_off, nodes, seq_off, seq, circular;
 };
 
@@ -185,6 +194,11 @@ dbg_status alloc_buf(dbg_ctx *ctx, DevBuf &b, size_t bytes);
 dbg_status ensure_status(dbg_ctx *ctx, size_t words);
 // creates the context's copy stream on first use
 dbg_status ensure_copy_stream(dbg_ctx *ctx);
+
+// Copies of one array spread over several streams in chunks, so that the
+// copy engines run side by side (one engine alone does not fill the
+// host link); *next is the stream that takes the next chunk.
+dbg_status copy_spread(cudaStream_t *streams, int n_streams, int *next, void *dst, const void *src, size_t bytes);
 
 // events owned for one call, destroyed when it returns
 struct EventSet {

@@ -111,6 +111,8 @@ _SIGNATURES = [
     ("dbg_sort_partition_first_set", ctypes.c_int, [_P, ctypes.c_int]),
     ("dbg_sort_local_rank_set", ctypes.c_int, [_P, ctypes.c_int]),
     ("dbg_sort_rank_fallbacks", ctypes.c_uint64, [_P]),
+    ("dbg_compact_mode_set", ctypes.c_int, [_P, ctypes.c_int]),
+    ("dbg_copy_streams_set", ctypes.c_int, [_P, ctypes.c_int]),
     ("dbg_sort_fallbacks", ctypes.c_uint64, [_P]),
     ("dbg_autotune", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_char_p, _P]),
 ]
@@ -576,6 +578,14 @@ def dbg_sort_local_rank_set(ctx: Context, on: bool) -> None:
 
 def dbg_sort_rank_fallbacks(ctx: Context) -> int:
     return int(_lib.dbg_sort_rank_fallbacks(ctx.handle))
+
+
+def dbg_compact_mode_set(ctx: Context, mode: int) -> None:
+    _check(_lib.dbg_compact_mode_set(ctx.handle, int(mode)), "dbg_compact_mode_set")
+
+
+def dbg_copy_streams_set(ctx: Context, n: int) -> None:
+    _check(_lib.dbg_copy_streams_set(ctx.handle, int(n)), "dbg_copy_streams_set")
 
 
 def dbg_sort_fallbacks(ctx: Context) -> int:
