@@ -143,9 +143,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def measured_traffic(workload_name, scale, variant):
-    """DRAM bytes per onesweep launch from the committed ncu summary, or None
-    when the kernel source or the chosen variant differs from the capture's."""
+def measured_traffic(workload_name, scale, variant, pass_bytes):
+    """DRAM bytes per onesweep launch from the committed ncu summary, scaled
+    from the captured launch to this one by algorithmic bytes (DRAM traffic
+    grows with the keys a launch moves), or None when the kernel source or
+    the chosen variant differs from the capture's."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "onesweep_large_k31.md")
     src = os.path.join(ROOT, "paper_1003_1940_gb300", "csrc", "k_build.cuh")
@@ -163,7 +165,10 @@ def measured_traffic(workload_name, scale, variant):
         return None
     # one captured figure per variant: "bytes_per_launch <variant name>: <bytes>"
     got = fields.get(f"bytes_per_launch {variant}")
-    return float(got) if got else None
+    if not got:
+        return None
+    alg = float(fields.get("algorithmic_bytes_per_launch", "0"))
+    return float(got) * (pass_bytes / alg) if alg > 0 and pass_bytes > 0 else float(got)
 
 
 def parse_cpulist(text):
@@ -439,7 +444,7 @@ def run_ours(args):
     pass_bytes = srt["bytes"] / max(1, n_pass)
     achieved = pass_bytes / (pass_ms / 1000.0) / 1e9 if pass_ms > 0 else 0.0
     ekind = 0 if k <= 31 else 2  # sort kind of the edge keys: 64- or 128-bit
-    traffic = measured_traffic(args.workload, args.scale, variants.get(ekind))
+    traffic = measured_traffic(args.workload, args.scale, variants.get(ekind), pass_bytes)
 
     stages = {name: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
