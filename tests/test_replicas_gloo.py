@@ -51,3 +51,18 @@ def test_host_binding_helpers():
         os.sched_setaffinity(0, info["_restore"])
     else:
         assert os.sched_getaffinity(0) == before and "_restore" not in info
+
+
+def test_measured_traffic_scales_with_the_launch():
+    """The roofline's DRAM traffic comes from the committed capture of the
+    onesweep pass, scaled to the measured launch by its algorithmic bytes;
+    another workload, scale or variant gives none."""
+    import bench
+    v = "1024x11 atomic persistent occ1 lb8 h16"
+    full = bench.measured_traffic("large", 1.0, v, 16.56e9)
+    assert full is not None and abs(full - 16.237e9) < 1e6
+    half = bench.measured_traffic("large", 1.0, v, 8.28e9)
+    assert abs(half - full / 2) < 1e6
+    assert bench.measured_traffic("long_k", 1.0, v, 16.56e9) is None
+    assert bench.measured_traffic("large", 0.1, v, 16.56e9) is None
+    assert bench.measured_traffic("large", 1.0, "512x8 atomic persistent occ2 lb4", 16.56e9) is None
