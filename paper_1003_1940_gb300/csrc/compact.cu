@@ -443,7 +443,8 @@ __device__ __forceinline__ uint32_t queue_heads(uint64_t base, uint64_t n, uint3
 // this node, mk[y ^ 1], takes y and goes on.  Plain loads and stores: two
 // walkers arriving together may both take a few nodes, which the pairing
 // step measures.  hrec[x] = (nodes walker x took, its last strand-node, the
-// other walker's head, the index of its first staged entry).
+// other walker's head, the index of its first staged entry); the walker
+// with the smaller head of each pair appends that head to `pairs`.
 //
 // Staging: each lane stages the strand-nodes its walks take, in walk order,
 // as entries (y << 2) | y's entry base (the base the arc into y appends), at
@@ -499,7 +500,8 @@ __global__ __launch_bounds__(WALK_BLOCK, 6) void k_mark_stage(W *__restrict__ mk
                                                            uint32_t *__restrict__ page_next,
                                                            unsigned long long *__restrict__ cursor,
                                                            uint64_t stage_cap, uint32_t *too_long,
-                                                           uint32_t *overflow) {
+                                                           uint32_t *overflow, uint32_t *__restrict__ pairs,
+                                                           uint32_t *pair_count) {
   __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
   __shared__ uint32_t s_next[WALK_WARPS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -537,6 +539,18 @@ __global__ __launch_bounds__(WALK_BLOCK, 6) void k_mark_stage(W *__restrict__ mk
         y = WalkWord<W>::next(wd);
       }
       hrec[x] = make_uint4(d, last, partner, first);
+      // append x when it is its pair's smaller head (one atomic per warp
+      // for the lanes here now)
+      const bool smaller = partner != NONE32 && partner > x;
+      const unsigned act = __activemask();
+      const unsigned want = __ballot_sync(act, smaller);
+      if (want) {
+        const int leader = __ffs(act) - 1;
+        uint32_t at = 0;
+        if (lane == leader) at = atomicAdd(pair_count, (uint32_t)__popc(want));
+        at = __shfl_sync(act, at, leader);
+        if (smaller) pairs[at + __popc(want & ((1u << lane) - 1u))] = x;
+      }
     }
     __syncwarp();
   }
@@ -553,28 +567,28 @@ __global__ __launch_bounds__(WALK_BLOCK, 6) void k_mark_stage(W *__restrict__ mk
   if (lane == 0 && lng) atomicAdd(too_long, lng);
 }
 
-// Per pair of walkers (handled by the smaller head): the unitig's length
+// Per pair of walkers (listed by the smaller head): the unitig's length
 // L = d_a + d_b - o, o the nodes both took (found by stepping from the
 // second walker's last node, read on the first walker's strands, to the
 // first walker's last node); the copy kept (the one whose first k-mer is
 // smaller) and its first node's tables: is_head, the unitig's length, the
 // kept copy's strand.
 template <class K>
-__global__ void k_mark_pair(const uint32_t *__restrict__ succ, uint64_t n, const uint4 *__restrict__ hrec,
+__global__ void k_mark_pair(const uint32_t *__restrict__ pairs, const uint32_t *__restrict__ pair_count,
+                            const uint32_t *__restrict__ succ, uint64_t n, const uint4 *__restrict__ hrec,
                             const uint64_t *__restrict__ node_keys, int k, uint32_t cap,
                             uint32_t *__restrict__ is_head, uint32_t *__restrict__ len_at_head,
                             uint8_t *__restrict__ hstrand, unsigned long long *covered, uint32_t *err) {
   unsigned long long cov = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    if (succ[i ^ 1] != NONE32) continue;  // not a list head
-    const uint32_t x = (uint32_t)i;
+  const uint32_t np = *pair_count;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = pairs[i];
     const uint4 ra = hrec[x];
     const uint32_t p = ra.z;
-    if (p >= n || p == x) {
+    if (p >= n || p <= x) {
       atomicOr(err, ERR_INTERNAL);
       continue;
     }
-    if (x > p) continue;
     const uint4 rb = hrec[p];
     if (rb.z != x) {
       atomicOr(err, ERR_INTERNAL);
@@ -905,19 +919,24 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
       DBG_TRY(alloc_buf(ctx, hrec, n1 * sizeof(uint4)));
       DBG_TRY(alloc_buf(ctx, stage, stage_cap * 4));
       DBG_TRY(alloc_buf(ctx, page_next, stage_cap / STAGE_PAGE * 4));
-      // counters: 11 too_long, 12-13 covered, 14-15 page cursor, 16 overflow
+      // counters: 11 too_long, 12-13 covered, 14-15 page cursor, 16 overflow,
+      // 17 pairs listed
       DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 10, 0, 8 * sizeof(uint32_t), s));
+      DevBuf pairs;
+      DBG_TRY(alloc_buf(ctx, pairs, V1 * 4));
       unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ctx->d_counters + 14);
       if (w32)
         DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 16.0 * V + 4.0 * V,
                    k_mark_stage<uint32_t><<<wgrid, WALK_BLOCK, 0, s>>>(
                        mk.as<uint32_t>(), succ.as<uint32_t>(), n, kWalkCap, hrec.as<uint4>(), stage.as<uint32_t>(),
-                       page_next.as<uint32_t>(), cursor, stage_cap, ctx->d_counters + 11, ctx->d_counters + 16));
+                       page_next.as<uint32_t>(), cursor, stage_cap, ctx->d_counters + 11, ctx->d_counters + 16,
+                       pairs.as<uint32_t>(), ctx->d_counters + 17));
       else
         DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 24.0 * V + 4.0 * V,
                    k_mark_stage<uint64_t><<<wgrid, WALK_BLOCK, 0, s>>>(
                        mk.as<uint64_t>(), succ.as<uint32_t>(), n, kWalkCap, hrec.as<uint4>(), stage.as<uint32_t>(),
-                       page_next.as<uint32_t>(), cursor, stage_cap, ctx->d_counters + 11, ctx->d_counters + 16));
+                       page_next.as<uint32_t>(), cursor, stage_cap, ctx->d_counters + 11, ctx->d_counters + 16,
+                       pairs.as<uint32_t>(), ctx->d_counters + 17));
       DBG_CUDA_TRY(cudaGetLastError());
       uint32_t flags[6] = {0, 0, 0, 0, 0, 0};  // counters 11..16
       DBG_TRY(read_small(ctx, ctx->d_counters + 11, sizeof(flags), flags));
@@ -926,7 +945,8 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
       uint64_t covered = 0;
       if (too_long == 0 && overflow == 0) {
         DBG_LAUNCH(ctx, ST_COMPACT_RANK, 8.0 * n + 32.0 * V,
-                   k_mark_pair<K><<<grid_of(n), 256, 0, s>>>(succ.as<uint32_t>(), n, hrec.as<uint4>(),
+                   k_mark_pair<K><<<grid_of(V), 256, 0, s>>>(pairs.as<uint32_t>(), ctx->d_counters + 17,
+                                                             succ.as<uint32_t>(), n, hrec.as<uint4>(),
                                                              g->node_keys.as<uint64_t>(), k, kWalkCap,
                                                              f_is_head.as<uint32_t>(), f_len.as<uint32_t>(),
                                                              f_strand.as<uint8_t>(),
