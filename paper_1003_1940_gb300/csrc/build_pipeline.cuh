@@ -417,18 +417,18 @@ dbg_status seg_sort_records(dbg_ctx *ctx, const K *kin, const uint32_t *vin, K *
                                 ST_LOCAL_SORT_NODES)));
   const int rank = local_rank_method(ctx, sizeof(K) == 16);
   const uint64_t tiles = (n + Sh::TILE - 1) / Sh::TILE;
-  if constexpr (sizeof(K) == 8) {
-    if (ctx->seg_rank && low_bits + 13 <= 64) {
+  {
+    if (ctx->seg_rank && (sizeof(K) == 16 || low_bits + 13 <= 64)) {
       // ranking within groups; tiles with a long group are listed and
       // sorted by the digit passes
-      static_assert(RANK_CAP == SEG_BLOCK * Sh::ITEMS, "same tile capacity as the digit-pass kernel");
-      set_smem_attrs(k_seg_rank, sizeof(SegRankSmem));
+      static_assert(SegRankSmem<K>::CAP == SEG_BLOCK * Sh::ITEMS, "same tile capacity as the digit-pass kernel");
+      set_smem_attrs(k_seg_rank<K>, sizeof(SegRankSmem<K>));
       DevBuf fb;
       DBG_TRY(alloc_buf(ctx, fb, (tiles + 1) * 4));
       uint32_t *fb_count = fb.as<uint32_t>(), *fb_list = fb_count + 1;
       DBG_CUDA_TRY(cudaMemsetAsync(fb_count, 0, 4, ctx->stream));
       DBG_LAUNCH(ctx, ST_LOCAL_SORT_NODES, 2.0 * (double)n * (sizeof(K) + 4),
-                 k_seg_rank<<<(unsigned)tiles, RANK_BLOCK, sizeof(SegRankSmem), ctx->stream>>>(
+                 k_seg_rank<K><<<(unsigned)tiles, RANK_BLOCK, sizeof(SegRankSmem<K>), ctx->stream>>>(
                      kin, vin, bound.as<uint64_t>(), osize.as<uint32_t>(), ooff.as<uint64_t>(), gk.as<K>(),
                      gv.as<uint32_t>(), kout, vout, low_bits, fb_list, fb_count));
       DBG_CUDA_TRY(cudaGetLastError());
@@ -939,10 +939,10 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   DBG_TRY(alloc_buf(ctx, rv_a, std::max<uint64_t>(1, R) * sizeof(uint32_t)));
   DBG_TRY(alloc_buf(ctx, rv_b, std::max<uint64_t>(1, R) * sizeof(uint32_t)));
   DBG_CUDA_TRY(cudaMemsetAsync(d_hist, 0, MAX_PASSES * RADIX * sizeof(unsigned long long), s));
-  // 64-bit records ranked within groups: align the digits with the top of
-  // the 2k-bit key, so that the global passes resolve 8 bits each of it and
+  // records ranked within groups: align the digits with the top of the
+  // 2k-bit key, so that the global passes resolve 8 bits each of it and
   // leave short groups
-  int adj = (sizeof(K) == 8 && ctx->seg_rank) ? (8 - nbits % 8) % 8 : 0;
+  int adj = ctx->seg_rank ? (8 - nbits % 8) % 8 : 0;
   int q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(R, nbits + adj) : 0;
   if (q0 == 0) {
     adj = 0;

@@ -323,37 +323,46 @@ __global__ __launch_bounds__(BLOCK, 2) void k_seg_sort(
   }
 }
 
-// Records by ranking within groups (64-bit keys).  The tile's keys are
-// already ordered by their high bits (from low_bits up), so a record's place
-// in the sorted tile is its group's start plus the number of records of its
-// group that precede it: those with smaller low bits, or equal low bits and
-// an earlier position (which keeps the sort stable).  Each record is staged
-// in shared memory as one word, (low bits << 13) | position, and ranked by
-// comparing that word with the group's others; no digit pass and no block
-// barrier is needed past the staging.  The work is the sum of the squared
-// group lengths, small when the global passes leave groups of a few dozen
-// records.  A tile with a group longer than RANK_GROUP_MAX is listed in
-// fb_list for the digit-pass kernel instead.
-constexpr int RANK_BLOCK = 512, RANK_CAP = SEG_BLOCK * 24, RANK_ITEMS = RANK_CAP / RANK_BLOCK;
+// Records by ranking within groups.  The tile's keys are already ordered
+// by their high bits (from low_bits up), so a record's place in the sorted
+// tile is its group's start plus the number of records of its group that
+// precede it: those with a smaller key, or an equal key and an earlier
+// position (which keeps the sort stable).  A 64-bit record is staged in
+// shared memory as one word, (low bits << 13) | position, and ranked by
+// comparing that word with the group's others; a 128-bit record as its key,
+// compared whole with the position as tie-break.  No digit pass and no
+// block barrier is needed past the staging.  The work is the sum of the
+// squared group lengths, small when the global passes leave groups of a
+// few dozen records.  A tile with a group longer than RANK_GROUP_MAX is
+// listed in fb_list for the digit-pass kernel instead.
+constexpr int RANK_BLOCK = 512;
 constexpr uint32_t RANK_GROUP_MAX = 512;
-static_assert(RANK_CAP <= 8192, "positions fit 13 bits");
 
+template <class K>
 struct SegRankSmem {
-  uint64_t pk[RANK_CAP];  // (low bits << 13) | position
-  uint32_t val[RANK_CAP];
-  uint16_t ord[RANK_CAP];           // group of each record
-  uint16_t gstart[RANK_CAP + 1];    // first position of each group, then cnt
-  uint32_t cnt[RANK_ITEMS * (RANK_BLOCK / 32) + 1];
+  static constexpr int CAP = SEG_BLOCK * (sizeof(K) == 8 ? 24 : 12);  // the digit-pass kernel's capacity
+  static constexpr int ITEMS = CAP / RANK_BLOCK;
+  static_assert(CAP <= 8192, "positions fit 13 bits");
+  using W = std::conditional_t<sizeof(K) == 8, uint64_t, K>;
+  W pk[CAP];  // 64-bit: (low bits << 13) | position; 128-bit: the key
+  uint32_t val[CAP];
+  uint16_t ord[CAP];           // group of each record
+  uint16_t gstart[CAP + 1];    // first position of each group, then cnt
+  uint32_t cnt[ITEMS * (RANK_BLOCK / 32) + 1];
   uint32_t maxg;
 };
 
-static __global__ __launch_bounds__(RANK_BLOCK, 2) void k_seg_rank(
-    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, const uint64_t *__restrict__ bound,
-    const uint32_t *__restrict__ osize, const uint64_t *__restrict__ ooff, const uint64_t *__restrict__ gk,
-    const uint32_t *__restrict__ gv, uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int low_bits,
+template <class K>
+__global__ __launch_bounds__(RANK_BLOCK, 2) void k_seg_rank(
+    const K *__restrict__ kin, const uint32_t *__restrict__ vin, const uint64_t *__restrict__ bound,
+    const uint32_t *__restrict__ osize, const uint64_t *__restrict__ ooff, const K *__restrict__ gk,
+    const uint32_t *__restrict__ gv, K *__restrict__ kout, uint32_t *__restrict__ vout, int low_bits,
     uint32_t *__restrict__ fb_list, uint32_t *__restrict__ fb_count) {
+  using S = SegRankSmem<K>;
+  constexpr int ITEMS = S::ITEMS;
+  constexpr bool WIDE = sizeof(K) == 16;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  SegRankSmem &sm = *reinterpret_cast<SegRankSmem *>(smem_raw);
+  S &sm = *reinterpret_cast<S *>(smem_raw);
   const int tid = threadIdx.x;
   const uint32_t tile = blockIdx.x;
   const uint64_t s = bound[tile];
@@ -367,25 +376,28 @@ static __global__ __launch_bounds__(RANK_BLOCK, 2) void k_seg_rank(
   }
   const uint32_t cnt = (uint32_t)(bound[tile + 1] - s);
   if (cnt == 0) return;
-  const uint64_t low_mask = (1ull << low_bits) - 1ull;
   if (tid == 0) sm.maxg = 0;
   // stage the records; a group starts where the high bits change
-  bool head[RANK_ITEMS];
-  uint32_t rk[RANK_ITEMS];
+  bool head[ITEMS];
+  uint32_t rk[ITEMS];
 #pragma unroll
-  for (int i = 0; i < RANK_ITEMS; i++) {
+  for (int i = 0; i < ITEMS; i++) {
     const uint32_t j = (uint32_t)i * RANK_BLOCK + tid;
     head[i] = false;
     if (j < cnt) {
-      const uint64_t x = kin[s + j];
-      head[i] = j == 0 || ((x ^ kin[s + j - 1]) >> low_bits) != 0;
-      sm.pk[j] = ((x & low_mask) << 13) | j;
+      const K x = kin[s + j];
+      head[i] = j == 0 || !KeyOps<K>::eq(KeyOps<K>::shr(x, low_bits), KeyOps<K>::shr(kin[s + j - 1], low_bits));
+      if constexpr (WIDE) {
+        sm.pk[j] = x;
+      } else {
+        sm.pk[j] = ((x & ((1ull << low_bits) - 1ull)) << 13) | j;
+      }
       sm.val[j] = vin[s + j];
     }
   }
-  const uint32_t G = tile_flag_ranks<RANK_BLOCK, RANK_ITEMS>(head, rk, sm.cnt);
+  const uint32_t G = tile_flag_ranks<RANK_BLOCK, ITEMS>(head, rk, sm.cnt);
 #pragma unroll
-  for (int i = 0; i < RANK_ITEMS; i++) {
+  for (int i = 0; i < ITEMS; i++) {
     const uint32_t j = (uint32_t)i * RANK_BLOCK + tid;
     if (j < cnt) {
       const uint32_t o = rk[i] + (head[i] ? 1u : 0u) - 1u;
@@ -406,11 +418,20 @@ static __global__ __launch_bounds__(RANK_BLOCK, 2) void k_seg_rank(
   }
   for (uint32_t i = tid; i < cnt; i += RANK_BLOCK) {
     const uint32_t o = sm.ord[i], a = sm.gstart[o], b = sm.gstart[o + 1];
-    const uint64_t p = sm.pk[i];
     uint32_t r = 0;
+    if constexpr (WIDE) {
+      const K x = sm.pk[i];
+      for (uint32_t t = a; t < b; t++) {
+        const K y = sm.pk[t];
+        r += (KeyOps<K>::less(y, x) || (t < i && KeyOps<K>::eq(y, x))) ? 1u : 0u;
+      }
+      kout[s + a + r] = x;
+    } else {
+      const uint64_t p = sm.pk[i];
 #pragma unroll 4
-    for (uint32_t t = a; t < b; t++) r += sm.pk[t] < p ? 1u : 0u;
-    kout[s + a + r] = kin[s + i];
+      for (uint32_t t = a; t < b; t++) r += sm.pk[t] < p ? 1u : 0u;
+      kout[s + a + r] = kin[s + i];
+    }
     vout[s + a + r] = sm.val[i];
   }
 }

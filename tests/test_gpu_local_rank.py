@@ -37,7 +37,9 @@ def same(a: dict, b: dict):
 def both_ways(dbg, reads, lengths, k, with_oracle=True):
     ctx = dbg.Context()
     _, ranked = gpu_graph(dbg, ctx, reads, lengths, k)
-    fallbacks = dbg.dbg_sort_rank_fallbacks(ctx)
+    # tiles sent to the digit passes, and tiles too long for any local pass
+    # (gathered and sorted globally)
+    fallbacks = dbg.dbg_sort_rank_fallbacks(ctx) + dbg.dbg_sort_fallbacks(ctx)
     ctx2 = dbg.Context()
     dbg.dbg_sort_local_rank_set(ctx2, False)
     _, digits = gpu_graph(dbg, ctx2, reads, lengths, k)
@@ -48,11 +50,10 @@ def both_ways(dbg, reads, lengths, k, with_oracle=True):
     return ranked, fallbacks
 
 
-@pytest.mark.parametrize("k", [9, 13, 21, 23, 25, 27, 29, 31, 33])
+@pytest.mark.parametrize("k", [9, 13, 21, 23, 25, 27, 29, 31, 33, 35, 45, 55, 63])
 def test_ranked_equals_digit_passes(dbg, k):
-    """2k mod 8 = 2 and 6 (digit alignment 6 and 2; k is odd) and 128-bit
-    keys (whose records keep the digit passes; their edge keys are
-    ranked)."""
+    """2k mod 8 = 2 and 6 (digit alignment 6 and 2; k is odd), for 64- and
+    128-bit keys."""
     reads, lengths = readgen.generate(readgen.ReadSetSpec(300_000, 30_000, 100, 0.01, k, 900 + k))
     lengths = lengths.copy()
     lengths[-1] = 100 - 9  # a ragged tail
@@ -74,15 +75,16 @@ def group_reads(prefix: str, n: int, k: int, seed: int):
     return np.ascontiguousarray(reads), np.full(n, k + 1, dtype=np.uint32)
 
 
+@pytest.mark.parametrize("k", [31, 55])
 @pytest.mark.parametrize("n_group,expect_fallback", [(200, False), (400, True), (2_000, True)])
-def test_long_groups(dbg, n_group, expect_fallback):
+def test_long_groups(dbg, k, n_group, expect_fallback):
     """Background reads plus n_group distinct k-mers with one 12-base
     prefix: a group of that many edge keys (the count pass ranks up to 256
     distinct keys in a group) and node records (the record pass ranks
-    groups of up to 512); longer groups send their tile to the digit
-    passes."""
-    k = 31
-    bg, bl = readgen.generate(readgen.ReadSetSpec(200_000, 20_000, 100, 0.01, k, 77))
+    groups of up to 512), for 64- and 128-bit keys; longer groups send their
+    tile to the digit passes, or, longer than a tile holds (3072 128-bit
+    records), to the global sort."""
+    bg, bl = readgen.generate(readgen.ReadSetSpec(200_000, 20_000, 100 if k < 33 else 150, 0.01, k, 77))
     gr, gl = group_reads("A" * 12, n_group, k, 78)
     reads = np.concatenate([bg, gr])
     lengths = np.concatenate([bl, gl])
