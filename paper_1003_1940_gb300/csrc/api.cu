@@ -382,7 +382,7 @@ dbg_status dbg_build(dbg_ctx *ctx, const char *reads, const uint32_t *lengths, u
     st = k <= 31 ? build_graph_u64(ctx, in, g) : build_graph_u128(ctx, in, g);
   }
   for (DevBuf *b : {&g->node_keys, &g->edge_keys, &g->src, &g->dst, &g->orient, &g->mult, &g->row_ptr,
-                    &g->adj_nbr, &g->adj_edge, &g->adj_role, &g->node_mult, &g->node_reads})
+                    &g->adj_nbr, &g->adj_edge, &g->adj_role, &g->adj_side, &g->node_mult, &g->node_reads})
     rebind(*b);
   d_len.release();
   cudaStreamSynchronize(s);
@@ -450,7 +450,7 @@ dbg_status dbg_build_bucketed(dbg_ctx *ctx, const char *reads, const uint32_t *l
                  : build_bucketed_u128(ctx, in, mem_budget, g, &g->edge_buckets, &g->node_buckets);
   }
   for (DevBuf *b : {&g->node_keys, &g->edge_keys, &g->src, &g->dst, &g->orient, &g->mult, &g->row_ptr,
-                    &g->adj_nbr, &g->adj_edge, &g->adj_role})
+                    &g->adj_nbr, &g->adj_edge, &g->adj_role, &g->adj_side})
     b->al = &g->al;
   d_len.release();
   cudaStreamSynchronize(s);

@@ -584,11 +584,12 @@ dbg_status sort_records(dbg_ctx *ctx, K **rk, K **rk_alt, uint32_t **rv, uint32_
 // K6 by reduce-then-scan over R sorted node records; returns the node count
 // and the number of edge ends.  E_all > 0: the records hold both ends of
 // all E_all edges, and src / dst are written through the partition of the
-// edge ends by edge range (k_scatter_ends) instead of at random.
+// edge ends by edge range (k_scatter_ends) instead of at random.  adj_side
+// (E_all > 0 only): the payloads carry the side bits, stored per slot.
 template <class K>
 dbg_status assign_node_ids(dbg_ctx *ctx, const K *rk, const uint32_t *rv, uint64_t R, K *node_keys,
                            uint64_t *row_ptr, dbg_graph *g, uint32_t base_v, uint64_t base_slot, uint64_t *V,
-                           uint64_t *ends, uint64_t E_all = 0) {
+                           uint64_t *ends, uint64_t E_all = 0, uint8_t *adj_side = nullptr) {
   cudaStream_t s = ctx->stream;
   const uint64_t tiles = (R + RS_TILE - 1) / RS_TILE;
   DevBuf hc, ec, ho, eo;
@@ -608,7 +609,7 @@ dbg_status assign_node_ids(dbg_ctx *ctx, const K *rk, const uint32_t *rv, uint64
     DBG_TRY(alloc_buf(ctx, part, 2 * E_all * 8));
     DBG_TRY(alloc_buf(ctx, fill, 256 * 4));
     DBG_CUDA_TRY(cudaMemsetAsync(fill.p, 0, 256 * 4, s));
-    const double wbytes = (double)R * (sizeof(K) + 4) + (double)nv * (sizeof(K) + 8) + (double)ne * 13;
+    const double wbytes = (double)R * (sizeof(K) + 4) + (double)nv * (sizeof(K) + 8) + (double)ne * (adj_side ? 14 : 13);
     if constexpr (sizeof(K) == 8) {
       // persistent CTAs, two per SM, with the next tile's records in flight
       constexpr size_t smem = sizeof(WriteNodesSmem<K>);
@@ -618,13 +619,14 @@ dbg_status assign_node_ids(dbg_ctx *ctx, const K *rk, const uint32_t *rv, uint64
                  k_write_nodes_p<K, true><<<grid, SCAN_BLOCK, smem, s>>>(
                      rk, rv, R, ho.as<uint64_t>(), eo.as<uint64_t>(), node_keys, row_ptr, g->src.as<uint32_t>(),
                      g->dst.as<uint32_t>(), g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), base_v,
-                     base_slot, part.as<uint64_t>(), fill.as<uint32_t>(), bshift, ctx->spin_limit, ctx->d_err));
+                     base_slot, part.as<uint64_t>(), fill.as<uint32_t>(), bshift, ctx->spin_limit, ctx->d_err,
+                     adj_side));
     } else {
       DBG_LAUNCH(ctx, ST_NODE_IDS, wbytes,
                  k_write_nodes<K, true><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(
                      rk, rv, R, ho.as<uint64_t>(), eo.as<uint64_t>(), node_keys, row_ptr, g->src.as<uint32_t>(),
                      g->dst.as<uint32_t>(), g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(), base_v,
-                     base_slot, part.as<uint64_t>(), fill.as<uint32_t>(), bshift));
+                     base_slot, part.as<uint64_t>(), fill.as<uint32_t>(), bshift, adj_side));
     }
     DBG_LAUNCH(ctx, ST_NODE_IDS, 2.0 * E_all * (8 + 4),
                k_scatter_ends<<<grid_for(2 * E_all, 256 * 16), 256, 0, s>>>(part.as<uint64_t>(), 2 * E_all,
@@ -948,12 +950,15 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
     adj = 0;
     q0 = ctx->hybrid_sort ? hybrid_first_pass<K>(R, nbits) : 0;
   }
+  // below 2^29 edges the payloads carry both sides of each edge end, and
+  // the node IDs pass stores them per adjacency slot (for the compaction)
+  const bool sides = E > 0 && E < (1ull << 29);
   if (E > 0) {
     DBG_LAUNCH(ctx, ST_ENDPOINTS, (double)E * (3 * sizeof(K) + 4 + 4 + 1 + 8),
                k_endpoints<K><<<grid_for(E, EMIT_TILE), EMIT_BLOCK, 0, s>>>(
         uniq.as<K>(), headpos.p ? headpos.as<uint32_t>() : nullptr, mult_tmp.as<uint32_t>(), E, k,
         g->edge_keys.as<K>(), g->mult.as<uint32_t>(),
-        g->orient.as<uint8_t>(), rk_a.as<K>(), rv_a.as<uint32_t>(), q0, npasses, d_hist, adj));
+        g->orient.as<uint8_t>(), rk_a.as<K>(), rv_a.as<uint32_t>(), q0, npasses, d_hist, adj, sides));
   }
   if (I > 0) {
     DBG_CUDA_TRY(cudaMemsetAsync(ctx->d_counters + 2, 0, sizeof(uint32_t), s));
@@ -984,11 +989,13 @@ dbg_status build_graph_impl(dbg_ctx *ctx, const BuildInput &in, dbg_graph *g) {
   DBG_TRY(alloc_buf(ctx, g->adj_edge, std::max<uint64_t>(1, 2 * E) * sizeof(uint32_t)));
   DBG_TRY(alloc_buf(ctx, g->adj_role, std::max<uint64_t>(1, 2 * E)));
   DBG_TRY(alloc_buf(ctx, g->adj_nbr, std::max<uint64_t>(1, 2 * E) * sizeof(uint32_t)));
+  if (sides) DBG_TRY(alloc_buf(ctx, g->adj_side, 2 * E));
   uint64_t V = 0;
   if (R > 0) {
     // node keys go to the free record buffer first (|V| is known only after)
     uint64_t ends = 0;
-    DBG_TRY(assign_node_ids<K>(ctx, rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g, 0u, 0ull, &V, &ends, E));
+    DBG_TRY(assign_node_ids<K>(ctx, rk, rv, R, rk_alt, row_tmp.as<uint64_t>(), g, 0u, 0ull, &V, &ends, E,
+                               sides ? g->adj_side.as<uint8_t>() : nullptr));
     DBG_TRY(check_device_error(ctx));
     if (ends != 2 * E) {
       set_error("adjacency holds %llu edge ends, expected %llu", (unsigned long long)ends,

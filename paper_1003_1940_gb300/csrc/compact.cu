@@ -34,12 +34,6 @@ __device__ __forceinline__ Key128 load_node_key<Key128>(const uint64_t *keys, ui
   return Key128{keys[2 * v], keys[2 * v + 1]};
 }
 
-// side of an edge end: 0 = left, 1 = right
-__device__ __forceinline__ uint32_t end_side(uint8_t orient, uint32_t role) {
-  const uint32_t o1 = orient >> 1, o2 = orient & 1u;
-  return role == 0 ? (o1 ? 0u : 1u) : (o2 ? 1u : 0u);
-}
-
 // Per node and side: the edge end alone on that side, if exactly one is
 // (with `literal`, only at nodes whose two sides each carry one end).
 // link_node[2v + side] = (w << 1) | side_at_w of the edge's other end, and
@@ -153,8 +147,9 @@ __global__ void k_successors(const uint32_t *__restrict__ link_node, const uint6
 template <class K>
 __global__ void k_side_cand(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ adj_nbr,
                             const uint32_t *__restrict__ adj_edge, const uint8_t *__restrict__ adj_role,
-                            const uint8_t *__restrict__ orient, const uint64_t *__restrict__ node_keys, uint64_t V,
-                            int k, bool literal, uint32_t *__restrict__ cand, uint32_t *__restrict__ lone) {
+                            const uint8_t *__restrict__ orient, const uint8_t *__restrict__ adj_side,
+                            const uint64_t *__restrict__ node_keys, uint64_t V, int k, bool literal,
+                            uint32_t *__restrict__ cand, uint32_t *__restrict__ lone) {
   const int lane = threadIdx.x & 31;
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g < V;
        g += (uint64_t)gridDim.x * blockDim.x) {
@@ -164,11 +159,19 @@ __global__ void k_side_cand(const uint64_t *__restrict__ row_ptr, const uint32_t
       uint32_t cnt[2] = {0, 0}, far[2] = {NONE32, NONE32};
       const uint64_t p0 = row_ptr[v], p1 = row_ptr[v + 1];
       for (uint64_t p = p0; p < p1; p++) {
-        const uint32_t e = adj_edge[p], role = adj_role[p];
-        const uint8_t o = orient[e];
-        const uint32_t sd = end_side(o, role);
+        uint32_t sd, fsd;
+        if (adj_side) {  // the build's per-slot sides: no gather of the edge's orient
+          const uint32_t b = adj_side[p];
+          sd = b & 1u;
+          fsd = b >> 1;
+        } else {
+          const uint32_t e = adj_edge[p], role = adj_role[p];
+          const uint8_t o = orient[e];
+          sd = end_side(o, role);
+          fsd = end_side(o, 1u - role);
+        }
         cnt[sd]++;
-        far[sd] = (adj_nbr[p] << 1) | end_side(o, 1u - role);
+        far[sd] = (adj_nbr[p] << 1) | fsd;
       }
       const K kv = load_node_key<K>(node_keys, v);
       const uint32_t entry[2] = {(uint32_t)KeyOps<K>::low2(kv), 3u - KeyOps<K>::digit(kv, 2 * (k - 1), 2)};
@@ -876,11 +879,13 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
       // words; then the arcs whose far side is lone too
       DevBuf lone;
       DBG_TRY(alloc_buf(ctx, lone, (V / 16 + 2) * 4));
-      DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 16.0 * V + (double)E2 * 10 + 8.0 * V * g->key_words + 8.0 * V + V / 4.0,
+      DBG_LAUNCH(ctx, ST_COMPACT_LINKS,
+                 16.0 * V + (double)E2 * (g->adj_side.p ? 5 : 10) + 8.0 * V * g->key_words + 8.0 * V + V / 4.0,
                  k_side_cand<K><<<grid_of(V), 256, 0, s>>>(g->row_ptr.as<uint64_t>(), g->adj_nbr.as<uint32_t>(),
                                                            g->adj_edge.as<uint32_t>(), g->adj_role.as<uint8_t>(),
-                                                           g->orient.as<uint8_t>(), g->node_keys.as<uint64_t>(), V, k,
-                                                           literal, mk.as<uint32_t>(), lone.as<uint32_t>()));
+                                                           g->orient.as<uint8_t>(), g->adj_side.as<uint8_t>(),
+                                                           g->node_keys.as<uint64_t>(), V, k, literal,
+                                                           mk.as<uint32_t>(), lone.as<uint32_t>()));
       DBG_LAUNCH(ctx, ST_COMPACT_LINKS, 12.0 * n,
                  k_succ_lone<<<grid_of(n), 256, 0, s>>>(mk.as<uint32_t>(), lone.as<uint32_t>(), n,
                                                         succ.as<uint32_t>()));

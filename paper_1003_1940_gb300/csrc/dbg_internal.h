@@ -139,6 +139,7 @@ struct dbg_graph {
   int device = 0;
   uint32_t edge_buckets = 1, node_buckets = 1;  // key ranges used (bucket path)
   dbg::DevBuf node_keys, edge_keys, src, dst, orient, mult, row_ptr, adj_nbr, adj_edge, adj_role;
+  dbg::DevBuf adj_side;    // per adjacency slot: its end's side | the far end's side << 1 (when built)
   dbg::DevBuf node_mult;   // k-mer occurrences per node, when the build counted them
   dbg::DevBuf node_reads;  // distinct reads per node, when the build counted them
   cudaStream_t copy_streams[dbg::kCopyStreams] = {};  // read-backs started by dbg_graph_*_async
@@ -150,7 +151,7 @@ struct dbg_graph {
   uint64_t device_bytes() const {
     uint64_t b = 0;
     for (const dbg::DevBuf *x : {&node_keys, &edge_keys, &src, &dst, &orient, &mult, &row_ptr, &adj_nbr,
-                                 &adj_edge, &adj_role, &node_mult, &node_reads})
+                                 &adj_edge, &adj_role, &adj_side, &node_mult, &node_reads})
       b += x->bytes;
     return b;
   }

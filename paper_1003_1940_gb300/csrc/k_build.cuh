@@ -1154,8 +1154,19 @@ static __global__ __launch_bounds__(SCAN_BLOCK) void k_scan_excl(const uint32_t 
 // key into the graph, and two node records per edge (payload e<<1 | role),
 // and accumulates the digit histograms of the node sort (pass ps takes the
 // 8 bits from 8 ps - adj up).  The multiplicity comes from the run heads
-// (headpos) or directly from mult_in.
+// (headpos) or directly from mult_in.  With `sides` (E < 2^29), each payload
+// also carries the side of its own end (bit 30) and of the edge's other end
+// (bit 31), for k_write_nodes to store per adjacency slot.
 // ---------------------------------------------------------------------------
+
+// Side of an edge end (0 = left, 1 = right): the src end (role 0) of
+// (u, v, o1, o2) sits on u's right side if o1 = 0, else its left; the dst
+// end (role 1) on v's left side if o2 = 0, else its right.
+__device__ __forceinline__ uint32_t end_side(uint8_t orient, uint32_t role) {
+  const uint32_t o1 = orient >> 1, o2 = orient & 1u;
+  return role == 0 ? (o1 ? 0u : 1u) : (o2 ? 1u : 0u);
+}
+
 template <class K>
 __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ uniq,
                                                           const uint32_t *__restrict__ headpos,
@@ -1164,7 +1175,8 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ 
                                                           uint32_t *__restrict__ mult,
                                                           uint8_t *__restrict__ orient, K *__restrict__ rkeys,
                                                           uint32_t *__restrict__ rvals, int first, int passes,
-                                                          unsigned long long *__restrict__ hist, int adj = 0) {
+                                                          unsigned long long *__restrict__ hist, int adj = 0,
+                                                          bool sides = false) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   for (int i = threadIdx.x; i < passes * RADIX; i += EMIT_BLOCK) s_hist[i] = 0;
   __syncthreads();
@@ -1182,12 +1194,14 @@ __global__ __launch_bounds__(EMIT_BLOCK) void k_endpoints(const K *__restrict__ 
     if (!KeyOps<K>::less(yh, xh)) { s = xh; d = yh; a = o1; b = o2; }
     else { s = yh; d = xh; a = !o2; b = !o1; }
     edge_keys[e] = z;
-    orient[e] = (uint8_t)((a << 1) | b);
+    const uint8_t o = (uint8_t)((a << 1) | b);
+    orient[e] = o;
     mult[e] = headpos ? headpos[e + 1] - headpos[e] : mult_in[e];
+    const uint32_t s0 = sides ? end_side(o, 0) : 0u, s1 = sides ? end_side(o, 1) : 0u;
     rkeys[2 * e] = s;
-    rvals[2 * e] = (uint32_t)(e << 1);
+    rvals[2 * e] = (uint32_t)(e << 1) | s0 << 30 | s1 << 31;
     rkeys[2 * e + 1] = d;
-    rvals[2 * e + 1] = (uint32_t)(e << 1) | 1u;
+    rvals[2 * e + 1] = (uint32_t)(e << 1) | 1u | s1 << 30 | s0 << 31;
     for (int ps = first; ps < passes; ps++) {
       atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(s, ps * RADIX_BITS - adj, RADIX_BITS)], 1u);
       atomicAdd(&s_hist[ps * RADIX + KeyOps<K>::digit(d, ps * RADIX_BITS - adj, RADIX_BITS)], 1u);
@@ -1590,7 +1604,7 @@ __global__ __launch_bounds__(SCAN_BLOCK, 2) void k_write_nodes(
     const uint64_t *__restrict__ eoff, K *__restrict__ node_keys, uint64_t *__restrict__ row_ptr,
     uint32_t *__restrict__ src, uint32_t *__restrict__ dst, uint32_t *__restrict__ adj_edge,
     uint8_t *__restrict__ adj_role, uint32_t base_v, uint64_t base_slot, uint64_t *__restrict__ ends,
-    uint32_t *__restrict__ bucket_fill, int bshift) {
+    uint32_t *__restrict__ bucket_fill, int bshift, uint8_t *__restrict__ adj_side = nullptr) {
   constexpr int WARPS = SCAN_BLOCK / 32;
   __shared__ uint32_t s_cnt_h[RS_ITEMS * WARPS + 1], s_cnt_e[RS_ITEMS * WARPS + 1];
   __shared__ uint32_t s_bcnt[PART ? 256 : 1], s_bbase[PART ? 256 : 1];
@@ -1624,6 +1638,10 @@ __global__ __launch_bounds__(SCAN_BLOCK, 2) void k_write_nodes(
       row_ptr[id] = base_slot + slot;
     }
     if (end[i]) {
+      if (adj_side) {  // the two side bits on top of the payload
+        adj_side[base_slot + slot] = (uint8_t)(val[i] >> 30);
+        val[i] &= 0x3fffffffu;
+      }
       const uint32_t e = val[i] >> 1, role = val[i] & 1u;
       adj_edge[base_slot + slot] = e;
       adj_role[base_slot + slot] = (uint8_t)role;
@@ -1670,7 +1688,8 @@ __global__ __launch_bounds__(SCAN_BLOCK, 2) void k_write_nodes_p(
     const uint64_t *__restrict__ eoff, K *__restrict__ node_keys, uint64_t *__restrict__ row_ptr,
     uint32_t *__restrict__ src, uint32_t *__restrict__ dst, uint32_t *__restrict__ adj_edge,
     uint8_t *__restrict__ adj_role, uint32_t base_v, uint64_t base_slot, uint64_t *__restrict__ ends,
-    uint32_t *__restrict__ bucket_fill, int bshift, uint32_t spin_limit, uint32_t *__restrict__ err) {
+    uint32_t *__restrict__ bucket_fill, int bshift, uint32_t spin_limit, uint32_t *__restrict__ err,
+    uint8_t *__restrict__ adj_side = nullptr) {
   using S = WriteNodesSmem<K>;
   constexpr uint32_t KB = RS_TILE * sizeof(K), VB = RS_TILE * sizeof(uint32_t);
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1749,6 +1768,10 @@ __global__ __launch_bounds__(SCAN_BLOCK, 2) void k_write_nodes_p(
         row_ptr[id] = base_slot + slot;
       }
       if (end[i]) {
+        if (adj_side) {  // the two side bits on top of the payload
+          adj_side[base_slot + slot] = (uint8_t)(val[i] >> 30);
+          val[i] &= 0x3fffffffu;
+        }
         const uint32_t e = val[i] >> 1, role = val[i] & 1u;
         adj_edge[base_slot + slot] = e;
         adj_role[base_slot + slot] = (uint8_t)role;

@@ -99,9 +99,9 @@ uint64_t build_footprint(uint64_t n, uint64_t bases, uint64_t N, uint64_t I, uin
   // the distinct keys' buffer and counts, the graph's edge arrays, two
   // record buffers (key + payload) and the gathered oversize records
   const uint64_t B = N * w + 4 * E + E * (w + 5) + 4 * R * (w + 4);
-  // records, row offsets, edge arrays, src / dst, adjacency, partitioned
-  // edge ends, node keys and row_ptr
-  const uint64_t C = 2 * R * (w + 4) + 8 * (R + 1) + E * (w + 5) + 8 * E + 18 * E + 16 * E + V * (w + 8);
+  // records, row offsets, edge arrays, src / dst, adjacency with its sides,
+  // partitioned edge ends, node keys and row_ptr
+  const uint64_t C = 2 * R * (w + 4) + 8 * (R + 1) + E * (w + 5) + 8 * E + 20 * E + 16 * E + V * (w + 8);
   const uint64_t tiles = N / 2048 + 1;  // per-tile bounds, counts and scan words
   return inputs + std::max({A, B, C}) + 64 * tiles + (64ull << 20);
 }
