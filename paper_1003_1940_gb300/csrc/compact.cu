@@ -574,13 +574,13 @@ __global__ __launch_bounds__(WALK_BLOCK, 6) void k_mark_stage(W *__restrict__ mk
 // L = d_a + d_b - o, o the nodes both took (found by stepping from the
 // second walker's last node, read on the first walker's strands, to the
 // first walker's last node); the copy kept (the one whose first k-mer is
-// smaller) and its first node's tables: is_head, the unitig's length, the
-// kept copy's strand.
+// smaller) and its first node's tables: its bit in the bitmap of unitig
+// heads, the unitig's length, the kept copy's strand.
 template <class K>
 __global__ void k_mark_pair(const uint32_t *__restrict__ pairs, const uint32_t *__restrict__ pair_count,
                             const uint32_t *__restrict__ succ, uint64_t n, const uint4 *__restrict__ hrec,
                             const uint64_t *__restrict__ node_keys, int k, uint32_t cap,
-                            uint32_t *__restrict__ is_head, uint32_t *__restrict__ len_at_head,
+                            uint32_t *__restrict__ head_bits, uint32_t *__restrict__ len_at_head,
                             uint8_t *__restrict__ hstrand, unsigned long long *covered, uint32_t *err) {
   unsigned long long cov = 0;
   const uint32_t np = *pair_count;
@@ -614,13 +614,38 @@ __global__ void k_mark_pair(const uint32_t *__restrict__ pairs, const uint32_t *
     const uint32_t L = ra.x + rb.x - o;
     const uint32_t kept = KeyOps<K>::less(strand_kmer<K>(node_keys, p, k), strand_kmer<K>(node_keys, x, k)) ? p : x;
     const uint32_t h = kept >> 1;
-    is_head[h] = 1;
+    atomicOr(head_bits + (h >> 5), 1u << (h & 31u));
     len_at_head[h] = L;
     hstrand[h] = (uint8_t)(kept & 1u);
     cov += L;
   }
   cov = __reduce_add_sync(0xffffffffu, (unsigned)cov);
   if ((threadIdx.x & 31) == 0 && cov) atomicAdd(covered, cov);
+}
+
+// Bits set in each 32-node word of the head bitmap.
+__global__ void k_head_popc(const uint32_t *__restrict__ head_bits, uint64_t nw, uint32_t *__restrict__ cnt) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (uint64_t)gridDim.x * blockDim.x)
+    cnt[i] = __popc(head_bits[i]);
+}
+
+// The unitigs in the order of their first nodes: unitig u = the u-th set bit
+// of the head bitmap (wpre = the exclusive scan of the words' bit counts),
+// with its first strand-node uy[u] = 2v + the kept strand and its length.
+__global__ void k_head_list(const uint32_t *__restrict__ head_bits, uint64_t nw, const uint64_t *__restrict__ wpre,
+                            const uint32_t *__restrict__ len_at_head, const uint8_t *__restrict__ hstrand,
+                            uint32_t *__restrict__ uy, uint32_t *__restrict__ ulen) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t b = head_bits[i];
+    uint64_t u = wpre[i];
+    while (b) {
+      const uint32_t v = (uint32_t)(i * 32) + (uint32_t)(__ffs(b) - 1);
+      uy[u] = 2 * v + hstrand[v];
+      ulen[u] = len_at_head[v];
+      u++;
+      b &= b - 1u;
+    }
+  }
 }
 
 // The index s entries after index q of the same walk (following the lanes'
@@ -646,20 +671,19 @@ __device__ __forceinline__ char base_char(uint32_t b) { return (char)((0x5447434
 // bases the kept walker's arcs appended; the rest is the reverse complement
 // of the first L - a characters of the other walker's string T (its head's
 // k-mer, then its arcs' bases): S[k - 2 + L - m] is the complement of T[m].
-// Groups of CG lanes take the unitigs of their warp's chunk of nodes in
-// turn, and each group writes a unitig's nodes and bases CG at a time, so
-// that every store of the group covers consecutive addresses.
+// Groups of CG lanes take the unitigs of their warp's chunk of the head
+// list in turn, and each group writes a unitig's nodes and bases CG at a
+// time, so that every store of the group covers consecutive addresses.
 constexpr int CG = 8;
+constexpr int COPY_CHUNK = 64;  // unitigs per warp chunk (about as many nodes as a walk chunk)
 
 template <class K>
 __global__ __launch_bounds__(WALK_BLOCK, 6) void k_stage_copy(
-    const uint32_t *__restrict__ is_head, const uint8_t *__restrict__ hstrand, const uint32_t *__restrict__ ulen,
-    const uint64_t *__restrict__ uidx, const uint64_t *__restrict__ off_by_v, const uint4 *__restrict__ hrec,
-    const uint32_t *__restrict__ stage, const uint32_t *__restrict__ page_next,
+    const uint32_t *__restrict__ uy, const uint32_t *__restrict__ ulen, const uint64_t *__restrict__ uoff,
+    const uint4 *__restrict__ hrec, const uint32_t *__restrict__ stage, const uint32_t *__restrict__ page_next,
     const uint64_t *__restrict__ node_keys, uint64_t V, uint64_t U, int k, uint64_t *__restrict__ nodes_out,
     char *__restrict__ seq, uint64_t *__restrict__ node_off, uint64_t *__restrict__ seq_off,
     uint8_t *__restrict__ circular) {
-  __shared__ uint32_t s_q[WALK_WARPS][WALK_CHUNK];
   __shared__ uint32_t s_next[WALK_WARPS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, gl = lane % CG;
   const unsigned gmask = ((1u << CG) - 1u) << (lane - gl);
@@ -667,9 +691,10 @@ __global__ __launch_bounds__(WALK_BLOCK, 6) void k_stage_copy(
     node_off[U] = V;
     seq_off[U] = V + U * (uint64_t)(k - 1);
   }
-  const uint64_t chunks = (V + WALK_CHUNK - 1) / WALK_CHUNK;
+  const uint64_t chunks = (U + COPY_CHUNK - 1) / COPY_CHUNK;
   for (uint64_t c = (uint64_t)blockIdx.x * WALK_WARPS + w; c < chunks; c += (uint64_t)gridDim.x * WALK_WARPS) {
-    const uint32_t cnt = queue_heads(c * WALK_CHUNK, V, s_q[w], [&](uint64_t v) { return is_head[v] != 0; });
+    const uint64_t u0 = c * COPY_CHUNK;
+    const uint32_t cnt = U - u0 < (uint64_t)COPY_CHUNK ? (uint32_t)(U - u0) : (uint32_t)COPY_CHUNK;
     if (lane == 0) s_next[w] = 0;
     __syncwarp();
     for (;;) {
@@ -677,11 +702,11 @@ __global__ __launch_bounds__(WALK_BLOCK, 6) void k_stage_copy(
       if (gl == 0) qi = atomicAdd(&s_next[w], 1u);
       qi = __shfl_sync(gmask, qi, 0, CG);
       if (qi >= cnt) break;
-      const uint32_t v = s_q[w][qi];
-      const uint32_t y = 2 * v + hstrand[v];
+      const uint64_t u = u0 + qi;
+      const uint32_t y = uy[u];
       const uint4 ra = hrec[y];
-      const uint32_t L = ulen[v], a = ra.x, bp = L - a;
-      const uint64_t u = uidx[v], off = off_by_v[v], so = off + u * (uint64_t)(k - 1);
+      const uint32_t L = ulen[u], a = ra.x, bp = L - a;
+      const uint64_t off = uoff[u], so = off + u * (uint64_t)(k - 1);
       if (gl == 0) {
         node_off[u] = off;
         seq_off[u] = so;
@@ -721,8 +746,8 @@ __global__ __launch_bounds__(WALK_BLOCK, 6) void k_stage_copy(
 // ones would start its fixed share of chunks only when another ends), at
 // most one per chunk
 template <class F>
-static unsigned walk_grid(const dbg_ctx *ctx, uint64_t n, F kern) {
-  const uint64_t chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
+static unsigned walk_grid(const dbg_ctx *ctx, uint64_t n, F kern, uint64_t chunk = WALK_CHUNK) {
+  const uint64_t chunks = (n + chunk - 1) / chunk;
   const uint64_t blocks = (chunks + WALK_WARPS - 1) / WALK_WARPS;
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   int per_sm = 0;
@@ -907,12 +932,14 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
     }
     // ---- fast path: short acyclic lists only ----
     if (fast) {
-      DevBuf f_is_head, f_len, f_strand, f_uidx, f_off, hrec, stage, page_next;
-      DBG_TRY(alloc_buf(ctx, f_is_head, V1 * 4));
+      // the heads of the unitigs as a bitmap over the nodes; their lengths
+      // and kept strands at the head nodes only
+      DevBuf f_bits, f_len, f_strand, hrec, stage, page_next;
+      const uint64_t nw = (V + 31) / 32, nw1 = std::max<uint64_t>(1, nw);
+      DBG_TRY(alloc_buf(ctx, f_bits, nw1 * 4));
       DBG_TRY(alloc_buf(ctx, f_len, V1 * 4));
       DBG_TRY(alloc_buf(ctx, f_strand, V1));
-      DBG_CUDA_TRY(cudaMemsetAsync(f_is_head.p, 0, V1 * 4, s));
-      DBG_CUDA_TRY(cudaMemsetAsync(f_len.p, 0, V1 * 4, s));
+      DBG_CUDA_TRY(cudaMemsetAsync(f_bits.p, 0, nw1 * 4, s));
       // the two walkers of each unitig meet half way and stage what they
       // take (k_mark_stage); each pair gives its unitig's length and kept
       // copy (k_mark_pair).  Staging room: every node once (the few that
@@ -953,7 +980,7 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
                    k_mark_pair<K><<<grid_of(V), 256, 0, s>>>(pairs.as<uint32_t>(), ctx->d_counters + 17,
                                                              succ.as<uint32_t>(), n, hrec.as<uint4>(),
                                                              g->node_keys.as<uint64_t>(), k, kWalkCap,
-                                                             f_is_head.as<uint32_t>(), f_len.as<uint32_t>(),
+                                                             f_bits.as<uint32_t>(), f_len.as<uint32_t>(),
                                                              f_strand.as<uint8_t>(),
                                                              reinterpret_cast<unsigned long long *>(ctx->d_counters + 12),
                                                              ctx->d_err));
@@ -962,16 +989,28 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
         DBG_TRY(check_device_error(ctx));
       }
       if (too_long == 0 && overflow == 0 && covered == V) {
-        DBG_TRY(alloc_buf(ctx, f_uidx, (V + 1) * 8));
-        DBG_TRY(alloc_buf(ctx, f_off, (V + 1) * 8));
+        // the unitigs in the order of their first nodes: a scan over the
+        // bitmap words, the list of heads, a scan over the unitigs' lengths
+        DevBuf wcnt, wpre, uy, ulen, uoff;
+        DBG_TRY(alloc_buf(ctx, wcnt, nw1 * 4));
+        DBG_TRY(alloc_buf(ctx, wpre, (nw + 1) * 8));
+        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 8.0 * nw,
+                   k_head_popc<<<grid_of(nw), 256, 0, s>>>(f_bits.as<uint32_t>(), nw, wcnt.as<uint32_t>()));
         uint32_t U32 = 0, total = 0;
-        DBG_TRY(scan_excl(ctx, f_is_head.as<uint32_t>(), V, f_uidx.as<uint64_t>(), &U32));
-        DBG_TRY(scan_excl(ctx, f_len.as<uint32_t>(), V, f_off.as<uint64_t>(), &total));
+        DBG_TRY(scan_excl(ctx, wcnt.as<uint32_t>(), nw, wpre.as<uint64_t>(), &U32));
+        const uint64_t Uf = U32;
+        DBG_TRY(alloc_buf(ctx, uy, std::max<uint64_t>(1, Uf) * 4));
+        DBG_TRY(alloc_buf(ctx, ulen, std::max<uint64_t>(1, Uf) * 4));
+        DBG_TRY(alloc_buf(ctx, uoff, (Uf + 1) * 8));
+        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 12.0 * nw + (double)Uf * (4 + 1 + 4 + 4),
+                   k_head_list<<<grid_of(nw), 256, 0, s>>>(f_bits.as<uint32_t>(), nw, wpre.as<uint64_t>(),
+                                                           f_len.as<uint32_t>(), f_strand.as<uint8_t>(),
+                                                           uy.as<uint32_t>(), ulen.as<uint32_t>()));
+        DBG_TRY(scan_excl(ctx, ulen.as<uint32_t>(), Uf, uoff.as<uint64_t>(), &total));
         if (total != V) {
           set_error("unitigs hold %u nodes, expected %llu", total, (unsigned long long)V);
           return DBG_EINTERNAL;
         }
-        const uint64_t Uf = U32;
         u->count = Uf;
         DBG_TRY(alloc_buf(ctx, u->node_off, (Uf + 1) * 8));
         DBG_TRY(alloc_buf(ctx, u->seq_off, (Uf + 1) * 8));
@@ -980,12 +1019,12 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
         u->total_bases = V + Uf * (uint64_t)(k - 1);
         DBG_TRY(alloc_buf(ctx, u->seq, std::max<uint64_t>(1, u->total_bases)));
         DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT,
-                   (double)V * (4 + 1 + 4 + 8 + 1) + (double)Uf * (16 + 32 + 8 * g->key_words * 2 + 16 + k),
-                   k_stage_copy<K><<<walk_grid(ctx, V, k_stage_copy<K>), WALK_BLOCK, 0, s>>>(
-                       f_is_head.as<uint32_t>(), f_strand.as<uint8_t>(), f_len.as<uint32_t>(), f_uidx.as<uint64_t>(),
-                       f_off.as<uint64_t>(), hrec.as<uint4>(), stage.as<uint32_t>(), page_next.as<uint32_t>(),
-                       g->node_keys.as<uint64_t>(), V, Uf, k, u->nodes.as<uint64_t>(), u->seq.as<char>(),
-                       u->node_off.as<uint64_t>(), u->seq_off.as<uint64_t>(), u->circular.as<uint8_t>()));
+                   (double)V * (4 + 8 + 1) + (double)Uf * (4 + 4 + 8 + 32 + 8 * g->key_words * 2 + 16 + k),
+                   k_stage_copy<K><<<walk_grid(ctx, Uf, k_stage_copy<K>, COPY_CHUNK), WALK_BLOCK, 0, s>>>(
+                       uy.as<uint32_t>(), ulen.as<uint32_t>(), uoff.as<uint64_t>(), hrec.as<uint4>(),
+                       stage.as<uint32_t>(), page_next.as<uint32_t>(), g->node_keys.as<uint64_t>(), V, Uf, k,
+                       u->nodes.as<uint64_t>(), u->seq.as<char>(), u->node_off.as<uint64_t>(),
+                       u->seq_off.as<uint64_t>(), u->circular.as<uint8_t>()));
         DBG_CUDA_TRY(cudaGetLastError());
         DBG_CUDA_TRY(cudaStreamSynchronize(s));
         return check_device_error(ctx);
