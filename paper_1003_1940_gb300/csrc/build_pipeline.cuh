@@ -47,11 +47,12 @@ void launch_onesweep(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *
                                                       epoch, ctx->spin_limit, ctx->d_err);
 }
 
-template <class K, bool V, int BLOCK, int ITEMS, int RANK, int MINB, int LB, int HB = 4>
+template <class K, bool V, int BLOCK, int ITEMS, int RANK, int MINB, int LB, int HB = 4, bool BULK = false>
 void launch_onesweep_p(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t *vin, uint32_t *vout, uint64_t n,
                        int shift, const uint64_t *digit_base, uint32_t epoch) {
-  auto kern = k_onesweep_p<K, V, BLOCK, ITEMS, RANK, MINB, LB, HB>;
-  constexpr size_t smem = sizeof(OnesweepPSmem<K, V, BLOCK, ITEMS, RANK, HB>);
+  auto kern = k_onesweep_p<K, V, BLOCK, ITEMS, RANK, MINB, LB, HB, BULK>;
+  constexpr size_t smem = sizeof(OnesweepPSmem<K, V, BLOCK, ITEMS, RANK, HB, BULK>);
+  static_assert(smem <= 227 * 1024, "onesweep variant exceeds the shared memory of a CTA");
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   const uint64_t tiles = (n + BLOCK * ITEMS - 1) / (BLOCK * ITEMS);
@@ -65,6 +66,8 @@ void launch_onesweep_p(dbg_ctx *ctx, const void *kin, void *kout, const uint32_t
   SortVariant { NAME, (B) * (I), &launch_onesweep_p<K, V, B, I, R, M, L> }
 #define DBG_SVH(K, V, B, I, R, M, L, NAME) \
   SortVariant { NAME, (B) * (I), &launch_onesweep_p<K, V, B, I, R, M, L, 2> }
+#define DBG_SVB(K, V, B, I, R, M, L, NAME) \
+  SortVariant { NAME, (B) * (I), &launch_onesweep_p<K, V, B, I, R, M, L, 2, true> }
 #define DBG_SV(K, V, B, I, R, T, M, NAME) \
   SortVariant { NAME, (B) * (I), &launch_onesweep<K, V, B, I, R, T, M, false> }
 #define DBG_SVE(K, V, B, I, R, T, M, NAME) \
@@ -123,6 +126,9 @@ template <> struct SortKind<uint64_t, false> {
         DBG_SVH(uint64_t, false, 1024, 10, RANK_ATOMIC, 1, 8, "1024x10 atomic persistent occ1 lb8 h16"),
         DBG_SVH(uint64_t, false, 1024, 11, RANK_ATOMIC, 1, 8, "1024x11 atomic persistent occ1 lb8 h16"),
         DBG_SVH(uint64_t, false, 1024, 12, RANK_MATCH, 1, 8, "1024x12 match persistent occ1 lb8 h16"),
+        DBG_SVB(uint64_t, false, 1024, 10, RANK_ATOMIC, 1, 8, "1024x10 atomic persistent occ1 lb8 h16 bulk"),
+        DBG_SVB(uint64_t, false, 1024, 11, RANK_MATCH, 1, 8, "1024x11 match persistent occ1 lb8 h16 bulk"),
+        DBG_SVB(uint64_t, false, 1024, 12, RANK_MATCH, 1, 8, "1024x12 match persistent occ1 lb8 h16 bulk"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -152,6 +158,8 @@ template <> struct SortKind<uint64_t, true> {
         DBG_SVP(uint64_t, true, 1024, 6, RANK_ATOMIC, 1, 4, "1024x6 atomic persistent occ1 lb4"),
         DBG_SVP(uint64_t, true, 1024, 6, RANK_ATOMIC, 1, 8, "1024x6 atomic persistent occ1 lb8"),
         DBG_SVH(uint64_t, true, 1024, 7, RANK_ATOMIC, 1, 8, "1024x7 atomic persistent occ1 lb8 h16"),
+        DBG_SVB(uint64_t, true, 1024, 6, RANK_ATOMIC, 1, 8, "1024x6 atomic persistent occ1 lb8 h16 bulk"),
+        DBG_SVB(uint64_t, true, 1024, 7, RANK_MATCH, 1, 8, "1024x7 match persistent occ1 lb8 h16 bulk"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -175,6 +183,7 @@ template <> struct SortKind<Key128, false> {
         DBG_SVP(Key128, false, 1024, 4, RANK_ATOMIC, 1, 4, "1024x4 atomic persistent occ1 lb4"),
         DBG_SVP(Key128, false, 1024, 5, RANK_ATOMIC, 1, 8, "1024x5 atomic persistent occ1 lb8"),
         DBG_SVH(Key128, false, 1024, 6, RANK_MATCH, 1, 8, "1024x6 match persistent occ1 lb8 h16"),
+        DBG_SVB(Key128, false, 1024, 5, RANK_ATOMIC, 1, 8, "1024x5 atomic persistent occ1 lb8 h16 bulk"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -193,6 +202,7 @@ template <> struct SortKind<Key128, true> {
         DBG_SVL(Key128, true, 256, 6, RANK_ATOMIC, true, 3, false, 8, "256x6 atomic tma occ3 lb8"),
         DBG_SVP(Key128, true, 256, 6, RANK_ATOMIC, 2, 4, "256x6 atomic persistent occ2 lb4"),
         DBG_SVP(Key128, true, 1024, 3, RANK_ATOMIC, 1, 4, "1024x3 atomic persistent occ1 lb4"),
+        DBG_SVB(Key128, true, 1024, 3, RANK_ATOMIC, 1, 8, "1024x3 atomic persistent occ1 lb8 h16 bulk"),
     };
     *count = sizeof(t) / sizeof(t[0]);
     return t;
@@ -201,6 +211,7 @@ template <> struct SortKind<Key128, true> {
 #undef DBG_SV
 #undef DBG_SVP
 #undef DBG_SVH
+#undef DBG_SVB
 #undef DBG_SVE
 #undef DBG_SVD
 #undef DBG_SVL

@@ -447,6 +447,18 @@ __device__ __forceinline__ void tma_load_bulk(void *dst, const void *src, uint32
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// one bulk copy shared -> global in this thread's bulk async-group (both
+// addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void tma_store_bulk(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// this thread's bulk stores have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // bounded wait on an mbarrier phase; false when the limit was reached
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t spin_limit) {
   for (uint32_t i = 0; i <= spin_limit; i++) {
@@ -818,14 +830,24 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep(
 // HB: bytes of a per-warp digit counter (2 halves the counters' shared
 // memory; a tile holds fewer than 2^16 keys); the lane-mask rows exist for
 // shared-memory atomicOr ranking only.
-template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK = RANK_ATOMIC, int HB = 4>
+// BULK: each digit's run is written out by bulk copies (cp.async.bulk),
+// which proceed while the CTA ranks its next tile.  A bulk copy moves whole
+// 16-byte units between 16-byte aligned addresses, so the run of digit d is
+// staged from slot place_d congruent to its first output index modulo ALIGN
+// (the elements in 16 bytes of keys and of payloads): place_d lies in
+// [start_d + (ALIGN-1) d, start_d + (ALIGN-1)(d+1)), start_d the run's
+// unpadded start, so runs never overlap and the tile needs (ALIGN-1) * 256
+// extra slots.
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK = RANK_ATOMIC, int HB = 4, bool BULK = false>
 struct OnesweepPSmem {
   static constexpr int WARPS = BLOCK / 32;
   static constexpr int TILE = BLOCK * ITEMS;
-  static_assert(HB == 4 || (HB == 2 && TILE < 65536), "digit counters must hold a tile's keys");
+  static constexpr int ALIGN = !BULK ? 1 : HAS_VAL ? 4 : (sizeof(K) >= 16 ? 1 : 16 / (int)sizeof(K));
+  static constexpr int SLOTS = TILE + (ALIGN - 1) * RADIX;
+  static_assert(HB == 4 || (HB == 2 && SLOTS < 65536), "digit counters must hold a tile's keys");
   using Hist = std::conditional_t<HB == 2, uint16_t, uint32_t>;
-  K keys[2][TILE];
-  uint32_t vals[2][HAS_VAL ? TILE : 1];
+  K keys[2][SLOTS];
+  uint32_t vals[2][HAS_VAL ? SLOTS : 1];
   Hist whist[WARPS][RADIX];
   uint32_t match[RANK == RANK_ATOMIC ? WARPS : 1][RADIX + 1];
   uint64_t gbase[RADIX];
@@ -834,12 +856,13 @@ struct OnesweepPSmem {
   uint32_t tnext;
 };
 
-template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, int MIN_BLOCKS, int LB, int HB = 4>
+template <class K, bool HAS_VAL, int BLOCK, int ITEMS, int RANK, int MIN_BLOCKS, int LB, int HB = 4,
+          bool BULK = false>
 __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
     const K *__restrict__ kin, K *__restrict__ kout, const uint32_t *__restrict__ vin, uint32_t *__restrict__ vout,
     uint64_t n, int shift, const uint64_t *__restrict__ digit_base, uint64_t *__restrict__ status,
     uint32_t *ticket, uint32_t epoch, uint32_t spin_limit, uint32_t *err) {
-  using S = OnesweepPSmem<K, HAS_VAL, BLOCK, ITEMS, RANK, HB>;
+  using S = OnesweepPSmem<K, HAS_VAL, BLOCK, ITEMS, RANK, HB, BULK>;
   using Hist = typename S::Hist;
   constexpr int WARPS = S::WARPS;
   constexpr int TILE = S::TILE;
@@ -857,6 +880,11 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
     tma_load_bulk(sm.keys[b], kin + t * TILE, KB, &sm.bar[b]);
     if (HAS_VAL) tma_load_bulk(sm.vals[b], vin + t * TILE, VB, &sm.bar[b]);
   };
+  // bulk write-out needs 16-byte aligned outputs; else the runs are staged
+  // unpadded and written by plain stores
+  const bool bulk_out =
+      BULK && ((reinterpret_cast<uintptr_t>(kout) | (HAS_VAL ? reinterpret_cast<uintptr_t>(vout) : 0)) & 15) == 0;
+  constexpr uint32_t AL = (uint32_t)S::ALIGN;
   if (RANK == RANK_ATOMIC)
     for (int i = tid; i < WARPS * (RADIX + 1); i += BLOCK) (&sm.match[0][0])[i] = 0;
   if (tid == 0) {
@@ -883,6 +911,7 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
         // give up on this launch; first let the copies in flight land
         if (tid == 0) atomicOr(err, ERR_TIMEOUT);
         mbar_wait(&sm.bar[b], ((phase >> b) & 1u) ^ 1u, spin_limit);
+        if (BULK && tid < RADIX) bulk_wait_all();
         return;
       }
     } else {
@@ -939,21 +968,29 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
       st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE, cnt));
     }
     const uint32_t tstart = block_excl_scan_256(cnt, sm.tmp);
+    uint64_t gstart = 0;  // (thread d < 256) digit d's first output index in this tile
+    uint32_t place = 0;   // and the slot its run is staged from
     if (tid < RADIX) {
-      uint32_t run = tstart;
-#pragma unroll
-      for (int w = 0; w < WARPS; w++) {
-        const uint32_t c = sm.whist[w][tid];
-        sm.whist[w][tid] = (Hist)run;
-        run += c;
-      }
       uint32_t excl = 0;
       if (tile > 0) {
         excl = LB > 1 ? lookback_exclusive_batched<LB>(status + tid, RADIX, tile, epoch, spin_limit, err)
                       : lookback_exclusive(status + tid, RADIX, tile, epoch, spin_limit, err);
         st_relaxed(status + (size_t)tile * RADIX + tid, lb_word(epoch, LB_INCLUSIVE, excl + cnt));
       }
-      sm.gbase[tid] = digit_base[tid] + excl - tstart;
+      gstart = digit_base[tid] + excl;
+      place = tstart;
+      if (BULK && bulk_out)
+        place = tstart + (AL - 1) * tid + (uint32_t)((gstart - tstart - (AL - 1) * tid) & (AL - 1));
+      uint32_t run = place;
+#pragma unroll
+      for (int w = 0; w < WARPS; w++) {
+        const uint32_t c = sm.whist[w][tid];
+        sm.whist[w][tid] = (Hist)run;
+        run += c;
+      }
+      sm.gbase[tid] = gstart - place;
+      // the other buffer's bulk stores (the previous tile) have read it
+      if (BULK) bulk_wait_read();
     }
     __syncthreads();
     // this tile's prefix is published: take the next ticket and start its
@@ -972,17 +1009,44 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
         if (HAS_VAL) sm.vals[b][q] = val[i];
       }
     }
-    __syncthreads();
-    for (uint32_t j = tid; j < tile_n; j += BLOCK) {
-      const K kk = sm.keys[b][j];
-      const uint32_t d = KeyOps<K>::digit(kk, shift, RADIX_BITS);
-      const uint64_t dst = sm.gbase[d] + j;
-      if (dst >= n) {  // only reachable if the digit counts were inconsistent
-        atomicOr(err, ERR_INTERNAL);
-        continue;
+    if (BULK && bulk_out) {
+      // the staged runs are read by the async proxy: thread d writes digit
+      // d's run, its unaligned ends by plain stores and the rest by bulk
+      // copies that complete while the next tile is ranked
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid < RADIX && cnt > 0) {
+        if (gstart + cnt > n) {  // only reachable if the digit counts were inconsistent
+          atomicOr(err, ERR_INTERNAL);
+        } else {
+          const uint32_t head = min(cnt, (uint32_t)((AL - (uint32_t)(gstart & (AL - 1))) & (AL - 1)));
+          const uint32_t mid = (cnt - head) & ~(AL - 1);
+          for (uint32_t j = 0; j < cnt; j++) {
+            if (j == head && mid > 0) {
+              tma_store_bulk(kout + gstart + head, &sm.keys[b][place + head], mid * (uint32_t)sizeof(K));
+              if (HAS_VAL) tma_store_bulk(vout + gstart + head, &sm.vals[b][place + head], mid * 4u);
+              j += mid - 1;
+              continue;
+            }
+            kout[gstart + j] = sm.keys[b][place + j];
+            if (HAS_VAL) vout[gstart + j] = sm.vals[b][place + j];
+          }
+          bulk_commit();
+        }
       }
-      kout[dst] = kk;
-      if (HAS_VAL) vout[dst] = sm.vals[b][j];
+    } else {
+      __syncthreads();
+      for (uint32_t j = tid; j < tile_n; j += BLOCK) {
+        const K kk = sm.keys[b][j];
+        const uint32_t d = KeyOps<K>::digit(kk, shift, RADIX_BITS);
+        const uint64_t dst = sm.gbase[d] + j;
+        if (dst >= n) {  // only reachable if the digit counts were inconsistent
+          atomicOr(err, ERR_INTERNAL);
+          continue;
+        }
+        kout[dst] = kk;
+        if (HAS_VAL) vout[dst] = sm.vals[b][j];
+      }
     }
     // this buffer's next use is a bulk copy (async proxy) after these
     // generic-proxy accesses
@@ -990,6 +1054,7 @@ __global__ __launch_bounds__(BLOCK, MIN_BLOCKS) void k_onesweep_p(
     __syncthreads();
     tile = sm.tnext;
   }
+  if (BULK && tid < RADIX) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
