@@ -575,13 +575,14 @@ __global__ __launch_bounds__(WALK_BLOCK, 6) void k_mark_stage(W *__restrict__ mk
 // second walker's last node, read on the first walker's strands, to the
 // first walker's last node); the copy kept (the one whose first k-mer is
 // smaller) and its first node's tables: its bit in the bitmap of unitig
-// heads, the unitig's length, the kept copy's strand.
+// heads, and the unitig's length << 1 | the kept copy's strand (one word,
+// one random store).
 template <class K>
 __global__ void k_mark_pair(const uint32_t *__restrict__ pairs, const uint32_t *__restrict__ pair_count,
                             const uint32_t *__restrict__ succ, uint64_t n, const uint4 *__restrict__ hrec,
                             const uint64_t *__restrict__ node_keys, int k, uint32_t cap,
                             uint32_t *__restrict__ head_bits, uint32_t *__restrict__ len_at_head,
-                            uint8_t *__restrict__ hstrand, unsigned long long *covered, uint32_t *err) {
+                            unsigned long long *covered, uint32_t *err) {
   unsigned long long cov = 0;
   const uint32_t np = *pair_count;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -615,8 +616,7 @@ __global__ void k_mark_pair(const uint32_t *__restrict__ pairs, const uint32_t *
     const uint32_t kept = KeyOps<K>::less(strand_kmer<K>(node_keys, p, k), strand_kmer<K>(node_keys, x, k)) ? p : x;
     const uint32_t h = kept >> 1;
     atomicOr(head_bits + (h >> 5), 1u << (h & 31u));
-    len_at_head[h] = L;
-    hstrand[h] = (uint8_t)(kept & 1u);
+    len_at_head[h] = L << 1 | (kept & 1u);
     cov += L;
   }
   cov = __reduce_add_sync(0xffffffffu, (unsigned)cov);
@@ -631,17 +631,19 @@ __global__ void k_head_popc(const uint32_t *__restrict__ head_bits, uint64_t nw,
 
 // The unitigs in the order of their first nodes: unitig u = the u-th set bit
 // of the head bitmap (wpre = the exclusive scan of the words' bit counts),
-// with its first strand-node uy[u] = 2v + the kept strand and its length.
+// with its first strand-node uy[u] = 2v + the kept strand and its length
+// (from the head's word, length << 1 | strand).
 __global__ void k_head_list(const uint32_t *__restrict__ head_bits, uint64_t nw, const uint64_t *__restrict__ wpre,
-                            const uint32_t *__restrict__ len_at_head, const uint8_t *__restrict__ hstrand,
-                            uint32_t *__restrict__ uy, uint32_t *__restrict__ ulen) {
+                            const uint32_t *__restrict__ len_at_head, uint32_t *__restrict__ uy,
+                            uint32_t *__restrict__ ulen) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t b = head_bits[i];
     uint64_t u = wpre[i];
     while (b) {
       const uint32_t v = (uint32_t)(i * 32) + (uint32_t)(__ffs(b) - 1);
-      uy[u] = 2 * v + hstrand[v];
-      ulen[u] = len_at_head[v];
+      const uint32_t w = len_at_head[v];
+      uy[u] = 2 * v + (w & 1u);
+      ulen[u] = w >> 1;
       u++;
       b &= b - 1u;
     }
@@ -934,11 +936,10 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
     if (fast) {
       // the heads of the unitigs as a bitmap over the nodes; their lengths
       // and kept strands at the head nodes only
-      DevBuf f_bits, f_len, f_strand, hrec, stage, page_next;
+      DevBuf f_bits, f_len, hrec, stage, page_next;
       const uint64_t nw = (V + 31) / 32, nw1 = std::max<uint64_t>(1, nw);
       DBG_TRY(alloc_buf(ctx, f_bits, nw1 * 4));
       DBG_TRY(alloc_buf(ctx, f_len, V1 * 4));
-      DBG_TRY(alloc_buf(ctx, f_strand, V1));
       DBG_CUDA_TRY(cudaMemsetAsync(f_bits.p, 0, nw1 * 4, s));
       // the two walkers of each unitig meet half way and stage what they
       // take (k_mark_stage); each pair gives its unitig's length and kept
@@ -981,7 +982,6 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
                                                              succ.as<uint32_t>(), n, hrec.as<uint4>(),
                                                              g->node_keys.as<uint64_t>(), k, kWalkCap,
                                                              f_bits.as<uint32_t>(), f_len.as<uint32_t>(),
-                                                             f_strand.as<uint8_t>(),
                                                              reinterpret_cast<unsigned long long *>(ctx->d_counters + 12),
                                                              ctx->d_err));
         DBG_CUDA_TRY(cudaGetLastError());
@@ -1002,10 +1002,10 @@ static dbg_status compact_impl(dbg_ctx *ctx, const dbg_graph *g, dbg_unitigs *u,
         DBG_TRY(alloc_buf(ctx, uy, std::max<uint64_t>(1, Uf) * 4));
         DBG_TRY(alloc_buf(ctx, ulen, std::max<uint64_t>(1, Uf) * 4));
         DBG_TRY(alloc_buf(ctx, uoff, (Uf + 1) * 8));
-        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 12.0 * nw + (double)Uf * (4 + 1 + 4 + 4),
+        DBG_LAUNCH(ctx, ST_COMPACT_OUTPUT, 12.0 * nw + (double)Uf * (4 + 4 + 4),
                    k_head_list<<<grid_of(nw), 256, 0, s>>>(f_bits.as<uint32_t>(), nw, wpre.as<uint64_t>(),
-                                                           f_len.as<uint32_t>(), f_strand.as<uint8_t>(),
-                                                           uy.as<uint32_t>(), ulen.as<uint32_t>()));
+                                                           f_len.as<uint32_t>(), uy.as<uint32_t>(),
+                                                           ulen.as<uint32_t>()));
         DBG_TRY(scan_excl(ctx, ulen.as<uint32_t>(), Uf, uoff.as<uint64_t>(), &total));
         if (total != V) {
           set_error("unitigs hold %u nodes, expected %llu", total, (unsigned long long)V);
