@@ -104,30 +104,46 @@ static __global__ void k_read_tile_sums(const uint32_t *__restrict__ len, uint64
   }
 }
 
-// one block: exclusive scan of the tile sums in place; totals -> totals[0..2]
+__device__ __forceinline__ Sum3 add3(Sum3 a, Sum3 b) { return Sum3{a.bases + b.bases, a.edges + b.edges, a.iso + b.iso}; }
+
+__device__ __forceinline__ Sum3 warp_incl_scan3(Sum3 v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Sum3 t{__shfl_up_sync(0xffffffffu, v.bases, o), __shfl_up_sync(0xffffffffu, v.edges, o),
+                 __shfl_up_sync(0xffffffffu, v.iso, o)};
+    if (lane >= o) v = add3(v, t);
+  }
+  return v;
+}
+
+// one block: exclusive scan of the tile sums in place, blockDim.x at a time
+// (warp scans, then a scan of the warp totals); totals -> totals[0..2]
 static __global__ void k_scan_tile_sums(Sum3 *tile_sums, uint32_t num_tiles, uint64_t *totals,
                                  uint64_t *base_off, uint64_t *edge_off, uint64_t n) {
+  __shared__ Sum3 wsum[32];
   __shared__ Sum3 carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   if (threadIdx.x == 0) carry = Sum3{0, 0, 0};
   __syncthreads();
   for (uint32_t start = 0; start < num_tiles; start += blockDim.x) {
-    uint32_t i = start + threadIdx.x;
-    Sum3 v = i < num_tiles ? tile_sums[i] : Sum3{0, 0, 0};
-    // simple serial-per-warp scan through shared memory (num_tiles is small)
-    __shared__ Sum3 buf[1024];
-    buf[threadIdx.x] = v;
+    const uint32_t i = start + threadIdx.x;
+    const Sum3 v = i < num_tiles ? tile_sums[i] : Sum3{0, 0, 0};
+    const Sum3 inc = warp_incl_scan3(v);
+    if (lane == 31) wsum[warp] = inc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      Sum3 run = carry;
-      for (uint32_t j = 0; j < blockDim.x && start + j < num_tiles; j++) {
-        Sum3 x = buf[j];
-        buf[j] = run;
-        run.bases += x.bases; run.edges += x.edges; run.iso += x.iso;
-      }
-      carry = run;
+    if (warp == 0) {
+      const Sum3 t = lane < nwarps ? wsum[lane] : Sum3{0, 0, 0};
+      const Sum3 ti = warp_incl_scan3(t);
+      if (lane < nwarps) wsum[lane] = Sum3{ti.bases - t.bases, ti.edges - t.edges, ti.iso - t.iso};
     }
     __syncthreads();
-    if (i < num_tiles) tile_sums[i] = buf[threadIdx.x];
+    const Sum3 before = add3(carry, wsum[warp]);
+    const Sum3 excl = Sum3{before.bases + inc.bases - v.bases, before.edges + inc.edges - v.edges,
+                           before.iso + inc.iso - v.iso};
+    if (i < num_tiles) tile_sums[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = add3(excl, v);
     __syncthreads();
   }
   if (threadIdx.x == 0) {
