@@ -138,7 +138,9 @@ __global__ void k_successors(const uint32_t *__restrict__ link_node, const uint6
 // The same arcs, for up to 2^29 - 1 strand-nodes, through a bitmap small
 // enough for L2 instead of a random load of the far node's link.  Per node
 // v (warps on 32 consecutive nodes): the lone end of each side as in
-// k_side_links; bit 2v + sd of `lone` set when side sd holds exactly one
+// k_side_links (each slot's side and its far end's side from adj_side, the
+// build's byte per slot, when it has one, else from the edge's orient);
+// bit 2v + sd of `lone` set when side sd holds exactly one
 // end (and, with `literal`, each side of v holds one); and for x = 2v + s
 // the candidate word (its would-be successor, entering the far node w by
 // the far end's side, unless that is v itself, with x's entry base).
