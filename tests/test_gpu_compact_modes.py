@@ -119,3 +119,31 @@ def test_modes_large_slice(dbg):
         assert got[mode]["seq"] == got[0]["seq"]
     res = check_unitigs_maximal(dbg, g, got[0])
     assert res["unitigs"] == len(got[0]["node_off"]) - 1 and res["mergeable"] > 0
+
+
+@pytest.mark.parametrize("k", [21, 33])
+def test_side_bytes_and_orient_gather_agree(dbg, k):
+    """dbg_build stores each adjacency slot's side bits, which the side pass
+    of the compaction reads in order; the same graph from dbg_build_bucketed
+    has none, and the side pass gathers each edge's orient instead.  Both
+    give the same unitigs and the same simplified graph (the literal rule),
+    and the unitigs are the oracle's."""
+    L = 100 if k < 33 else 150
+    reads, lengths = readgen.generate(readgen.ReadSetSpec(60_000, 12_000, L, 0.005, k, 500 + k,
+                                                          repeat_fraction=0.02))
+    ctx = dbg.Context()
+    g = dbg.dbg_build(ctx, reads, lengths, k)
+    gb = dbg.dbg_build_bucketed(ctx, reads, lengths, k, 4 << 20)
+    a = dbg.dbg_unitigs_get(dbg.dbg_compact(ctx, g))
+    b = dbg.dbg_unitigs_get(dbg.dbg_compact(ctx, gb))
+    for f in FIELDS:
+        np.testing.assert_array_equal(b[f], a[f], err_msg=f)
+    assert b["seq"] == a["seq"]
+    assert_unitigs_equal(a, oracle.compact(oracle.build_graph(reads, lengths, k)))
+    sa = dbg.dbg_simple_get(dbg.dbg_simplify(ctx, g, 3))
+    sb = dbg.dbg_simple_get(dbg.dbg_simplify(ctx, gb, 3))
+    for f in sa:
+        if isinstance(sa[f], np.ndarray):
+            np.testing.assert_array_equal(sb[f], sa[f], err_msg=f)
+        else:
+            assert sb[f] == sa[f], f
