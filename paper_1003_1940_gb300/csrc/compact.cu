@@ -198,19 +198,42 @@ __global__ void k_side_cand(const uint64_t *__restrict__ row_ptr, const uint32_t
 }
 
 // Keeps the candidates whose successor's side is lone too: mk[x] (in
-// place) and succ[x].
+// place) and succ[x].  Each thread takes SL_U strand-nodes a grid stride
+// apart, their candidate loads and then their bitmap lookups (L2 hits at
+// random) in flight together.
+constexpr int SL_U = 4;
+
 __global__ void k_succ_lone(uint32_t *__restrict__ mk, const uint32_t *__restrict__ lone, uint64_t n,
                             uint32_t *__restrict__ succ) {
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t c = mk[x];
-    uint32_t out = NONE32;
-    if (!WalkWord<uint32_t>::tail(c)) {
-      const uint32_t y = WalkWord<uint32_t>::next(c);
-      if ((__ldg(lone + (y >> 5)) >> (y & 31)) & 1u) out = y;
-      else c = WalkWord<uint32_t>::make(NONE32, WalkWord<uint32_t>::base(c));
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x0 < n; x0 += stride * SL_U) {
+    uint32_t c[SL_U], bits[SL_U];
+#pragma unroll
+    for (int u = 0; u < SL_U; u++) {
+      const uint64_t x = x0 + (uint64_t)u * stride;
+      c[u] = x < n ? mk[x] : 0u;
     }
-    mk[x] = c;
-    succ[x] = out;
+#pragma unroll
+    for (int u = 0; u < SL_U; u++) {
+      const uint64_t x = x0 + (uint64_t)u * stride;
+      bits[u] = 0;
+      if (x < n && !WalkWord<uint32_t>::tail(c[u])) {
+        const uint32_t y = WalkWord<uint32_t>::next(c[u]);
+        bits[u] = __ldg(lone + (y >> 5)) >> (y & 31);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SL_U; u++) {
+      const uint64_t x = x0 + (uint64_t)u * stride;
+      if (x >= n) break;
+      uint32_t out = NONE32;
+      if (!WalkWord<uint32_t>::tail(c[u])) {
+        if (bits[u] & 1u) out = WalkWord<uint32_t>::next(c[u]);
+        else c[u] = WalkWord<uint32_t>::make(NONE32, WalkWord<uint32_t>::base(c[u]));
+      }
+      mk[x] = c[u];
+      succ[x] = out;
+    }
   }
 }
 
